@@ -1,0 +1,573 @@
+"""Plain FP64 CPU oracle for the Monte Carlo evaluation of Hugenholtz diagrams.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` import this package.  It shares no
+code with the product library (``paper_2603_24532_b300``) and imports nothing
+from it.
+
+Contents
+--------
+* ``build()`` compiles ``oracle.c`` with gcc into ``liboracle.so`` (ctypes).
+* ``enumerate_diagrams(n)`` -- brute-force list of the order-n Hugenholtz
+  diagrams with two-body vertices (Table I of arXiv:2603.24532 counts them:
+  1, 3, 39, 840 at n = 2..5) in the canonical line/port/chord convention below.
+* ``Diagram`` -- one diagram with the oracle's own derived quantities.
+* ``integrand`` / ``vegas_iteration`` / ``refine`` / ``combine`` -- the
+  per-sample integrand, one VEGAS iteration (multi-threaded over sample ranges
+  with a fixed-order reduction), grid refinement and iteration combination.
+* ``discrete_diagram`` and ``rspt_coefficients`` -- the finite-space check of
+  the diagram rules against exact Rayleigh-Schroedinger perturbation theory.
+
+Canonical convention for a diagram (the oracle's reading; a product generator
+that follows the same written rules must produce the same lists):
+
+1. Vertices 0..n-1 in time order.  The adjacency matrix A[i][j] counts lines
+   from vertex i to vertex j (zero diagonal, row and column sums 2, connected).
+   Diagrams are ordered lexicographically by the row-major entries of A.
+2. Lines are listed by (src, dst) in row-major order of A, A[i][j] copies each.
+   src < dst: particle; src > dst: hole.
+3. Vertex v is <o1 o2|V|i1 i2> with (o1, o2) the lines leaving v and (i1, i2)
+   the lines entering v, each pair in increasing line index.
+4. Chords: scan particles (increasing index) then holes (increasing index),
+   union-find over vertices; a line that joins two components is a tree line,
+   otherwise a chord.  Chords are listed in increasing line index.
+
+Parity status: every function here is pinned by a ``-m "not gpu"`` test
+(tests/test_oracle_pins.py, tests/test_oracle_rspt.py, tests/test_philox.py,
+tests/test_census.py); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lib = None
+_lock = threading.Lock()
+
+MAXC = 7
+MAXL = 12
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain gcc, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P = ctypes.POINTER
+            L.oracle_info_ints.restype = ctypes.c_int
+            L.oracle_derive.restype = ctypes.c_int
+            L.oracle_derive.argtypes = [ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
+            L.oracle_integrand.restype = ctypes.c_double
+            L.oracle_integrand.argtypes = [P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)]
+            L.oracle_integrand_momenta.restype = ctypes.c_double
+            L.oracle_integrand_momenta.argtypes = [P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double),
+                                                   P(ctypes.c_double)]
+            L.oracle_first_order_integrand.restype = ctypes.c_double
+            L.oracle_first_order_integrand.argtypes = [P(ctypes.c_double), P(ctypes.c_double)]
+            L.oracle_philox4x32_10.restype = None
+            L.oracle_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
+            L.oracle_vegas_samples.restype = None
+            L.oracle_vegas_samples.argtypes = [ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double), ctypes.c_int,
+                                               ctypes.c_int, P(ctypes.c_double), ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                               P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                               P(ctypes.c_double)]
+            L.oracle_refine.restype = None
+            L.oracle_refine.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int, ctypes.c_double,
+                                        P(ctypes.c_double)]
+            L.oracle_discrete_diagram.restype = ctypes.c_double
+            L.oracle_discrete_diagram.argtypes = [P(ctypes.c_int), ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
+                                                  P(ctypes.c_double)]
+            _lib = L
+    return _lib
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return ctypes.POINTER(ctypes.c_double)()
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ----------------------------------------------------------------------------
+# Philox4x32-10
+# ----------------------------------------------------------------------------
+def philox4x32_10(ctr: Sequence[int], key: Sequence[int]) -> List[int]:
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return list(o)
+
+
+# ----------------------------------------------------------------------------
+# Diagram enumeration (Table I counts; OEIS A064732)
+# ----------------------------------------------------------------------------
+def _row_choices(n: int, i: int):
+    """All rows of length n with zero at i, entries >= 0, summing to 2."""
+    out = []
+    others = [j for j in range(n) if j != i]
+    for a in others:
+        for b in others:
+            if b < a:
+                continue
+            row = [0] * n
+            row[a] += 1
+            row[b] += 1
+            out.append(tuple(row))
+    return sorted(set(out))
+
+
+def _connected(A) -> bool:
+    n = len(A)
+    seen = {0}
+    stack = [0]
+    while stack:
+        v = stack.pop()
+        for u in range(n):
+            if (A[v][u] or A[u][v]) and u not in seen:
+                seen.add(u)
+                stack.append(u)
+    return len(seen) == n
+
+
+def adjacency_matrices(n: int) -> List[tuple]:
+    """All n x n matrices (zero diagonal, row/col sums 2, connected), sorted
+    lexicographically by their row-major entries."""
+    rows = [_row_choices(n, i) for i in range(n)]
+    out = []
+    for combo in itertools.product(*rows):
+        ok = True
+        for j in range(n):
+            if sum(combo[i][j] for i in range(n)) != 2:
+                ok = False
+                break
+        if ok and _connected(combo):
+            out.append(tuple(tuple(r) for r in combo))
+    out.sort(key=lambda A: tuple(x for r in A for x in r))
+    return out
+
+
+@dataclass
+class Diagram:
+    n: int
+    A: tuple
+    lines: List[tuple]          # (src, dst)
+    ports: List[tuple]          # (o1, o2, i1, i2) per vertex
+    chords: List[int]
+    diagram_id: int = -1
+    info: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def nl(self) -> int:
+        return 2 * self.n
+
+    @property
+    def d(self) -> int:
+        return 3 * (self.n + 1)
+
+    def hole(self, l: int) -> bool:
+        s, t = self.lines[l]
+        return s > t
+
+    @property
+    def h(self) -> int:
+        """number of hole lines"""
+        return int(self.info[_OI_H])
+
+    @property
+    def n_eq(self) -> int:
+        """number of ordered vertex pairs joined by two equivalent lines"""
+        return int(self.info[_OI_NEQ])
+
+    @property
+    def l0(self) -> int:
+        """closed loops of the all-direct vertex pairing"""
+        return int(self.info[_OI_L0])
+
+    def coef(self) -> np.ndarray:
+        nl, nc = self.nl, self.n + 1
+        c = np.asarray(self.info[_OI_COEF:_OI_COEF + MAXL * MAXC]).reshape(MAXL, MAXC)
+        return c[:nl, :nc].copy()
+
+    def cut_lines(self, m: int) -> List[int]:
+        return [l for l, (s, t) in enumerate(self.lines) if min(s, t) <= m < max(s, t)]
+
+    def arrays(self):
+        lines = np.asarray([x for st in self.lines for x in st], dtype=np.int32)
+        ports = np.asarray([x for p in self.ports for x in p], dtype=np.int32)
+        chords = np.asarray(self.chords, dtype=np.int32)
+        return lines, ports, chords
+
+
+_OI_H, _OI_NEQ, _OI_L0 = 3, 4, 5
+_OI_COEF = 8 + MAXL + MAXL + 4 * 6 + MAXC
+
+
+def diagram_from_matrix(A, diagram_id: int = -1) -> Diagram:
+    n = len(A)
+    lines = []
+    for i in range(n):
+        for j in range(n):
+            for _ in range(A[i][j]):
+                lines.append((i, j))
+    ports = []
+    for v in range(n):
+        outs = [l for l, (s, t) in enumerate(lines) if s == v]
+        ins = [l for l, (s, t) in enumerate(lines) if t == v]
+        ports.append((outs[0], outs[1], ins[0], ins[1]))
+    parent = list(range(n))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    order = [l for l, (s, t) in enumerate(lines) if s < t] + [l for l, (s, t) in enumerate(lines) if s > t]
+    chords = []
+    for l in order:
+        s, t = lines[l]
+        rs, rt = find(s), find(t)
+        if rs == rt:
+            chords.append(l)
+        else:
+            parent[rs] = rt
+    chords.sort()
+    D = Diagram(n=n, A=tuple(tuple(r) for r in A), lines=lines, ports=ports, chords=chords, diagram_id=diagram_id)
+    derive(D)
+    return D
+
+
+def derive(D: Diagram) -> Diagram:
+    L = lib()
+    info = np.zeros(L.oracle_info_ints(), dtype=np.int32)
+    lines, ports, chords = D.arrays()
+    ok = L.oracle_derive(D.n, _ip(lines), _ip(ports), _ip(chords), _ip(info))
+    if not ok:
+        raise ValueError("oracle_derive rejected the diagram")
+    D.info = info
+    return D
+
+
+_cache = {}
+
+
+def enumerate_diagrams(n: int) -> List[Diagram]:
+    if n not in _cache:
+        _cache[n] = [diagram_from_matrix(A, k) for k, A in enumerate(adjacency_matrices(n))]
+    return _cache[n]
+
+
+def mirror_matrix(A) -> tuple:
+    """Time reversal plus arrow reversal: A'[i][j] = A[n-1-j][n-1-i]."""
+    n = len(A)
+    return tuple(tuple(A[n - 1 - j][n - 1 - i] for j in range(n)) for i in range(n))
+
+
+def is_anomalous(D: Diagram) -> bool:
+    """A hole and a particle line forced to carry the same momentum (equal
+    coefficient rows up to sign): n_k (1 - n_k) = 0 at T = 0, so the diagram
+    vanishes identically."""
+    C = D.coef()
+    for a in range(D.nl):
+        for b in range(D.nl):
+            if D.hole(a) and not D.hole(b):
+                if np.array_equal(C[a], C[b]) or np.array_equal(C[a], -C[b]):
+                    return True
+    return False
+
+
+# ----------------------------------------------------------------------------
+# Physics parameters
+# ----------------------------------------------------------------------------
+@dataclass
+class Physics:
+    kF_n: float = 1.0
+    kF_p: float = 0.0
+    hbar2_over_m: float = 41.47
+    C_S: float = -50.0
+    C_Y: float = -200.0
+    m_pi: float = 0.7
+    Lam: float = 2.0
+    reg_power: int = 4
+    K_max: float = 7.0
+
+    def array(self) -> np.ndarray:
+        return np.asarray([self.kF_n, self.kF_p, self.hbar2_over_m, self.C_S, self.C_Y, self.m_pi, self.Lam,
+                           float(self.reg_power), self.K_max], dtype=np.float64)
+
+    @property
+    def density(self) -> float:
+        return (self.kF_n ** 3 + self.kF_p ** 3) / (3.0 * math.pi ** 2)
+
+
+def integrand(D: Diagram, ph: Physics, x: np.ndarray, with_cond: bool = False):
+    """f(x) for one point (x in [0,1]^d); optionally the denominator condition number."""
+    L = lib()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    cond = ctypes.c_double(0.0)
+    f = L.oracle_integrand(_ip(D.info), _dp(ph.array()), _dp(x), ctypes.byref(cond))
+    return (f, cond.value) if with_cond else f
+
+
+def integrand_momenta(D: Diagram, ph: Physics, chord_k: np.ndarray) -> float:
+    """Integrand at given chord momenta ((n+1) x 3), without map Jacobian and measure."""
+    ck = np.ascontiguousarray(chord_k, dtype=np.float64).ravel()
+    return lib().oracle_integrand_momenta(_ip(D.info), _dp(ph.array()), _dp(ck), None)
+
+
+def line_momenta(D: Diagram, chord_k: np.ndarray) -> np.ndarray:
+    return D.coef() @ np.asarray(chord_k, dtype=np.float64).reshape(D.n + 1, 3)
+
+
+def first_order_integrand(ph: Physics, x: np.ndarray) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().oracle_first_order_integrand(_dp(ph.array()), _dp(x))
+
+
+# ----------------------------------------------------------------------------
+# VEGAS
+# ----------------------------------------------------------------------------
+def uniform_grid(d: int, nb: int = 50) -> np.ndarray:
+    return np.tile(np.linspace(0.0, 1.0, nb + 1), (d, 1))
+
+
+@dataclass
+class IterationResult:
+    sum_w: float
+    sum_w2: float
+    hist: np.ndarray
+    n: int
+
+    @property
+    def mean(self) -> float:
+        return self.sum_w / self.n
+
+    @property
+    def var_of_mean(self) -> float:
+        return (self.sum_w2 / self.n - self.mean ** 2) / (self.n - 1)
+
+
+def vegas_samples(kind: int, D: Optional[Diagram], ph_arr: np.ndarray, d: int, grid: np.ndarray, seed: int,
+                  sid: int, t: int, s_begin: int, s_end: int, dump: bool = False):
+    L = lib()
+    nb = grid.shape[1] - 1
+    grid = np.ascontiguousarray(grid, dtype=np.float64)
+    sums = np.zeros(2)
+    hist = np.zeros(d * nb)
+    info = D.info if D is not None else np.zeros(L.oracle_info_ints(), dtype=np.int32)
+    cnt = s_end - s_begin
+    dx = np.zeros(cnt * d) if dump else None
+    dw = np.zeros(cnt) if dump else None
+    L.oracle_vegas_samples(kind, _ip(info), _dp(ph_arr), d, nb, _dp(grid), seed, sid, t, s_begin, s_end,
+                           _dp(sums), _dp(hist), _dp(dx), _dp(dw))
+    if dump:
+        return sums, hist.reshape(d, nb), dx.reshape(cnt, d), dw
+    return sums, hist.reshape(d, nb)
+
+
+def vegas_iteration(D: Optional[Diagram], ph, grid: np.ndarray, seed: int, sid: int, t: int, n_samples: int,
+                    threads: Optional[int] = None, kind: int = 0, first: int = 0) -> IterationResult:
+    """One VEGAS iteration over samples [first, first + n_samples): sample ranges
+    run on `threads` Python threads (ctypes releases the GIL) and are reduced in
+    range order."""
+    if isinstance(ph, Physics):
+        ph_arr = ph.array()
+    else:
+        ph_arr = np.asarray(ph, dtype=np.float64)
+    d = grid.shape[0]
+    nb = grid.shape[1] - 1
+    threads = threads or (os.cpu_count() or 1)
+    threads = max(1, min(threads, n_samples))
+    bounds = [first + (n_samples * k) // threads for k in range(threads + 1)]
+    results = [None] * threads
+
+    def work(k):
+        results[k] = vegas_samples(kind, D, ph_arr, d, grid, seed, sid, t, bounds[k], bounds[k + 1])
+
+    ths = [threading.Thread(target=work, args=(k,)) for k in range(threads)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    sw = sw2 = 0.0
+    hist = np.zeros((d, nb))
+    for s, h in results:
+        sw += s[0]
+        sw2 += s[1]
+        hist += h
+    return IterationResult(sw, sw2, hist, n_samples)
+
+
+def refine(grid: np.ndarray, hist: np.ndarray, alpha: float = 1.5) -> np.ndarray:
+    L = lib()
+    d, nbp1 = grid.shape
+    out = np.zeros_like(grid)
+    for a in range(d):
+        g = np.ascontiguousarray(grid[a])
+        h = np.ascontiguousarray(hist[a])
+        o = np.zeros(nbp1)
+        L.oracle_refine(_dp(h), _dp(g), nbp1 - 1, alpha, _dp(o))
+        out[a] = o
+    return out
+
+
+def combine(means: Sequence[float], variances: Sequence[float]):
+    """Inverse-variance weighted mean of the iteration estimates, its standard
+    error and chi^2 per degree of freedom."""
+    means = np.asarray(means, dtype=np.float64)
+    variances = np.asarray(variances, dtype=np.float64)
+    if np.all(variances == 0.0):
+        return float(means[-1]), 0.0, 0.0
+    wts = 1.0 / variances
+    mean = float(np.sum(means * wts) / np.sum(wts))
+    sigma = float(1.0 / math.sqrt(np.sum(wts)))
+    dof = len(means) - 1
+    chi2 = float(np.sum((means - mean) ** 2 * wts) / dof) if dof > 0 else 0.0
+    return mean, sigma, chi2
+
+
+def vegas(D: Optional[Diagram], ph, n_iter: int, n_samples: int, seed: int = 1, sid: int = 0, nb: int = 50,
+          alpha: float = 1.5, threads: Optional[int] = None, kind: int = 0, d: Optional[int] = None):
+    """Full VEGAS run: iterate, refine after every iteration, combine all iterations."""
+    if d is None:
+        d = D.d if kind == 0 else 6
+    grid = uniform_grid(d, nb)
+    means, vars_ = [], []
+    for t in range(n_iter):
+        r = vegas_iteration(D, ph, grid, seed, sid, t, n_samples, threads=threads, kind=kind)
+        means.append(r.mean)
+        vars_.append(r.var_of_mean)
+        grid = refine(grid, r.hist, alpha)
+    return combine(means, vars_) + (grid,)
+
+
+# ----------------------------------------------------------------------------
+# Finite-space Rayleigh-Schroedinger check of the diagram rules
+# ----------------------------------------------------------------------------
+def discrete_diagram(D: Diagram, nh: int, np_: int, wbar: np.ndarray, eps: np.ndarray) -> float:
+    w = np.ascontiguousarray(wbar, dtype=np.float64).ravel()
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    return lib().oracle_discrete_diagram(_ip(D.info), nh, np_, _dp(w), _dp(e))
+
+
+def random_antisymmetric_w(N: int, rng: np.random.Generator, scale: float = 0.3) -> np.ndarray:
+    """Real wbar[p,q,r,s] = -wbar[q,p,r,s] = -wbar[p,q,s,r] = wbar[r,s,p,q]."""
+    w = rng.normal(size=(N, N, N, N)) * scale
+    w = w - w.transpose(1, 0, 2, 3)
+    w = w - w.transpose(0, 1, 3, 2)
+    w = 0.5 * (w + w.transpose(2, 3, 0, 1))
+    return w
+
+
+def _apply_annihilate(det: int, p: int):
+    if not (det >> p) & 1:
+        return None, 0
+    sign = -1 if bin(det & ((1 << p) - 1)).count("1") % 2 else 1
+    return det & ~(1 << p), sign
+
+
+def _apply_create(det: int, p: int):
+    if (det >> p) & 1:
+        return None, 0
+    sign = -1 if bin(det & ((1 << p) - 1)).count("1") % 2 else 1
+    return det | (1 << p), sign
+
+
+def rspt_coefficients(wbar: np.ndarray, eps: np.ndarray, nh: int, max_order: int = 5) -> List[float]:
+    """Exact Rayleigh-Schroedinger energy coefficients E^(1..max_order) of
+    H = H0 + W_N in the determinant space of N orbitals with nh holes, where
+    H0 = sum_p eps_p a+_p a_p and W_N is the normal-ordered two-body part of
+    (1/4) sum wbar_pqrs a+_p a+_q a_s a_r with respect to the reference that
+    fills orbitals 0..nh-1."""
+    N = len(eps)
+    dets = [sum(1 << k for k in occ) for occ in itertools.combinations(range(N), nh)]
+    index = {dd: k for k, dd in enumerate(dets)}
+    M = len(dets)
+    W = np.zeros((M, M))
+    for col, det in enumerate(dets):
+        for p in range(N):
+            for q in range(N):
+                for r in range(N):
+                    for s in range(N):
+                        val = wbar[p, q, r, s]
+                        if val == 0.0:
+                            continue
+                        d1, s1 = _apply_annihilate(det, r)
+                        if d1 is None:
+                            continue
+                        d2, s2 = _apply_annihilate(d1, s)
+                        if d2 is None:
+                            continue
+                        d3, s3 = _apply_create(d2, q)
+                        if d3 is None:
+                            continue
+                        d4, s4 = _apply_create(d3, p)
+                        if d4 is None:
+                            continue
+                        W[index[d4], col] += 0.25 * val * s1 * s2 * s3 * s4
+    F = np.zeros((M, M))
+    f = np.zeros((N, N))
+    for p in range(N):
+        for q in range(N):
+            f[p, q] = sum(wbar[p, i, q, i] for i in range(nh))
+    for col, det in enumerate(dets):
+        for p in range(N):
+            for q in range(N):
+                if f[p, q] == 0.0:
+                    continue
+                d1, s1 = _apply_annihilate(det, q)
+                if d1 is None:
+                    continue
+                d2, s2 = _apply_create(d1, p)
+                if d2 is None:
+                    continue
+                F[index[d2], col] += f[p, q] * s1 * s2
+    const = sum(f[i, i] for i in range(nh)) - 0.5 * sum(wbar[i, j, i, j] for i in range(nh) for j in range(nh))
+    WN = W - F + const * np.eye(M)
+    H0 = np.array([sum(eps[k] for k in range(N) if (det >> k) & 1) for det in dets])
+    ref = index[sum(1 << k for k in range(nh))]
+    E0 = H0[ref]
+    R = np.zeros(M)
+    for k in range(M):
+        if k != ref:
+            R[k] = 1.0 / (E0 - H0[k])
+    psi = [np.zeros(M)]
+    psi[0][ref] = 1.0
+    E = [E0]
+    for k in range(1, max_order + 1):
+        Ek = float((WN @ psi[k - 1])[ref])
+        E.append(Ek)
+        rhs = WN @ psi[k - 1]
+        for j in range(1, k + 1):
+            rhs = rhs - E[j] * psi[k - j]
+        nxt = R * rhs
+        nxt[ref] = 0.0
+        psi.append(nxt)
+    return E[1:], WN, ref

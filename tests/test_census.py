@@ -1,0 +1,82 @@
+"""Generator pins for the oracle's diagram enumeration and derived rules:
+Table I counts (golden), hole-number distributions, anomalous and mirror
+structure, and the third-order prefactors of Eqs. (3)-(5)."""
+import collections
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import golden_rows
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_table1_counts(n):
+    want = {int(r[0]): int(r[1]) for r in golden_rows("table1_counts.txt")}
+    assert len(O.enumerate_diagrams(n)) == want[n]
+
+
+def test_hole_distribution_and_ladders():
+    h4 = collections.Counter(D.h for D in O.enumerate_diagrams(4))
+    assert dict(h4) == {2: 1, 3: 7, 4: 23, 5: 7, 6: 1}
+    h5 = collections.Counter(D.h for D in O.enumerate_diagrams(5))
+    assert dict(h5) == {2: 1, 3: 21, 4: 207, 5: 382, 6: 207, 7: 21, 8: 1}
+
+
+def test_anomalous_and_mirror_structure():
+    # anomalous: a hole and a particle line forced to equal momentum
+    assert sum(O.is_anomalous(D) for D in O.enumerate_diagrams(3)) == 0
+    assert sum(O.is_anomalous(D) for D in O.enumerate_diagrams(4)) == 6
+    assert sum(O.is_anomalous(D) for D in O.enumerate_diagrams(5)) == 172
+    for n, selfm, orbits in ((4, 23, 27), (5, 84, 375)):
+        Ds = O.enumerate_diagrams(n)
+        idx = {D.A: k for k, D in enumerate(Ds)}
+        assert sum(O.mirror_matrix(D.A) == D.A for D in Ds) == selfm
+        # mirror of a diagram is a diagram; mirror is an involution; h is kept
+        for D in Ds:
+            M = O.mirror_matrix(D.A)
+            assert M in idx and O.mirror_matrix(M) == D.A
+            assert Ds[idx[M]].h == D.h
+            assert O.is_anomalous(Ds[idx[M]]) == O.is_anomalous(D)
+        orb = {min(idx[D.A], idx[O.mirror_matrix(D.A)]) for D in Ds if not O.is_anomalous(D)}
+        # n = 5: equals N_diag^(eff) = 375 of Table I
+        assert len(orb) == orbits
+
+
+def test_third_order_matches_eqs_3_to_5():
+    rows = {r[0]: (float(r[1]), int(r[2]), int(r[3])) for r in golden_rows("eq3_5_third_order.txt")}
+    got = {}
+    for D in O.enumerate_diagrams(3):
+        pref = (-1) ** (D.h + D.l0) / 2 ** D.n_eq
+        nh = D.h
+        npart = D.nl - D.h
+        name = {4: "hh", 3: "ph", 2: "pp"}[nh]
+        got[name] = (pref, nh, npart)
+        for m in range(2):
+            cut = D.cut_lines(m)
+            assert sum(D.hole(l) for l in cut) == 2 and sum(not D.hole(l) for l in cut) == 2
+    assert got == rows
+
+
+def test_second_order_is_eq2():
+    (D,) = O.enumerate_diagrams(2)
+    assert (-1) ** (D.h + D.l0) / 2 ** D.n_eq == 0.25   # Eq. (2): 1/(4 D_ijab)
+    assert D.h == 2 and len(D.cut_lines(0)) == 4
+
+
+def test_momentum_conservation_rows():
+    for n in (2, 3, 4, 5):
+        for D in O.enumerate_diagrams(n)[:60]:
+            C = D.coef()
+            for v in range(n):
+                s = np.zeros(n + 1, dtype=int)
+                for l, (a, b) in enumerate(D.lines):
+                    if b == v:
+                        s += C[l]
+                    if a == v:
+                        s -= C[l]
+                assert not s.any()
+            for c, l in enumerate(D.chords):
+                e = np.zeros(n + 1, dtype=int)
+                e[c] = 1
+                assert (C[l] == e).all()

@@ -1,0 +1,197 @@
+"""Pins of the oracle's integrand and VEGAS against closed forms, independent
+quadratures, exact symmetries and scaling laws (arXiv:2603.24532 Sec. II,
+Eqs. (1)-(6); VEGAS per Lepage 1978)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import quad_pins as Q
+
+
+def within(est, sig, ref, k=3.0):
+    return abs(est - ref) <= k * sig
+
+
+# --- first order (Eq. (1) potential term) -----------------------------------------------
+
+@pytest.mark.parametrize("g,kfp", [(2, 0.0), (4, 1.0)])
+def test_first_order_contact_closed_form(g, kfp):
+    """Unregulated contact: E/N = C_S n (g - 1)/(2g) (= C_S n/4 for neutrons)."""
+    ph = O.Physics(kF_n=1.0, kF_p=kfp, C_S=-50.0, C_Y=0.0, Lam=1e6)
+    ref = Q.first_order_contact(1.0, g, -50.0)
+    if g == 2:
+        assert ref == pytest.approx(-0.42217, abs=1e-5)
+    m, s, chi, _ = O.vegas(None, ph, 8, 1 << 15, seed=3, kind=1, d=6)
+    assert within(m, s, ref)
+    assert s < 2e-3 * abs(ref)
+
+
+@pytest.mark.parametrize("g,kfp", [(2, 0.0), (4, 1.0)])
+def test_first_order_full_potential_quadrature(g, kfp):
+    ph = O.Physics(kF_n=1.0, kF_p=kfp)
+    ref = Q.first_order_full_v(1.0, g, ph.C_S, ph.C_Y, ph.m_pi, ph.Lam)
+    m, s, chi, _ = O.vegas(None, ph, 8, 1 << 15, seed=5, kind=1, d=6)
+    assert within(m, s, ref)
+    assert s < 2e-3 * abs(ref)
+
+
+# --- second order (Eq. (2)) ---------------------------------------------------------------
+
+_Q2 = {}
+
+
+def q2(CY, g=2):
+    if (CY, g) not in _Q2:
+        _Q2[(CY, g)] = Q.second_order(1.0, g, 41.47, -50.0, CY, 0.7, 2.0, n_rad=10, n_ang=10)
+    return _Q2[(CY, g)]
+
+
+@pytest.mark.parametrize("CY", [0.0, -200.0])
+def test_second_order_vs_gauss_legendre(CY):
+    (D,) = O.enumerate_diagrams(2)
+    ph = O.Physics(C_Y=CY)
+    m, s, chi, _ = O.vegas(D, ph, 10, 1 << 16, seed=1)
+    assert within(m, s, q2(CY))
+    assert s < 5e-3 * abs(q2(CY))
+
+
+def test_second_order_snm_vs_gauss_legendre():
+    (D,) = O.enumerate_diagrams(2)
+    ph = O.Physics(kF_n=1.0, kF_p=1.0)
+    m, s, chi, _ = O.vegas(D, ph, 10, 1 << 15, seed=2)
+    assert within(m, s, q2(-200.0, g=4))
+
+
+def test_planted_spin_sum_error_is_caught():
+    """Dropping the direct-exchange cross term of the spin sum (a plausible
+    mistake) moves the reference far outside the oracle's error bar."""
+    (D,) = O.enumerate_diagrams(2)
+    m, s, chi, _ = O.vegas(D, O.Physics(), 10, 1 << 16, seed=1)
+    wrong = Q.second_order(1.0, 2, 41.47, -50.0, -200.0, 0.7, 2.0, n_rad=8, n_ang=8, cross=False)
+    assert not within(m, s, wrong, k=10)
+
+
+# --- exact symmetries and scaling laws (per sample) -----------------------------------
+
+def _valid_point(D, ph, rng, tries=2000):
+    for _ in range(tries):
+        x = rng.random(D.d)
+        f = O.integrand(D, ph, x)
+        if f != 0.0:
+            return x, f
+    raise RuntimeError("no non-zero sample")
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_coupling_and_mass_scaling(n):
+    """E_G(lambda C_S, lambda C_Y) = lambda^n E_G; E_G(s hbar^2/m) = s^-(n-1) E_G."""
+    rng = np.random.default_rng(100 + n)
+    ph = O.Physics()
+    for D in O.enumerate_diagrams(n)[:: max(1, len(O.enumerate_diagrams(n)) // 6)]:
+        if O.is_anomalous(D):
+            continue
+        x, f = _valid_point(D, ph, rng)
+        lam, s = 1.7, 0.6
+        f1 = O.integrand(D, O.Physics(C_S=lam * ph.C_S, C_Y=lam * ph.C_Y), x)
+        f2 = O.integrand(D, O.Physics(hbar2_over_m=s * ph.hbar2_over_m), x)
+        assert f1 == pytest.approx(lam ** n * f, rel=1e-12)
+        assert f2 == pytest.approx(s ** (-(n - 1)) * f, rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_anomalous_diagrams_vanish(n):
+    rng = np.random.default_rng(n)
+    ph = O.Physics()
+    for D in O.enumerate_diagrams(n):
+        if not O.is_anomalous(D):
+            continue
+        for _ in range(20):
+            assert O.integrand(D, ph, rng.random(D.d)) == 0.0
+
+
+def _valid_chords(D, ph, rng, tries=20000):
+    """Random chord momenta (hole chords in the Fermi ball, particle chords in a
+    shell) at which the integrand is non-zero."""
+    kfs = [k for k in (ph.kF_n, ph.kF_p) if k > 0]
+    for _ in range(tries):
+        ck = np.zeros((D.n + 1, 3))
+        for c, l in enumerate(D.chords):
+            v = rng.normal(size=3)
+            v /= np.linalg.norm(v)
+            r = rng.uniform(0.0, max(kfs)) if D.hole(l) else rng.uniform(min(kfs), 3.0)
+            ck[c] = r * v
+        f = O.integrand_momenta(D, ph, ck)
+        if f != 0.0:
+            return ck, f
+    raise RuntimeError("no non-zero configuration")
+
+
+@pytest.mark.parametrize("n,matter", [(3, "pnm"), (4, "pnm"), (4, "snm"), (5, "pnm"), (4, "asym")])
+def test_mirror_pairs_equal_per_sample(n, matter):
+    """Time reversal + arrow reversal maps a diagram to its complex-conjugate
+    partner; with a real symmetric V the two integrands agree when every line
+    carries the same momentum."""
+    rng = np.random.default_rng(7 * n)
+    ph = {"pnm": O.Physics(), "snm": O.Physics(kF_n=1.0, kF_p=1.0), "asym": O.Physics(kF_n=1.2, kF_p=0.9)}[matter]
+    Ds = O.enumerate_diagrams(n)
+    idx = {D.A: k for k, D in enumerate(Ds)}
+    checked = 0
+    for D in Ds[:: max(1, len(Ds) // 25)]:
+        if O.is_anomalous(D):
+            continue
+        M = Ds[idx[O.mirror_matrix(D.A)]]
+        # mirror line of (u -> v) is (n-1-v -> n-1-u); equivalent lines are interchangeable
+        img, used = {}, set()
+        for l, (u, v) in enumerate(D.lines):
+            for lm, st in enumerate(M.lines):
+                if st == (n - 1 - v, n - 1 - u) and lm not in used:
+                    used.add(lm)
+                    img[lm] = l
+                    break
+        for _ in range(3):
+            ck, f = _valid_chords(D, ph, rng)
+            kl = O.line_momenta(D, ck)
+            mk = np.array([kl[img[lm]] for lm in M.chords])
+            fm = O.integrand_momenta(M, ph, mk)
+            assert fm == pytest.approx(f, rel=1e-12, abs=0.0)
+            checked += 1
+    assert checked > 0
+
+
+# --- VEGAS on test integrands (Lepage 1978) -----------------------------------------------
+
+def test_vegas_separable_gaussian():
+    d = 4
+    ref = math.erf(0.5 / (0.1 * math.sqrt(2))) ** d
+    m, s, chi, grid = O.vegas(None, np.array([0.5, 0.1]), 10, 1 << 14, seed=9, kind=2, d=d)
+    assert within(m, s, ref)
+    assert s < 3e-3
+    # the adapted grid concentrates its bins around the peak
+    w = np.diff(grid[0])
+    assert w[24] < 0.5 / 50 and w[0] > 2.0 / 50
+
+
+def test_vegas_product_of_sines():
+    m, s, chi, grid = O.vegas(None, np.array([0.0, 0.0]), 10, 1 << 14, seed=4, kind=3, d=9)
+    assert within(m, s, 1.0)
+
+
+def test_refine_keeps_uniform_grid_and_endpoints():
+    g = O.uniform_grid(3, 50)
+    h = np.ones((3, 50))
+    g2 = O.refine(g, h)
+    assert np.allclose(g2, g, atol=1e-14)
+    rng = np.random.default_rng(0)
+    h = rng.random((3, 50)) ** 4
+    g3 = O.refine(g, h)
+    assert np.all(np.diff(g3, axis=1) > 0)
+    assert np.all(g3[:, 0] == 0.0) and np.all(g3[:, -1] == 1.0)
+    # all-zero histogram keeps the grid
+    assert np.array_equal(O.refine(g3, np.zeros((3, 50))), g3)
+
+
+def test_combination_weighted_mean():
+    m, s, chi = O.combine([1.0, 3.0], [1.0, 1.0])
+    assert m == 2.0 and s == pytest.approx(1 / math.sqrt(2)) and chi == pytest.approx(2.0)
