@@ -84,6 +84,8 @@ def lib():
             L.oracle_integrand_momenta.restype = ctypes.c_double
             L.oracle_integrand_momenta.argtypes = [P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double),
                                                    P(ctypes.c_double)]
+            L.oracle_line_ksq.restype = None
+            L.oracle_line_ksq.argtypes = [P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)]
             L.oracle_first_order_integrand.restype = ctypes.c_double
             L.oracle_first_order_integrand.argtypes = [P(ctypes.c_double), P(ctypes.c_double)]
             L.oracle_philox4x32_10.restype = None
@@ -342,6 +344,21 @@ def integrand_momenta(D: Diagram, ph: Physics, chord_k: np.ndarray) -> float:
     return lib().oracle_integrand_momenta(_ip(D.info), _dp(ph.array()), _dp(ck), None)
 
 
+def line_ksq(D: Diagram, ph: Physics, x: np.ndarray) -> np.ndarray:
+    """|k_l|^2 of every line at the point x."""
+    out = np.zeros(D.nl)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    lib().oracle_line_ksq(_ip(D.info), _dp(ph.array()), _dp(xx), _dp(out))
+    return out
+
+
+def diagram_from_lists(n, lines, ports, chords) -> Diagram:
+    """A diagram given in the line/port/chord form (e.g. a descriptor produced elsewhere)."""
+    D = Diagram(n=n, A=None, lines=[tuple(x) for x in lines], ports=[tuple(p) for p in ports],
+                chords=list(chords))
+    return derive(D)
+
+
 def line_momenta(D: Diagram, chord_k: np.ndarray) -> np.ndarray:
     return D.coef() @ np.asarray(chord_k, dtype=np.float64).reshape(D.n + 1, 3)
 
@@ -440,16 +457,21 @@ def refine(grid: np.ndarray, hist: np.ndarray, alpha: float = 1.5) -> np.ndarray
 
 def combine(means: Sequence[float], variances: Sequence[float]):
     """Inverse-variance weighted mean of the iteration estimates, its standard
-    error and chi^2 per degree of freedom."""
+    error and chi^2 per degree of freedom.  Iterations whose sample variance is
+    exactly zero (an integrand that vanished on every sample) carry no weight;
+    if every iteration has zero variance the last estimate is returned with
+    zero error."""
     means = np.asarray(means, dtype=np.float64)
     variances = np.asarray(variances, dtype=np.float64)
-    if np.all(variances == 0.0):
+    pos = variances > 0.0
+    if not np.any(pos):
         return float(means[-1]), 0.0, 0.0
-    wts = 1.0 / variances
-    mean = float(np.sum(means * wts) / np.sum(wts))
+    m_, v_ = means[pos], variances[pos]
+    wts = 1.0 / v_
+    mean = float(np.sum(m_ * wts) / np.sum(wts))
     sigma = float(1.0 / math.sqrt(np.sum(wts)))
-    dof = len(means) - 1
-    chi2 = float(np.sum((means - mean) ** 2 * wts) / dof) if dof > 0 else 0.0
+    dof = len(m_) - 1
+    chi2 = float(np.sum((m_ - mean) ** 2 * wts) / dof) if dof > 0 else 0.0
     return mean, sigma, chi2
 
 

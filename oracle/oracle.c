@@ -294,6 +294,7 @@ typedef struct {
     double Vd[O_MAXN], Ve[O_MAXN];
     int label[O_MAXL];
     int last_line_of_vertex[O_MAXN];
+    int absmode;              /* 1: sum |terms| (condition number of the spin sum) */
 } spin_enum;
 
 static int line_is_hole(const int* info, int l) { return info[OI_SRC + l] > info[OI_DST + l]; }
@@ -311,6 +312,11 @@ static double vertex_value(const spin_enum* S, int v) {
     const int* pt = S->info + OI_PORT + 4 * v;
     int o1 = S->label[pt[0]], o2 = S->label[pt[1]], i1 = S->label[pt[2]], i2 = S->label[pt[3]];
     double val = 0.0;
+    if (S->absmode) {
+        if (o1 == i1 && o2 == i2) val += fabs(S->Vd[v]);
+        if (o1 == i2 && o2 == i1) val += fabs(S->Ve[v]);
+        return val;
+    }
     if (o1 == i1 && o2 == i2) val += S->Vd[v];
     if (o1 == i2 && o2 == i1) val -= S->Ve[v];
     return val;
@@ -447,10 +453,38 @@ double oracle_integrand_momenta(const int* info, const double* ph, const double*
         dprod *= D;
         condsum += mag / fabs(D);
     }
-    if (cond) *cond = condsum;
+    if (cond) {
+        /* rounding amplification: energy denominators plus the cancellation in the
+         * spin sum, sum |terms| / |sum| */
+        S.absmode = 1;
+        double sabs = spin_sum(&S);
+        *cond = condsum + sabs / fabs(ssum);
+    }
     int h = info[OI_H], l0 = info[OI_L0], neq = info[OI_NEQ];
     double sign = ((h + l0) % 2 == 0) ? 1.0 : -1.0;
     return sign / pow(2.0, neq) / density(ph) * ssum / dprod;
+}
+
+/* Squared line momenta |k_l|^2 at the point x (chord map + momentum routing), for
+ * classifying samples that sit within rounding of a Fermi surface. */
+void oracle_line_ksq(const int* info, const double* ph, const double* x, double* out) {
+    int nl = info[OI_NL], nc = info[OI_NC];
+    double chord_k[O_MAXC * 3];
+    for (int c = 0; c < nc; ++c) {
+        int l = info[OI_CHORD + c];
+        double lo, hi;
+        chord_range(ph, line_is_hole(info, l), &lo, &hi);
+        chord_map(x + 3 * c, lo, hi, chord_k + 3 * c);
+    }
+    for (int l = 0; l < nl; ++l) {
+        double k[3];
+        for (int a = 0; a < 3; ++a) {
+            double s = 0.0;
+            for (int c = 0; c < nc; ++c) s += info[OI_COEF + l * O_MAXC + c] * chord_k[3 * c + a];
+            k[a] = s;
+        }
+        out[l] = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    }
 }
 
 /*
