@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark: batched VEGAS evaluation of all third-order Hugenholtz diagrams of
+pure neutron matter over a density scan (3 diagrams x kF in {0.8, ..., 1.7} fm^-1,
+2^22 samples per integral per iteration), on one B300.
+
+A step is one VEGAS iteration over all 30 integrals: Philox sampling, VEGAS map,
+integrand, per-chunk sums and histograms, the fixed-order reduction, the
+combination of the iteration into each estimate and the grid refinement.
+The headline arm runs it batched (one persistent launch per iteration, CUDA
+graph) in mixed precision; the FP64 batched path and the plain per-diagram FP64
+loop run the same workload beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "integrand evals/s; diagrams to 0.1% err/s vs plain FP64 loop; p50/p99 EOS latency"
+UNIT = "integrand evals/s"
+KF_SCAN = [round(0.8 + 0.1 * i, 2) for i in range(10)]
+SAMPLES = 1 << 22
+ORDER = 3
+WORKLOAD = "third-order Hugenholtz diagrams (pp, hh, ph), pure neutron matter, kF 0.8..1.7 fm^-1 (10 points), 12D, 2^22 samples/iteration"
+
+# FP64 pipe work per sample of an order-3 integral in the formulation of csrc/mbpt_device.cuh, in
+# DADD-equivalents (sqrt = 8.6, reciprocal/division = 5.7, from the pipe microbenchmark):
+# map 2/axis (24) + chord map 34.3/chord (137.2) + tree lines 9/line (18) = 179.2 on every sample;
+# live samples add denominators (8), weight (9) and sums (2).  Dead samples add the sums only.
+FP64_OPS_ALL = 179.2 + 2.0
+FP64_OPS_LIVE_EXTRA = 17.0
+# nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second
+FP64_PEAK_NOMINAL = 1.25e12 / 2.0
+# measured DFMA issue rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu)
+FP64_PEAK_MEASURED = 4.73e11
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_integrals(M, ctx, precision, seed_base=1, stream_base=0):
+    descs = M.mbpt_generate(ORDER)
+    gs, meta = [], []
+    for ki, kf in enumerate(KF_SCAN):
+        ph = M.physics(kF_n=kf, kF_p=0.0, K_max=kf + 6.0)
+        for d in descs:
+            sid = stream_base + 100 * ki + d.diagram_id
+            cfg = M.vegas_cfg(samples=SAMPLES, seed=seed_base, stream_id=sid, precision=precision)
+            gs.append(M.mbpt_create_diagram(ctx, d, ph, cfg))
+            meta.append((kf, d.diagram_id))
+    return gs, meta
+
+
+def l2_flush(torch, buf):
+    buf.add_(1)
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2603_24532_b300 import mbpt as M
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    arena = torch.empty(8 << 30, dtype=torch.uint8, device=dev)
+    ctx = M.mbpt_ctx_create(local, arena.numel(), arena_ptr=arena.data_ptr())
+    stream = torch.cuda.ExternalStream(M.mbpt_ctx_stream(ctx), device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)    # 256 MiB > 126 MB L2
+
+    def timed_steps(gs, k, per_diagram=False):
+        ms_it, ms_step = [], []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.add_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            if per_diagram:
+                it = 0.0
+                for g in gs:
+                    M.mbpt_vegas_iterate(ctx, [g], 1)
+                    it += M.mbpt_ctx_last_timing(ctx)[0]
+                with torch.cuda.stream(stream):
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                ms_it.append(it)
+            else:
+                M.mbpt_vegas_iterate(ctx, gs, 1)
+                with torch.cuda.stream(stream):
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                ms_it.append(M.mbpt_ctx_last_timing(ctx)[0])
+            ms_step.append(e0.elapsed_time(e1))
+        return np.array(ms_it), np.array(ms_step)
+
+    # ---- headline: batched, mixed precision
+    gs, meta = build_integrals(M, ctx, M.MBPT_MIXED, seed_base=1 + rank, stream_base=10000 * rank)
+    n_int = len(gs)
+    timed_steps(gs, args.warmup)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ms_it, ms_step = timed_steps(gs, args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_step = float(np.mean(ms_step))
+    if dist:
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    evals_step = n_int * SAMPLES
+    value = world * evals_step / (t_step * 1e-3)
+    res_mixed = [M.mbpt_estimate(g) for g in gs]
+
+    # live-sample fraction on the adapted grids (for the algorithmic FP64 work per sample)
+    live = []
+    for g in gs[:: max(1, n_int // 6)]:
+        _, w = M.mbpt_dump_samples(g, 10 ** 6, 0, 1 << 15, 12, with_x=False)
+        live.append(np.mean(w != 0))
+    live_frac = float(np.mean(live))
+    ops = FP64_OPS_ALL + FP64_OPS_LIVE_EXTRA * live_frac
+    it_ms = float(np.mean(ms_it))
+    achieved = ops * evals_step / (it_ms * 1e-3)
+
+    # ---- e2e through the public API: per step H2D of the work table inside mbpt_vegas_iterate and a
+    # D2H read of every integral's estimate
+    h2d = n_int * (96 + 8) + 32
+    d2h = n_int * 80 + 4
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        M.mbpt_vegas_iterate(ctx, gs, 1)
+        _ = [M.mbpt_estimate(g).mean for g in gs]
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_value = world * evals_step / e2e_s
+    for g in gs:
+        M.mbpt_destroy_diagram(g)
+
+    # ---- FP64 batched, same workload
+    g64, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
+    timed_steps(g64, args.warmup)
+    it64, st64 = timed_steps(g64, args.steps)
+    res64 = [M.mbpt_estimate(g) for g in g64]
+    for g in g64:
+        M.mbpt_destroy_diagram(g)
+    v64 = world * evals_step / (float(np.mean(st64)) * 1e-3)
+
+    # ---- plain per-diagram FP64 loop: one launch per integral per iteration
+    gk0, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
+    timed_steps(gk0, max(1, args.warmup // 2), per_diagram=True)
+    itk0, stk0 = timed_steps(gk0, max(2, args.steps // 2), per_diagram=True)
+    for g in gk0:
+        M.mbpt_destroy_diagram(g)
+    vk0 = world * evals_step / (float(np.mean(stk0)) * 1e-3)
+
+    # ---- time to 0.1 % statistical error per integral, from each run's own variance
+    def diags_per_s(results, rate):
+        need = 0.0
+        for r in results:
+            if r.mean == 0.0 or r.sigma == 0.0:
+                continue
+            need += r.n_evals * (r.sigma / (1e-3 * abs(r.mean))) ** 2
+        return len(results) / (need / rate) if need > 0 else None
+
+    d_mixed = diags_per_s(res_mixed, value)
+    d_k0 = diags_per_s(res64, vk0)
+    M.mbpt_ctx_destroy(ctx)
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+
+    cpu = cpu_baseline(budget_s=args.cpu_seconds) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "integrals": n_int, "samples_per_iter": SAMPLES,
+                   "precision": "mixed (FP32 potentials and spin sum; FP64 map, momenta, denominators, sums, grid)",
+                   "step": "one batched VEGAS iteration over all integrals (sample, integrate, reduce, combine, refine)",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e9, "peak": FP64_PEAK_NOMINAL / 1e9,
+                     "unit": "FP64 Gop/s (DADD-equivalents)", "frac": achieved / FP64_PEAK_NOMINAL,
+                     "peak_kind": "nominal 1.25 TFLOP/s FP64 of the recipe at 2032 MHz",
+                     "frac_of_measured_dfma": achieved / FP64_PEAK_MEASURED,
+                     "ops_per_sample": ops, "live_fraction": live_frac, "kernel": "k_iterate",
+                     "kernel_ms": it_ms, "traffic": None},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "fp64_batched": {"value": v64, "unit": UNIT, "kernel_ms": float(np.mean(it64))},
+        "k0_plain_fp64_per_diagram": {"value": vk0, "unit": UNIT, "launches_per_step": 2 * n_int},
+        "speedup_vs_k0": value / vk0,
+        "diagrams_to_0p1pct_per_s": {"batched_mixed": d_mixed, "k0_plain_fp64": d_k0,
+                                     "ratio": (d_mixed / d_k0) if (d_mixed and d_k0) else None},
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(budget_s=12.0, steps=None):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same
+    workload (every integral, the same number of samples each, uniform grid)."""
+    import oracle as O
+
+    Ds = O.enumerate_diagrams(ORDER)
+    cores = os.cpu_count() or 1
+    # calibrate on one integral
+    po = O.Physics(kF_n=1.2, K_max=7.2)
+    grid = O.uniform_grid(12, 50)
+    m, dt = 1 << 14, 0.0
+    while dt < 0.3 and m < (1 << 22):
+        m *= 2
+        t0 = time.perf_counter()
+        for D in Ds:
+            O.vegas_iteration(D, po, grid, 1, 0, 0, m, threads=cores)
+        dt = time.perf_counter() - t0
+    per = dt / (m * len(Ds))
+    n = int(max(1024, min(1 << 22, budget_s / (per * len(KF_SCAN) * len(Ds)))))
+    t0 = time.perf_counter()
+    total = 0
+    for ki, kf in enumerate(KF_SCAN):
+        po = O.Physics(kF_n=kf, K_max=kf + 6.0)
+        for D in Ds:
+            O.vegas_iteration(D, po, grid, 1, 100 * ki + D.diagram_id, 0, n, threads=cores)
+            total += n
+    dt = time.perf_counter() - t0
+    return {"value": total / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d samples of each of the 30 integrals (uniform grid, iteration 0), %.1f s" % (n, dt)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    cb = None
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(budget_s=args.ref_seconds)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "integrals": 30, "samples_per_iter": SAMPLES,
+                       "step": "bounded sample of one iteration of every integral on the host cores"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

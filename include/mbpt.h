@@ -1,0 +1,256 @@
+/*
+ * mbpt.h -- C ABI of the B300 (sm_103a) Monte Carlo evaluator of
+ * zero-temperature Hugenholtz diagrams for the energy per particle of infinite
+ * nucleon matter (arXiv:2603.24532, "Many-body perturbation theory for the
+ * nuclear equation of state up to fifth order").
+ *
+ * What the library computes (Sec. II, Eqs. (2)-(6); Sec. III.C):
+ *   for a diagram G of order n (n = 2..5 vertices, 2n lines, n+1 loop momenta)
+ *   and a physics point (Fermi momenta kF_n, kF_p, potential V(p,p')),
+ *     E_G/N = (1/n_dens) (-1)^(h+l0) 2^(-n_eq)
+ *             sum_{spins, isospins} int prod_c d^3l_c/(2pi)^3
+ *             prod_lines Theta_l  prod_vertices <o1 o2|V|i1 i2>  / prod_cuts D_m
+ *   with Theta_l = n_k (holes) or 1 - n_k (particles), n_k = theta(kF - k),
+ *   D_m = sum_{holes in cut m} eps - sum_{particles in cut m} eps,
+ *   eps(k) = (hbar^2/2m) k^2 (free spectrum), estimated by VEGAS importance
+ *   sampling (Lepage) with Philox4x32-10 random numbers.
+ *
+ * Conventions for every call:
+ *   - Every function returns an mbpt_status; nothing throws across the ABI.
+ *     Out-parameters are written only when MBPT_OK is returned.  On error,
+ *     mbpt_last_error() returns a message for the calling thread.
+ *   - Input structs are owned by the caller and copied during the call.
+ *   - Device memory is owned by the context: it either lives in a caller
+ *     supplied device arena (mbpt_ctx_create with arena != NULL, e.g. a
+ *     torch-allocated buffer) or in one cudaMalloc'ed arena of the requested
+ *     size that mbpt_ctx_destroy frees.  Per-integral state is carved out of
+ *     that arena; when it is full, creation fails with MBPT_ENOMEM.
+ *   - A context is bound to one device and one CUDA stream and is not
+ *     thread-safe: one host thread drives it.  Work is queued asynchronously
+ *     on the context stream; mbpt_estimate / mbpt_get_state synchronise it.
+ *   - Units: momenta fm^-1, energies MeV, hbar^2/m MeV fm^2, C_S MeV fm^3,
+ *     C_Y MeV fm.  Results are contributions to E/N in MeV.
+ */
+#ifndef MBPT_H
+#define MBPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbpt_ctx mbpt_ctx;     /* opaque: device, stream, arena, graphs */
+typedef struct mbpt_diag mbpt_diag;   /* opaque: one integral = diagram x physics point */
+
+typedef enum {
+    MBPT_OK = 0,
+    MBPT_EINVAL = -1,     /* invalid argument or descriptor */
+    MBPT_ENOMEM = -2,     /* arena or host allocation exhausted */
+    MBPT_ECUDA = -3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    MBPT_EDEVICE = -4,    /* a kernel reported an out-of-range index in its error word */
+    MBPT_ETIMEOUT = -5,   /* a bounded device wait gave up */
+    MBPT_ENUMERIC = -6,   /* NaN or Inf in an integral's accumulators */
+    MBPT_EBUSY = -7       /* operation not allowed while work is queued */
+} mbpt_status;
+
+typedef enum {
+    MBPT_FP64 = 0,        /* every step in FP64 */
+    MBPT_MIXED = 1        /* potential matrix elements (exp, Yukawa) and the spin
+                             sum in FP32; sampling map, momenta, energy
+                             denominators, weights, sums and grid in FP64 */
+} mbpt_precision;
+
+#define MBPT_MAX_ORDER 6          /* generator; the device path runs 2..5 */
+#define MBPT_MAX_DEVICE_ORDER 5
+#define MBPT_MAX_LINES 12
+#define MBPT_MAX_CHORDS 7
+#define MBPT_MAX_BINS 64
+
+/* descriptor flags */
+#define MBPT_FLAG_ANOMALOUS   1   /* a hole and a particle forced to equal momentum: zero at T = 0 */
+#define MBPT_FLAG_SELF_MIRROR 2   /* equal to its own time-and-arrow reversal */
+
+/*
+ * One Hugenholtz diagram with two-body vertices (Sec. II, Table I).
+ * Vertices 0..order-1 are in time order (0 = earliest).  Line l runs from
+ * vertex line_src[l] to line_dst[l]; line_src < line_dst is a particle line,
+ * line_src > line_dst a hole line.  Vertex v stands for the antisymmetrised
+ * matrix element <vtx_out[v][0] vtx_out[v][1]|V|vtx_in[v][0] vtx_in[v][1]>
+ * (lines leaving v on the left, lines entering v on the right).  The n+1
+ * chords are lines whose momenta are the integration variables; every line
+ * momentum is k_l = sum_c line_coef[l][c] * k_chord(c), coefficients in
+ * {-1,0,1}.  The sign (-1)^(h+l0), the weight 2^(-n_eq), the energy-
+ * denominator cuts and the spin-sum table are derived from this description
+ * by the library; line_coef is checked against momentum conservation.
+ */
+typedef struct {
+    int32_t order;
+    int32_t n_lines;
+    int8_t line_src[MBPT_MAX_LINES];
+    int8_t line_dst[MBPT_MAX_LINES];
+    int8_t vtx_out[MBPT_MAX_ORDER][2];
+    int8_t vtx_in[MBPT_MAX_ORDER][2];
+    int8_t n_chords;
+    int8_t chord_line[MBPT_MAX_CHORDS];
+    int8_t line_coef[MBPT_MAX_LINES][MBPT_MAX_CHORDS];
+    int32_t diagram_id;      /* position in mbpt_generate's order */
+    int32_t mirror_id;       /* diagram_id of the time-and-arrow-reversed partner */
+    int32_t flags;           /* MBPT_FLAG_* */
+} mbpt_diagram_desc;
+
+/*
+ * Physics point.  V(p, p') = [C_S + C_Y/(|p - p'|^2 + m_pi^2)] exp(-(p/Lambda)^r - (p'/Lambda)^r)
+ * with r = reg_power (nonlocal regulator of Sec. III.B); p, p' are half the
+ * relative momenta of the outgoing and incoming pairs of a vertex.
+ * A species with kF = 0 is absent: pure neutron matter has kF_p = 0,
+ * symmetric matter kF_n = kF_p.  Hole chords are sampled in [0, max kF],
+ * particle chords in [smallest present kF, K_max].
+ * map_kind 0: chord momentum from (k, cos theta, phi) with a rational azimuth
+ * (the only map implemented).
+ */
+typedef struct {
+    double kF_n, kF_p;
+    double hbar2_over_m;
+    double C_S, C_Y, m_pi, Lambda;
+    int32_t reg_power;       /* even, 2..8 */
+    int32_t map_kind;        /* 0 */
+    double K_max;
+} mbpt_physics;
+
+/*
+ * VEGAS settings of one integral (Lepage 1978; Sec. III.C).  Sample s of the
+ * integral's iteration t uses Philox4x32-10 with key (seed low word, seed high
+ * word) and counter (s, t, stream_id, j), j = 0..ceil(d/4)-1; axis a takes word
+ * a.  The grid is refined after every iteration (smoothing (7,1)/8 and
+ * (1,6,1)/8, compression exponent alpha) until `freeze_after` iterations have
+ * run (0 = never freeze).  The integral stops iterating once its combined
+ * standard error is <= max(target_rel*|mean|, target_abs) (0, 0 = never).
+ */
+typedef struct {
+    int32_t n_bins;            /* 2..MBPT_MAX_BINS (50 in the paper's setup) */
+    int32_t precision;         /* mbpt_precision */
+    double alpha;              /* grid compression exponent, 1.5 */
+    uint64_t seed;
+    uint32_t stream_id;        /* identifies the integral's random stream */
+    uint32_t freeze_after;
+    uint64_t samples_per_iter; /* >= 2, < 2^32 */
+    double target_rel;
+    double target_abs;
+} mbpt_vegas_cfg;
+
+typedef struct {
+    double mean;               /* inverse-variance weighted mean over iterations (MeV) */
+    double sigma;              /* its standard error */
+    double chi2_dof;           /* chi^2 of the iteration estimates per degree of freedom */
+    double last_mean;          /* estimate of the last iteration alone */
+    double last_sigma;
+    int64_t n_iter;            /* iterations combined */
+    int64_t n_evals;           /* integrand evaluations so far */
+    int32_t converged;         /* 1 once the target error was reached */
+    int32_t status;            /* MBPT_OK or MBPT_ENUMERIC */
+} mbpt_result;
+
+/* ---- generator (CPU) ------------------------------------------------------ */
+
+/*
+ * Enumerate all connected order-n Hugenholtz diagrams with two-body vertices
+ * (Table I: 1, 3, 39, 840, 27300 for n = 2..6) in a deterministic order:
+ * adjacency matrices A (A[i][j] = lines from vertex i to j; zero diagonal,
+ * row and column sums 2) sorted by their row-major entries; lines listed in
+ * row-major order of A; ports in increasing line index; chords chosen by a
+ * spanning forest that takes particle lines first, then hole lines.
+ * out may be NULL to query the count.  Returns MBPT_EINVAL for n outside 2..6
+ * and MBPT_ENOMEM when cap is too small (*count still receives the count).
+ */
+int mbpt_generate(int order, mbpt_diagram_desc* out, int cap, int* count);
+
+/* ---- context ------------------------------------------------------------- */
+
+/*
+ * Create a context on `device`.  If arena != NULL it must be a device pointer
+ * to arena_bytes of memory (256-byte aligned) owned by the caller that stays
+ * valid until mbpt_ctx_destroy; otherwise the library cudaMallocs arena_bytes.
+ * `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ */
+int mbpt_ctx_create(mbpt_ctx** ctx, int device, void* arena, size_t arena_bytes, void* cuda_stream);
+int mbpt_ctx_destroy(mbpt_ctx* ctx);
+/* Bytes of the arena in use and free (largest block) -- for admission control. */
+int mbpt_ctx_mem(const mbpt_ctx* ctx, size_t* used, size_t* largest_free);
+/* Device bytes one integral with this descriptor and configuration needs. */
+int mbpt_diag_bytes(const mbpt_diagram_desc* desc, const mbpt_vegas_cfg* cfg, size_t* bytes);
+
+/*
+ * Kernel launch shape of mbpt_vegas_iterate for one order: threads per block
+ * (64..512, multiple of 32) and samples per thread per chunk (1..256).  The
+ * autotuner sets these; chunk results depend on them (not on the batch mix).
+ */
+int mbpt_ctx_set_launch(mbpt_ctx* ctx, int order, int threads_per_block, int samples_per_thread);
+int mbpt_ctx_get_launch(const mbpt_ctx* ctx, int order, int* threads_per_block, int* samples_per_thread);
+
+/*
+ * Device time of the last mbpt_vegas_iterate iteration: the sample-evaluation
+ * launch and the reduce/combine/refine launch, in milliseconds, from CUDA
+ * events recorded around them on the context stream.  Synchronises on the
+ * last iteration.  MBPT_EINVAL if nothing has run yet.
+ */
+int mbpt_ctx_last_timing(mbpt_ctx* ctx, double* iterate_ms, double* finalize_ms);
+/* The CUDA stream the context queues its work on (its own stream when created with NULL). */
+int mbpt_ctx_stream(const mbpt_ctx* ctx, void** cuda_stream);
+
+/* ---- integrals ------------------------------------------------------------ */
+
+/*
+ * Validate and compile a descriptor for a physics point into a device-resident
+ * integral with a uniform VEGAS grid.  Returns MBPT_EINVAL for an invalid
+ * descriptor (ports not matching lines, chords not completing a spanning tree,
+ * line_coef violating momentum conservation, order outside 2..5), invalid
+ * physics (kF < 0, both kF zero, K_max <= kF, odd reg_power) or configuration,
+ * and MBPT_ENOMEM when the arena cannot hold its state.
+ */
+int mbpt_create_diagram(mbpt_ctx* ctx, const mbpt_diagram_desc* desc, const mbpt_physics* physics,
+                        const mbpt_vegas_cfg* cfg, mbpt_diag** out);
+int mbpt_destroy_diagram(mbpt_diag* diag);
+
+/*
+ * Run n_iters VEGAS iterations on the k integrals as one batch: per
+ * iteration one persistent launch evaluates all samples of all integrals not
+ * yet converged (Sec. III.C "integrand evaluation distributed ... via CUDA"),
+ * then a second launch reduces the per-chunk sums in a fixed order, combines
+ * the iteration into each integral's running estimate and refines its grid.
+ * The pair is captured once per context in a CUDA graph and replayed.
+ * Asynchronous on the context stream.  All diags must belong to ctx.
+ */
+int mbpt_vegas_iterate(mbpt_ctx* ctx, mbpt_diag* const* diags, int k, int n_iters);
+
+/* Synchronise and read an integral's estimate. */
+int mbpt_estimate(const mbpt_diag* diag, mbpt_result* out);
+
+/*
+ * Checkpoint: the grid, the iteration history and counters as a host byte
+ * image.  With buf == NULL (or cap too small) *need receives the size and
+ * MBPT_ENOMEM is returned if buf != NULL.  mbpt_set_state restores an image
+ * taken from an integral with the same descriptor shape and configuration.
+ */
+int mbpt_get_state(const mbpt_diag* diag, void* buf, size_t cap, size_t* need);
+int mbpt_set_state(mbpt_diag* diag, const void* buf, size_t len);
+
+/*
+ * Test hook: evaluate samples [first, first + count) of iteration `iter` with
+ * the integral's current grid and copy to host memory the mapped points
+ * x[count][d] (in [0,1]^d) and weights w[count] = J_vegas * f(x).  Does not
+ * touch the integral's accumulators.  x may be NULL.
+ */
+int mbpt_dump_samples(mbpt_diag* diag, int64_t iter, int64_t first, int64_t count, double* x, double* w);
+
+/* Test hook: Philox4x32-10 on the device for counters (ctr0 + i, ctr1, ctr2,
+ * ctr3), i < count; out receives 4*count words. */
+int mbpt_philox_device(mbpt_ctx* ctx, const uint32_t ctr[4], const uint32_t key[2], int64_t count, uint32_t* out);
+
+const char* mbpt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBPT_H */

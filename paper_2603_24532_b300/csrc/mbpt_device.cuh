@@ -1,0 +1,325 @@
+// Device code of libmbpt: Philox4x32-10, the VEGAS map, the Hugenholtz-diagram
+// integrand and the per-chunk sample loop (arXiv:2603.24532 Sec. II, III.C).
+//
+// Cost model on B300: an FP64 instruction costs ~64 FP32/INT instructions, so
+// every step that does not need FP64 runs in FP32 or integer arithmetic, and the
+// FP64 instruction count per sample is fixed by the order n alone (no
+// data-dependent predication of FP64 work): structure that varies between
+// diagrams is applied through integer selects on uniform indices.
+#pragma once
+#include <stdint.h>
+
+#include "mbpt_internal.h"
+
+namespace mbpt {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of
+// (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)),
+// key bumped by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t* out) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// select v[idx] for a uniform index with integer selects (no predicated FP64 work)
+template <int NS>
+__device__ __forceinline__ double sel(const double (&v)[16], int idx) {
+    double r = v[0];
+#pragma unroll
+    for (int j = 1; j < NS; ++j) r = (idx == j) ? v[j] : r;
+    return r;
+}
+
+__device__ __forceinline__ double neg_if(double x, int neg) {
+    // flip the sign bit with an integer op
+    long long b = __double_as_longlong(x) ^ ((long long)(neg != 0) << 63);
+    return __longlong_as_double(b);
+}
+
+// grid entry in shared memory: FP64 mode (e_i, de_i); mixed mode (e_i - de_i, de_i)
+struct Grid2 {
+    double a, de;
+};
+
+constexpr int kGridStride = MBPT_MAX_BINS;   // bins per axis row in shared memory
+
+// Result of one sample.
+struct SampleOut {
+    double w;              // J_vegas * f(x)
+    uint32_t binpack[5];   // bin index of axis a in byte (a & 3) of word a >> 2
+};
+
+// V(p, p') for one vertex, FP32, from P = 2p and P' = 2p'.
+__device__ __forceinline__ void vertex_pot_f32(const DiagRec& R, float Px, float Py, float Pz, float Qx, float Qy,
+                                               float Qz, float& vd, float& ve) {
+    const float pp = fmaf(Px, Px, fmaf(Py, Py, Pz * Pz));
+    const float qq = fmaf(Qx, Qx, fmaf(Qy, Qy, Qz * Qz));
+    const float pq = fmaf(Px, Qx, fmaf(Py, Qy, Pz * Qz));
+    const float s = pp + qq;
+    const float qd = fmaf(-2.0f, pq, s);      // |P - P'|^2
+    const float qe = fmaf(2.0f, pq, s);       // |P + P'|^2
+    const float a = pp * R.regc2f, b = qq * R.regc2f;
+    float ah = a, bh = b;
+    for (int i = 1; i < R.reg_half; ++i) { ah *= a; bh *= b; }
+    const float F = exp2f(-(ah + bh));        // exp(-(p/L)^r - (p'/L)^r)
+    vd = (R.CSf + __fdividef(R.CY4f, qd + R.mpi2_4f)) * F;
+    ve = (R.CSf + __fdividef(R.CY4f, qe + R.mpi2_4f)) * F;
+}
+
+// V(p, p') for one vertex, FP64.
+__device__ __forceinline__ void vertex_pot_f64(const DiagRec& R, double Px, double Py, double Pz, double Qx,
+                                               double Qy, double Qz, double& vd, double& ve) {
+    const double pp = fma(Px, Px, fma(Py, Py, Pz * Pz));
+    const double qq = fma(Qx, Qx, fma(Qy, Qy, Qz * Qz));
+    const double pq = fma(Px, Qx, fma(Py, Qy, Pz * Qz));
+    const double s = pp + qq;
+    const double qd = fma(-2.0, pq, s);
+    const double qe = fma(2.0, pq, s);
+    const double a = pp * R.regc, b = qq * R.regc;
+    double ah = a, bh = b;
+    for (int i = 1; i < R.reg_half; ++i) { ah *= a; bh *= b; }
+    const double F = exp(-(ah + bh));
+    vd = (R.CS + R.CY4 / (qd + R.mpi2_4)) * F;
+    ve = (R.CS + R.CY4 / (qe + R.mpi2_4)) * F;
+}
+
+// ---------------------------------------------------------------------------
+// One sample of an order-N diagram.
+//  s: sample index within the iteration, t: iteration, sid: stream id, (k0,k1): key
+//  x_out (optional): the mapped point in [0,1]^d
+// ---------------------------------------------------------------------------
+template <int N, int PREC>
+__device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* __restrict__ gs, uint32_t s,
+                                                 uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1,
+                                                 double* x_out) {
+    constexpr int L = N + 1;          // chords
+    constexpr int D = 3 * L;          // dimensions
+    constexpr int NL = 2 * N;         // lines
+    constexpr int NBLK = (D + 3) / 4; // Philox blocks
+    SampleOut o;
+    const uint32_t nb = (uint32_t)R.nb;
+
+    // --- counter-based random numbers
+    uint32_t u[4 * NBLK];
+#pragma unroll
+    for (int j = 0; j < NBLK; ++j) philox4x32_10(s, t, sid, (uint32_t)j, k0, k1, &u[4 * j]);
+
+    // --- VEGAS map: y = (u + 1/2) 2^-32, i = floor(y nb), x = e_i + (y nb - i) de_i.
+    // (2u+1) nb < 2^39, so bin index and fraction are exact integer arithmetic.
+    double x[D];
+    double jv = 1.0;
+#pragma unroll
+    for (int w = 0; w < 5; ++w) o.binpack[w] = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const uint64_t r = (2ull * (uint64_t)u[a] + 1ull) * (uint64_t)nb;
+        const uint32_t i = (uint32_t)(r >> 33);
+        const uint64_t fb = r & ((1ull << 33) - 1ull);
+        const double m = __longlong_as_double((long long)(0x3FF0000000000000ull | (fb << 19)));   // 1 + frac
+        const Grid2 g = gs[a * kGridStride + i];
+        if (PREC == MBPT_FP64) x[a] = fma(m - 1.0, g.de, g.a);
+        else x[a] = fma(m, g.de, g.a);
+        jv *= g.de;
+        o.binpack[a >> 2] |= i << (8 * (a & 3));
+        if (x_out) x_out[a] = x[a];
+    }
+
+    // --- chord momenta: k = lo + rng x0, cos(t) = 2 x1 - 1, sin(t) = 2 sqrt(x1 (1 - x1)),
+    // rational azimuth a = x2 (1 - x2), b = x2 - 1/2: cos(phi) = (a^2 - b^2)/(a^2 + b^2),
+    // sin(phi) = 2ab/(a^2 + b^2), dphi/dx2 = 2/(1/2 - a).  Jacobian k^2 (1/2 - a)/(a^2+b^2) times
+    // the constant 4 rng folded into pref.
+    double K[3][16];
+    double U[16];
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        K[0][l] = 0.0;
+        K[1][l] = 0.0;
+        K[2][l] = 0.0;
+        U[l] = 0.0;
+    }
+    double jc = 1.0;
+#pragma unroll
+    for (int c = 0; c < L; ++c) {
+        const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
+        const double k = fma(R.chord_rng[c], x0, R.chord_lo[c]);
+        const double ct = fma(2.0, x1, -1.0);
+        const double sq = sqrt(fma(-x1, x1, x1));
+        const double a = fma(-x2, x2, x2);
+        const double b = x2 - 0.5;
+        const double bb = b * b;
+        const double mm = fma(a, a, bb);
+        const double rr = 1.0 / mm;
+        const double ncos = fma(a, a, -bb);
+        const double nsin = (a + a) * b;
+        const double R2 = (k + k) * sq * rr;
+        K[0][c] = R2 * ncos;
+        K[1][c] = R2 * nsin;
+        K[2][c] = k * ct;
+        const double k2 = k * k;
+        U[c] = k2;
+        jc *= k2 * ((0.5 - a) * rr);
+    }
+    // --- tree lines from momentum conservation: k = k_a + k_b - k_c
+#pragma unroll
+    for (int j = 0; j < N - 1; ++j) {
+        const int ia = R.tree_a[j], ib = R.tree_b[j], ic = R.tree_c[j];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            K[q][L + j] = (sel<NL>(K[q], ia) + sel<NL>(K[q], ib)) - sel<NL>(K[q], ic);
+        U[L + j] = fma(K[0][L + j], K[0][L + j], fma(K[1][L + j], K[1][L + j], K[2][L + j] * K[2][L + j]));
+    }
+
+    // --- Fermi-sea steps: hole k^2 < kF^2, particle k^2 >= kF^2 (non-negative doubles compare
+    // as their bit patterns)
+    uint32_t okn = 0, okp = 0;
+    {
+        const long long bn = __double_as_longlong(R.kf2_n), bp = __double_as_longlong(R.kf2_p);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const long long bu = __double_as_longlong(U[l]);
+            const bool hole = (R.hole_slots >> l) & 1u;
+            const bool on = hole ? (bu < bn) : (bu >= bn);
+            const bool op = hole ? (bu < bp) : (bu >= bp);
+            okn |= (uint32_t)on << l;
+            okp |= (uint32_t)op << l;
+        }
+    }
+    const uint32_t all = R.all_slots;
+    bool live;
+    if (R.asym) live = ((okn | okp) == all);
+    else live = (okn == all);
+    if (!live) {
+        o.w = 0.0;
+        return o;
+    }
+
+    // --- energy denominators (FP64): D~_m = D~_{m-1} + sum over the four lines of vertex m
+    double Dprod = 1.0;
+    {
+        double Dm = 0.0;
+#pragma unroll
+        for (int m = 0; m < N - 1; ++m) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double uv = neg_if(sel<NL>(U, R.cut_slot[m][k]), R.cut_neg[m][k]);
+                if (m == 0 && k == 0) Dm = uv;
+                else Dm += uv;
+            }
+            Dprod = (m == 0) ? Dm : Dprod * Dm;
+        }
+    }
+
+    // --- spin(-isospin) sum of the antisymmetrised vertex products
+    double S;
+    if (PREC == MBPT_MIXED) {
+        float lf[3][L];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int c = 0; c < L; ++c) lf[q][c] = (float)K[q][c];
+        float prod[1 << N];
+        prod[0] = 1.0f;
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+            float P[3], Q[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float p = 0.0f, qq = 0.0f;
+#pragma unroll
+                for (int c = 0; c < L; ++c) {
+                    p = fmaf(R.vcoef_out[v][c], lf[q][c], p);
+                    qq = fmaf(R.vcoef_in[v][c], lf[q][c], qq);
+                }
+                P[q] = p;
+                Q[q] = qq;
+            }
+            float vd, ve;
+            vertex_pot_f32(R, P[0], P[1], P[2], Q[0], Q[1], Q[2], vd, ve);
+#pragma unroll
+            for (int j = 0; j < (1 << v); ++j) {
+                prod[j + (1 << v)] = prod[j] * ve;
+                prod[j] *= vd;
+            }
+        }
+        float sum = 0.0f;
+        if (!R.asym) {
+#pragma unroll
+            for (int tt = 0; tt < (1 << N); ++tt) sum = fmaf(R.gcoef_f[tt], prod[tt], sum);
+        } else {
+#pragma unroll
+            for (int tt = 0; tt < (1 << N); ++tt) {
+                float f = R.gsign_f[tt];
+                const int nlp = R.nloops[tt];
+                for (int lp = 0; lp < nlp; ++lp) {
+                    const uint32_t msk = R.loop_mask[tt][lp];
+                    const int fn = (msk & ~okn) == 0u;
+                    const int fp = (msk & ~okp) == 0u;
+                    f *= (float)(2 * (fn + fp));
+                }
+                sum = fmaf(f, prod[tt], sum);
+            }
+        }
+        S = (double)sum;
+    } else {
+        double prod[1 << N];
+        prod[0] = 1.0;
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+            double P[3], Q[3];
+            const int o1 = R.port_slot[v][0], o2 = R.port_slot[v][1], i1 = R.port_slot[v][2], i2 = R.port_slot[v][3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                P[q] = sel<NL>(K[q], o1) - sel<NL>(K[q], o2);
+                Q[q] = sel<NL>(K[q], i1) - sel<NL>(K[q], i2);
+            }
+            double vd, ve;
+            vertex_pot_f64(R, P[0], P[1], P[2], Q[0], Q[1], Q[2], vd, ve);
+#pragma unroll
+            for (int j = 0; j < (1 << v); ++j) {
+                prod[j + (1 << v)] = prod[j] * ve;
+                prod[j] *= vd;
+            }
+        }
+        double sum = 0.0;
+        if (!R.asym) {
+#pragma unroll
+            for (int tt = 0; tt < (1 << N); ++tt) sum = fma(R.gcoef_d[tt], prod[tt], sum);
+        } else {
+#pragma unroll
+            for (int tt = 0; tt < (1 << N); ++tt) {
+                float f = R.gsign_f[tt];
+                const int nlp = R.nloops[tt];
+                for (int lp = 0; lp < nlp; ++lp) {
+                    const uint32_t msk = R.loop_mask[tt][lp];
+                    const int fn = (msk & ~okn) == 0u;
+                    const int fp = (msk & ~okp) == 0u;
+                    f *= (float)(2 * (fn + fp));
+                }
+                sum = fma((double)f, prod[tt], sum);
+            }
+        }
+        S = sum;
+    }
+
+    // --- weight: w = pref * J_vegas * J_chords * S / prod_m D~_m
+    o.w = (R.pref * jv * jc * S) / Dprod;
+    return o;
+}
+
+}  // namespace mbpt

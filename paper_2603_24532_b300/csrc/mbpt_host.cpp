@@ -1,0 +1,479 @@
+// Host side of libmbpt: the diagram generator (Table I of arXiv:2603.24532),
+// descriptor validation and the compilation of a descriptor + physics point +
+// VEGAS setup into the device record DiagRec.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <map>
+#include <vector>
+
+#include "mbpt_internal.h"
+
+namespace mbpt {
+namespace {
+
+using Mat = std::array<int8_t, 36>;   // row-major n x n, n <= 6
+
+void fill_rows(int n, int i, std::vector<std::array<int8_t, 6>>& rows) {
+    // all rows with zero at i, non-negative entries summing to 2, ascending lexicographic order
+    rows.clear();
+    std::vector<std::array<int8_t, 6>> tmp;
+    for (int a = 0; a < n; ++a) {
+        if (a == i) continue;
+        for (int b = a; b < n; ++b) {
+            if (b == i) continue;
+            std::array<int8_t, 6> r{};
+            r[a] += 1;
+            r[b] += 1;
+            tmp.push_back(r);
+        }
+    }
+    std::sort(tmp.begin(), tmp.end(), [n](const std::array<int8_t, 6>& x, const std::array<int8_t, 6>& y) {
+        for (int k = 0; k < n; ++k)
+            if (x[k] != y[k]) return x[k] < y[k];
+        return false;
+    });
+    rows = tmp;
+}
+
+bool connected(int n, const Mat& A) {
+    int seen = 1, stack[6], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        int v = stack[--sp];
+        for (int u = 0; u < n; ++u)
+            if ((A[v * n + u] || A[u * n + v]) && !(seen >> u & 1)) {
+                seen |= 1 << u;
+                stack[sp++] = u;
+            }
+    }
+    return seen == (1 << n) - 1;
+}
+
+void enumerate_rec(int n, int i, Mat& A, int colsum[6], const std::vector<std::vector<std::array<int8_t, 6>>>& rows,
+                   std::vector<Mat>& out) {
+    if (i == n) {
+        for (int j = 0; j < n; ++j)
+            if (colsum[j] != 2) return;
+        if (connected(n, A)) out.push_back(A);
+        return;
+    }
+    for (const auto& r : rows[i]) {
+        bool ok = true;
+        for (int j = 0; j < n; ++j)
+            if (colsum[j] + r[j] > 2) { ok = false; break; }
+        if (!ok) continue;
+        for (int j = 0; j < n; ++j) { A[i * n + j] = r[j]; colsum[j] += r[j]; }
+        enumerate_rec(n, i + 1, A, colsum, rows, out);
+        for (int j = 0; j < n; ++j) { colsum[j] -= r[j]; A[i * n + j] = 0; }
+    }
+}
+
+std::vector<Mat> all_matrices(int n) {
+    std::vector<std::vector<std::array<int8_t, 6>>> rows(n);
+    for (int i = 0; i < n; ++i) fill_rows(n, i, rows[i]);
+    std::vector<Mat> out;
+    Mat A{};
+    int colsum[6] = {0};
+    enumerate_rec(n, 0, A, colsum, rows, out);
+    return out;   // nested loops over lexicographically sorted rows: already in row-major lexicographic order
+}
+
+int find_root(int* parent, int a) {
+    while (parent[a] != a) a = parent[a] = parent[parent[a]];
+    return a;
+}
+
+// Momentum routing: for chord c, walk the tree path from the chord's end back to its start;
+// tree lines traversed along their arrow get +1, against it -1.
+bool route_chords(int n, int nl, const int8_t* src, const int8_t* dst, const int8_t* chords, int nc,
+                  int8_t coef[MBPT_MAX_LINES][MBPT_MAX_CHORDS]) {
+    bool is_chord[MBPT_MAX_LINES] = {false};
+    for (int c = 0; c < nc; ++c) is_chord[chords[c]] = true;
+    for (int l = 0; l < nl; ++l)
+        for (int c = 0; c < MBPT_MAX_CHORDS; ++c) coef[l][c] = 0;
+    for (int c = 0; c < nc; ++c) {
+        int lc = chords[c];
+        coef[lc][c] = 1;
+        // BFS over tree lines from dst(lc) to src(lc)
+        int prev_line[6], prev_v[6];
+        for (int v = 0; v < n; ++v) prev_line[v] = -2;
+        int q[6], qh = 0, qt = 0;
+        int start = dst[lc], goal = src[lc];
+        prev_line[start] = -1;
+        q[qt++] = start;
+        while (qh < qt) {
+            int v = q[qh++];
+            for (int l = 0; l < nl; ++l) {
+                if (is_chord[l]) continue;
+                int u = -1;
+                if (src[l] == v) u = dst[l];
+                else if (dst[l] == v) u = src[l];
+                if (u < 0 || prev_line[u] != -2) continue;
+                prev_line[u] = l;
+                prev_v[u] = v;
+                q[qt++] = u;
+            }
+        }
+        if (prev_line[goal] == -2) return false;
+        for (int v = goal; v != start; v = prev_v[v]) {
+            int l = prev_line[v];
+            int from = prev_v[v];
+            // traversal goes from `from` to `v`
+            if (src[l] == from && dst[l] == v) coef[l][c] += 1;
+            else coef[l][c] -= 1;
+        }
+    }
+    return true;
+}
+
+void build_desc(int n, const Mat& A, int id, mbpt_diagram_desc& d) {
+    memset(&d, 0, sizeof(d));
+    d.order = n;
+    d.n_lines = 2 * n;
+    int nl = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < A[i * n + j]; ++k) {
+                d.line_src[nl] = (int8_t)i;
+                d.line_dst[nl] = (int8_t)j;
+                ++nl;
+            }
+    for (int v = 0; v < n; ++v) {
+        int no = 0, ni = 0;
+        for (int l = 0; l < nl; ++l) {
+            if (d.line_src[l] == v) d.vtx_out[v][no++] = (int8_t)l;
+            if (d.line_dst[l] == v) d.vtx_in[v][ni++] = (int8_t)l;
+        }
+    }
+    int parent[6];
+    for (int v = 0; v < n; ++v) parent[v] = v;
+    int order_l[MBPT_MAX_LINES], no = 0;
+    for (int l = 0; l < nl; ++l) if (d.line_src[l] < d.line_dst[l]) order_l[no++] = l;
+    for (int l = 0; l < nl; ++l) if (d.line_src[l] > d.line_dst[l]) order_l[no++] = l;
+    bool chord[MBPT_MAX_LINES] = {false};
+    for (int k = 0; k < nl; ++k) {
+        int l = order_l[k];
+        int a = find_root(parent, d.line_src[l]), b = find_root(parent, d.line_dst[l]);
+        if (a == b) chord[l] = true;
+        else parent[a] = b;
+    }
+    int nc = 0;
+    for (int l = 0; l < nl; ++l) if (chord[l]) d.chord_line[nc++] = (int8_t)l;
+    d.n_chords = (int8_t)nc;
+    route_chords(n, nl, d.line_src, d.line_dst, d.chord_line, nc, d.line_coef);
+    d.diagram_id = id;
+}
+
+bool anomalous(const mbpt_diagram_desc& d) {
+    int nl = d.n_lines, nc = d.n_chords;
+    for (int a = 0; a < nl; ++a) {
+        if (!(d.line_src[a] > d.line_dst[a])) continue;
+        for (int b = 0; b < nl; ++b) {
+            if (!(d.line_src[b] < d.line_dst[b])) continue;
+            bool eq = true, neg = true;
+            for (int c = 0; c < nc; ++c) {
+                if (d.line_coef[a][c] != d.line_coef[b][c]) eq = false;
+                if (d.line_coef[a][c] != -d.line_coef[b][c]) neg = false;
+            }
+            if (eq || neg) return true;
+        }
+    }
+    return false;
+}
+
+Mat mirror(int n, const Mat& A) {
+    Mat M{};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) M[i * n + j] = A[(n - 1 - j) * n + (n - 1 - i)];
+    return M;
+}
+
+void set_err(char* err, size_t len, const char* msg) {
+    if (err && len) snprintf(err, len, "%s", msg);
+}
+
+}  // namespace
+
+int validate_descriptor(const mbpt_diagram_desc& d, char* err, size_t errlen) {
+    int n = d.order;
+    if (n < 2 || n > MBPT_MAX_DEVICE_ORDER) { set_err(err, errlen, "order must be 2..5"); return MBPT_EINVAL; }
+    int nl = d.n_lines;
+    if (nl != 2 * n) { set_err(err, errlen, "n_lines must be 2*order"); return MBPT_EINVAL; }
+    for (int l = 0; l < nl; ++l) {
+        int s = d.line_src[l], t = d.line_dst[l];
+        if (s < 0 || s >= n || t < 0 || t >= n || s == t) { set_err(err, errlen, "line endpoints out of range"); return MBPT_EINVAL; }
+    }
+    for (int v = 0; v < n; ++v) {
+        int no = 0, ni = 0;
+        for (int l = 0; l < nl; ++l) { no += d.line_src[l] == v; ni += d.line_dst[l] == v; }
+        if (no != 2 || ni != 2) { set_err(err, errlen, "every vertex needs two outgoing and two incoming lines"); return MBPT_EINVAL; }
+        for (int k = 0; k < 2; ++k) {
+            int lo = d.vtx_out[v][k], li = d.vtx_in[v][k];
+            if (lo < 0 || lo >= nl || li < 0 || li >= nl || d.line_src[lo] != v || d.line_dst[li] != v) {
+                set_err(err, errlen, "vertex ports do not match the lines");
+                return MBPT_EINVAL;
+            }
+        }
+        if (d.vtx_out[v][0] == d.vtx_out[v][1] || d.vtx_in[v][0] == d.vtx_in[v][1]) {
+            set_err(err, errlen, "a vertex lists the same line twice");
+            return MBPT_EINVAL;
+        }
+    }
+    int nc = d.n_chords;
+    if (nc != n + 1) { set_err(err, errlen, "n_chords must be order+1"); return MBPT_EINVAL; }
+    bool is_chord[MBPT_MAX_LINES] = {false};
+    for (int c = 0; c < nc; ++c) {
+        int l = d.chord_line[c];
+        if (l < 0 || l >= nl || is_chord[l]) { set_err(err, errlen, "invalid chord list"); return MBPT_EINVAL; }
+        is_chord[l] = true;
+    }
+    int parent[8];
+    for (int v = 0; v < n; ++v) parent[v] = v;
+    for (int l = 0; l < nl; ++l) {
+        if (is_chord[l]) continue;
+        int a = find_root(parent, d.line_src[l]), b = find_root(parent, d.line_dst[l]);
+        if (a == b) { set_err(err, errlen, "non-chord lines contain a cycle"); return MBPT_EINVAL; }
+        parent[a] = b;
+    }
+    for (int v = 1; v < n; ++v)
+        if (find_root(parent, v) != find_root(parent, 0)) { set_err(err, errlen, "diagram is not connected"); return MBPT_EINVAL; }
+    for (int l = 0; l < nl; ++l)
+        for (int c = 0; c < nc; ++c)
+            if (d.line_coef[l][c] < -1 || d.line_coef[l][c] > 1) { set_err(err, errlen, "line_coef outside {-1,0,1}"); return MBPT_EINVAL; }
+    for (int c = 0; c < nc; ++c)
+        for (int cc = 0; cc < nc; ++cc)
+            if (d.line_coef[d.chord_line[c]][cc] != (c == cc)) { set_err(err, errlen, "chord rows of line_coef must be unit vectors"); return MBPT_EINVAL; }
+    for (int v = 0; v < n; ++v)
+        for (int c = 0; c < nc; ++c) {
+            int s = 0;
+            for (int l = 0; l < nl; ++l) {
+                if (d.line_dst[l] == v) s += d.line_coef[l][c];
+                if (d.line_src[l] == v) s -= d.line_coef[l][c];
+            }
+            if (s) { set_err(err, errlen, "line_coef violates momentum conservation"); return MBPT_EINVAL; }
+        }
+    return MBPT_OK;
+}
+
+int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbpt_vegas_cfg& cfg, DiagRec* r,
+                   char* err, size_t errlen) {
+    int st = validate_descriptor(d, err, errlen);
+    if (st) return st;
+    if (!(ph.kF_n >= 0.0) || !(ph.kF_p >= 0.0) || !(ph.kF_n > 0.0 || ph.kF_p > 0.0)) {
+        set_err(err, errlen, "Fermi momenta must be >= 0 and not both zero");
+        return MBPT_EINVAL;
+    }
+    double kfmax = ph.kF_n > ph.kF_p ? ph.kF_n : ph.kF_p;
+    double kfmin = kfmax;
+    if (ph.kF_n > 0.0 && ph.kF_n < kfmin) kfmin = ph.kF_n;
+    if (ph.kF_p > 0.0 && ph.kF_p < kfmin) kfmin = ph.kF_p;
+    if (!(ph.K_max > kfmax) || !(ph.hbar2_over_m > 0.0) || !(ph.Lambda > 0.0) || !(ph.m_pi >= 0.0) ||
+        ph.reg_power < 2 || ph.reg_power > 8 || (ph.reg_power & 1) || ph.map_kind != 0) {
+        set_err(err, errlen, "invalid physics parameters (K_max > kF, hbar2_over_m > 0, Lambda > 0, even reg_power 2..8, map_kind 0)");
+        return MBPT_EINVAL;
+    }
+    if (cfg.n_bins < 2 || cfg.n_bins > MBPT_MAX_BINS || cfg.samples_per_iter < 2 ||
+        cfg.samples_per_iter >= (1ull << 32) || !(cfg.alpha >= 0.0) ||
+        (cfg.precision != MBPT_FP64 && cfg.precision != MBPT_MIXED) || !(cfg.target_rel >= 0.0) ||
+        !(cfg.target_abs >= 0.0)) {
+        set_err(err, errlen, "invalid VEGAS configuration");
+        return MBPT_EINVAL;
+    }
+    memset(r, 0, sizeof(*r));
+    int n = d.order, nl = d.n_lines, nc = d.n_chords;
+    r->order = n;
+    r->n_lines = nl;
+    r->n_chords = nc;
+    r->d = 3 * nc;
+    r->nb = cfg.n_bins;
+    r->precision = cfg.precision;
+    r->reg_half = ph.reg_power / 2;
+    r->all_slots = (1u << nl) - 1u;
+    // --- slots: chords first, then tree lines in post-order of a spanning tree rooted at vertex 0
+    int slot_of[MBPT_MAX_LINES];
+    bool is_chord[MBPT_MAX_LINES] = {false};
+    for (int l = 0; l < nl; ++l) slot_of[l] = -1;
+    for (int c = 0; c < nc; ++c) {
+        slot_of[(int)d.chord_line[c]] = c;
+        is_chord[(int)d.chord_line[c]] = true;
+    }
+    int parent_edge[8], depth[8], order_v[8], nv = 0;
+    for (int v = 0; v < n; ++v) { parent_edge[v] = -2; depth[v] = 0; }
+    parent_edge[0] = -1;
+    order_v[nv++] = 0;
+    for (int qh = 0; qh < nv; ++qh) {
+        int v = order_v[qh];
+        for (int l = 0; l < nl; ++l) {
+            if (is_chord[l]) continue;
+            int u = -1;
+            if (d.line_src[l] == v) u = d.line_dst[l];
+            else if (d.line_dst[l] == v) u = d.line_src[l];
+            if (u < 0 || parent_edge[u] != -2) continue;
+            parent_edge[u] = l;
+            depth[u] = depth[v] + 1;
+            order_v[nv++] = u;
+        }
+    }
+    int next_slot = nc, t = 0;
+    for (int k = nv - 1; k >= 1; --k) {     // reverse BFS order: children before parents
+        int v = order_v[k];
+        int e = parent_edge[v];
+        // the other three lines at v: same side as e (C) and opposite side (A, B)
+        bool e_in = d.line_dst[e] == v;
+        int A, B, C;
+        if (e_in) {
+            A = d.vtx_out[v][0]; B = d.vtx_out[v][1];
+            C = d.vtx_in[v][0] == e ? d.vtx_in[v][1] : d.vtx_in[v][0];
+        } else {
+            A = d.vtx_in[v][0]; B = d.vtx_in[v][1];
+            C = d.vtx_out[v][0] == e ? d.vtx_out[v][1] : d.vtx_out[v][0];
+        }
+        if (slot_of[A] < 0 || slot_of[B] < 0 || slot_of[C] < 0) {
+            set_err(err, errlen, "internal: momentum routing order");
+            return MBPT_EINVAL;
+        }
+        r->tree_a[t] = (int8_t)slot_of[A];
+        r->tree_b[t] = (int8_t)slot_of[B];
+        r->tree_c[t] = (int8_t)slot_of[C];
+        slot_of[e] = next_slot++;
+        ++t;
+    }
+    for (int l = 0; l < nl; ++l) r->line_slot[l] = (int8_t)slot_of[l];
+    int h = 0;
+    for (int l = 0; l < nl; ++l)
+        if (d.line_src[l] > d.line_dst[l]) { r->hole_slots |= 1u << slot_of[l]; ++h; }
+    // --- ranges of the chord momenta
+    for (int c = 0; c < nc; ++c) {
+        bool hole = d.line_src[(int)d.chord_line[c]] > d.line_dst[(int)d.chord_line[c]];
+        r->chord_lo[c] = hole ? 0.0 : kfmin;
+        r->chord_rng[c] = hole ? kfmax : ph.K_max - kfmin;
+    }
+    // --- vertices
+    for (int v = 0; v < n; ++v) {
+        int o1 = d.vtx_out[v][0], o2 = d.vtx_out[v][1], i1 = d.vtx_in[v][0], i2 = d.vtx_in[v][1];
+        r->port_slot[v][0] = (int8_t)slot_of[o1];
+        r->port_slot[v][1] = (int8_t)slot_of[o2];
+        r->port_slot[v][2] = (int8_t)slot_of[i1];
+        r->port_slot[v][3] = (int8_t)slot_of[i2];
+        for (int c = 0; c < nc; ++c) {
+            r->vcoef_out[v][c] = (float)(d.line_coef[o1][c] - d.line_coef[o2][c]);
+            r->vcoef_in[v][c] = (float)(d.line_coef[i1][c] - d.line_coef[i2][c]);
+        }
+    }
+    // --- energy denominators: cut m lies between vertices m and m+1 and holds the lines with
+    // min(src,dst) <= m < max(src,dst).  D~_m = sum_holes k^2 - sum_particles k^2 over the cut,
+    // updated at vertex m: lines starting there enter, lines ending there leave.
+    for (int m = 0; m < n - 1; ++m) {
+        int k = 0;
+        for (int l = 0; l < nl; ++l) {
+            int s = d.line_src[l], tt = d.line_dst[l];
+            if (s != m && tt != m) continue;
+            int lo = s < tt ? s : tt;
+            bool hole = s > tt;
+            bool enter = (lo == m);
+            bool add = (hole == enter);     // hole entering: +, particle entering: -, leaving: opposite
+            r->cut_slot[m][k] = (int8_t)slot_of[l];
+            r->cut_neg[m][k] = add ? 0 : 1;
+            ++k;
+        }
+        if (k != 4) {
+            set_err(err, errlen, "internal: vertex without four lines");
+            return MBPT_EINVAL;
+        }
+    }
+    // --- equivalent line pairs
+    int neq = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int cnt = 0;
+            for (int l = 0; l < nl; ++l) cnt += (d.line_src[l] == i && d.line_dst[l] == j);
+            if (cnt == 2) ++neq;
+        }
+    // --- spin-sum terms: loops when vertex v continues i1->o1, i2->o2 (direct) or
+    // i1->o2, i2->o1 (exchange)
+    bool sym = (ph.kF_p == 0.0) || (ph.kF_n == 0.0) || (ph.kF_n == ph.kF_p);
+    int species = (ph.kF_n > 0.0) + (ph.kF_p > 0.0);
+    double g = 2.0 * species;
+    r->asym = sym ? 0 : 1;
+    for (int term = 0; term < (1 << n); ++term) {
+        int seen = 0, loops = 0;
+        for (int start = 0; start < nl; ++start) {
+            if ((seen >> start) & 1) continue;
+            uint32_t mask = 0;
+            int l = start;
+            while (!((seen >> l) & 1)) {
+                seen |= 1 << l;
+                mask |= 1u << slot_of[l];
+                int v = d.line_dst[l];
+                bool ex = (term >> v) & 1;
+                bool first = d.vtx_in[v][0] == l;
+                l = (first != ex) ? d.vtx_out[v][0] : d.vtx_out[v][1];
+            }
+            if (loops < kMaxLoops) r->loop_mask[term][loops] = mask;
+            ++loops;
+        }
+        if (loops > kMaxLoops) {
+            set_err(err, errlen, "internal: too many loops");
+            return MBPT_EINVAL;
+        }
+        r->nloops[term] = loops;
+        r->gsign_f[term] = (loops & 1) ? -1.0f : 1.0f;
+        double c = ((loops & 1) ? -1.0 : 1.0) * pow(g, loops);
+        r->gcoef_d[term] = c;
+        r->gcoef_f[term] = (float)c;
+    }
+    // --- physics
+    if (sym) {
+        double kf = ph.kF_n > 0.0 ? ph.kF_n : ph.kF_p;
+        r->kf2_n = kf * kf;
+        r->kf2_p = kf * kf;
+    } else {
+        r->kf2_n = ph.kF_n * ph.kF_n;
+        r->kf2_p = ph.kF_p * ph.kF_p;
+    }
+    r->CS = ph.C_S;
+    r->CY4 = 4.0 * ph.C_Y;
+    r->mpi2_4 = 4.0 * ph.m_pi * ph.m_pi;
+    r->regc = 1.0 / (4.0 * ph.Lambda * ph.Lambda);
+    r->CSf = (float)r->CS;
+    r->CY4f = (float)r->CY4;
+    r->mpi2_4f = (float)r->mpi2_4;
+    r->regc2f = (float)(r->regc * pow(1.4426950408889634, 1.0 / r->reg_half));
+    const double pi = 3.14159265358979323846;
+    double dens = (ph.kF_n * ph.kF_n * ph.kF_n + ph.kF_p * ph.kF_p * ph.kF_p) / (3.0 * pi * pi);
+    // (-1)^h 2^-n_eq / n_dens * (2pi)^-3(n+1) * (2/(hbar^2/m))^(n-1) * N_b^d * prod_c 4 (range_c)
+    double pref = ((h & 1) ? -1.0 : 1.0) / pow(2.0, neq) / pow(2.0 * pi, 3.0 * nc) / dens *
+                  pow(2.0 / ph.hbar2_over_m, n - 1) * pow((double)cfg.n_bins, 3.0 * nc);
+    for (int c = 0; c < nc; ++c) pref *= 4.0 * r->chord_rng[c];
+    r->pref = pref;
+    return MBPT_OK;
+}
+
+}  // namespace mbpt
+
+using namespace mbpt;
+
+extern "C" int mbpt_generate(int order, mbpt_diagram_desc* out, int cap, int* count) {
+    if (order < 2 || order > MBPT_MAX_ORDER || !count) return MBPT_EINVAL;
+    std::vector<Mat> mats = all_matrices(order);
+    int total = (int)mats.size();
+    *count = total;
+    if (!out) return MBPT_OK;
+    if (cap < total) return MBPT_ENOMEM;
+    std::map<Mat, int> index;
+    for (int k = 0; k < total; ++k) index[mats[k]] = k;
+    for (int k = 0; k < total; ++k) {
+        build_desc(order, mats[k], k, out[k]);
+        Mat M = mirror(order, mats[k]);
+        out[k].mirror_id = index.count(M) ? index[M] : -1;
+        int flags = 0;
+        if (anomalous(out[k])) flags |= MBPT_FLAG_ANOMALOUS;
+        if (out[k].mirror_id == k) flags |= MBPT_FLAG_SELF_MIRROR;
+        out[k].flags = flags;
+    }
+    return MBPT_OK;
+}

@@ -1,0 +1,103 @@
+// Internal data layout shared by the host runtime and the device kernels of
+// libmbpt (not part of the public ABI).
+#pragma once
+#include <stdint.h>
+
+#include "../../include/mbpt.h"
+
+namespace mbpt {
+
+constexpr int kMaxD = 3 * (MBPT_MAX_DEVICE_ORDER + 1);   // 18 dimensions at order 5
+constexpr int kMaxTerms = 1 << MBPT_MAX_DEVICE_ORDER;    // 32 spin-sum terms
+constexpr int kMaxLoops = MBPT_MAX_DEVICE_ORDER + 1;     // loops of one term: at most n+1
+constexpr int kMaxIters = 512;                           // iteration history kept per integral
+constexpr int kThreads = 256;                            // threads per block of the iterate kernel
+constexpr int kWarps = kThreads / 32;
+
+// Compiled, device-resident description of one integral (diagram x physics x VEGAS setup).
+//
+// Line momenta live in "slots": slots 0..n are the chords (the integration
+// variables), slots n+1..2n-1 the remaining (tree) lines in an order in which
+// each tree line follows from momentum conservation at one vertex whose other
+// three lines are already known:  k[slot] = k[tree_a] + k[tree_b] - k[tree_c].
+// All bit masks below are over slots.
+struct alignas(16) DiagRec {
+    int32_t order, n_lines, n_chords, d;
+    int32_t nb, precision, asym, reg_half;      // asym: per-loop species sums; reg_half = r/2
+    uint32_t hole_slots;                         // slots holding hole lines
+    uint32_t all_slots;                          // (1 << 2n) - 1
+    int8_t tree_a[MBPT_MAX_DEVICE_ORDER], tree_b[MBPT_MAX_DEVICE_ORDER], tree_c[MBPT_MAX_DEVICE_ORDER];
+    // energy denominators, built cut by cut: D~_m = D~_{m-1} + sum_k sign[m][k] |k_slot[m][k]|^2
+    // over the four lines of vertex m (D~_-1 = 0); D_m = (hbar^2/2m) D~_m
+    int8_t cut_slot[MBPT_MAX_DEVICE_ORDER][4];
+    int8_t cut_neg[MBPT_MAX_DEVICE_ORDER][4];    // 1: subtract
+    // vertex v = <o1 o2|V|i1 i2>: slots of o1, o2, i1, i2
+    int8_t port_slot[MBPT_MAX_DEVICE_ORDER][4];
+    // P_v = k_o1 - k_o2 and P'_v = k_i1 - k_i2 as chord combinations (coefficients -2..2)
+    float vcoef_out[MBPT_MAX_DEVICE_ORDER][8];
+    float vcoef_in[MBPT_MAX_DEVICE_ORDER][8];
+    // spin(-isospin) sum, term t: bit v of t set = vertex v taken in exchange
+    float gcoef_f[kMaxTerms];                    // (-1)^L(t) g^L(t)   (one Fermi momentum)
+    double gcoef_d[kMaxTerms];
+    float gsign_f[kMaxTerms];                    // (-1)^L(t)           (per-loop species sums)
+    int32_t nloops[kMaxTerms];
+    uint32_t loop_mask[kMaxTerms][kMaxLoops];
+    // chord sampling: radial range [lo, lo + rng]
+    double chord_lo[8], chord_rng[8];
+    // physics
+    double kf2_n, kf2_p;                         // squared Fermi momenta (0 = species absent)
+    double CS, CY4, mpi2_4;                      // with P = 2p: V = [C_S + 4C_Y/(|P-P'|^2 + 4m_pi^2)] F
+    double regc;                                 // (|P|^2 regc)^reg_half = (p/Lambda)^r
+    double pref;                                 // all constant factors of the weight
+    float CSf, CY4f, mpi2_4f, regc2f;            // FP32 copies; regc2f folds in log2(e)^(1/reg_half)
+    int8_t line_slot[MBPT_MAX_LINES];            // slot of each descriptor line
+    int8_t pad[4];
+};
+
+// Per-integral running state (device).
+struct alignas(16) DiagState {
+    double sum_inv_var;     // sum over iterations with non-zero variance of 1/sigma_t^2
+    double sum_mean_w;      // ... of I_t/sigma_t^2
+    double last_mean, last_var;
+    double mean, sigma, chi2;
+    int64_t n_evals;
+    int32_t iter;           // iterations done; Philox counter word 1 of the next iteration
+    int32_t converged;
+    int32_t status;
+    int32_t n_used;         // iterations entering the weighted mean
+    double hist_mean[kMaxIters];
+    double hist_var[kMaxIters];
+};
+
+// One entry of the batch work table.
+struct alignas(16) WorkItem {
+    const DiagRec* rec;
+    DiagState* state;
+    double* grid;          // d rows of nb+1 edges
+    uint64_t samples;      // per iteration
+    uint64_t seed;
+    uint32_t stream_id;
+    uint32_t chunk_begin;  // first global chunk of this integral
+    uint32_t n_chunks;
+    uint32_t freeze_after;
+    double alpha, target_rel, target_abs;
+    int32_t spt;           // samples per thread per chunk
+    int32_t hist_stride;   // floats per chunk histogram slot
+    int32_t pad0, pad1;
+};
+
+struct alignas(16) WorkHeader {
+    uint32_t n_items;
+    uint32_t total_chunks;
+    uint32_t chunk_counter;   // dynamic chunk scheduling, reset before every iterate launch
+    uint32_t error;           // non-zero: a kernel saw an out-of-range index
+    uint64_t hist_floats;     // size of the chunk histogram scratch
+    uint64_t pad;
+};
+
+// host-side helpers (mbpt_host.cpp)
+int compile_record(const mbpt_diagram_desc& desc, const mbpt_physics& ph, const mbpt_vegas_cfg& cfg,
+                   DiagRec* rec, char* err, size_t errlen);
+int validate_descriptor(const mbpt_diagram_desc& desc, char* err, size_t errlen);
+
+}  // namespace mbpt

@@ -1,0 +1,967 @@
+// libmbpt runtime: context, device arena, batch work table, the VEGAS iteration
+// kernels (sample evaluation + per-chunk sums and histograms; fixed-order
+// reduction, iteration combination and grid refinement) and the C ABI.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "mbpt_device.cuh"
+#include "mbpt_internal.h"
+
+using namespace mbpt;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(MBPT_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device arena: first-fit allocator with coalescing over one device buffer.
+// ---------------------------------------------------------------------------
+struct Arena {
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_blocks;   // offset -> size
+    std::map<size_t, size_t> used;          // offset -> size
+    static constexpr size_t kAlign = 256;
+
+    void init(char* b, size_t s) {
+        base = b;
+        size = s & ~(kAlign - 1);
+        free_blocks.clear();
+        used.clear();
+        if (size) free_blocks[0] = size;
+    }
+    void* alloc(size_t bytes) {
+        bytes = (bytes + kAlign - 1) & ~(kAlign - 1);
+        if (bytes == 0) bytes = kAlign;
+        for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+            if (it->second >= bytes) {
+                size_t off = it->first, sz = it->second;
+                free_blocks.erase(it);
+                if (sz > bytes) free_blocks[off + bytes] = sz - bytes;
+                used[off] = bytes;
+                return base + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void* p) {
+        if (!p) return;
+        size_t off = (size_t)((char*)p - base);
+        auto it = used.find(off);
+        if (it == used.end()) return;
+        size_t sz = it->second;
+        used.erase(it);
+        auto nx = free_blocks.lower_bound(off);
+        if (nx != free_blocks.end() && off + sz == nx->first) {
+            sz += nx->second;
+            nx = free_blocks.erase(nx);
+        }
+        if (nx != free_blocks.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += sz;
+                return;
+            }
+        }
+        free_blocks[off] = sz;
+    }
+    size_t in_use() const {
+        size_t s = 0;
+        for (auto& kv : used) s += kv.second;
+        return s;
+    }
+    size_t largest_free() const {
+        size_t s = 0;
+        for (auto& kv : free_blocks) s = std::max(s, kv.second);
+        return s;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+struct alignas(16) ChunkSmem {
+    DiagRec rec;
+    Grid2 grid[kMaxD * kGridStride];
+    float hist[kWarps][kMaxD * MBPT_MAX_BINS];
+    double red[2][kWarps];
+    uint32_t chunk, item, iter, skip;
+};
+
+__device__ __forceinline__ void load_record(DiagRec* dst, const DiagRec* src) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(DiagRec) / 16); i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, int nb, int prec) {
+    for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
+        const int a = idx / nb, i = idx - a * nb;
+        const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
+        const double de = e1 - e0;
+        Grid2 g;
+        g.de = de;
+        g.a = (prec == MBPT_FP64) ? e0 : e0 - de;
+        gs[a * kGridStride + i] = g;
+    }
+}
+
+template <int N, int PREC>
+__device__ __forceinline__ void run_chunk(ChunkSmem& S, const WorkItem& W, uint32_t chunk_local, double& sw,
+                                          double& sw2) {
+    const DiagRec& R = S.rec;
+    const uint32_t cs = blockDim.x * (uint32_t)W.spt;
+    const uint64_t first = (uint64_t)chunk_local * cs;
+    const uint32_t t = S.iter;
+    const uint32_t k0 = (uint32_t)W.seed, k1 = (uint32_t)(W.seed >> 32);
+    float* hist = S.hist[threadIdx.x >> 5];
+    const int nb = R.nb;
+    constexpr int D = 3 * (N + 1);
+    for (int j = 0; j < W.spt; ++j) {
+        const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
+        if (s < W.samples) {
+            const SampleOut o = eval_sample<N, PREC>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1, nullptr);
+            sw += o.w;
+            sw2 = fma(o.w, o.w, sw2);
+            if (o.w != 0.0) {
+                const float wf = (float)o.w;
+                float w2 = wf * wf;
+                if (!(w2 <= 3.0e38f)) w2 = 3.0e38f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const uint32_t i = (o.binpack[a >> 2] >> (8 * (a & 3))) & 0xffu;
+                    atomicAdd(&hist[a * nb + i], w2);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Persistent kernel: blocks take chunks (a fixed range of one integral's samples) from a global
+// counter; each chunk's sum w, sum w^2 and histogram go to the chunk's own slot, so the result of a
+// chunk does not depend on which block ran it or what else is in the batch.
+__global__ void __launch_bounds__(kThreads) k_iterate(WorkHeader* hdr, const WorkItem* __restrict__ items,
+                                                     double* __restrict__ csum, float* __restrict__ chist) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ChunkSmem& S = *reinterpret_cast<ChunkSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t n_items = hdr->n_items, total = hdr->total_chunks;
+    for (;;) {
+        if (tid == 0) {
+            const uint32_t c = atomicAdd(&hdr->chunk_counter, 1u);
+            uint32_t it = 0;
+            if (c < total) {
+                uint32_t lo = 0, hi = n_items;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (items[mid].chunk_begin <= c) lo = mid;
+                    else hi = mid;
+                }
+                it = lo;
+                if (c - items[it].chunk_begin >= items[it].n_chunks) atomicOr(&hdr->error, 1u);
+            }
+            S.chunk = c;
+            S.item = it;
+            S.skip = (c < total) ? (uint32_t)items[it].state->converged : 1u;
+            S.iter = (c < total) ? (uint32_t)items[it].state->iter : 0u;
+        }
+        __syncthreads();
+        const uint32_t chunk = S.chunk;
+        if (chunk >= total) break;
+        if (S.skip) {
+            __syncthreads();
+            continue;
+        }
+        const WorkItem& W = items[S.item];
+        load_record(&S.rec, W.rec);
+        __syncthreads();
+        const int d = S.rec.d, nb = S.rec.nb, prec = S.rec.precision, order = S.rec.order;
+        load_grid(S.grid, W.grid, d, nb, prec);
+        for (int i = tid; i < kWarps * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
+        __syncthreads();
+        double sw = 0.0, sw2 = 0.0;
+        const uint32_t cl = chunk - W.chunk_begin;
+        switch (order * 2 + prec) {
+            case 2 * 2 + MBPT_FP64: run_chunk<2, MBPT_FP64>(S, W, cl, sw, sw2); break;
+            case 2 * 2 + MBPT_MIXED: run_chunk<2, MBPT_MIXED>(S, W, cl, sw, sw2); break;
+            case 3 * 2 + MBPT_FP64: run_chunk<3, MBPT_FP64>(S, W, cl, sw, sw2); break;
+            case 3 * 2 + MBPT_MIXED: run_chunk<3, MBPT_MIXED>(S, W, cl, sw, sw2); break;
+            case 4 * 2 + MBPT_FP64: run_chunk<4, MBPT_FP64>(S, W, cl, sw, sw2); break;
+            case 4 * 2 + MBPT_MIXED: run_chunk<4, MBPT_MIXED>(S, W, cl, sw, sw2); break;
+            case 5 * 2 + MBPT_FP64: run_chunk<5, MBPT_FP64>(S, W, cl, sw, sw2); break;
+            case 5 * 2 + MBPT_MIXED: run_chunk<5, MBPT_MIXED>(S, W, cl, sw, sw2); break;
+            default:
+                if (tid == 0) atomicOr(&hdr->error, 2u);
+        }
+        sw = warp_sum(sw);
+        sw2 = warp_sum(sw2);
+        if (lane == 0) {
+            S.red[0][warp] = sw;
+            S.red[1][warp] = sw2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < kWarps; ++w) {
+                a += S.red[0][w];
+                b += S.red[1][w];
+            }
+            csum[2 * (size_t)chunk] = a;
+            csum[2 * (size_t)chunk + 1] = b;
+        }
+        float* dst = chist + (size_t)chunk * (size_t)W.hist_stride;
+        for (int i = tid; i < d * nb; i += blockDim.x) {
+            float v = 0.0f;
+            for (int w = 0; w < kWarps; ++w) v += S.hist[w][i];
+            dst[i] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Grid refinement of one axis (Lepage 1978 with (7,1)/8 and (1,6,1)/8 smoothing):
+// dbar -> r = dbar/sum -> m = ((r-1)/ln r)^alpha -> new edges at equal shares of the
+// piecewise-linear cumulative of m.
+__device__ void refine_axis(double* grid, const double* old, const double* h, double* m, int nb, double alpha) {
+    m[0] = (7.0 * h[0] + h[1]) / 8.0;
+    for (int i = 1; i < nb - 1; ++i) m[i] = (h[i - 1] + 6.0 * h[i] + h[i + 1]) / 8.0;
+    m[nb - 1] = (h[nb - 2] + 7.0 * h[nb - 1]) / 8.0;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += m[i];
+    if (!(tot > 0.0)) return;
+    double msum = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        const double r = m[i] / tot;
+        double v;
+        if (r <= 0.0) v = 0.0;
+        else if (r >= 1.0) v = 1.0;
+        else v = pow((r - 1.0) / log(r), alpha);
+        m[i] = v;
+        msum += v;
+    }
+    const double share = msum / nb;
+    int j = 0;
+    double cum = 0.0;
+    for (int k = 1; k < nb; ++k) {
+        const double target = k * share;
+        while (j < nb - 1 && cum + m[j] < target) {
+            cum += m[j];
+            ++j;
+        }
+        double frac = m[j] > 0.0 ? (target - cum) / m[j] : 0.0;
+        if (frac > 1.0) frac = 1.0;
+        if (frac < 0.0) frac = 0.0;
+        grid[k] = old[j] + frac * (old[j + 1] - old[j]);
+    }
+    grid[0] = old[0];
+    grid[nb] = old[nb];
+}
+
+// Per integral: fixed-order reduction of the chunk slots, combination of the iteration into the
+// running estimate, convergence test and grid refinement.
+__global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkItem* __restrict__ items,
+                                                 const double* __restrict__ csum, const float* __restrict__ chist,
+                                                 double* const* __restrict__ last_hist) {
+    __shared__ double hsum[kMaxD * MBPT_MAX_BINS];
+    __shared__ double tmp[kMaxD * MBPT_MAX_BINS];
+    __shared__ double old[kMaxD * (MBPT_MAX_BINS + 1)];
+    __shared__ double red[2][8];
+    __shared__ int s_skip, s_refine;
+    const int tid = threadIdx.x;
+    for (uint32_t ii = blockIdx.x; ii < hdr->n_items; ii += gridDim.x) {
+        const WorkItem& W = items[ii];
+        DiagState* st = W.state;
+        if (tid == 0) s_skip = st->converged;
+        __syncthreads();
+        if (s_skip) {
+            __syncthreads();
+            continue;
+        }
+        double a = 0.0, b = 0.0;
+        for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x) {
+            a += csum[2 * (size_t)(W.chunk_begin + c)];
+            b += csum[2 * (size_t)(W.chunk_begin + c) + 1];
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = a;
+            red[1][tid >> 5] = b;
+        }
+        const int d = W.rec->d, nb = W.rec->nb;
+        for (int i = tid; i < d * nb; i += blockDim.x) {
+            double acc = 0.0;
+            for (uint32_t c = 0; c < W.n_chunks; ++c)
+                acc += (double)chist[(size_t)(W.chunk_begin + c) * (size_t)W.hist_stride + i];
+            hsum[i] = acc;
+            last_hist[ii][i] = acc;
+        }
+        for (int i = tid; i < d * (nb + 1); i += blockDim.x) old[i] = W.grid[i];
+        __syncthreads();
+        if (tid == 0) {
+            double A = 0.0, B = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                A += red[0][w];
+                B += red[1][w];
+            }
+            const double M = (double)W.samples;
+            const double I = A / M;
+            const double var = (B / M - I * I) / (M - 1.0);
+            const int t = st->iter;
+            if (t < kMaxIters) {
+                st->hist_mean[t] = I;
+                st->hist_var[t] = var;
+            }
+            st->last_mean = I;
+            st->last_var = var;
+            if (!isfinite(I) || !isfinite(var)) st->status = MBPT_ENUMERIC;
+            if (var > 0.0) {
+                st->sum_inv_var += 1.0 / var;
+                st->sum_mean_w += I / var;
+                st->n_used += 1;
+            }
+            double mean, sigma, chi2 = 0.0;
+            if (st->sum_inv_var > 0.0) {
+                mean = st->sum_mean_w / st->sum_inv_var;
+                sigma = sqrt(1.0 / st->sum_inv_var);
+                const int T = t + 1 < kMaxIters ? t + 1 : kMaxIters;
+                if (st->n_used > 1) {
+                    double c2 = 0.0;
+                    for (int k = 0; k < T; ++k)
+                        if (st->hist_var[k] > 0.0) {
+                            const double dd = st->hist_mean[k] - mean;
+                            c2 += dd * dd / st->hist_var[k];
+                        }
+                    chi2 = c2 / (st->n_used - 1);
+                }
+            } else {
+                mean = I;
+                sigma = 0.0;
+            }
+            st->mean = mean;
+            st->sigma = sigma;
+            st->chi2 = chi2;
+            st->n_evals += (int64_t)W.samples;
+            st->iter = t + 1;
+            const bool has_target = (W.target_rel > 0.0) || (W.target_abs > 0.0);
+            const double goal = fmax(W.target_rel * fabs(mean), W.target_abs);
+            if (has_target && st->iter >= 2 && sigma <= goal) st->converged = 1;
+            s_refine = (W.freeze_after == 0u) || ((uint32_t)st->iter < W.freeze_after);
+        }
+        __syncthreads();
+        if (s_refine && tid < d) refine_axis(W.grid + tid * (nb + 1), old + tid * (nb + 1), hsum + tid * nb,
+                                             tmp + tid * MBPT_MAX_BINS, nb, W.alpha);
+        __syncthreads();
+    }
+}
+
+// Test hook kernel: samples [first, first+count) of iteration `iter`, mapped point and weight.
+template <int N, int PREC>
+__device__ void dump_one(const DiagRec& R, const Grid2* gs, uint32_t s, uint32_t t, uint32_t sid, uint32_t k0,
+                         uint32_t k1, double* x, double* w) {
+    const SampleOut o = eval_sample<N, PREC>(R, gs, s, t, sid, k0, k1, x);
+    *w = o.w;
+}
+
+__global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, const double* grid, uint64_t seed, uint32_t sid,
+                                             uint32_t iter, uint64_t first, uint64_t count, double* xo,
+                                             double* wo) {
+    __shared__ DiagRec R;
+    __shared__ Grid2 gs[kMaxD * kGridStride];
+    load_record(&R, rec);
+    __syncthreads();
+    load_grid(gs, grid, R.d, R.nb, R.precision);
+    __syncthreads();
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint32_t s = (uint32_t)(first + i);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    double* x = xo + i * R.d;
+    double* w = wo + i;
+    switch (R.order * 2 + R.precision) {
+        case 2 * 2 + MBPT_FP64: dump_one<2, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 2 * 2 + MBPT_MIXED: dump_one<2, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 3 * 2 + MBPT_FP64: dump_one<3, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 3 * 2 + MBPT_MIXED: dump_one<3, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 4 * 2 + MBPT_FP64: dump_one<4, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 4 * 2 + MBPT_MIXED: dump_one<4, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 5 * 2 + MBPT_FP64: dump_one<5, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 5 * 2 + MBPT_MIXED: dump_one<5, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        default: *w = 0.0;
+    }
+}
+
+__global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                         uint64_t count, uint32_t* out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    uint32_t o[4];
+    philox4x32_10(c0 + (uint32_t)i, c1, c2, c3, k0, k1, o);
+    for (int j = 0; j < 4; ++j) out[4 * i + j] = o[j];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context and integral objects
+// ---------------------------------------------------------------------------
+struct mbpt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool own_arena = false;
+    Arena arena;
+    int sms = 0;
+    int iterate_blocks = 0;     // persistent grid of k_iterate
+    int finalize_blocks = 0;
+    size_t iterate_smem = 0;
+    int spt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};
+    // batch buffers (arena)
+    WorkHeader* d_hdr = nullptr;
+    WorkItem* d_items = nullptr;
+    double** d_last_hist = nullptr;
+    double* d_csum = nullptr;
+    float* d_chist = nullptr;
+    size_t items_cap = 0, chunks_cap = 0, hist_cap = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // around k_iterate and k_finalize (graph nodes)
+    std::set<mbpt_diag*> diags;
+    std::vector<WorkItem> h_items;
+    std::vector<double*> h_last_hist;
+};
+
+struct mbpt_diag {
+    mbpt_ctx* ctx = nullptr;
+    mbpt_diagram_desc desc;
+    mbpt_physics phys;
+    mbpt_vegas_cfg cfg;
+    DiagRec* d_rec = nullptr;
+    DiagState* d_state = nullptr;
+    double* d_grid = nullptr;
+    double* d_last_hist = nullptr;
+    int d = 0, nb = 0;
+};
+
+namespace {
+
+size_t state_block_bytes(int d, int nb) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return up(sizeof(DiagRec)) + up(sizeof(DiagState)) + up(sizeof(double) * d * (nb + 1)) +
+           up(sizeof(double) * d * nb);
+}
+
+void invalidate_graph(mbpt_ctx* c) {
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+}
+
+int ensure_batch_buffers(mbpt_ctx* c, size_t n_items, size_t n_chunks, size_t hist_floats) {
+    bool changed = false;
+    if (!c->d_hdr) {
+        c->d_hdr = (WorkHeader*)c->arena.alloc(sizeof(WorkHeader));
+        if (!c->d_hdr) return fail(MBPT_ENOMEM, "arena exhausted (work header)");
+        changed = true;
+    }
+    if (n_items > c->items_cap) {
+        size_t cap = std::max(n_items, c->items_cap * 2);
+        c->arena.release(c->d_items);
+        c->arena.release(c->d_last_hist);
+        c->d_items = (WorkItem*)c->arena.alloc(sizeof(WorkItem) * cap);
+        c->d_last_hist = (double**)c->arena.alloc(sizeof(double*) * cap);
+        if (!c->d_items || !c->d_last_hist) {
+            c->items_cap = 0;
+            return fail(MBPT_ENOMEM, "arena exhausted (work table)");
+        }
+        c->items_cap = cap;
+        changed = true;
+    }
+    if (n_chunks > c->chunks_cap) {
+        size_t cap = std::max(n_chunks, c->chunks_cap + c->chunks_cap / 2);
+        c->arena.release(c->d_csum);
+        c->d_csum = (double*)c->arena.alloc(sizeof(double) * 2 * cap);
+        if (!c->d_csum) {
+            cap = n_chunks;
+            c->d_csum = (double*)c->arena.alloc(sizeof(double) * 2 * cap);
+        }
+        if (!c->d_csum) {
+            c->chunks_cap = 0;
+            return fail(MBPT_ENOMEM, "arena exhausted (chunk sums)");
+        }
+        c->chunks_cap = cap;
+        changed = true;
+    }
+    if (hist_floats > c->hist_cap) {
+        size_t cap = std::max(hist_floats, c->hist_cap + c->hist_cap / 2);
+        c->arena.release(c->d_chist);
+        c->d_chist = (float*)c->arena.alloc(sizeof(float) * cap);
+        if (!c->d_chist) {
+            cap = hist_floats;
+            c->d_chist = (float*)c->arena.alloc(sizeof(float) * cap);
+        }
+        if (!c->d_chist) {
+            c->hist_cap = 0;
+            return fail(MBPT_ENOMEM, "arena exhausted (chunk histograms)");
+        }
+        c->hist_cap = cap;
+        changed = true;
+    }
+    if (changed) invalidate_graph(c);
+    return MBPT_OK;
+}
+
+int capture_graph(mbpt_ctx* c) {
+    if (c->graph) return MBPT_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(&c->d_hdr->chunk_counter, 0, sizeof(uint32_t), c->stream);
+    cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal);
+    k_iterate<<<c->iterate_blocks, kThreads, c->iterate_smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
+                                                                           c->d_chist);
+    cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal);
+    k_finalize<<<c->finalize_blocks, 256, 0, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist,
+                                                         c->d_last_hist);
+    cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(MBPT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return fail(MBPT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return MBPT_OK;
+}
+
+int check_device_error(mbpt_ctx* c) {
+    if (!c->d_hdr) return MBPT_OK;
+    uint32_t err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, &c->d_hdr->error, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (err) return fail(MBPT_EDEVICE, "a kernel reported an out-of-range index (error word " + std::to_string(err) + ")");
+    return MBPT_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* mbpt_last_error(void) { return g_err.c_str(); }
+
+int mbpt_ctx_create(mbpt_ctx** out, int device, void* arena, size_t arena_bytes, void* cuda_stream) {
+    if (!out || arena_bytes < (1u << 20)) return fail(MBPT_EINVAL, "ctx_create: out is NULL or arena < 1 MiB");
+    if (arena && ((uintptr_t)arena & 255)) return fail(MBPT_EINVAL, "ctx_create: arena must be 256-byte aligned");
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(MBPT_EINVAL, "ctx_create: no such device");
+    DeviceGuard dg(device);
+    mbpt_ctx* c = new (std::nothrow) mbpt_ctx();
+    if (!c) return fail(MBPT_ENOMEM, "ctx_create: host allocation");
+    c->device = device;
+    cudaDeviceProp p;
+    cudaError_t e = cudaGetDeviceProperties(&p, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(MBPT_ECUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
+    }
+    c->sms = p.multiProcessorCount;
+    char* base = (char*)arena;
+    if (!base) {
+        e = cudaMalloc((void**)&base, arena_bytes);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(MBPT_ENOMEM, std::string("cudaMalloc arena: ") + cudaGetErrorString(e));
+        }
+        c->own_arena = true;
+    }
+    c->arena.init(base, arena_bytes);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            if (c->own_arena) cudaFree(base);
+            delete c;
+            return fail(MBPT_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    c->iterate_smem = sizeof(ChunkSmem);
+    e = cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->iterate_smem);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate, kThreads, c->iterate_smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        if (c->own_arena) cudaFree(base);
+        delete c;
+        return fail(MBPT_ECUDA, std::string("k_iterate occupancy: ") + cudaGetErrorString(e));
+    }
+    c->iterate_blocks = per_sm * c->sms;
+    c->finalize_blocks = 2 * c->sms;
+    for (int i = 0; i < 3; ++i) {
+        e = cudaEventCreate(&c->ev[i]);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(c->ev[j]);
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            if (c->own_arena) cudaFree(base);
+            delete c;
+            return fail(MBPT_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = c;
+    return MBPT_OK;
+}
+
+int mbpt_ctx_destroy(mbpt_ctx* c) {
+    if (!c) return fail(MBPT_EINVAL, "ctx_destroy: NULL");
+    DeviceGuard dg(c->device);
+    cudaStreamSynchronize(c->stream);
+    invalidate_graph(c);
+    for (mbpt_diag* d : c->diags) delete d;
+    c->diags.clear();
+    if (c->own_arena) cudaFree(c->arena.base);
+    for (int i = 0; i < 3; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return MBPT_OK;
+}
+
+int mbpt_ctx_last_timing(mbpt_ctx* c, double* iterate_ms, double* finalize_ms) {
+    if (!c || !iterate_ms || !finalize_ms) return fail(MBPT_EINVAL, "last_timing: NULL argument");
+    if (!c->graph) return fail(MBPT_EINVAL, "last_timing: no iteration has run");
+    DeviceGuard dg(c->device);
+    CUDA_TRY(cudaEventSynchronize(c->ev[2]));
+    float a = 0.0f, b = 0.0f;
+    CUDA_TRY(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
+    *iterate_ms = a;
+    *finalize_ms = b;
+    return MBPT_OK;
+}
+
+int mbpt_ctx_stream(const mbpt_ctx* c, void** stream) {
+    if (!c || !stream) return fail(MBPT_EINVAL, "ctx_stream: NULL argument");
+    *stream = (void*)c->stream;
+    return MBPT_OK;
+}
+
+int mbpt_ctx_mem(const mbpt_ctx* c, size_t* used, size_t* largest_free) {
+    if (!c || !used || !largest_free) return fail(MBPT_EINVAL, "ctx_mem: NULL argument");
+    *used = c->arena.in_use();
+    *largest_free = c->arena.largest_free();
+    return MBPT_OK;
+}
+
+int mbpt_diag_bytes(const mbpt_diagram_desc* desc, const mbpt_vegas_cfg* cfg, size_t* bytes) {
+    if (!desc || !cfg || !bytes) return fail(MBPT_EINVAL, "diag_bytes: NULL argument");
+    if (desc->n_chords < 1 || desc->n_chords > MBPT_MAX_CHORDS || cfg->n_bins < 2 || cfg->n_bins > MBPT_MAX_BINS)
+        return fail(MBPT_EINVAL, "diag_bytes: invalid sizes");
+    *bytes = state_block_bytes(3 * desc->n_chords, cfg->n_bins);
+    return MBPT_OK;
+}
+
+int mbpt_ctx_set_launch(mbpt_ctx* c, int order, int tpb, int spt) {
+    if (!c || order < 2 || order > MBPT_MAX_DEVICE_ORDER) return fail(MBPT_EINVAL, "set_launch: bad order");
+    if (tpb != kThreads) return fail(MBPT_EINVAL, "set_launch: threads_per_block must be 256");
+    if (spt < 1 || spt > 256) return fail(MBPT_EINVAL, "set_launch: samples_per_thread must be 1..256");
+    c->spt[order] = spt;
+    return MBPT_OK;
+}
+
+int mbpt_ctx_get_launch(const mbpt_ctx* c, int order, int* tpb, int* spt) {
+    if (!c || !tpb || !spt || order < 2 || order > MBPT_MAX_DEVICE_ORDER) return fail(MBPT_EINVAL, "get_launch: bad argument");
+    *tpb = kThreads;
+    *spt = c->spt[order];
+    return MBPT_OK;
+}
+
+int mbpt_create_diagram(mbpt_ctx* c, const mbpt_diagram_desc* desc, const mbpt_physics* ph,
+                        const mbpt_vegas_cfg* cfg, mbpt_diag** out) {
+    if (!c || !desc || !ph || !cfg || !out) return fail(MBPT_EINVAL, "create_diagram: NULL argument");
+    DiagRec rec;
+    char err[256] = {0};
+    int st = compile_record(*desc, *ph, *cfg, &rec, err, sizeof(err));
+    if (st) return fail(st, std::string("create_diagram: ") + err);
+    DeviceGuard dg(c->device);
+    const int d = rec.d, nb = rec.nb;
+    char* blk = (char*)c->arena.alloc(state_block_bytes(d, nb));
+    if (!blk) return fail(MBPT_ENOMEM, "create_diagram: arena exhausted");
+    mbpt_diag* g = new (std::nothrow) mbpt_diag();
+    if (!g) {
+        c->arena.release(blk);
+        return fail(MBPT_ENOMEM, "create_diagram: host allocation");
+    }
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    g->ctx = c;
+    g->desc = *desc;
+    g->phys = *ph;
+    g->cfg = *cfg;
+    g->d = d;
+    g->nb = nb;
+    g->d_rec = (DiagRec*)blk;
+    g->d_state = (DiagState*)(blk + up(sizeof(DiagRec)));
+    g->d_grid = (double*)(blk + up(sizeof(DiagRec)) + up(sizeof(DiagState)));
+    g->d_last_hist = (double*)((char*)g->d_grid + up(sizeof(double) * d * (nb + 1)));
+    std::vector<double> grid((size_t)d * (nb + 1));
+    for (int a = 0; a < d; ++a)
+        for (int i = 0; i <= nb; ++i) grid[(size_t)a * (nb + 1) + i] = (double)i / nb;
+    DiagState s0;
+    memset(&s0, 0, sizeof(s0));
+    cudaError_t e = cudaMemcpyAsync(g->d_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->d_grid, grid.data(), sizeof(double) * grid.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_last_hist, 0, sizeof(double) * d * nb, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->arena.release(blk);
+        delete g;
+        return fail(MBPT_ECUDA, std::string("create_diagram upload: ") + cudaGetErrorString(e));
+    }
+    c->diags.insert(g);
+    *out = g;
+    return MBPT_OK;
+}
+
+int mbpt_destroy_diagram(mbpt_diag* g) {
+    if (!g || !g->ctx) return fail(MBPT_EINVAL, "destroy_diagram: NULL");
+    mbpt_ctx* c = g->ctx;
+    if (!c->diags.count(g)) return fail(MBPT_EINVAL, "destroy_diagram: unknown integral");
+    DeviceGuard dg(c->device);
+    cudaStreamSynchronize(c->stream);   // no queued work may still reference it
+    c->arena.release(g->d_rec);
+    c->diags.erase(g);
+    delete g;
+    return MBPT_OK;
+}
+
+int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters) {
+    if (!c || k < 0 || n_iters < 0 || (k > 0 && !diags)) return fail(MBPT_EINVAL, "vegas_iterate: bad argument");
+    if (k == 0 || n_iters == 0) return MBPT_OK;
+    DeviceGuard dg(c->device);
+    c->h_items.clear();
+    c->h_last_hist.clear();
+    uint64_t chunk = 0;
+    int stride = 0;
+    std::set<mbpt_diag*> seen;
+    for (int i = 0; i < k; ++i) {
+        mbpt_diag* g = diags[i];
+        if (!g || !c->diags.count(g)) return fail(MBPT_EINVAL, "vegas_iterate: integral not owned by this context");
+        if (!seen.insert(g).second) return fail(MBPT_EINVAL, "vegas_iterate: integral listed twice");
+        stride = std::max(stride, g->d * g->nb);
+    }
+    for (int i = 0; i < k; ++i) {
+        mbpt_diag* g = diags[i];
+        WorkItem w;
+        memset(&w, 0, sizeof(w));
+        w.rec = g->d_rec;
+        w.state = g->d_state;
+        w.grid = g->d_grid;
+        w.samples = g->cfg.samples_per_iter;
+        w.seed = g->cfg.seed;
+        w.stream_id = g->cfg.stream_id;
+        w.spt = c->spt[g->desc.order];
+        const uint64_t cs = (uint64_t)kThreads * (uint64_t)w.spt;
+        w.n_chunks = (uint32_t)((w.samples + cs - 1) / cs);
+        w.chunk_begin = (uint32_t)chunk;
+        w.freeze_after = g->cfg.freeze_after;
+        w.alpha = g->cfg.alpha;
+        w.target_rel = g->cfg.target_rel;
+        w.target_abs = g->cfg.target_abs;
+        w.hist_stride = stride;
+        chunk += w.n_chunks;
+        if (chunk >= (1ull << 31)) return fail(MBPT_EINVAL, "vegas_iterate: batch too large");
+        c->h_items.push_back(w);
+        c->h_last_hist.push_back(g->d_last_hist);
+    }
+    int st = ensure_batch_buffers(c, (size_t)k, (size_t)chunk, (size_t)chunk * (size_t)stride);
+    if (st) return st;
+    WorkHeader h;
+    memset(&h, 0, sizeof(h));
+    h.n_items = (uint32_t)k;
+    h.total_chunks = (uint32_t)chunk;
+    h.hist_floats = (uint64_t)chunk * (uint64_t)stride;
+    CUDA_TRY(cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(WorkItem) * k, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_last_hist, c->h_last_hist.data(), sizeof(double*) * k, cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    st = capture_graph(c);
+    if (st) return st;
+    for (int it = 0; it < n_iters; ++it) CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+    CUDA_TRY(cudaGetLastError());
+    return MBPT_OK;
+}
+
+int mbpt_estimate(const mbpt_diag* g, mbpt_result* out) {
+    if (!g || !out || !g->ctx) return fail(MBPT_EINVAL, "estimate: NULL argument");
+    mbpt_ctx* c = g->ctx;
+    DeviceGuard dg(c->device);
+    int st = check_device_error(c);
+    if (st) return st;
+    DiagState s;
+    CUDA_TRY(cudaMemcpyAsync(&s, g->d_state, offsetof(DiagState, hist_mean), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    out->mean = s.mean;
+    out->sigma = s.sigma;
+    out->chi2_dof = s.chi2;
+    out->last_mean = s.last_mean;
+    out->last_sigma = s.last_var > 0.0 ? sqrt(s.last_var) : 0.0;
+    out->n_iter = s.iter;
+    out->n_evals = s.n_evals;
+    out->converged = s.converged;
+    out->status = s.status;
+    return MBPT_OK;
+}
+
+// checkpoint image: header, DiagState, grid, last histogram
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t d, nb, order;
+    int32_t pad;
+};
+static const uint32_t kMagic = 0x4D425054u;   // "MBPT"
+
+int mbpt_get_state(const mbpt_diag* g, void* buf, size_t cap, size_t* need) {
+    if (!g || !need) return fail(MBPT_EINVAL, "get_state: NULL argument");
+    const size_t n_grid = (size_t)g->d * (g->nb + 1), n_hist = (size_t)g->d * g->nb;
+    const size_t bytes = sizeof(StateHeader) + sizeof(DiagState) + sizeof(double) * (n_grid + n_hist);
+    *need = bytes;
+    if (!buf) return MBPT_OK;
+    if (cap < bytes) return fail(MBPT_ENOMEM, "get_state: buffer too small");
+    mbpt_ctx* c = g->ctx;
+    DeviceGuard dg(c->device);
+    char* p = (char*)buf;
+    StateHeader h = {kMagic, 1u, g->d, g->nb, g->desc.order, 0};
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    CUDA_TRY(cudaMemcpyAsync(p, g->d_state, sizeof(DiagState), cudaMemcpyDeviceToHost, c->stream));
+    p += sizeof(DiagState);
+    CUDA_TRY(cudaMemcpyAsync(p, g->d_grid, sizeof(double) * n_grid, cudaMemcpyDeviceToHost, c->stream));
+    p += sizeof(double) * n_grid;
+    CUDA_TRY(cudaMemcpyAsync(p, g->d_last_hist, sizeof(double) * n_hist, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return MBPT_OK;
+}
+
+int mbpt_set_state(mbpt_diag* g, const void* buf, size_t len) {
+    if (!g || !buf) return fail(MBPT_EINVAL, "set_state: NULL argument");
+    const size_t n_grid = (size_t)g->d * (g->nb + 1), n_hist = (size_t)g->d * g->nb;
+    const size_t bytes = sizeof(StateHeader) + sizeof(DiagState) + sizeof(double) * (n_grid + n_hist);
+    if (len != bytes) return fail(MBPT_EINVAL, "set_state: wrong image size");
+    StateHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (h.magic != kMagic || h.version != 1u || h.d != g->d || h.nb != g->nb || h.order != g->desc.order)
+        return fail(MBPT_EINVAL, "set_state: image does not match this integral");
+    const char* p = (const char*)buf + sizeof(h);
+    DiagState s;
+    memcpy(&s, p, sizeof(s));
+    // validate the grid: monotone from 0 to 1
+    const double* grid = (const double*)(p + sizeof(DiagState));
+    for (int a = 0; a < g->d; ++a) {
+        const double* e = grid + (size_t)a * (g->nb + 1);
+        if (e[0] != 0.0 || e[g->nb] != 1.0) return fail(MBPT_EINVAL, "set_state: grid must span [0, 1]");
+        for (int i = 0; i < g->nb; ++i)
+            if (!(e[i + 1] >= e[i])) return fail(MBPT_EINVAL, "set_state: grid must be non-decreasing");
+    }
+    mbpt_ctx* c = g->ctx;
+    DeviceGuard dg(c->device);
+    CUDA_TRY(cudaMemcpyAsync(g->d_state, p, sizeof(DiagState), cudaMemcpyHostToDevice, c->stream));
+    p += sizeof(DiagState);
+    CUDA_TRY(cudaMemcpyAsync(g->d_grid, p, sizeof(double) * n_grid, cudaMemcpyHostToDevice, c->stream));
+    p += sizeof(double) * n_grid;
+    CUDA_TRY(cudaMemcpyAsync(g->d_last_hist, p, sizeof(double) * n_hist, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return MBPT_OK;
+}
+
+int mbpt_dump_samples(mbpt_diag* g, int64_t iter, int64_t first, int64_t count, double* x, double* w) {
+    if (!g || !w || iter < 0 || iter >= (1ll << 32) || first < 0 || count < 0 || first + count > (1ll << 32))
+        return fail(MBPT_EINVAL, "dump_samples: bad argument");
+    if (count == 0) return MBPT_OK;
+    mbpt_ctx* c = g->ctx;
+    DeviceGuard dg(c->device);
+    double* dx = (double*)c->arena.alloc(sizeof(double) * (size_t)count * g->d);
+    double* dw = (double*)c->arena.alloc(sizeof(double) * (size_t)count);
+    if (!dx || !dw) {
+        c->arena.release(dx);
+        c->arena.release(dw);
+        return fail(MBPT_ENOMEM, "dump_samples: arena exhausted");
+    }
+    const int blocks = (int)((count + 255) / 256);
+    k_dump<<<blocks, 256, 0, c->stream>>>(g->d_rec, g->d_grid, g->cfg.seed, g->cfg.stream_id, (uint32_t)iter,
+                                          (uint64_t)first, (uint64_t)count, dx, dw);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && x)
+        e = cudaMemcpyAsync(x, dx, sizeof(double) * (size_t)count * g->d, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, dw, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->arena.release(dx);
+    c->arena.release(dw);
+    if (e != cudaSuccess) return fail(MBPT_ECUDA, std::string("dump_samples: ") + cudaGetErrorString(e));
+    return MBPT_OK;
+}
+
+int mbpt_philox_device(mbpt_ctx* c, const uint32_t ctr[4], const uint32_t key[2], int64_t count, uint32_t* out) {
+    if (!c || !ctr || !key || !out || count < 0 || count > (1ll << 26)) return fail(MBPT_EINVAL, "philox_device: bad argument");
+    if (count == 0) return MBPT_OK;
+    DeviceGuard dg(c->device);
+    uint32_t* d = (uint32_t*)c->arena.alloc(sizeof(uint32_t) * 4 * (size_t)count);
+    if (!d) return fail(MBPT_ENOMEM, "philox_device: arena exhausted");
+    k_philox<<<(unsigned)((count + 255) / 256), 256, 0, c->stream>>>(ctr[0], ctr[1], ctr[2], ctr[3], key[0], key[1],
+                                                                   (uint64_t)count, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, d, sizeof(uint32_t) * 4 * (size_t)count, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->arena.release(d);
+    if (e != cudaSuccess) return fail(MBPT_ECUDA, std::string("philox_device: ") + cudaGetErrorString(e));
+    return MBPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Per-sample parity hands the same VEGAS grid to both sides;
+FP64 mode must match to 1e-12 relative (widened only by the conditioning of the
+energy denominators), mixed mode is reported against FP64 with a 1e-4 bound."""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import EPS, fp64_tol, make_desc, matter_pair, near_surface, oracle_dump, random_grid
+from paper_2603_24532_b300 import mbpt as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = M.mbpt_ctx_create(0, 2 << 30)
+    yield c
+    M.mbpt_ctx_destroy(c)
+
+
+def _pick(n, k, rng):
+    Ds = O.enumerate_diagrams(n)
+    if len(Ds) <= k:
+        return Ds
+    idx = sorted(rng.choice(len(Ds), size=k, replace=False))
+    return [Ds[i] for i in idx]
+
+
+def test_philox_device_matches_oracle(ctx):
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        ctr = [int(v) for v in rng.integers(0, 2 ** 32, size=4)]
+        key = [int(v) for v in rng.integers(0, 2 ** 32, size=2)]
+        got = M.mbpt_philox_device(ctx, ctr, key, 300)
+        for i in (0, 1, 77, 299):
+            want = O.philox4x32_10([(ctr[0] + i) & 0xFFFFFFFF, ctr[1], ctr[2], ctr[3]], key)
+            assert list(got[i]) == want
+
+
+CASES = [(2, "pnm", 1), (2, "snm", 1), (3, "pnm", 3), (3, "snm", 3), (3, "asym", 3), (4, "pnm", 8), (4, "snm", 5),
+         (4, "asym", 5), (5, "pnm", 8), (5, "asym", 3)]
+
+
+@pytest.mark.parametrize("n,matter,k", CASES)
+def test_per_sample_parity_fp64(ctx, n, matter, k):
+    rng = np.random.default_rng(1000 * n + len(matter))
+    po, pm = matter_pair(matter)
+    count = 1536 if n >= 5 else 3072
+    for D in _pick(n, k, rng):
+        cfg = M.vegas_cfg(samples=1 << 16, seed=12345, stream_id=D.diagram_id + 7, precision=M.MBPT_FP64)
+        g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
+        try:
+            grid = random_grid(D.d, 50, rng)
+            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+            t, first = 3, 1021          # ragged offset, non-zero iteration counter
+            xg, wg = M.mbpt_dump_samples(g, t, first, count, D.d)
+            xo, wo = oracle_dump(D, po, grid, 12345, D.diagram_id + 7, t, first, count)
+            assert np.max(np.abs(xg - xo)) <= 4 * EPS
+            ns = near_surface(D, po, xo)
+            assert ns.sum() <= 2, "too many samples on a Fermi surface"
+            ok = ~ns
+            # exact zeros agree
+            assert np.array_equal(wg[ok] == 0.0, wo[ok] == 0.0)
+            tol = fp64_tol(D, po, xo, wo) + 1e-15 * np.mean(np.abs(wo))
+            err = np.abs(wg - wo)
+            bad = ok & (err > tol)
+            assert not bad.any(), (D.diagram_id, np.max(err[ok] / np.maximum(np.abs(wo[ok]), 1e-300)))
+            if O.is_anomalous(D):
+                assert not wg.any()
+            else:
+                assert (wo != 0).sum() > 0
+        finally:
+            M.mbpt_destroy_diagram(g)
+
+
+@pytest.mark.parametrize("n,matter", [(3, "pnm"), (4, "snm"), (5, "pnm"), (4, "asym")])
+def test_mixed_precision_deviation(ctx, n, matter):
+    """Mixed mode (FP32 potentials and spin sum) on identical samples: aggregate
+    deviation from the FP64 oracle below 1e-4 relative."""
+    rng = np.random.default_rng(7 * n)
+    po, pm = matter_pair(matter)
+    for D in _pick(n, 3, rng):
+        if O.is_anomalous(D):
+            continue
+        cfg = M.vegas_cfg(samples=1 << 16, seed=99, stream_id=D.diagram_id, precision=M.MBPT_MIXED)
+        g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
+        try:
+            grid = random_grid(D.d, 50, rng, strength=0.5)
+            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+            xg, wg = M.mbpt_dump_samples(g, 0, 0, 2048, D.d)
+            xo, wo = oracle_dump(D, po, grid, 99, D.diagram_id, 0, 0, 2048)
+            ok = ~near_surface(D, po, xo)
+            l1 = np.sum(np.abs(wg[ok] - wo[ok])) / max(np.sum(np.abs(wo[ok])), 1e-300)
+            assert l1 < 1e-4, l1
+            s_o = np.sum(wo[ok])
+            assert abs(np.sum(wg[ok]) - s_o) <= 1e-4 * np.sum(np.abs(wo[ok]))
+        finally:
+            M.mbpt_destroy_diagram(g)
+
+
+@pytest.mark.parametrize("prec", [M.MBPT_FP64, M.MBPT_MIXED])
+def test_one_iteration_sums_histogram_and_refinement(ctx, prec):
+    """One batched iteration on a ragged sample count: sum w, sum w^2 against the
+    oracle on the same grid; the histogram (FP32 accumulation) to 1e-5; the refined
+    grid against the oracle's refinement of the GPU histogram to 1e-12."""
+    rng = np.random.default_rng(5)
+    po, pm = matter_pair("pnm")
+    D = O.enumerate_diagrams(3)[1]
+    M_s = 40000 + 123
+    cfg = M.vegas_cfg(samples=M_s, seed=3, stream_id=11, precision=prec)
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
+    try:
+        grid = random_grid(D.d, 50, rng, strength=0.5)
+        M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+        M.mbpt_vegas_iterate(ctx, [g], 1)
+        r = M.mbpt_estimate(g)
+        img = M.mbpt_get_state(g)
+        ref = O.vegas_iteration(D, po, grid, 3, 11, 0, M_s)
+        rel = 1e-11 if prec == M.MBPT_FP64 else 1e-4
+        assert r.n_iter == 1 and r.n_evals == M_s
+        assert r.last_mean == pytest.approx(ref.mean, rel=rel)
+        assert r.last_sigma == pytest.approx(np.sqrt(ref.var_of_mean), rel=10 * rel)
+        h = M.state_last_hist(img, D.d, 50)
+        hn, rn = h / h.sum(axis=1, keepdims=True), ref.hist / ref.hist.sum(axis=1, keepdims=True)
+        assert np.max(np.abs(hn - rn)) < (1e-5 if prec == M.MBPT_FP64 else 1e-3)
+        new_grid = M.state_grid(img, D.d, 50)
+        assert np.max(np.abs(new_grid - O.refine(grid, h))) < 1e-12
+    finally:
+        M.mbpt_destroy_diagram(g)
+
+
+def test_second_order_estimate_config1(ctx):
+    """Config 1: one second-order diagram, neutron matter kF = 1, 10 x 2^18 samples,
+    FP64: the GPU estimate agrees with the oracle's own VEGAS run and with the
+    deterministic quadrature of Eq. (2) within 3 combined standard errors."""
+    import quad_pins as Q
+    po, pm = matter_pair("pnm")
+    pm.K_max = 7.0
+    po.K_max = 7.0
+    (D,) = O.enumerate_diagrams(2)
+    cfg = M.vegas_cfg(samples=1 << 18, seed=1, stream_id=0, precision=M.MBPT_FP64)
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
+    try:
+        M.mbpt_vegas_iterate(ctx, [g], 10)
+        r = M.mbpt_estimate(g)
+    finally:
+        M.mbpt_destroy_diagram(g)
+    mo, so, chi, _ = O.vegas(D, po, 10, 1 << 18, seed=1, sid=0)
+    quad = Q.second_order(1.0, 2, 41.47, -50.0, -200.0, 0.7, 2.0, n_rad=10, n_ang=10)
+    assert r.n_iter == 10 and r.n_evals == 10 * (1 << 18)
+    assert abs(r.mean - mo) <= 3 * np.hypot(r.sigma, so)
+    assert abs(r.mean - quad) <= 3 * r.sigma
+    assert r.sigma < 3e-3 * abs(quad)
+
+
+def _run(ctx, specs, iters):
+    gs = [M.mbpt_create_diagram(ctx, d, p, c) for d, p, c in specs]
+    try:
+        M.mbpt_vegas_iterate(ctx, gs, iters)
+        return [M.mbpt_estimate(g).as_dict() for g in gs], [M.mbpt_get_state(g) for g in gs]
+    finally:
+        for g in gs:
+            M.mbpt_destroy_diagram(g)
+
+
+def _specs():
+    po, pm = matter_pair("pnm")
+    ps, pms = matter_pair("snm")
+    out = []
+    for n, k in ((2, 1), (3, 3), (4, 2)):
+        for D in O.enumerate_diagrams(n)[:k]:
+            out.append((make_desc(D), pm, M.vegas_cfg(samples=50000 + 17 * D.diagram_id, seed=5,
+                                                       stream_id=100 * n + D.diagram_id, precision=M.MBPT_MIXED)))
+    D = O.enumerate_diagrams(3)[2]
+    out.append((make_desc(D), pms, M.vegas_cfg(samples=30001, seed=5, stream_id=999, precision=M.MBPT_FP64)))
+    return out
+
+
+def test_deterministic_and_alone_equals_mix(ctx):
+    specs = _specs()
+    a, sa = _run(ctx, specs, 3)
+    b, sb = _run(ctx, specs, 3)
+    assert a == b and sa == sb          # run to run: bit for bit
+    for i in (0, 3, len(specs) - 1):
+        alone, salone = _run(ctx, [specs[i]], 3)
+        assert alone[0] == a[i] and salone[0] == sa[i]
+
+
+def test_checkpoint_restore_continues_bitwise(ctx):
+    d, p, c = _specs()[2]
+    g = M.mbpt_create_diagram(ctx, d, p, c)
+    M.mbpt_vegas_iterate(ctx, [g], 2)
+    ck = M.mbpt_get_state(g)
+    M.mbpt_vegas_iterate(ctx, [g], 2)
+    ra = M.mbpt_estimate(g).as_dict()
+    M.mbpt_destroy_diagram(g)
+    h = M.mbpt_create_diagram(ctx, d, p, c)
+    M.mbpt_set_state(h, ck)
+    M.mbpt_vegas_iterate(ctx, [h], 2)
+    rb = M.mbpt_estimate(h).as_dict()
+    M.mbpt_destroy_diagram(h)
+    assert ra == rb and ra["n_iter"] == 4
+
+
+def test_anomalous_integral_is_exactly_zero(ctx):
+    po, pm = matter_pair("pnm")
+    D = next(D for D in O.enumerate_diagrams(4) if O.is_anomalous(D))
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=20000, target_rel=1e-3))
+    try:
+        M.mbpt_vegas_iterate(ctx, [g], 5)
+        r = M.mbpt_estimate(g)
+        # every sample is exactly zero; with a target the integral converges after two iterations
+        assert r.mean == 0.0 and r.sigma == 0.0 and r.n_iter == 2 and r.converged == 1
+    finally:
+        M.mbpt_destroy_diagram(g)
+
+
+def test_targets_stop_iterating(ctx):
+    po, pm = matter_pair("pnm")
+    (D,) = O.enumerate_diagrams(2)
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=1 << 16, target_rel=0.05))
+    try:
+        M.mbpt_vegas_iterate(ctx, [g], 20)
+        r = M.mbpt_estimate(g)
+        assert r.converged == 1 and r.n_iter < 20 and r.sigma <= 0.05 * abs(r.mean)
+    finally:
+        M.mbpt_destroy_diagram(g)
+
+
+def test_freeze_keeps_grid(ctx):
+    po, pm = matter_pair("pnm")
+    D = O.enumerate_diagrams(3)[0]
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=20000, freeze_after=2))
+    try:
+        M.mbpt_vegas_iterate(ctx, [g], 2)
+        g2 = M.state_grid(M.mbpt_get_state(g), D.d, 50)
+        M.mbpt_vegas_iterate(ctx, [g], 2)
+        g4 = M.state_grid(M.mbpt_get_state(g), D.d, 50)
+        assert np.array_equal(g2, g4)
+    finally:
+        M.mbpt_destroy_diagram(g)
+
+
+def test_edge_cases_and_errors(ctx):
+    po, pm = matter_pair("pnm")
+    D = O.enumerate_diagrams(3)[1]
+    good = make_desc(D)
+    M.mbpt_vegas_iterate(ctx, [], 3)                       # empty batch is a no-op
+    # smallest sample count
+    g = M.mbpt_create_diagram(ctx, good, pm, M.vegas_cfg(samples=2))
+    M.mbpt_vegas_iterate(ctx, [g], 1)
+    assert M.mbpt_estimate(g).n_evals == 2
+    with pytest.raises(M.MbptError):
+        M.mbpt_vegas_iterate(ctx, [g, g], 1)               # same integral twice
+    with pytest.raises(M.MbptError):
+        M.mbpt_set_state(g, b"\0" * 16)
+    M.mbpt_destroy_diagram(g)
+    bad = make_desc(D)
+    bad.line_coef[D.n + 1][0] = 1 - bad.line_coef[D.n + 1][0]   # break momentum conservation
+    bad2 = make_desc(D)
+    bad2.vtx_out[0][0] = bad2.vtx_in[0][0]
+    bad3 = make_desc(D)
+    bad3.order = 6
+    for d in (bad, bad2, bad3):
+        with pytest.raises(M.MbptError) as e:
+            M.mbpt_create_diagram(ctx, d, pm, M.vegas_cfg())
+        assert e.value.status == M.MBPT_EINVAL
+    for kw in (dict(kF_n=0.0, kF_p=0.0), dict(reg_power=3), dict(K_max=0.5)):
+        p = M.physics(**kw)
+        with pytest.raises(M.MbptError) as e:
+            M.mbpt_create_diagram(ctx, good, p, M.vegas_cfg())
+        assert e.value.status == M.MBPT_EINVAL
+    with pytest.raises(M.MbptError) as e:
+        M.mbpt_create_diagram(ctx, good, pm, M.vegas_cfg(samples=1))
+    assert e.value.status == M.MBPT_EINVAL
+
+
+def test_arena_exhaustion_is_enomem():
+    small = M.mbpt_ctx_create(0, 1 << 20)
+    try:
+        po, pm = matter_pair("pnm")
+        D = O.enumerate_diagrams(5)[10]
+        made = []
+        with pytest.raises(M.MbptError) as e:
+            for _ in range(1000):
+                made.append(M.mbpt_create_diagram(small, make_desc(D), pm, M.vegas_cfg()))
+        assert e.value.status == M.MBPT_ENOMEM and len(made) > 10
+        for g in made:
+            M.mbpt_destroy_diagram(g)
+        used, free = M.mbpt_ctx_mem(small)
+        assert used == 0
+    finally:
+        M.mbpt_ctx_destroy(small)
