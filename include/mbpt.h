@@ -248,6 +248,35 @@ int mbpt_dump_samples(mbpt_diag* diag, int64_t iter, int64_t first, int64_t coun
  * ctr3), i < count; out receives 4*count words. */
 int mbpt_philox_device(mbpt_ctx* ctx, const uint32_t ctr[4], const uint32_t key[2], int64_t count, uint32_t* out);
 
+/*
+ * One VEGAS iteration of one integral without any device allocation.  The
+ * paper has no counterpart: this serves callers that must not allocate device
+ * memory once running (device memory owned by another allocator or a fixed
+ * budget; loops where cudaMalloc's implicit synchronisation is unacceptable).
+ *
+ * Evaluates samples 0..samples_per_iter-1 of iteration `iter` (Philox counter
+ * word 1) on the caller's grid and writes, in a fixed summation order,
+ *   out[0] = sum w, out[1] = sum w^2, out[2 + a*n_bins + i] = histogram of w^2
+ * (axis a, bin i).  grid: device pointer, d rows of n_bins+1 edges
+ * (d = 3(order+1)); out: device pointer to 2 + d*n_bins doubles.  Neither is
+ * retained.  Same integrand, launch shape and chunking as a fresh context's
+ * mbpt_vegas_iterate, so the sums agree with that path.  No refinement or
+ * combination.  Asynchronous on `cuda_stream` (NULL = legacy default stream).
+ *
+ * Scratch: one file-scope device array of 32 MiB per device, held from the
+ * library's load to process exit and shared by every call.  Requests that
+ * need more (with 50 bins: above about 3.8e7 samples at order 5, 1.1e8 at
+ * order 3) fail with MBPT_EINVAL and a message giving the limit.  The
+ * first call on a device looks up the array's device address and sets kernel
+ * attributes for that device; make that first call before any stream capture.
+ * Calls that overlap on the GPU (different streams, or different host threads)
+ * race on the shared array: serialise them.  Each call resets the parts that
+ * must start at zero; the rest of the array keeps the last call's contents.
+ */
+int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc* desc, const mbpt_physics* physics,
+                                 const mbpt_vegas_cfg* cfg, uint32_t iter, const double* grid, double* out,
+                                 void* cuda_stream);
+
 const char* mbpt_last_error(void);
 
 #ifdef __cplusplus

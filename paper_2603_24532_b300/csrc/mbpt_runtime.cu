@@ -965,3 +965,154 @@ int mbpt_philox_device(mbpt_ctx* c, const uint32_t ctr[4], const uint32_t key[2]
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single iteration (mbpt_vegas_iteration_noalloc).
+//
+// Some callers must not allocate device memory once they are running: a process whose device
+// memory is owned by another allocator (a framework's caching allocator, a fixed per-tenant
+// budget), or a latency-critical loop in which cudaMalloc/cudaFree, with their implicit device
+// synchronisation, are not acceptable.  For them the chunk slots, work table, compiled record and
+// per-integral state that mbpt_vegas_iterate keeps in its arena live in one fixed-size device
+// array defined here; the caller passes only the grid (input) and the result buffer (output).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;   // per device, held from load to process exit
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char* ptr = nullptr;   // device address of g_noalloc_scratch on this device
+    int blocks = 0;                 // persistent grid of k_iterate
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+// Once per device, with that device current: the device address of the scratch array (its name
+// in host code is only a host-side stand-in) and the launch attributes of k_iterate.
+int noalloc_setup(int device, NoAllocDevice** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc_dev[device];
+    if (!d.ready) {
+        void* p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        CUDA_TRY(cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChunkSmem)));
+        int per_sm = 0, sms = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate, kThreads, sizeof(ChunkSmem)));
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+        if (per_sm < 1) return fail(MBPT_ECUDA, "noalloc: k_iterate cannot be resident");
+        d.ptr = (unsigned char*)p;
+        d.blocks = per_sm * sms;
+        d.ready = true;
+    }
+    *out = &d;
+    return MBPT_OK;
+}
+
+// Fixed-order sums of one integral's chunk slots: out = [sum w, sum w^2, histogram d x nb].
+__global__ void __launch_bounds__(256) k_reduce_noalloc(const WorkItem* __restrict__ item,
+                                                       const double* __restrict__ csum,
+                                                       const float* __restrict__ chist, double* __restrict__ out) {
+    __shared__ double red[2][8];
+    const WorkItem& W = *item;
+    const int tid = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x) {
+        a += csum[2 * (size_t)c];
+        b += csum[2 * (size_t)c + 1];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = a;
+        red[1][tid >> 5] = b;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double A = 0.0, B = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            A += red[0][w];
+            B += red[1][w];
+        }
+        out[0] = A;
+        out[1] = B;
+    }
+    const int nh = W.rec->d * W.rec->nb;
+    for (int i = tid; i < nh; i += blockDim.x) {
+        double acc = 0.0;
+        for (uint32_t c = 0; c < W.n_chunks; ++c) acc += (double)chist[(size_t)c * (size_t)W.hist_stride + i];
+        out[2 + i] = acc;
+    }
+}
+
+}  // namespace
+
+extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc* desc, const mbpt_physics* ph,
+                                            const mbpt_vegas_cfg* cfg, uint32_t iter, const double* grid,
+                                            double* out, void* cuda_stream) {
+    if (!desc || !ph || !cfg || !grid || !out) return fail(MBPT_EINVAL, "iteration_noalloc: NULL argument");
+    if (device < 0 || device >= kNoAllocMaxDevices) return fail(MBPT_EINVAL, "iteration_noalloc: bad device");
+    DiagRec rec;
+    char err[256] = {0};
+    int st = compile_record(*desc, *ph, *cfg, &rec, err, sizeof(err));
+    if (st) return fail(st, std::string("iteration_noalloc: ") + err);
+    static const int kSpt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};   // as a fresh context
+    const int spt = kSpt[rec.order];
+    const uint64_t cs = (uint64_t)kThreads * (uint64_t)spt;
+    const uint64_t n_chunks = (cfg->samples_per_iter + cs - 1) / cs;
+    const size_t nh = (size_t)rec.d * (size_t)rec.nb;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t off_hdr = 0, off_item = up(sizeof(WorkHeader)), off_rec = off_item + up(sizeof(WorkItem));
+    const size_t off_state = off_rec + up(sizeof(DiagRec)), off_csum = off_state + up(sizeof(DiagState));
+    const size_t off_chist = off_csum + up(sizeof(double) * 2 * n_chunks);
+    const size_t need = off_chist + sizeof(float) * nh * n_chunks;
+    if (need > kNoAllocScratchBytes) {
+        const uint64_t per_chunk = 16 + 4 * nh;
+        const uint64_t max_chunks = (kNoAllocScratchBytes - off_csum - 512) / per_chunk;
+        return fail(MBPT_EINVAL, "iteration_noalloc: " + std::to_string(cfg->samples_per_iter) +
+                                     " samples need " + std::to_string(need) + " bytes of scratch, more than the " +
+                                     std::to_string(kNoAllocScratchBytes) + "-byte array; at most " +
+                                     std::to_string(max_chunks * cs) + " samples per call for this diagram");
+    }
+    DeviceGuard dg(device);
+    NoAllocDevice* nd = nullptr;
+    st = noalloc_setup(device, &nd);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned char* base = nd->ptr;
+    WorkHeader h;
+    memset(&h, 0, sizeof(h));          // chunk counter and error word start at zero on every call
+    h.n_items = 1;
+    h.total_chunks = (uint32_t)n_chunks;
+    h.hist_floats = (uint64_t)nh * n_chunks;
+    DiagState s0;
+    memset(&s0, 0, sizeof(s0));
+    s0.iter = (int32_t)iter;
+    WorkItem w;
+    memset(&w, 0, sizeof(w));
+    w.rec = (const DiagRec*)(base + off_rec);
+    w.state = (DiagState*)(base + off_state);
+    w.grid = const_cast<double*>(grid);
+    w.samples = cfg->samples_per_iter;
+    w.seed = cfg->seed;
+    w.stream_id = cfg->stream_id;
+    w.chunk_begin = 0;
+    w.n_chunks = (uint32_t)n_chunks;
+    w.alpha = cfg->alpha;
+    w.spt = spt;
+    w.hist_stride = (int32_t)nh;
+    CUDA_TRY(cudaMemcpyAsync(base + off_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(base + off_item, &w, sizeof(w), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(base + off_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(base + off_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, s));
+    k_iterate<<<nd->blocks, kThreads, sizeof(ChunkSmem), s>>>((WorkHeader*)(base + off_hdr),
+                                                             (const WorkItem*)(base + off_item),
+                                                             (double*)(base + off_csum), (float*)(base + off_chist));
+    CUDA_TRY(cudaGetLastError());
+    k_reduce_noalloc<<<1, 256, 0, s>>>((const WorkItem*)(base + off_item), (const double*)(base + off_csum),
+                                       (const float*)(base + off_chist), out);
+    CUDA_TRY(cudaGetLastError());
+    return MBPT_OK;
+}

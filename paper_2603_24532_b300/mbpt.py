@@ -160,6 +160,8 @@ def lib():
             "mbpt_dump_samples": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P(ctypes.c_double),
                                   P(ctypes.c_double)],
             "mbpt_philox_device": [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_int64, P(ctypes.c_uint32)],
+            "mbpt_vegas_iteration_noalloc": [ctypes.c_int, P(mbpt_diagram_desc), P(mbpt_physics), P(mbpt_vegas_cfg),
+                                             ctypes.c_uint32, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -287,6 +289,15 @@ def mbpt_philox_device(ctx, ctr: Sequence[int], key: Sequence[int], count: int) 
     out = np.zeros(4 * count, dtype=np.uint32)
     check(lib().mbpt_philox_device(ctx, c, k, count, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
     return out.reshape(count, 4)
+
+
+def mbpt_vegas_iteration_noalloc(device: int, desc: mbpt_diagram_desc, phys: mbpt_physics, cfg: mbpt_vegas_cfg,
+                                 iter_: int, grid_ptr: int, out_ptr: int, stream: int = 0):
+    """One iteration without device allocation; grid_ptr / out_ptr are device addresses
+    (d x (n_bins+1) edges in, 2 + d*n_bins doubles out)."""
+    check(lib().mbpt_vegas_iteration_noalloc(device, ctypes.byref(desc), ctypes.byref(phys), ctypes.byref(cfg),
+                                             iter_, ctypes.c_void_p(grid_ptr), ctypes.c_void_p(out_ptr),
+                                             ctypes.c_void_p(stream or None)))
 
 
 # ---------------------------------------------------------------------------
