@@ -68,7 +68,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -165,9 +165,12 @@ def run_gpu(args):
             ms_step.append(e0.elapsed_time(e1))
         return np.array(ms_it), np.array(ms_step)
 
-    # ---- headline: batched, mixed precision
+    from paper_2603_24532_b300.autotune import autotune
+
+    # ---- headline: batched, mixed precision, launch shape from the autotuner (untimed, states restored)
     gs, meta = build_integrals(M, ctx, M.MBPT_MIXED, seed_base=1 + rank, stream_base=10000 * rank)
     n_int = len(gs)
+    tuned = autotune(ctx, gs, trials=1)["best"] if args.autotune else None
     timed_steps(gs, args.warmup)
     if dist:
         dist.barrier()
@@ -209,8 +212,9 @@ def run_gpu(args):
     for g in gs:
         M.mbpt_destroy_diagram(g)
 
-    # ---- FP64 batched, same workload
+    # ---- FP64 batched, same workload (tuned the same way)
     g64, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
+    tuned64 = autotune(ctx, g64, trials=1)["best"] if args.autotune else None
     timed_steps(g64, args.warmup)
     it64, st64 = timed_steps(g64, args.steps)
     res64 = [M.mbpt_estimate(g) for g in g64]
@@ -218,7 +222,10 @@ def run_gpu(args):
         M.mbpt_destroy_diagram(g)
     v64 = world * evals_step / (float(np.mean(st64)) * 1e-3)
 
-    # ---- plain per-diagram FP64 loop: one launch per integral per iteration
+    # ---- plain per-diagram FP64 loop: one launch per integral per iteration, default launch shape
+    M.mbpt_ctx_set_kernel(ctx, 256, 2)
+    for o in (2, 3, 4, 5):
+        M.mbpt_ctx_set_launch(ctx, o, 32)
     gk0, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
     timed_steps(gk0, max(1, args.warmup // 2), per_diagram=True)
     itk0, stk0 = timed_steps(gk0, max(2, args.steps // 2), per_diagram=True)
@@ -254,7 +261,8 @@ def run_gpu(args):
                    "precision": "mixed (FP32 potentials and spin sum; FP64 map, momenta, denominators, sums, grid)",
                    "step": "one batched VEGAS iteration over all integrals (sample, integrate, reduce, combine, refine)",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "launch": tuned},
         "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e9, "peak": FP64_PEAK_NOMINAL / 1e9,
                      "unit": "FP64 Gop/s (DADD-equivalents)", "frac": achieved / FP64_PEAK_NOMINAL,
                      "peak_kind": "nominal 1.25 TFLOP/s FP64 of the recipe at 2032 MHz",
@@ -265,7 +273,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
-        "fp64_batched": {"value": v64, "unit": UNIT, "kernel_ms": float(np.mean(it64))},
+        "fp64_batched": {"value": v64, "unit": UNIT, "kernel_ms": float(np.mean(it64)), "launch": tuned64},
         "k0_plain_fp64_per_diagram": {"value": vk0, "unit": UNIT, "launches_per_step": 2 * n_int},
         "speedup_vs_k0": value / vk0,
         "diagrams_to_0p1pct_per_s": {"batched_mixed": d_mixed, "k0_plain_fp64": d_k0,
@@ -334,10 +342,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":

@@ -182,12 +182,20 @@ int mbpt_ctx_mem(const mbpt_ctx* ctx, size_t* used, size_t* largest_free);
 int mbpt_diag_bytes(const mbpt_diagram_desc* desc, const mbpt_vegas_cfg* cfg, size_t* bytes);
 
 /*
- * Kernel launch shape of mbpt_vegas_iterate for one order: threads per block
- * (64..512, multiple of 32) and samples per thread per chunk (1..256).  The
- * autotuner sets these; chunk results depend on them (not on the batch mix).
+ * Launch shape of mbpt_vegas_iterate.  The sample-evaluation kernel is compiled
+ * in a few shapes (threads per block x minimum resident blocks per SM, which
+ * caps registers per thread); mbpt_kernel_variants lists them (count first,
+ * then up to cap shapes).  mbpt_ctx_set_kernel selects one for a context and
+ * mbpt_ctx_set_launch sets the samples per thread of a chunk (1..256) for one
+ * order; a chunk is threads x samples_per_thread consecutive samples of one
+ * integral.  The autotuner sets these.  Results of an integral depend on its
+ * chunking (summation order), not on the rest of the batch.
  */
-int mbpt_ctx_set_launch(mbpt_ctx* ctx, int order, int threads_per_block, int samples_per_thread);
-int mbpt_ctx_get_launch(const mbpt_ctx* ctx, int order, int* threads_per_block, int* samples_per_thread);
+int mbpt_kernel_variants(int* threads_per_block, int* min_blocks_per_sm, int cap, int* count);
+int mbpt_ctx_set_kernel(mbpt_ctx* ctx, int threads_per_block, int min_blocks_per_sm);
+int mbpt_ctx_set_launch(mbpt_ctx* ctx, int order, int samples_per_thread);
+int mbpt_ctx_get_launch(const mbpt_ctx* ctx, int order, int* threads_per_block, int* min_blocks_per_sm,
+                        int* samples_per_thread);
 
 /*
  * Device time of the last mbpt_vegas_iterate iteration: the sample-evaluation
@@ -212,6 +220,12 @@ int mbpt_ctx_stream(const mbpt_ctx* ctx, void** cuda_stream);
 int mbpt_create_diagram(mbpt_ctx* ctx, const mbpt_diagram_desc* desc, const mbpt_physics* physics,
                         const mbpt_vegas_cfg* cfg, mbpt_diag** out);
 int mbpt_destroy_diagram(mbpt_diag* diag);
+/*
+ * Change an integral's samples per iteration, freeze point and targets for its
+ * next iterations (PVegas' adaptive number of samples per iteration, Sec. III.C).
+ * Seed, stream id, bins, alpha and precision must be unchanged (MBPT_EINVAL).
+ */
+int mbpt_set_config(mbpt_diag* diag, const mbpt_vegas_cfg* cfg);
 
 /*
  * Run n_iters VEGAS iterations on the k integrals as one batch: per
@@ -226,6 +240,8 @@ int mbpt_vegas_iterate(mbpt_ctx* ctx, mbpt_diag* const* diags, int k, int n_iter
 
 /* Synchronise and read an integral's estimate. */
 int mbpt_estimate(const mbpt_diag* diag, mbpt_result* out);
+/* The same for k integrals of one context with a single synchronisation; out[i] for diags[i]. */
+int mbpt_estimate_batch(mbpt_diag* const* diags, int k, mbpt_result* out);
 
 /*
  * Checkpoint: the grid, the iteration history and counters as a host byte

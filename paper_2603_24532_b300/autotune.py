@@ -1,0 +1,48 @@
+"""Launch-shape autotuner for the batched VEGAS iteration.
+
+Times one iteration of the caller's own batch for every compiled kernel shape
+(threads per block x minimum resident blocks, i.e. a register cap) and every
+candidate samples-per-thread, restoring every integral's state (grid, sums,
+iteration counter) after each trial so tuning leaves no trace in the results,
+and leaves the fastest setting on the context.
+"""
+from __future__ import annotations
+
+from typing import Dict, Iterable, Optional, Sequence
+
+import numpy as np
+
+from . import mbpt as M
+
+DEFAULT_SPT = (8, 16, 32, 64)
+
+
+def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: Optional[Sequence] = None,
+             trials: int = 2, orders: Iterable[int] = (2, 3, 4, 5)) -> Dict:
+    if not diags:
+        raise ValueError("autotune needs a non-empty batch")
+    states = [M.mbpt_get_state(g) for g in diags]
+    table = []
+    try:
+        for tpb, minb in (variants or M.mbpt_kernel_variants()):
+            M.mbpt_ctx_set_kernel(ctx, tpb, minb)
+            for spt in spts:
+                for o in orders:
+                    M.mbpt_ctx_set_launch(ctx, o, spt)
+                M.mbpt_vegas_iterate(ctx, diags, 1)          # graph capture, first-touch
+                ms = []
+                for _ in range(trials):
+                    M.mbpt_vegas_iterate(ctx, diags, 1)
+                    it_ms, fin_ms = M.mbpt_ctx_last_timing(ctx)
+                    ms.append(it_ms + fin_ms)
+                table.append({"threads": tpb, "min_blocks": minb, "spt": spt, "ms": float(np.median(ms))})
+                for g, st in zip(diags, states):
+                    M.mbpt_set_state(g, st)
+    finally:
+        for g, st in zip(diags, states):
+            M.mbpt_set_state(g, st)
+    best = min(table, key=lambda r: r["ms"])
+    M.mbpt_ctx_set_kernel(ctx, best["threads"], best["min_blocks"])
+    for o in orders:
+        M.mbpt_ctx_set_launch(ctx, o, best["spt"])
+    return {"best": best, "table": table}

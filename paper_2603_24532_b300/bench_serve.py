@@ -1,0 +1,48 @@
+"""Serving benchmark: replay a Poisson stream of equation-of-state requests against the
+continuous-batching server on one GPU and report latency percentiles and throughput.
+
+    python -m paper_2603_24532_b300.bench_serve [--requests 1200] [--rate 20] [--seed 7]
+        [--budget-gb 40] [--time-limit 300]
+
+Requests (seed 7, exponential gaps of mean 1/rate): n ~ U[0.04, 0.20] fm^-3, delta from
+{0, 0.25, 0.5, 0.75, 1}, order cap from {2, 3, 4}, relative target from {1%, 0.3%, 0.1%};
+admission by a fixed grid/accumulator memory budget.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+from . import serve as S
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=1200)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--budget-gb", type=float, default=40.0)
+    ap.add_argument("--arena-gb", type=float, default=48.0)
+    ap.add_argument("--time-limit", type=float, default=None)
+    ap.add_argument("--max-iters", type=int, default=60)
+    a = ap.parse_args()
+    be = S.MbptBackend(arena_bytes=int(a.arena_gb * (1 << 30)))
+    srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters)
+    trace = S.poisson_trace(a.requests, a.rate, a.seed)
+    t0 = time.perf_counter()
+    done = srv.run(trace, realtime=True, time_limit=a.time_limit)
+    wall = time.perf_counter() - t0
+    st = S.latency_stats(done)
+    n_int = sum(len(r.integrals) for r in done)
+    caps = {c: sum(1 for r in done if r.cap == c) for c in (2, 3, 4)}
+    out = {"workload": "EOS request stream, Poisson rate %.1f/s seed %d, %d requests" % (a.rate, a.seed, a.requests),
+           "completed": len(done), "wall_s": wall, "latency": st,
+           "diagrams_per_s": n_int / wall, "evals_per_s": srv.evals / wall, "rounds": srv.rounds,
+           "completed_by_cap": caps, "budget_bytes": srv.budget}
+    print(json.dumps(out))
+    be.close()
+
+
+if __name__ == "__main__":
+    main()

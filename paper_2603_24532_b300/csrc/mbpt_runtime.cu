@@ -101,13 +101,15 @@ struct Arena {
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-struct alignas(16) ChunkSmem {
+template <int NW>
+struct alignas(16) ChunkSmemT {
     DiagRec rec;
     Grid2 grid[kMaxD * kGridStride];
-    float hist[kWarps][kMaxD * MBPT_MAX_BINS];
-    double red[2][kWarps];
+    float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
+    double red[2][NW];
     uint32_t chunk, item, iter, skip;
 };
+using ChunkSmem = ChunkSmemT<kWarps>;
 
 __device__ __forceinline__ void load_record(DiagRec* dst, const DiagRec* src) {
     const uint4* s = reinterpret_cast<const uint4*>(src);
@@ -127,8 +129,8 @@ __device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, 
     }
 }
 
-template <int N, int PREC>
-__device__ __forceinline__ void run_chunk(ChunkSmem& S, const WorkItem& W, uint32_t chunk_local, double& sw,
+template <int N, int PREC, int NW>
+__device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
     const DiagRec& R = S.rec;
     const uint32_t cs = blockDim.x * (uint32_t)W.spt;
@@ -167,10 +169,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Persistent kernel: blocks take chunks (a fixed range of one integral's samples) from a global
 // counter; each chunk's sum w, sum w^2 and histogram go to the chunk's own slot, so the result of a
 // chunk does not depend on which block ran it or what else is in the batch.
-__global__ void __launch_bounds__(kThreads) k_iterate(WorkHeader* hdr, const WorkItem* __restrict__ items,
-                                                     double* __restrict__ csum, float* __restrict__ chist) {
+// Compiled in several launch shapes (threads per block x minimum resident blocks, i.e. a register cap);
+// the autotuner picks one per context.
+template <int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_iterate_t(WorkHeader* hdr, const WorkItem* __restrict__ items,
+                                                        double* __restrict__ csum, float* __restrict__ chist) {
+    constexpr int NW = TPB / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ChunkSmem& S = *reinterpret_cast<ChunkSmem*>(smem_raw);
+    ChunkSmemT<NW>& S = *reinterpret_cast<ChunkSmemT<NW>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t n_items = hdr->n_items, total = hdr->total_chunks;
     for (;;) {
@@ -204,19 +210,19 @@ __global__ void __launch_bounds__(kThreads) k_iterate(WorkHeader* hdr, const Wor
         __syncthreads();
         const int d = S.rec.d, nb = S.rec.nb, prec = S.rec.precision, order = S.rec.order;
         load_grid(S.grid, W.grid, d, nb, prec);
-        for (int i = tid; i < kWarps * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
+        for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
         __syncthreads();
         double sw = 0.0, sw2 = 0.0;
         const uint32_t cl = chunk - W.chunk_begin;
         switch (order * 2 + prec) {
-            case 2 * 2 + MBPT_FP64: run_chunk<2, MBPT_FP64>(S, W, cl, sw, sw2); break;
-            case 2 * 2 + MBPT_MIXED: run_chunk<2, MBPT_MIXED>(S, W, cl, sw, sw2); break;
-            case 3 * 2 + MBPT_FP64: run_chunk<3, MBPT_FP64>(S, W, cl, sw, sw2); break;
-            case 3 * 2 + MBPT_MIXED: run_chunk<3, MBPT_MIXED>(S, W, cl, sw, sw2); break;
-            case 4 * 2 + MBPT_FP64: run_chunk<4, MBPT_FP64>(S, W, cl, sw, sw2); break;
-            case 4 * 2 + MBPT_MIXED: run_chunk<4, MBPT_MIXED>(S, W, cl, sw, sw2); break;
-            case 5 * 2 + MBPT_FP64: run_chunk<5, MBPT_FP64>(S, W, cl, sw, sw2); break;
-            case 5 * 2 + MBPT_MIXED: run_chunk<5, MBPT_MIXED>(S, W, cl, sw, sw2); break;
+            case 2 * 2 + MBPT_FP64: run_chunk<2, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 2 * 2 + MBPT_MIXED: run_chunk<2, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+            case 3 * 2 + MBPT_FP64: run_chunk<3, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 3 * 2 + MBPT_MIXED: run_chunk<3, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+            case 4 * 2 + MBPT_FP64: run_chunk<4, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 4 * 2 + MBPT_MIXED: run_chunk<4, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+            case 5 * 2 + MBPT_FP64: run_chunk<5, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 5 * 2 + MBPT_MIXED: run_chunk<5, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
             default:
                 if (tid == 0) atomicOr(&hdr->error, 2u);
         }
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) k_iterate(WorkHeader* hdr, const Wor
         __syncthreads();
         if (tid == 0) {
             double a = 0.0, b = 0.0;
-            for (int w = 0; w < kWarps; ++w) {
+            for (int w = 0; w < NW; ++w) {
                 a += S.red[0][w];
                 b += S.red[1][w];
             }
@@ -239,12 +245,26 @@ __global__ void __launch_bounds__(kThreads) k_iterate(WorkHeader* hdr, const Wor
         float* dst = chist + (size_t)chunk * (size_t)W.hist_stride;
         for (int i = tid; i < d * nb; i += blockDim.x) {
             float v = 0.0f;
-            for (int w = 0; w < kWarps; ++w) v += S.hist[w][i];
+            for (int w = 0; w < NW; ++w) v += S.hist[w][i];
             dst[i] = v;
         }
         __syncthreads();
     }
 }
+
+typedef void (*IterateFn)(WorkHeader*, const WorkItem*, double*, float*);
+struct KernelVariant {
+    int tpb, minb;
+    IterateFn fn;
+    size_t smem;
+};
+const KernelVariant kVariants[] = {
+    {256, 2, k_iterate_t<256, 2>, sizeof(ChunkSmemT<8>)},
+    {128, 4, k_iterate_t<128, 4>, sizeof(ChunkSmemT<4>)},
+    {256, 1, k_iterate_t<256, 1>, sizeof(ChunkSmemT<8>)},
+    {128, 3, k_iterate_t<128, 3>, sizeof(ChunkSmemT<4>)},
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
 // Grid refinement of one axis (Lepage 1978 with (7,1)/8 and (1,6,1)/8 smoothing):
 // dbar -> r = dbar/sum -> m = ((r-1)/ln r)^alpha -> new edges at equal shares of the
@@ -439,9 +459,9 @@ struct mbpt_ctx {
     bool own_arena = false;
     Arena arena;
     int sms = 0;
-    int iterate_blocks = 0;     // persistent grid of k_iterate
+    int variant = 0;                       // index into kVariants
+    int variant_blocks[kNumVariants] = {0};  // persistent grid of each k_iterate variant
     int finalize_blocks = 0;
-    size_t iterate_smem = 0;
     int spt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};
     // batch buffers (arena)
     WorkHeader* d_hdr = nullptr;
@@ -544,8 +564,8 @@ int capture_graph(mbpt_ctx* c) {
     CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(&c->d_hdr->chunk_counter, 0, sizeof(uint32_t), c->stream);
     cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal);
-    k_iterate<<<c->iterate_blocks, kThreads, c->iterate_smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
-                                                                           c->d_chist);
+    const KernelVariant& kv = kVariants[c->variant];
+    kv.fn<<<c->variant_blocks[c->variant], kv.tpb, kv.smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist);
     cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal);
     k_finalize<<<c->finalize_blocks, 256, 0, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist,
                                                          c->d_last_hist);
@@ -630,18 +650,19 @@ int mbpt_ctx_create(mbpt_ctx** out, int device, void* arena, size_t arena_bytes,
         }
         c->own_stream = true;
     }
-    c->iterate_smem = sizeof(ChunkSmem);
-    e = cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->iterate_smem);
-    int per_sm = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate, kThreads, c->iterate_smem);
-    if (e != cudaSuccess || per_sm < 1) {
-        if (c->own_stream) cudaStreamDestroy(c->stream);
-        if (c->own_arena) cudaFree(base);
-        delete c;
-        return fail(MBPT_ECUDA, std::string("k_iterate occupancy: ") + cudaGetErrorString(e));
+    for (int v = 0; v < kNumVariants; ++v) {
+        const KernelVariant& kv = kVariants[v];
+        e = cudaFuncSetAttribute(kv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem);
+        int per_sm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv.fn, kv.tpb, kv.smem);
+        if (e != cudaSuccess || per_sm < 1) {
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            if (c->own_arena) cudaFree(base);
+            delete c;
+            return fail(MBPT_ECUDA, std::string("k_iterate occupancy: ") + cudaGetErrorString(e));
+        }
+        c->variant_blocks[v] = per_sm * c->sms;
     }
-    c->iterate_blocks = per_sm * c->sms;
     c->finalize_blocks = 2 * c->sms;
     for (int i = 0; i < 3; ++i) {
         e = cudaEventCreate(&c->ev[i]);
@@ -706,17 +727,45 @@ int mbpt_diag_bytes(const mbpt_diagram_desc* desc, const mbpt_vegas_cfg* cfg, si
     return MBPT_OK;
 }
 
-int mbpt_ctx_set_launch(mbpt_ctx* c, int order, int tpb, int spt) {
+int mbpt_kernel_variants(int* tpb, int* minb, int cap, int* count) {
+    if (!count) return fail(MBPT_EINVAL, "kernel_variants: NULL count");
+    *count = kNumVariants;
+    if (!tpb || !minb) return MBPT_OK;
+    if (cap < kNumVariants) return fail(MBPT_ENOMEM, "kernel_variants: cap too small");
+    for (int v = 0; v < kNumVariants; ++v) {
+        tpb[v] = kVariants[v].tpb;
+        minb[v] = kVariants[v].minb;
+    }
+    return MBPT_OK;
+}
+
+int mbpt_ctx_set_kernel(mbpt_ctx* c, int tpb, int minb) {
+    if (!c) return fail(MBPT_EINVAL, "set_kernel: NULL context");
+    for (int v = 0; v < kNumVariants; ++v)
+        if (kVariants[v].tpb == tpb && kVariants[v].minb == minb) {
+            if (v != c->variant) {
+                DeviceGuard dg(c->device);
+                cudaStreamSynchronize(c->stream);
+                invalidate_graph(c);
+                c->variant = v;
+            }
+            return MBPT_OK;
+        }
+    return fail(MBPT_EINVAL, "set_kernel: no compiled variant with this shape (see mbpt_kernel_variants)");
+}
+
+int mbpt_ctx_set_launch(mbpt_ctx* c, int order, int spt) {
     if (!c || order < 2 || order > MBPT_MAX_DEVICE_ORDER) return fail(MBPT_EINVAL, "set_launch: bad order");
-    if (tpb != kThreads) return fail(MBPT_EINVAL, "set_launch: threads_per_block must be 256");
     if (spt < 1 || spt > 256) return fail(MBPT_EINVAL, "set_launch: samples_per_thread must be 1..256");
     c->spt[order] = spt;
     return MBPT_OK;
 }
 
-int mbpt_ctx_get_launch(const mbpt_ctx* c, int order, int* tpb, int* spt) {
-    if (!c || !tpb || !spt || order < 2 || order > MBPT_MAX_DEVICE_ORDER) return fail(MBPT_EINVAL, "get_launch: bad argument");
-    *tpb = kThreads;
+int mbpt_ctx_get_launch(const mbpt_ctx* c, int order, int* tpb, int* minb, int* spt) {
+    if (!c || !tpb || !minb || !spt || order < 2 || order > MBPT_MAX_DEVICE_ORDER)
+        return fail(MBPT_EINVAL, "get_launch: bad argument");
+    *tpb = kVariants[c->variant].tpb;
+    *minb = kVariants[c->variant].minb;
     *spt = c->spt[order];
     return MBPT_OK;
 }
@@ -769,6 +818,22 @@ int mbpt_create_diagram(mbpt_ctx* c, const mbpt_diagram_desc* desc, const mbpt_p
     return MBPT_OK;
 }
 
+int mbpt_set_config(mbpt_diag* g, const mbpt_vegas_cfg* cfg) {
+    if (!g || !cfg || !g->ctx || !g->ctx->diags.count(g)) return fail(MBPT_EINVAL, "set_config: bad argument");
+    const mbpt_vegas_cfg& o = g->cfg;
+    if (cfg->n_bins != o.n_bins || cfg->precision != o.precision || cfg->seed != o.seed ||
+        cfg->stream_id != o.stream_id || cfg->alpha != o.alpha)
+        return fail(MBPT_EINVAL, "set_config: only samples_per_iter, freeze_after and the targets may change");
+    if (cfg->samples_per_iter < 2 || cfg->samples_per_iter >= (1ull << 32) || !(cfg->target_rel >= 0.0) ||
+        !(cfg->target_abs >= 0.0))
+        return fail(MBPT_EINVAL, "set_config: invalid samples or targets");
+    g->cfg.samples_per_iter = cfg->samples_per_iter;
+    g->cfg.freeze_after = cfg->freeze_after;
+    g->cfg.target_rel = cfg->target_rel;
+    g->cfg.target_abs = cfg->target_abs;
+    return MBPT_OK;
+}
+
 int mbpt_destroy_diagram(mbpt_diag* g) {
     if (!g || !g->ctx) return fail(MBPT_EINVAL, "destroy_diagram: NULL");
     mbpt_ctx* c = g->ctx;
@@ -807,7 +872,7 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         w.seed = g->cfg.seed;
         w.stream_id = g->cfg.stream_id;
         w.spt = c->spt[g->desc.order];
-        const uint64_t cs = (uint64_t)kThreads * (uint64_t)w.spt;
+        const uint64_t cs = (uint64_t)kVariants[c->variant].tpb * (uint64_t)w.spt;
         w.n_chunks = (uint32_t)((w.samples + cs - 1) / cs);
         w.chunk_begin = (uint32_t)chunk;
         w.freeze_after = g->cfg.freeze_after;
@@ -856,6 +921,37 @@ int mbpt_estimate(const mbpt_diag* g, mbpt_result* out) {
     out->n_evals = s.n_evals;
     out->converged = s.converged;
     out->status = s.status;
+    return MBPT_OK;
+}
+
+int mbpt_estimate_batch(mbpt_diag* const* diags, int k, mbpt_result* out) {
+    if (k < 0 || (k > 0 && (!diags || !out))) return fail(MBPT_EINVAL, "estimate_batch: bad argument");
+    if (k == 0) return MBPT_OK;
+    mbpt_ctx* c = diags[0] ? diags[0]->ctx : nullptr;
+    if (!c) return fail(MBPT_EINVAL, "estimate_batch: NULL integral");
+    for (int i = 0; i < k; ++i)
+        if (!diags[i] || diags[i]->ctx != c || !c->diags.count(diags[i]))
+            return fail(MBPT_EINVAL, "estimate_batch: integrals must belong to one context");
+    DeviceGuard dg(c->device);
+    int st = check_device_error(c);
+    if (st) return st;
+    std::vector<DiagState> hs((size_t)k);
+    for (int i = 0; i < k; ++i)
+        CUDA_TRY(cudaMemcpyAsync(&hs[i], diags[i]->d_state, offsetof(DiagState, hist_mean), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < k; ++i) {
+        const DiagState& s = hs[i];
+        out[i].mean = s.mean;
+        out[i].sigma = s.sigma;
+        out[i].chi2_dof = s.chi2;
+        out[i].last_mean = s.last_mean;
+        out[i].last_sigma = s.last_var > 0.0 ? sqrt(s.last_var) : 0.0;
+        out[i].n_iter = s.iter;
+        out[i].n_evals = s.n_evals;
+        out[i].converged = s.converged;
+        out[i].status = s.status;
+    }
     return MBPT_OK;
 }
 
@@ -998,9 +1094,11 @@ int noalloc_setup(int device, NoAllocDevice** out) {
     if (!d.ready) {
         void* p = nullptr;
         CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        CUDA_TRY(cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChunkSmem)));
+        CUDA_TRY(cudaFuncSetAttribute(k_iterate_t<kThreads, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(ChunkSmem)));
         int per_sm = 0, sms = 0;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate, kThreads, sizeof(ChunkSmem)));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate_t<kThreads, 2>, kThreads,
+                                                               sizeof(ChunkSmem)));
         CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
         if (per_sm < 1) return fail(MBPT_ECUDA, "noalloc: k_iterate cannot be resident");
         d.ptr = (unsigned char*)p;
@@ -1058,7 +1156,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     char err[256] = {0};
     int st = compile_record(*desc, *ph, *cfg, &rec, err, sizeof(err));
     if (st) return fail(st, std::string("iteration_noalloc: ") + err);
-    static const int kSpt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};   // as a fresh context
+    static const int kSpt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};   // as a fresh context (256 threads)
     const int spt = kSpt[rec.order];
     const uint64_t cs = (uint64_t)kThreads * (uint64_t)spt;
     const uint64_t n_chunks = (cfg->samples_per_iter + cs - 1) / cs;
@@ -1107,7 +1205,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     CUDA_TRY(cudaMemcpyAsync(base + off_item, &w, sizeof(w), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(base + off_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(base + off_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, s));
-    k_iterate<<<nd->blocks, kThreads, sizeof(ChunkSmem), s>>>((WorkHeader*)(base + off_hdr),
+    k_iterate_t<kThreads, 2><<<nd->blocks, kThreads, sizeof(ChunkSmem), s>>>((WorkHeader*)(base + off_hdr),
                                                              (const WorkItem*)(base + off_item),
                                                              (double*)(base + off_csum), (float*)(base + off_chist));
     CUDA_TRY(cudaGetLastError());

@@ -147,14 +147,18 @@ def lib():
             "mbpt_ctx_destroy": [vp],
             "mbpt_ctx_mem": [vp, P(ctypes.c_size_t), P(ctypes.c_size_t)],
             "mbpt_diag_bytes": [P(mbpt_diagram_desc), P(mbpt_vegas_cfg), P(ctypes.c_size_t)],
-            "mbpt_ctx_set_launch": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
-            "mbpt_ctx_get_launch": [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
+            "mbpt_kernel_variants": [P(ctypes.c_int), P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)],
+            "mbpt_ctx_set_kernel": [vp, ctypes.c_int, ctypes.c_int],
+            "mbpt_ctx_set_launch": [vp, ctypes.c_int, ctypes.c_int],
+            "mbpt_ctx_get_launch": [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
             "mbpt_ctx_last_timing": [vp, P(ctypes.c_double), P(ctypes.c_double)],
             "mbpt_ctx_stream": [vp, P(vp)],
             "mbpt_create_diagram": [vp, P(mbpt_diagram_desc), P(mbpt_physics), P(mbpt_vegas_cfg), P(vp)],
             "mbpt_destroy_diagram": [vp],
+            "mbpt_set_config": [vp, P(mbpt_vegas_cfg)],
             "mbpt_vegas_iterate": [vp, P(vp), ctypes.c_int, ctypes.c_int],
             "mbpt_estimate": [vp, P(mbpt_result)],
+            "mbpt_estimate_batch": [P(vp), ctypes.c_int, P(mbpt_result)],
             "mbpt_get_state": [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
             "mbpt_set_state": [vp, vp, ctypes.c_size_t],
             "mbpt_dump_samples": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P(ctypes.c_double),
@@ -219,14 +223,27 @@ def mbpt_diag_bytes(desc: mbpt_diagram_desc, cfg: mbpt_vegas_cfg) -> int:
     return b.value
 
 
-def mbpt_ctx_set_launch(ctx, order: int, threads_per_block: int, samples_per_thread: int):
-    check(lib().mbpt_ctx_set_launch(ctx, order, threads_per_block, samples_per_thread))
+def mbpt_kernel_variants():
+    n = ctypes.c_int()
+    check(lib().mbpt_kernel_variants(None, None, 0, ctypes.byref(n)))
+    t = (ctypes.c_int * n.value)()
+    m = (ctypes.c_int * n.value)()
+    check(lib().mbpt_kernel_variants(t, m, n.value, ctypes.byref(n)))
+    return list(zip(list(t), list(m)))
+
+
+def mbpt_ctx_set_kernel(ctx, threads_per_block: int, min_blocks_per_sm: int):
+    check(lib().mbpt_ctx_set_kernel(ctx, threads_per_block, min_blocks_per_sm))
+
+
+def mbpt_ctx_set_launch(ctx, order: int, samples_per_thread: int):
+    check(lib().mbpt_ctx_set_launch(ctx, order, samples_per_thread))
 
 
 def mbpt_ctx_get_launch(ctx, order: int):
-    t, s = ctypes.c_int(), ctypes.c_int()
-    check(lib().mbpt_ctx_get_launch(ctx, order, ctypes.byref(t), ctypes.byref(s)))
-    return t.value, s.value
+    t, m, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().mbpt_ctx_get_launch(ctx, order, ctypes.byref(t), ctypes.byref(m), ctypes.byref(s)))
+    return t.value, m.value, s.value
 
 
 def mbpt_ctx_last_timing(ctx):
@@ -252,6 +269,10 @@ def mbpt_destroy_diagram(diag):
     check(lib().mbpt_destroy_diagram(diag))
 
 
+def mbpt_set_config(diag, cfg: mbpt_vegas_cfg):
+    check(lib().mbpt_set_config(diag, ctypes.byref(cfg)))
+
+
 def mbpt_vegas_iterate(ctx, diags: Sequence, n_iters: int):
     arr = (ctypes.c_void_p * max(1, len(diags)))(*[d.value for d in diags])
     check(lib().mbpt_vegas_iterate(ctx, arr, len(diags), n_iters))
@@ -261,6 +282,16 @@ def mbpt_estimate(diag) -> mbpt_result:
     r = mbpt_result()
     check(lib().mbpt_estimate(diag, ctypes.byref(r)))
     return r
+
+
+def mbpt_estimate_batch(diags: Sequence) -> List[mbpt_result]:
+    k = len(diags)
+    if k == 0:
+        return []
+    arr = (ctypes.c_void_p * k)(*[d.value for d in diags])
+    out = (mbpt_result * k)()
+    check(lib().mbpt_estimate_batch(arr, k, out))
+    return list(out)
 
 
 def mbpt_get_state(diag) -> bytes:

@@ -1,0 +1,323 @@
+"""Continuous-batching server for equation-of-state requests.
+
+A request asks for the correlation energy per particle sum_{k=2}^{cap} E^(k)/N of nucleon
+matter at density n (fm^-3) and isospin asymmetry delta, to a relative statistical error
+`target`.  It expands into one integral per non-anomalous Hugenholtz diagram of orders
+2..cap at kF_n = (3 pi^2 n (1 + delta)/2)^(1/3), kF_p = (3 pi^2 n (1 - delta)/2)^(1/3)
+(Sec. II; a species with zero density is absent).
+
+The loop (one "round" per VEGAS iteration of every resident integral):
+  1. admit waiting requests in arrival order while the device arena holds their integrals
+     (memory admission: state bytes from mbpt_diag_bytes, budget in bytes) and the slot
+     limit allows;
+  2. run one batched iteration of all resident, unfinished integrals (one graph replay);
+  3. read the estimates; after the first round of a request its summed estimate E_sum sets a
+     per-integral error budget sigma_G <= target |E_sum| / sqrt(N_int); integrals that reach
+     their budget (after at least `min_iters` iterations) retire and stop consuming samples;
+  4. a request completes when all its integrals have retired (or hit `max_iters`); its
+     integrals are destroyed, freeing arena memory for waiting requests.
+
+Requests that arrive while others are on the GPU join the next round: their integrals run in
+the same persistent launch as everything else.  Each integral's random stream is keyed by
+(request id, order, diagram id), and every quantity that decides its iterations is local to
+its request, so a request's result is the same alone and in a mix.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+HBAR2_OVER_M = 41.47
+
+
+def fermi_momenta(n_dens: float, delta: float):
+    """kF_n, kF_p of matter with total density n and asymmetry delta = (n_n - n_p)/n."""
+    nn = 0.5 * n_dens * (1.0 + delta)
+    npr = 0.5 * n_dens * (1.0 - delta)
+    kn = (3.0 * math.pi ** 2 * nn) ** (1.0 / 3.0) if nn > 0 else 0.0
+    kp = (3.0 * math.pi ** 2 * npr) ** (1.0 / 3.0) if npr > 1e-15 else 0.0
+    return kn, kp
+
+
+@dataclass
+class Request:
+    n_dens: float
+    delta: float
+    cap: int
+    target: float
+    arrival: float = 0.0
+    rid: int = -1
+    # filled by the server
+    admitted: Optional[float] = None
+    completed: Optional[float] = None
+    energy: Optional[float] = None
+    sigma: Optional[float] = None
+    per_order: Dict[int, float] = field(default_factory=dict)
+    integrals: list = field(default_factory=list)
+    budget: Optional[float] = None
+    rounds: int = 0
+
+    @property
+    def latency(self) -> Optional[float]:
+        if self.completed is None:
+            return None
+        return self.completed - self.arrival
+
+
+@dataclass
+class Integral:
+    req: Request
+    order: int
+    diagram_id: int
+    handle: object
+    bytes: int
+    cfg: object = None
+    samples: int = 0
+    evals: int = 0
+    mean: float = 0.0
+    sigma: float = float("inf")
+    n_iter: int = 0
+    done: bool = False
+
+
+class MbptBackend:
+    """The C ABI as the server's backend (all work on the GPU)."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, arena_ptr: int = 0, stream: int = 0,
+                 precision: Optional[int] = None):
+        from . import mbpt as M
+        self.M = M
+        self.ctx = M.mbpt_ctx_create(device, arena_bytes, arena_ptr=arena_ptr, stream=stream)
+        self.precision = M.MBPT_MIXED if precision is None else precision
+        self._descs = {}
+
+    def diagrams(self, order: int):
+        if order not in self._descs:
+            self._descs[order] = [d for d in self.M.mbpt_generate(order) if not d.anomalous]
+        return self._descs[order]
+
+    def physics(self, kF_n: float, kF_p: float):
+        return self.M.physics(kF_n=kF_n, kF_p=kF_p, K_max=max(kF_n, kF_p) + 6.0)
+
+    def cfg(self, samples: int, stream_id: int, seed: int):
+        return self.M.vegas_cfg(samples=samples, seed=seed, stream_id=stream_id, precision=self.precision)
+
+    def nbytes(self, desc, cfg) -> int:
+        return self.M.mbpt_diag_bytes(desc, cfg)
+
+    def create(self, desc, phys, cfg):
+        try:
+            return self.M.mbpt_create_diagram(self.ctx, desc, phys, cfg)
+        except self.M.MbptError as e:
+            if e.status == self.M.MBPT_ENOMEM:
+                raise MemoryError(str(e)) from e
+            raise
+
+    def iterate(self, handles: Sequence):
+        self.M.mbpt_vegas_iterate(self.ctx, list(handles), 1)
+
+    def estimate(self, h):
+        r = self.M.mbpt_estimate(h)
+        return r.mean, r.sigma, r.n_iter
+
+    def estimate_many(self, handles: Sequence):
+        return [(r.mean, r.sigma, r.n_iter) for r in self.M.mbpt_estimate_batch(list(handles))]
+
+    def set_samples(self, h, cfg, samples: int):
+        cfg.samples_per_iter = int(samples)
+        self.M.mbpt_set_config(h, cfg)
+
+    def destroy(self, h):
+        self.M.mbpt_destroy_diagram(h)
+
+    def close(self):
+        self.M.mbpt_ctx_destroy(self.ctx)
+
+
+SAMPLES_BY_ORDER = {2: 1 << 16, 3: 1 << 16, 4: 1 << 16, 5: 1 << 16}   # pilot iteration
+MIN_SAMPLES, MAX_SAMPLES = 1 << 14, 1 << 21
+
+
+class Server:
+    def __init__(self, backend, budget_bytes: int = 40 << 30, max_integrals: int = 1 << 16,
+                 samples_by_order: Optional[Dict[int, int]] = None, min_iters: int = 3, max_iters: int = 60,
+                 seed: int = 1, clock: Callable[[], float] = time.perf_counter, adaptive: bool = True):
+        self.b = backend
+        self.adaptive = adaptive
+        self.budget = budget_bytes
+        self.max_integrals = max_integrals
+        self.samples = dict(SAMPLES_BY_ORDER if samples_by_order is None else samples_by_order)
+        self.min_iters = min_iters
+        self.max_iters = max_iters
+        self.seed = seed
+        self.clock = clock
+        self.waiting: List[Request] = []
+        self.active: List[Request] = []
+        self.done: List[Request] = []
+        self.used_bytes = 0
+        self.n_integrals = 0
+        self.rounds = 0
+        self.evals = 0
+        self._next_id = 0
+
+    # ---- request bookkeeping ------------------------------------------------------------
+    def submit(self, req: Request) -> int:
+        if req.rid < 0:
+            req.rid = self._next_id
+        self._next_id = max(self._next_id, req.rid + 1)
+        if req.cap < 2:
+            raise ValueError("order cap must be >= 2")
+        self.waiting.append(req)
+        return req.rid
+
+    def _plan(self, req: Request):
+        kn, kp = fermi_momenta(req.n_dens, req.delta)
+        phys = self.b.physics(kn, kp)
+        plan = []
+        for order in range(2, req.cap + 1):
+            for d in self.b.diagrams(order):
+                sid = (req.rid * 8 + order) * 1024 + d.diagram_id
+                cfg = self.b.cfg(self.samples[order], sid & 0xFFFFFFFF, self.seed)
+                plan.append((order, d, phys, cfg, self.b.nbytes(d, cfg)))
+        return plan
+
+    def _admit(self, now: float):
+        while self.waiting:
+            req = self.waiting[0]
+            plan = self._plan(req)
+            need = sum(p[4] for p in plan)
+            if need > self.budget:
+                # can never fit: reject rather than block the queue
+                self.waiting.pop(0)
+                req.completed = now
+                req.energy = float("nan")
+                self.done.append(req)
+                continue
+            if self.used_bytes + need > self.budget or self.n_integrals + len(plan) > self.max_integrals:
+                return
+            created = []
+            try:
+                for order, d, phys, cfg, nb in plan:
+                    h = self.b.create(d, phys, cfg)
+                    created.append(Integral(req, order, d.diagram_id, h, nb, cfg, self.samples[order]))
+            except MemoryError:
+                # the arena refused (its scratch competes with integral state): roll back, retry later
+                for it in created:
+                    self.b.destroy(it.handle)
+                return
+            self.waiting.pop(0)
+            req.admitted = now
+            req.integrals = created
+            self.used_bytes += need
+            self.n_integrals += len(plan)
+            self.active.append(req)
+
+    def _retire_and_complete(self, now: float):
+        live = [it for req in self.active for it in req.integrals if not it.done]
+        if hasattr(self.b, "estimate_many"):
+            ests = self.b.estimate_many([it.handle for it in live])
+        else:
+            ests = [self.b.estimate(it.handle) for it in live]
+        for it, e in zip(live, ests):
+            it.mean, it.sigma, it.n_iter = e
+        still = []
+        for req in self.active:
+            req.rounds += 1
+            e_sum = sum(it.mean for it in req.integrals)
+            if req.budget is None:
+                # per-integral error budget from the first (pilot) estimate of the request's sum
+                req.budget = req.target * abs(e_sum) / math.sqrt(len(req.integrals))
+            for it in req.integrals:
+                if it.done:
+                    continue
+                it.evals += it.samples
+                if (it.n_iter >= self.min_iters and it.sigma <= req.budget) or it.n_iter >= self.max_iters:
+                    it.done = True
+                elif self.adaptive and hasattr(self.b, "set_samples") and it.sigma > 0.0 and req.budget > 0.0:
+                    # samples still needed if sigma ~ 1/sqrt(evaluations), spread over a few iterations
+                    need = it.evals * ((it.sigma / req.budget) ** 2 - 1.0)
+                    left = max(1, self.min_iters - it.n_iter, 4)
+                    nxt = int(min(MAX_SAMPLES, max(MIN_SAMPLES, need / left)))
+                    nxt = 1 << max(0, int(round(math.log2(nxt))))
+                    if nxt != it.samples:
+                        self.b.set_samples(it.handle, it.cfg, nxt)
+                        it.samples = nxt
+            if all(it.done for it in req.integrals):
+                req.energy = e_sum
+                req.sigma = math.sqrt(sum(it.sigma ** 2 for it in req.integrals))
+                for order in range(2, req.cap + 1):
+                    req.per_order[order] = sum(it.mean for it in req.integrals if it.order == order)
+                req.completed = now
+                for it in req.integrals:
+                    self.b.destroy(it.handle)
+                    self.used_bytes -= it.bytes
+                self.n_integrals -= len(req.integrals)
+                self.done.append(req)
+            else:
+                still.append(req)
+        self.active = still
+
+    def step(self) -> bool:
+        """One round; returns False when there is nothing to run."""
+        now = self.clock()
+        self._admit(now)
+        handles = [it.handle for req in self.active for it in req.integrals if not it.done]
+        if not handles:
+            return False
+        self.b.iterate(handles)
+        self.evals += sum(it.samples for req in self.active for it in req.integrals if not it.done)
+        self.rounds += 1
+        self._retire_and_complete(self.clock())
+        return True
+
+    def run(self, trace: Sequence[Request], realtime: bool = True, time_limit: Optional[float] = None):
+        """Replay a trace: request i becomes visible at t0 + trace[i].arrival (wall clock when
+        realtime, else all at once in order).  Returns the completed requests."""
+        pending = sorted(trace, key=lambda r: r.arrival)
+        t0 = self.clock()
+        k = 0
+        while k < len(pending) or self.waiting or self.active:
+            now = self.clock() - t0
+            while k < len(pending) and (not realtime or pending[k].arrival <= now):
+                r = pending[k]
+                r.arrival = t0 + r.arrival if realtime else self.clock()
+                self.submit(r)
+                k += 1
+            ran = self.step()
+            if not ran and k < len(pending) and realtime:
+                wait = pending[k].arrival - (self.clock() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+            if time_limit is not None and self.clock() - t0 > time_limit:
+                break
+        return self.done
+
+
+def poisson_trace(n_requests: int, rate: float = 20.0, seed: int = 7) -> List[Request]:
+    """Synthetic EOS request stream: exponential inter-arrival gaps (mean 1/rate), and per
+    request, in this draw order: n ~ U[0.04, 0.20] fm^-3, delta from {0, .25, .5, .75, 1},
+    order cap from {2, 3, 4}, target from {1 %, 0.3 %, 0.1 %}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        n = rng.uniform(0.04, 0.20)
+        delta = [0.0, 0.25, 0.5, 0.75, 1.0][rng.integers(0, 5)]
+        cap = [2, 3, 4][rng.integers(0, 3)]
+        target = [0.01, 0.003, 0.001][rng.integers(0, 3)]
+        out.append(Request(n_dens=n, delta=delta, cap=cap, target=target, arrival=t, rid=i))
+    return out
+
+
+def latency_stats(done: Sequence[Request]):
+    lat = np.array([r.latency for r in done if r.latency is not None and r.energy is not None
+                    and np.isfinite(r.energy)])
+    if len(lat) == 0:
+        return {"p50_s": None, "p99_s": None, "n": 0}
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(np.mean(lat)), "n": int(len(lat))}

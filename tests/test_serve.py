@@ -1,0 +1,169 @@
+"""Serving loop (continuous batching of EOS requests): scheduling logic on CPU with a
+deterministic fake backend; a GPU test that a request's result is the same alone and
+in a mix of concurrent requests."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2603_24532_b300 import serve as S
+
+
+class FakeDesc:
+    def __init__(self, order, i):
+        self.order = order
+        self.diagram_id = i
+        self.anomalous = False
+
+
+class FakeBackend:
+    """Integral i converges like sigma0/sqrt(iterations) around a value fixed by its
+    stream id; memory 25 kB per integral; an optional arena limit raises MemoryError."""
+
+    COUNTS = {2: 1, 3: 3, 4: 33, 5: 668}
+
+    def __init__(self, arena_limit=None):
+        self.live = {}
+        self.next = 0
+        self.arena_limit = arena_limit
+        self.iterated = []
+
+    def diagrams(self, order):
+        return [FakeDesc(order, i) for i in range(self.COUNTS[order])]
+
+    def physics(self, kn, kp):
+        return (kn, kp)
+
+    def cfg(self, samples, sid, seed):
+        return (samples, sid, seed)
+
+    def nbytes(self, d, cfg):
+        return 25_000
+
+    def create(self, d, phys, cfg):
+        if self.arena_limit is not None and len(self.live) >= self.arena_limit:
+            raise MemoryError("arena")
+        h = self.next
+        self.next += 1
+        sid = cfg[1]
+        self.live[h] = {"sid": sid, "it": 0, "val": -0.5 / d.order ** 2 * (1 + (sid % 7) / 10.0)}
+        return h
+
+    def iterate(self, handles):
+        self.iterated.append(len(handles))
+        for h in handles:
+            self.live[h]["it"] += 1
+
+    def estimate(self, h):
+        s = self.live[h]
+        it = s["it"]
+        rng = np.random.default_rng(s["sid"] * 1000 + it)
+        sigma = 0.05 * abs(s["val"]) / math.sqrt(it)
+        return s["val"] + 0.1 * sigma * rng.standard_normal(), sigma, it
+
+    def destroy(self, h):
+        del self.live[h]
+
+
+def test_fermi_momenta():
+    kn, kp = S.fermi_momenta(0.16, 0.0)
+    assert kn == pytest.approx(kp) and kn == pytest.approx((3 * math.pi ** 2 * 0.08) ** (1 / 3))
+    kn, kp = S.fermi_momenta(0.1, 1.0)
+    assert kp == 0.0 and kn == pytest.approx((3 * math.pi ** 2 * 0.1) ** (1 / 3))
+
+
+def test_trace_is_deterministic_and_in_range():
+    a = S.poisson_trace(200)
+    b = S.poisson_trace(200)
+    assert [(r.arrival, r.n_dens, r.delta, r.cap, r.target) for r in a] == \
+           [(r.arrival, r.n_dens, r.delta, r.cap, r.target) for r in b]
+    assert all(0.04 <= r.n_dens <= 0.2 and r.cap in (2, 3, 4) and r.target in (0.01, 0.003, 0.001) for r in a)
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    assert 0.03 < np.mean(gaps) < 0.07          # mean 1/20 s
+
+
+def test_all_requests_complete_and_memory_is_released():
+    be = FakeBackend()
+    srv = S.Server(be, budget_bytes=10 ** 9, min_iters=2, max_iters=50, clock=iter(range(10 ** 6)).__next__)
+    trace = S.poisson_trace(30)
+    done = srv.run(trace, realtime=False)
+    assert len(done) == 30 and all(r.energy is not None and np.isfinite(r.energy) for r in done)
+    assert srv.used_bytes == 0 and srv.n_integrals == 0 and not be.live
+    for r in done:
+        assert r.sigma <= r.target * abs(r.energy) * 1.5 or r.rounds >= 50
+
+
+def test_admission_respects_memory_budget_and_fifo():
+    be = FakeBackend()
+    # room for 40 integrals: a cap-4 request (37 integrals) blocks the next one until it completes
+    srv = S.Server(be, budget_bytes=40 * 25_000, min_iters=2, clock=iter(range(10 ** 6)).__next__)
+    reqs = [S.Request(0.1, 0.0, 4, 0.01, rid=0), S.Request(0.1, 0.0, 4, 0.01, rid=1),
+            S.Request(0.1, 0.0, 2, 0.01, rid=2)]
+    for r in reqs:
+        srv.submit(r)
+    srv.step()
+    assert [r.rid for r in srv.active] == [0] and len(srv.waiting) == 2
+    assert max(be.iterated) <= 40
+    while srv.step():
+        assert srv.used_bytes <= 40 * 25_000
+    assert [r.rid for r in srv.done] == [0, 1, 2]   # FIFO: the small request does not overtake
+
+
+def test_oversized_request_is_rejected_not_blocking():
+    be = FakeBackend()
+    srv = S.Server(be, budget_bytes=10 * 25_000, clock=iter(range(10 ** 6)).__next__)
+    big, small = S.Request(0.1, 0.0, 4, 0.01, rid=0), S.Request(0.1, 0.0, 2, 0.01, rid=1)
+    srv.submit(big)
+    srv.submit(small)
+    while srv.step():
+        pass
+    assert math.isnan(big.energy) and np.isfinite(small.energy)
+
+
+def test_arena_refusal_rolls_back():
+    be = FakeBackend(arena_limit=5)
+    srv = S.Server(be, budget_bytes=10 ** 9, clock=iter(range(10 ** 6)).__next__)
+    srv.submit(S.Request(0.1, 0.0, 3, 0.01, rid=0))   # 4 integrals
+    srv.submit(S.Request(0.1, 0.0, 3, 0.01, rid=1))   # would need 8 > 5
+    srv.step()
+    assert len(be.live) == 4 and len(srv.waiting) == 1
+    while srv.step():
+        pass
+    assert len(srv.done) == 2
+
+
+def test_result_same_alone_and_in_mix_fake():
+    trace = S.poisson_trace(12)
+    be = FakeBackend()
+    mix = {r.rid: r.energy for r in S.Server(be, clock=iter(range(10 ** 6)).__next__).run(trace, realtime=False)}
+    for rid in (0, 5, 11):
+        r0 = S.poisson_trace(12)[rid]
+        alone = S.Server(FakeBackend(), clock=iter(range(10 ** 6)).__next__).run([r0], realtime=False)
+        assert alone[0].energy == mix[rid]
+
+
+@pytest.mark.gpu
+def test_result_same_alone_and_in_mix_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    trace = [r for r in S.poisson_trace(40) if r.cap <= 3][:6]
+    for r in trace:
+        r.target = 0.01
+    small = {2: 1 << 15, 3: 1 << 16, 4: 1 << 16}
+    be = S.MbptBackend(arena_bytes=2 << 30)
+    try:
+        mix = S.Server(be, samples_by_order=small, max_iters=30).run([S.Request(**_req(r)) for r in trace],
+                                                                     realtime=False)
+        mixd = {r.rid: (r.energy, r.sigma, dict(r.per_order)) for r in mix}
+        assert len(mixd) == len(trace)
+        for r in trace[:3]:
+            alone = S.Server(be, samples_by_order=small, max_iters=30).run([S.Request(**_req(r))], realtime=False)
+            assert (alone[0].energy, alone[0].sigma, dict(alone[0].per_order)) == mixd[r.rid]
+            assert alone[0].energy < 0.0
+    finally:
+        be.close()
+
+
+def _req(r):
+    return dict(n_dens=r.n_dens, delta=r.delta, cap=r.cap, target=r.target, arrival=0.0, rid=r.rid)
