@@ -35,12 +35,13 @@ SAMPLES = 1 << 22
 ORDER = 3
 WORKLOAD = "third-order Hugenholtz diagrams (pp, hh, ph), pure neutron matter, kF 0.8..1.7 fm^-1 (10 points), 12D, 2^22 samples/iteration"
 
-# FP64 pipe work per sample of an order-3 integral in the formulation of csrc/mbpt_device.cuh, in
-# DADD-equivalents (sqrt = 8.6, reciprocal/division = 5.7, from the pipe microbenchmark):
-# map 2/axis (24) + chord map 34.3/chord (137.2) + tree lines 9/line (18) = 179.2 on every sample;
-# live samples add denominators (8), weight (9) and sums (2).  Dead samples add the sums only.
-FP64_OPS_ALL = 179.2 + 2.0
-FP64_OPS_LIVE_EXTRA = 17.0
+# FP64 operations per sample of an order-3 integral, mixed precision (FP32 sampling map), in the
+# formulation of csrc/mbpt_device.cuh: chord momenta 3 products + |l|^2 3 + Jacobian 1 = 7 per chord
+# (28) + tree lines 6 sums + |k|^2 3 = 9 per line (18) + sum w, sum w^2 (2) = 48 on every sample;
+# live samples add the energy denominators (7 sums, 1 product), the weight (4 products) and the
+# Newton reciprocal of the denominator product (4) = 16.
+FP64_OPS_ALL = 48.0
+FP64_OPS_LIVE_EXTRA = 16.0
 # nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second
 FP64_PEAK_NOMINAL = 1.25e12 / 2.0
 # measured DFMA issue rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu)
@@ -209,6 +210,46 @@ def run_gpu(args):
         _ = [M.mbpt_estimate(g).mean for g in gs]
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_value = world * evals_step / e2e_s
+    # ---- precision: mixed modes vs FP64 on identical counters and grids, paired over several
+    # iterations (each trial restores the same grid and sets the iteration counter), per integral;
+    # the scale of a near-zero diagram is 1e-3 of its order's sum
+    imgs = [M.mbpt_get_state(g) for g in gs]
+    twins = {}
+    for name, prec in (("fp64", M.MBPT_FP64), ("map64", M.MBPT_MIXED_MAP64)):
+        twins[name] = []
+        for (kf, did) in meta:
+            d = M.mbpt_generate(ORDER)[did]
+            ph = M.physics(kF_n=kf, kF_p=0.0, K_max=kf + 6.0)
+            sid = 10000 * rank + 100 * KF_SCAN.index(kf) + did
+            twins[name].append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=SAMPLES, seed=1 + rank,
+                                                                              stream_id=sid, precision=prec)))
+    sets = {"mixed": gs, "fp64": twins["fp64"], "map64": twins["map64"]}
+    trials = 6
+    means = {k: np.zeros((trials, n_int)) for k in sets}
+    t0_iter = 1000
+    for k in range(trials):
+        for name, arr in sets.items():
+            for g, img in zip(arr, imgs):
+                M.mbpt_set_state(g, M.state_with_iter(img, t0_iter + k))
+            M.mbpt_vegas_iterate(ctx, arr, 1)
+            means[name][k] = [r.last_mean for r in M.mbpt_estimate_batch(arr)]
+    ref = means["fp64"]
+    scale = np.zeros(n_int)
+    for ki in range(len(KF_SCAN)):
+        sl = slice(3 * ki, 3 * ki + 3)
+        scale[sl] = np.maximum(np.abs(ref[:, sl]).mean(axis=0), 1e-3 * abs(np.sum(ref[:, sl].mean(axis=0))))
+    precision_dev = {"definition": "paired over %d iterations on identical counters and grids: mean of "
+                                   "(I_mode - I_fp64) / max(|I_fp64|, 1e-3 |order sum|) per integral" % trials}
+    for name in ("mixed", "map64"):
+        dif = (means[name] - ref) / scale
+        mdif, se = dif.mean(axis=0), dif.std(axis=0, ddof=1) / np.sqrt(trials)
+        precision_dev[name] = {"max_abs_mean": float(np.max(np.abs(mdif))),
+                               "median_abs_mean": float(np.median(np.abs(mdif))),
+                               "max_single_iteration": float(np.max(np.abs(dif))),
+                               "max_abs_mean_over_se": float(np.max(np.abs(mdif) / np.maximum(se, 1e-300)))}
+    for arr in twins.values():
+        for g in arr:
+            M.mbpt_destroy_diagram(g)
     for g in gs:
         M.mbpt_destroy_diagram(g)
 
@@ -258,7 +299,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "integrals": n_int, "samples_per_iter": SAMPLES,
-                   "precision": "mixed (FP32 potentials and spin sum; FP64 map, momenta, denominators, sums, grid)",
+                   "precision": "mixed (FP32 potentials, spin sum and sampling map; FP64 line momenta, Fermi steps, energy denominators, sums, grid)",
                    "step": "one batched VEGAS iteration over all integrals (sample, integrate, reduce, combine, refine)",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
@@ -276,6 +317,7 @@ def run_gpu(args):
         "fp64_batched": {"value": v64, "unit": UNIT, "kernel_ms": float(np.mean(it64)), "launch": tuned64},
         "k0_plain_fp64_per_diagram": {"value": vk0, "unit": UNIT, "launches_per_step": 2 * n_int},
         "speedup_vs_k0": value / vk0,
+        "mixed_vs_fp64_deviation": precision_dev,
         "diagrams_to_0p1pct_per_s": {"batched_mixed": d_mixed, "k0_plain_fp64": d_k0,
                                      "ratio": (d_mixed / d_k0) if (d_mixed and d_k0) else None},
     }

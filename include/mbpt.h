@@ -57,9 +57,13 @@ typedef enum {
 
 typedef enum {
     MBPT_FP64 = 0,        /* every step in FP64 */
-    MBPT_MIXED = 1        /* potential matrix elements (exp, Yukawa) and the spin
-                             sum in FP32; sampling map, momenta, energy
-                             denominators, weights, sums and grid in FP64 */
+    MBPT_MIXED = 1,       /* potential matrix elements (exp, Yukawa), their products
+                             and the spin sum in FP32; the sampling map (VEGAS map,
+                             chord magnitudes and directions, Jacobians) in FP32,
+                             placing each chord momentum at an exact FP64 point;
+                             line momenta, Fermi steps, energy denominators,
+                             weights, sums and the grid update in FP64 */
+    MBPT_MIXED_MAP64 = 2  /* as MBPT_MIXED but with the sampling map in FP64 */
 } mbpt_precision;
 
 #define MBPT_MAX_ORDER 6          /* generator; the device path runs 2..5 */

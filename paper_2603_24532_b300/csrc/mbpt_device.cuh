@@ -52,9 +52,84 @@ __device__ __forceinline__ double neg_if(double x, int neg) {
     return __longlong_as_double(b);
 }
 
-// grid entry in shared memory: FP64 mode (e_i, de_i); mixed mode (e_i - de_i, de_i)
+// Exact widening of a positive normal float to double with integer operations only (keeps the
+// conversion off the FP64 pipe): rebias the exponent (127 -> 1023) and move the 23-bit mantissa up.
+__device__ __forceinline__ double widen_pos_normal(float f) {
+    const unsigned long long b = (unsigned long long)__float_as_uint(f);
+    const unsigned long long e = ((b >> 23) & 0xFFull) + (1023ull - 127ull);
+    return __longlong_as_double((long long)((e << 52) | ((b & 0x7FFFFFull) << 29)));
+}
+
+// double -> float with integer operations only (the hardware conversion runs on the FP64 pipe):
+// keep the sign, rebias the exponent (1023 -> 127), truncate the mantissa to 23 bits; values below
+// the normal float range become signed zero, values above it infinity.  Relative error < 2^-23.
+__device__ __forceinline__ float narrow_trunc(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FFull) - 1023 + 127;
+    const unsigned int m = (unsigned int)(b >> 29) & 0x7FFFFFu;
+    unsigned int r = sign | ((unsigned int)e << 23) | m;
+    r = (e <= 0) ? sign : r;
+    r = (e >= 255) ? (sign | 0x7F800000u) : r;
+    return __uint_as_float(r);
+}
+
+// float -> double exactly with integer operations; zero and subnormal floats give signed zero.
+__device__ __forceinline__ double widen_f(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned int ef = (u >> 23) & 0xFFu;
+    const unsigned long long body =
+        ((unsigned long long)(ef + (1023u - 127u)) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)(sign | (ef == 0u ? 0ull : body)));
+}
+
+// x != 0 without an FP64 compare
+__device__ __forceinline__ bool nonzero(double x) {
+    return (((unsigned long long)__double_as_longlong(x)) << 1) != 0ull;
+}
+
+// sqrt(q), q >= 0: Newton-Raphson on s^2 = q started from the FP32 hardware reciprocal square
+// root y ~ 1/sqrt(q) (relative error e0 ~ 1e-7): s <- s + (y/2)(q - s^2).  With the slope held at
+// y/2 the error goes e -> -e0 e - e^2/2, so two steps reach FP64 rounding (5 FP64 operations
+// instead of the ~9 DADD-equivalents of the IEEE square root on this part).
+__device__ __forceinline__ double sqrt_nr(double q) {
+    const float y = rsqrtf(fmaxf(narrow_trunc(q), 1.17549435e-38f));
+    const double h = widen_pos_normal(0.5f * y);
+    double s = q * widen_pos_normal(y);
+    s = fma(h, fma(-s, s, q), s);
+    s = fma(h, fma(-s, s, q), s);
+    return s;
+}
+
+// 1/m for m > 0 in a range where m and the FP32 reciprocal are normal floats: Newton-Raphson r <- r + r (1 - m r)
+// from the FP32 estimate, two steps (error e -> e^2 each).
+__device__ __forceinline__ double rcp_nr(double m) {
+    double r = widen_pos_normal(__frcp_rn(narrow_trunc(m)));
+    r = fma(r, fma(-m, r, 1.0), r);
+    r = fma(r, fma(-m, r, 1.0), r);
+    return r;
+}
+
+// 1/D for a finite, normal, non-zero D: scale |D| into [1, 2) by exponent arithmetic, take the
+// Newton-refined reciprocal there and move the exponent back (4 FP64 operations instead of an
+// IEEE division).
+__device__ __forceinline__ double rcp_scaled(double D) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(D);
+    const long long e = (long long)((b >> 52) & 0x7FFull) - 1023;
+    const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+    const double r = rcp_nr(m);                        // in (1/2, 1]
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(r) - ((unsigned long long)e << 52);
+    return __longlong_as_double((long long)(rb | (b & 0x8000000000000000ull)));
+}
+
+// Grid entry in shared memory (16 bytes).  FP64 map: (e_i, de_i) in FP64 mode, (e_i - de_i, de_i)
+// with the FP32 potentials; FP32 map (MBPT_MIXED): floats (e_i, de_i, -, -).
 struct Grid2 {
     double a, de;
+};
+struct Grid4f {
+    float e, de, pad0, pad1;
 };
 
 constexpr int kGridStride = MBPT_MAX_BINS;   // bins per axis row in shared memory
@@ -120,26 +195,9 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
 #pragma unroll
     for (int j = 0; j < NBLK; ++j) philox4x32_10(s, t, sid, (uint32_t)j, k0, k1, &u[4 * j]);
 
-    // --- VEGAS map: y = (u + 1/2) 2^-32, i = floor(y nb), x = e_i + (y nb - i) de_i.
-    // (2u+1) nb < 2^39, so bin index and fraction are exact integer arithmetic.
-    double x[D];
-    double jv = 1.0;
-#pragma unroll
-    for (int w = 0; w < 5; ++w) o.binpack[w] = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        const uint64_t r = (2ull * (uint64_t)u[a] + 1ull) * (uint64_t)nb;
-        const uint32_t i = (uint32_t)(r >> 33);
-        const uint64_t fb = r & ((1ull << 33) - 1ull);
-        const double m = __longlong_as_double((long long)(0x3FF0000000000000ull | (fb << 19)));   // 1 + frac
-        const Grid2 g = gs[a * kGridStride + i];
-        if (PREC == MBPT_FP64) x[a] = fma(m - 1.0, g.de, g.a);
-        else x[a] = fma(m, g.de, g.a);
-        jv *= g.de;
-        o.binpack[a >> 2] |= i << (8 * (a & 3));
-        if (x_out) x_out[a] = x[a];
-    }
-
+    // --- VEGAS map: y = (u + 1/2) 2^-32, i = floor(y nb), x = e_i + (y nb - i) de_i, J = prod nb de_i
+    // (nb^d is folded into pref).  (2u+1) nb < 2^39, so the bin index and the fraction are exact
+    // integer arithmetic.
     // --- chord momenta: k = lo + rng x0, cos(t) = 2 x1 - 1, sin(t) = 2 sqrt(x1 (1 - x1)),
     // rational azimuth a = x2 (1 - x2), b = x2 - 1/2: cos(phi) = (a^2 - b^2)/(a^2 + b^2),
     // sin(phi) = 2ab/(a^2 + b^2), dphi/dx2 = 2/(1/2 - a).  Jacobian k^2 (1/2 - a)/(a^2+b^2) times
@@ -153,27 +211,100 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         K[2][l] = 0.0;
         U[l] = 0.0;
     }
-    double jc = 1.0;
+    float lf[3][L];           // chord momenta in FP32 for the potentials
+    double jv = 1.0, jc = 1.0;
 #pragma unroll
-    for (int c = 0; c < L; ++c) {
-        const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-        const double k = fma(R.chord_rng[c], x0, R.chord_lo[c]);
-        const double ct = fma(2.0, x1, -1.0);
-        const double sq = sqrt(fma(-x1, x1, x1));
-        const double a = fma(-x2, x2, x2);
-        const double b = x2 - 0.5;
-        const double bb = b * b;
-        const double mm = fma(a, a, bb);
-        const double rr = 1.0 / mm;
-        const double ncos = fma(a, a, -bb);
-        const double nsin = (a + a) * b;
-        const double R2 = (k + k) * sq * rr;
-        K[0][c] = R2 * ncos;
-        K[1][c] = R2 * nsin;
-        K[2][c] = k * ct;
-        const double k2 = k * k;
-        U[c] = k2;
-        jc *= k2 * ((0.5 - a) * rr);
+    for (int w = 0; w < 5; ++w) o.binpack[w] = 0;
+    if (PREC == MBPT_MIXED) {
+        // Sampling map in FP32.  It only decides where the sample lies: each chord momentum is the
+        // exact FP64 product of an FP32 magnitude and an FP32 unit direction, so lines, steps and
+        // energy denominators below are evaluated in FP64 at that point; the map's Jacobian is
+        // good to FP32 rounding (a relative weight error ~1e-7 per sample).
+        const Grid4f* gf = reinterpret_cast<const Grid4f*>(gs);
+        float xf[D];
+        float mp = 1.0f;          // Jacobian prod de_i as mantissa product x 2^ex (no FP32 underflow)
+        int ex = 0;
+        bool zero_bin = false;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const uint64_t r = (2ull * (uint64_t)u[a] + 1ull) * (uint64_t)nb;
+            const uint32_t i = (uint32_t)(r >> 33);
+            const uint32_t fb = (uint32_t)((r >> 10) & 0x7FFFFFull);          // top 23 bits of the fraction
+            const float frac = __uint_as_float(0x3F800000u | fb) - 1.0f;
+            const Grid4f g = gf[a * kGridStride + i];
+            xf[a] = fmaf(frac, g.de, g.e);
+            const uint32_t bits = __float_as_uint(g.de);
+            zero_bin |= (bits == 0u);
+            ex += (int)(bits >> 23) - 127;
+            mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+            o.binpack[a >> 2] |= i << (8 * (a & 3));
+            if (x_out) x_out[a] = widen_f(xf[a]);
+        }
+        jv = zero_bin ? 0.0 : __longlong_as_double(__double_as_longlong(widen_pos_normal(mp)) + ((long long)ex << 52));
+#pragma unroll
+        for (int c = 0; c < L; ++c) {
+            const float x0 = xf[3 * c], x1 = xf[3 * c + 1], x2 = xf[3 * c + 2];
+            const float k = fmaf(R.chord_rng_f[c], x0, R.chord_lo_f[c]);
+            const float ct = fmaf(2.0f, x1, -1.0f);
+            const float sq = sqrtf(fmaf(-x1, x1, x1));
+            const float a = fmaf(-x2, x2, x2);
+            const float b = x2 - 0.5f;
+            const float bb = b * b;
+            const float mm = fmaf(a, a, bb);
+            const float rr = __frcp_rn(mm);
+            const float R2 = 2.0f * sq * rr;
+            const float nx = R2 * fmaf(a, a, -bb), ny = R2 * ((a + a) * b), nz = ct;
+            const double kd = widen_f(k);
+            K[0][c] = kd * widen_f(nx);      // exact: 24-bit x 24-bit
+            K[1][c] = kd * widen_f(ny);
+            K[2][c] = kd * widen_f(nz);
+            U[c] = fma(K[0][c], K[0][c], fma(K[1][c], K[1][c], K[2][c] * K[2][c]));
+            lf[0][c] = k * nx;
+            lf[1][c] = k * ny;
+            lf[2][c] = k * nz;
+            jc *= widen_f(k * k * ((0.5f - a) * rr));
+        }
+    } else {
+        double x[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const uint64_t r = (2ull * (uint64_t)u[a] + 1ull) * (uint64_t)nb;
+            const uint32_t i = (uint32_t)(r >> 33);
+            const uint64_t fb = r & ((1ull << 33) - 1ull);
+            const double m = __longlong_as_double((long long)(0x3FF0000000000000ull | (fb << 19)));   // 1 + frac
+            const Grid2 g = gs[a * kGridStride + i];
+            if (PREC == MBPT_FP64) x[a] = fma(m - 1.0, g.de, g.a);
+            else x[a] = fma(m, g.de, g.a);
+            jv *= g.de;
+            o.binpack[a >> 2] |= i << (8 * (a & 3));
+            if (x_out) x_out[a] = x[a];
+        }
+#pragma unroll
+        for (int c = 0; c < L; ++c) {
+            const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
+            const double k = fma(R.chord_rng[c], x0, R.chord_lo[c]);
+            const double ct = fma(2.0, x1, -1.0);
+            const double sq = sqrt_nr(fma(-x1, x1, x1));
+            const double a = fma(-x2, x2, x2);
+            const double b = x2 - 0.5;
+            const double bb = b * b;
+            const double mm = fma(a, a, bb);
+            const double rr = rcp_nr(mm);           // mm = (1/2 - a)^2 in [1/16, 1/4]
+            const double ncos = fma(a, a, -bb);
+            const double nsin = (a + a) * b;
+            const double R2 = (k + k) * sq * rr;
+            K[0][c] = R2 * ncos;
+            K[1][c] = R2 * nsin;
+            K[2][c] = k * ct;
+            const double k2 = k * k;
+            U[c] = k2;
+            jc *= k2 * ((0.5 - a) * rr);
+            if (PREC != MBPT_FP64) {
+                lf[0][c] = narrow_trunc(K[0][c]);
+                lf[1][c] = narrow_trunc(K[1][c]);
+                lf[2][c] = narrow_trunc(K[2][c]);
+            }
+        }
     }
     // --- tree lines from momentum conservation: k = k_a + k_b - k_c
 #pragma unroll
@@ -227,12 +358,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
 
     // --- spin(-isospin) sum of the antisymmetrised vertex products
     double S;
-    if (PREC == MBPT_MIXED) {
-        float lf[3][L];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int c = 0; c < L; ++c) lf[q][c] = (float)K[q][c];
+    if (PREC != MBPT_FP64) {
         float prod[1 << N];
         prod[0] = 1.0f;
 #pragma unroll
@@ -275,7 +401,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
                 sum = fmaf(f, prod[tt], sum);
             }
         }
-        S = (double)sum;
+        S = widen_f(sum);
     } else {
         double prod[1 << N];
         prod[0] = 1.0;
@@ -318,7 +444,8 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
     }
 
     // --- weight: w = pref * J_vegas * J_chords * S / prod_m D~_m
-    o.w = (R.pref * jv * jc * S) / Dprod;
+    if (PREC == MBPT_FP64) o.w = (R.pref * (jv * jc) * S) / Dprod;
+    else o.w = (R.pref * (jv * jc) * S) * rcp_scaled(Dprod);
     return o;
 }
 

@@ -278,7 +278,7 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
     }
     if (cfg.n_bins < 2 || cfg.n_bins > MBPT_MAX_BINS || cfg.samples_per_iter < 2 ||
         cfg.samples_per_iter >= (1ull << 32) || !(cfg.alpha >= 0.0) ||
-        (cfg.precision != MBPT_FP64 && cfg.precision != MBPT_MIXED) || !(cfg.target_rel >= 0.0) ||
+        (cfg.precision != MBPT_FP64 && cfg.precision != MBPT_MIXED && cfg.precision != MBPT_MIXED_MAP64) || !(cfg.target_rel >= 0.0) ||
         !(cfg.target_abs >= 0.0)) {
         set_err(err, errlen, "invalid VEGAS configuration");
         return MBPT_EINVAL;
@@ -351,6 +351,8 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         bool hole = d.line_src[(int)d.chord_line[c]] > d.line_dst[(int)d.chord_line[c]];
         r->chord_lo[c] = hole ? 0.0 : kfmin;
         r->chord_rng[c] = hole ? kfmax : ph.K_max - kfmin;
+        r->chord_lo_f[c] = (float)r->chord_lo[c];
+        r->chord_rng_f[c] = (float)r->chord_rng[c];
     }
     // --- vertices
     for (int v = 0; v < n; ++v) {

@@ -44,6 +44,7 @@ struct alignas(16) DiagRec {
     uint32_t loop_mask[kMaxTerms][kMaxLoops];
     // chord sampling: radial range [lo, lo + rng]
     double chord_lo[8], chord_rng[8];
+    float chord_lo_f[8], chord_rng_f[8];
     // physics
     double kf2_n, kf2_p;                         // squared Fermi momenta (0 = species absent)
     double CS, CY4, mpi2_4;                      // with P = 2p: V = [C_S + 4C_Y/(|P-P'|^2 + 4m_pi^2)] F

@@ -117,15 +117,39 @@ __device__ __forceinline__ void load_record(DiagRec* dst, const DiagRec* src) {
     for (int i = threadIdx.x; i < (int)(sizeof(DiagRec) / 16); i += blockDim.x) d[i] = s[i];
 }
 
+// The FP32 sampling map needs every bin wider than float resolution; an iteration whose grid has a
+// narrower bin samples with the FP64 map instead (decided per integral and iteration, so every chunk
+// of the integral takes the same path).  Must be called by every thread of the block.
+__device__ __forceinline__ int effective_precision(int prec, const double* grid, int d, int nb) {
+    if (prec != MBPT_MIXED) return prec;
+    int bad = 0;
+    for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
+        const int a = idx / nb, i = idx - a * nb;
+        const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
+        if (e1 > e0 && !((float)e1 > (float)e0)) bad = 1;
+    }
+    return __syncthreads_or(bad) ? MBPT_MIXED_MAP64 : prec;
+}
+
 __device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, int nb, int prec) {
     for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
         const int a = idx / nb, i = idx - a * nb;
         const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
         const double de = e1 - e0;
-        Grid2 g;
-        g.de = de;
-        g.a = (prec == MBPT_FP64) ? e0 : e0 - de;
-        gs[a * kGridStride + i] = g;
+        if (prec == MBPT_MIXED) {
+            // FP32 bins tile [0, 1] exactly: width = difference of the rounded edges
+            Grid4f g;
+            g.e = (float)e0;
+            g.de = (float)e1 - g.e;
+            g.pad0 = 0.0f;
+            g.pad1 = 0.0f;
+            reinterpret_cast<Grid4f*>(gs)[a * kGridStride + i] = g;
+        } else {
+            Grid2 g;
+            g.de = de;
+            g.a = (prec == MBPT_FP64) ? e0 : e0 - de;
+            gs[a * kGridStride + i] = g;
+        }
     }
 }
 
@@ -146,8 +170,8 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
             const SampleOut o = eval_sample<N, PREC>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1, nullptr);
             sw += o.w;
             sw2 = fma(o.w, o.w, sw2);
-            if (o.w != 0.0) {
-                const float wf = (float)o.w;
+            if (nonzero(o.w)) {
+                const float wf = narrow_trunc(o.w);
                 float w2 = wf * wf;
                 if (!(w2 <= 3.0e38f)) w2 = 3.0e38f;
 #pragma unroll
@@ -208,21 +232,26 @@ __global__ void __launch_bounds__(TPB, MINB) k_iterate_t(WorkHeader* hdr, const 
         const WorkItem& W = items[S.item];
         load_record(&S.rec, W.rec);
         __syncthreads();
-        const int d = S.rec.d, nb = S.rec.nb, prec = S.rec.precision, order = S.rec.order;
+        const int d = S.rec.d, nb = S.rec.nb, order = S.rec.order;
+        const int prec = effective_precision(S.rec.precision, W.grid, d, nb);
         load_grid(S.grid, W.grid, d, nb, prec);
         for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
         __syncthreads();
         double sw = 0.0, sw2 = 0.0;
         const uint32_t cl = chunk - W.chunk_begin;
-        switch (order * 2 + prec) {
-            case 2 * 2 + MBPT_FP64: run_chunk<2, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 2 * 2 + MBPT_MIXED: run_chunk<2, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
-            case 3 * 2 + MBPT_FP64: run_chunk<3, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 3 * 2 + MBPT_MIXED: run_chunk<3, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
-            case 4 * 2 + MBPT_FP64: run_chunk<4, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 4 * 2 + MBPT_MIXED: run_chunk<4, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
-            case 5 * 2 + MBPT_FP64: run_chunk<5, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 5 * 2 + MBPT_MIXED: run_chunk<5, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+        switch (order * 3 + prec) {
+            case 2 * 3 + MBPT_FP64: run_chunk<2, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 2 * 3 + MBPT_MIXED: run_chunk<2, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+            case 2 * 3 + MBPT_MIXED_MAP64: run_chunk<2, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
+            case 3 * 3 + MBPT_FP64: run_chunk<3, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 3 * 3 + MBPT_MIXED: run_chunk<3, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+            case 3 * 3 + MBPT_MIXED_MAP64: run_chunk<3, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
+            case 4 * 3 + MBPT_FP64: run_chunk<4, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 4 * 3 + MBPT_MIXED: run_chunk<4, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+            case 4 * 3 + MBPT_MIXED_MAP64: run_chunk<4, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
+            case 5 * 3 + MBPT_FP64: run_chunk<5, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
+            case 5 * 3 + MBPT_MIXED: run_chunk<5, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
+            case 5 * 3 + MBPT_MIXED_MAP64: run_chunk<5, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
             default:
                 if (tid == 0) atomicOr(&hdr->error, 2u);
         }
@@ -417,23 +446,28 @@ __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, const double* 
     __shared__ Grid2 gs[kMaxD * kGridStride];
     load_record(&R, rec);
     __syncthreads();
-    load_grid(gs, grid, R.d, R.nb, R.precision);
+    const int prec = effective_precision(R.precision, grid, R.d, R.nb);
+    load_grid(gs, grid, R.d, R.nb, prec);
     __syncthreads();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const uint32_t s = (uint32_t)(first + i);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    double* x = xo + i * R.d;
+    double* x = xo ? xo + i * R.d : nullptr;
     double* w = wo + i;
-    switch (R.order * 2 + R.precision) {
-        case 2 * 2 + MBPT_FP64: dump_one<2, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 2 * 2 + MBPT_MIXED: dump_one<2, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 3 * 2 + MBPT_FP64: dump_one<3, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 3 * 2 + MBPT_MIXED: dump_one<3, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 4 * 2 + MBPT_FP64: dump_one<4, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 4 * 2 + MBPT_MIXED: dump_one<4, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 5 * 2 + MBPT_FP64: dump_one<5, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 5 * 2 + MBPT_MIXED: dump_one<5, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+    switch (R.order * 3 + prec) {
+        case 2 * 3 + MBPT_FP64: dump_one<2, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 2 * 3 + MBPT_MIXED: dump_one<2, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 2 * 3 + MBPT_MIXED_MAP64: dump_one<2, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 3 * 3 + MBPT_FP64: dump_one<3, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 3 * 3 + MBPT_MIXED: dump_one<3, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 3 * 3 + MBPT_MIXED_MAP64: dump_one<3, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 4 * 3 + MBPT_FP64: dump_one<4, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 4 * 3 + MBPT_MIXED: dump_one<4, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 4 * 3 + MBPT_MIXED_MAP64: dump_one<4, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 5 * 3 + MBPT_FP64: dump_one<5, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 5 * 3 + MBPT_MIXED: dump_one<5, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
+        case 5 * 3 + MBPT_MIXED_MAP64: dump_one<5, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
         default: *w = 0.0;
     }
 }
@@ -1022,9 +1056,9 @@ int mbpt_dump_samples(mbpt_diag* g, int64_t iter, int64_t first, int64_t count, 
     if (count == 0) return MBPT_OK;
     mbpt_ctx* c = g->ctx;
     DeviceGuard dg(c->device);
-    double* dx = (double*)c->arena.alloc(sizeof(double) * (size_t)count * g->d);
+    double* dx = x ? (double*)c->arena.alloc(sizeof(double) * (size_t)count * g->d) : nullptr;
     double* dw = (double*)c->arena.alloc(sizeof(double) * (size_t)count);
-    if (!dx || !dw) {
+    if ((x && !dx) || !dw) {
         c->arena.release(dx);
         c->arena.release(dw);
         return fail(MBPT_ENOMEM, "dump_samples: arena exhausted");

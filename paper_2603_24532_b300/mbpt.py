@@ -22,6 +22,7 @@ MBPT_ENUMERIC = -6
 MBPT_EBUSY = -7
 MBPT_FP64 = 0
 MBPT_MIXED = 1
+MBPT_MIXED_MAP64 = 2
 MAX_ORDER = 6
 MAX_LINES = 12
 MAX_CHORDS = 7
@@ -347,6 +348,14 @@ def state_grid(image: bytes, d: int, nb: int) -> np.ndarray:
 def state_last_hist(image: bytes, d: int, nb: int) -> np.ndarray:
     off = STATE_HEADER_BYTES + DIAGSTATE_BYTES + 8 * d * (nb + 1)
     return np.frombuffer(image, dtype=np.float64, count=d * nb, offset=off).reshape(d, nb).copy()
+
+
+def state_with_iter(image: bytes, iteration: int) -> bytes:
+    """Image with the iteration counter (the next iteration's Philox counter word 1) replaced."""
+    off = STATE_HEADER_BYTES + 7 * 8 + 8
+    b = bytearray(image)
+    b[off:off + 4] = int(iteration).to_bytes(4, "little", signed=True)
+    return bytes(b)
 
 
 def state_with_grid(image: bytes, grid: np.ndarray) -> bytes:

@@ -53,7 +53,8 @@ def oracle_dump(D, po, grid, seed, sid, t, first, count):
 
 
 def near_surface(D, po, x, rel=1e-9):
-    """True where some line momentum sits within rel*kF^2 of a Fermi surface."""
+    """(mixed precision places samples with an FP32 map: compare with rel ~ 1e-5 there)"""
+    # True where some line momentum sits within rel*kF^2 of a Fermi surface.
     kf2 = [k * k for k in (po.kF_n, po.kF_p) if k > 0]
     out = np.zeros(len(x), dtype=bool)
     for i in range(len(x)):

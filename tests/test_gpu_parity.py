@@ -77,23 +77,25 @@ def test_per_sample_parity_fp64(ctx, n, matter, k):
             M.mbpt_destroy_diagram(g)
 
 
+@pytest.mark.parametrize("prec", [M.MBPT_MIXED, M.MBPT_MIXED_MAP64])
 @pytest.mark.parametrize("n,matter", [(3, "pnm"), (4, "snm"), (5, "pnm"), (4, "asym")])
-def test_mixed_precision_deviation(ctx, n, matter):
-    """Mixed mode (FP32 potentials and spin sum) on identical samples: aggregate
-    deviation from the FP64 oracle below 1e-4 relative."""
+def test_mixed_precision_deviation(ctx, n, matter, prec):
+    """Mixed modes (FP32 potentials and spin sum; FP32 or FP64 sampling map) on identical
+    samples: aggregate deviation from the FP64 oracle below 1e-4 relative."""
     rng = np.random.default_rng(7 * n)
     po, pm = matter_pair(matter)
     for D in _pick(n, 3, rng):
         if O.is_anomalous(D):
             continue
-        cfg = M.vegas_cfg(samples=1 << 16, seed=99, stream_id=D.diagram_id, precision=M.MBPT_MIXED)
+        cfg = M.vegas_cfg(samples=1 << 16, seed=99, stream_id=D.diagram_id, precision=prec)
         g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
         try:
             grid = random_grid(D.d, 50, rng, strength=0.5)
             M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
             xg, wg = M.mbpt_dump_samples(g, 0, 0, 2048, D.d)
             xo, wo = oracle_dump(D, po, grid, 99, D.diagram_id, 0, 0, 2048)
-            ok = ~near_surface(D, po, xo)
+            assert np.max(np.abs(xg - xo)) <= (4 * EPS if prec == M.MBPT_MIXED_MAP64 else 2e-7)
+            ok = ~near_surface(D, po, xo, rel=1e-5 if prec == M.MBPT_MIXED else 1e-9)
             l1 = np.sum(np.abs(wg[ok] - wo[ok])) / max(np.sum(np.abs(wo[ok])), 1e-300)
             assert l1 < 1e-4, l1
             s_o = np.sum(wo[ok])
@@ -102,7 +104,7 @@ def test_mixed_precision_deviation(ctx, n, matter):
             M.mbpt_destroy_diagram(g)
 
 
-@pytest.mark.parametrize("prec", [M.MBPT_FP64, M.MBPT_MIXED])
+@pytest.mark.parametrize("prec", [M.MBPT_FP64, M.MBPT_MIXED, M.MBPT_MIXED_MAP64])
 def test_one_iteration_sums_histogram_and_refinement(ctx, prec):
     """One batched iteration on a ragged sample count: sum w, sum w^2 against the
     oracle on the same grid; the histogram (FP32 accumulation) to 1e-5; the refined
