@@ -42,6 +42,8 @@ WORKLOAD = "third-order Hugenholtz diagrams (pp, hh, ph), pure neutron matter, k
 # Newton reciprocal of the denominator product (4) = 16.
 FP64_OPS_ALL = 48.0
 FP64_OPS_LIVE_EXTRA = 16.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_iterate launch (profiles/k_iterate_third_order_scan.md)
+TRAFFIC_BYTES = 337152
 # nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second
 FP64_PEAK_NOMINAL = 1.25e12 / 2.0
 # measured DFMA issue rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu)
@@ -309,7 +311,9 @@ def run_gpu(args):
                      "peak_kind": "nominal 1.25 TFLOP/s FP64 of the recipe at 2032 MHz",
                      "frac_of_measured_dfma": achieved / FP64_PEAK_MEASURED,
                      "ops_per_sample": ops, "live_fraction": live_frac, "kernel": "k_iterate",
-                     "kernel_ms": it_ms, "traffic": None},
+                     "kernel_ms": it_ms, "traffic": TRAFFIC_BYTES,
+                     "traffic_note": "ncu dram read+write of one k_iterate launch on the 30 x 2^20 profiling case "
+                                     "(grids and records; chunk slots stay in L2), not proportional to samples"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
