@@ -108,11 +108,11 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_integrals(M, ctx, precision, seed_base=1, stream_base=0):
+def build_integrals(M, ctx, precision, seed_base=1, stream_base=0, map_kind=0):
     descs = M.mbpt_generate(ORDER)
     gs, meta = [], []
     for ki, kf in enumerate(KF_SCAN):
-        ph = M.physics(kF_n=kf, kF_p=0.0, K_max=kf + 6.0)
+        ph = M.physics(kF_n=kf, kF_p=0.0, K_max=kf + 6.0, map_kind=map_kind)
         for d in descs:
             sid = stream_base + 100 * ki + d.diagram_id
             cfg = M.vegas_cfg(samples=SAMPLES, seed=seed_base, stream_id=sid, precision=precision)
@@ -255,6 +255,15 @@ def run_gpu(args):
     for g in gs:
         M.mbpt_destroy_diagram(g)
 
+    # ---- the same scan with the rotational reduction of the chord map (9D instead of 12D; NEXT row)
+    grot, _ = build_integrals(M, ctx, M.MBPT_MIXED, seed_base=1 + rank, stream_base=10000 * rank, map_kind=1)
+    timed_steps(grot, args.warmup)
+    itrot, strot = timed_steps(grot, max(4, args.steps // 4))
+    res_rot = M.mbpt_estimate_batch(grot)
+    for g in grot:
+        M.mbpt_destroy_diagram(g)
+    vrot = world * evals_step / (float(np.mean(strot)) * 1e-3)
+
     # ---- FP64 batched, same workload (tuned the same way)
     g64, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
     tuned64 = autotune(ctx, g64, trials=1)["best"] if args.autotune else None
@@ -286,6 +295,7 @@ def run_gpu(args):
         return len(results) / (need / rate) if need > 0 else None
 
     d_mixed = diags_per_s(res_mixed, value)
+    d_rot = diags_per_s(res_rot, vrot)
     d_k0 = diags_per_s(res64, vk0)
     M.mbpt_ctx_destroy(ctx)
     if dist:
@@ -323,7 +333,10 @@ def run_gpu(args):
         "speedup_vs_k0": value / vk0,
         "mixed_vs_fp64_deviation": precision_dev,
         "diagrams_to_0p1pct_per_s": {"batched_mixed": d_mixed, "k0_plain_fp64": d_k0,
-                                     "ratio": (d_mixed / d_k0) if (d_mixed and d_k0) else None},
+                                     "ratio": (d_mixed / d_k0) if (d_mixed and d_k0) else None,
+                                     "batched_mixed_rotational_9d": d_rot},
+        "rotational_9d": {"value": vrot, "unit": UNIT, "kernel_ms": float(np.mean(itrot)),
+                          "note": "same scan with chord 0 along z and chord 1 in the xz plane (d = 9)"},
     }
     print(json.dumps(line))
     if dist:

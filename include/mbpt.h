@@ -111,15 +111,18 @@ typedef struct {
  * A species with kF = 0 is absent: pure neutron matter has kF_p = 0,
  * symmetric matter kF_n = kF_p.  Hole chords are sampled in [0, max kF],
  * particle chords in [smallest present kF, K_max].
- * map_kind 0: chord momentum from (k, cos theta, phi) with a rational azimuth
- * (the only map implemented).
+ * map_kind 0: every chord momentum from (k, cos theta, phi), rational azimuth;
+ * d = 3(order+1) dimensions.  map_kind 1: rotational invariance of the
+ * integrand (Sec. III.C, "N_dim - 3"): chord 0 along z (k only), chord 1 in the
+ * xz plane (k, cos theta), the fixed angles integrated analytically (4 pi 2 pi);
+ * d = 3 order.
  */
 typedef struct {
     double kF_n, kF_p;
     double hbar2_over_m;
     double C_S, C_Y, m_pi, Lambda;
     int32_t reg_power;       /* even, 2..8 */
-    int32_t map_kind;        /* 0 */
+    int32_t map_kind;        /* 0 or 1 */
     double K_max;
 } mbpt_physics;
 

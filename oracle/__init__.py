@@ -319,10 +319,15 @@ class Physics:
     Lam: float = 2.0
     reg_power: int = 4
     K_max: float = 7.0
+    map_kind: int = 0
 
     def array(self) -> np.ndarray:
         return np.asarray([self.kF_n, self.kF_p, self.hbar2_over_m, self.C_S, self.C_Y, self.m_pi, self.Lam,
-                           float(self.reg_power), self.K_max], dtype=np.float64)
+                           float(self.reg_power), self.K_max, float(self.map_kind)], dtype=np.float64)
+
+    def dim(self, D: "Diagram") -> int:
+        """integration dimension of diagram D under this chord map"""
+        return D.d - 3 * self.map_kind
 
     @property
     def density(self) -> float:
@@ -479,7 +484,7 @@ def vegas(D: Optional[Diagram], ph, n_iter: int, n_samples: int, seed: int = 1, 
           alpha: float = 1.5, threads: Optional[int] = None, kind: int = 0, d: Optional[int] = None):
     """Full VEGAS run: iterate, refine after every iteration, combine all iterations."""
     if d is None:
-        d = D.d if kind == 0 else 6
+        d = (ph.dim(D) if isinstance(ph, Physics) else D.d) if kind == 0 else 6
     grid = uniform_grid(d, nb)
     means, vars_ = [], []
     for t in range(n_iter):

@@ -228,6 +228,7 @@ int oracle_derive(int n, const int* lines, const int* ports, const int* chords, 
  *   ph[3] C_S (MeV fm^3), ph[4] C_Y (MeV fm), ph[5] m_pi (fm^-1),
  *   ph[6] Lambda (fm^-1), ph[7] regulator exponent (even integer),
  *   ph[8] K_max: upper end of the radial range of particle chords (fm^-1)
+ *   ph[9] chord map: 0 full directions, 1 rotational reduction (see chord_momenta)
  * The potential is V(p, p') = [C_S + C_Y / (|p - p'|^2 + m_pi^2)]
  *                             * exp(-(|p|/Lambda)^r - (|p'|/Lambda)^r).
  * ------------------------------------------------------------------------- */
@@ -384,19 +385,48 @@ static double density(const double* ph) {
  * condition number sum_m (sum_{l in C_m} eps_l) / |D_m| used by the parity
  * tolerance.
  */
+/*
+ * Chord momenta of the point x and the Jacobian of the chord map.  ph[9] selects the map:
+ *   0: every chord from chord_map on axes 3c..3c+2;
+ *   1: rotational invariance of the integrand (Sec. III.C): chord 0 = (0, 0, k) from axis 0 with
+ *      Jacobian 4 pi range k^2 (all its directions integrated out), chord 1 =
+ *      k (sin t, 0, cos t) from axes 1, 2 (cos t = 2 x - 1) with Jacobian 2 pi 2 range k^2 (all its
+ *      azimuths integrated out), chords c >= 2 from chord_map on axes 3c-3..3c-1.
+ */
+static double chord_momenta(const int* info, const double* ph, const double* x, double* chord_k) {
+    int nc = info[OI_NC];
+    int mapk = (int)ph[9];
+    double jac = 1.0;
+    for (int c = 0; c < nc; ++c) {
+        int l = info[OI_CHORD + c];
+        double lo, hi;
+        chord_range(ph, line_is_hole(info, l), &lo, &hi);
+        double* out = chord_k + 3 * c;
+        if (mapk == 1 && c == 0) {
+            double k = lo + (hi - lo) * x[0];
+            out[0] = 0.0; out[1] = 0.0; out[2] = k;
+            jac *= 4.0 * M_PI * (hi - lo) * k * k;
+        } else if (mapk == 1 && c == 1) {
+            double k = lo + (hi - lo) * x[1];
+            double ct = 2.0 * x[2] - 1.0;
+            double st = 2.0 * sqrt(x[2] * (1.0 - x[2]));
+            out[0] = k * st; out[1] = 0.0; out[2] = k * ct;
+            jac *= 2.0 * M_PI * 2.0 * (hi - lo) * k * k;
+        } else {
+            int off = mapk == 1 ? 3 * c - 3 : 3 * c;
+            jac *= chord_map(x + off, lo, hi, out);
+        }
+    }
+    return jac;
+}
+
 double oracle_integrand_momenta(const int* info, const double* ph, const double* chord_k_flat, double* cond);
 
 double oracle_integrand(const int* info, const double* ph, const double* x, double* cond) {
     int nc = info[OI_NC];
     double chord_k[O_MAXC * 3];
-    double jac = 1.0;
     if (cond) *cond = 0.0;
-    for (int c = 0; c < nc; ++c) {
-        int l = info[OI_CHORD + c];
-        double lo, hi;
-        chord_range(ph, line_is_hole(info, l), &lo, &hi);
-        jac *= chord_map(x + 3 * c, lo, hi, chord_k + 3 * c);
-    }
+    double jac = chord_momenta(info, ph, x, chord_k);
     double core = oracle_integrand_momenta(info, ph, chord_k, cond);
     if (core == 0.0) return 0.0;
     return jac * core / pow(2.0 * M_PI, 3.0 * nc);
@@ -470,12 +500,7 @@ double oracle_integrand_momenta(const int* info, const double* ph, const double*
 void oracle_line_ksq(const int* info, const double* ph, const double* x, double* out) {
     int nl = info[OI_NL], nc = info[OI_NC];
     double chord_k[O_MAXC * 3];
-    for (int c = 0; c < nc; ++c) {
-        int l = info[OI_CHORD + c];
-        double lo, hi;
-        chord_range(ph, line_is_hole(info, l), &lo, &hi);
-        chord_map(x + 3 * c, lo, hi, chord_k + 3 * c);
-    }
+    chord_momenta(info, ph, x, chord_k);
     for (int l = 0; l < nl; ++l) {
         double k[3];
         for (int a = 0; a < 3; ++a) {

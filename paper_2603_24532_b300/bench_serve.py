@@ -36,10 +36,17 @@ def main():
     st = S.latency_stats(done)
     n_int = sum(len(r.integrals) for r in done)
     caps = {c: sum(1 for r in done if r.cap == c) for c in (2, 3, 4)}
+    met = [r for r in done if r.energy is not None and r.sigma is not None and r.sigma <= r.target * abs(r.energy)]
+    rounds = [r.rounds for r in done]
     out = {"workload": "EOS request stream, Poisson rate %.1f/s seed %d, %d requests" % (a.rate, a.seed, a.requests),
            "completed": len(done), "wall_s": wall, "latency": st,
            "diagrams_per_s": n_int / wall, "evals_per_s": srv.evals / wall, "rounds": srv.rounds,
-           "completed_by_cap": caps, "budget_bytes": srv.budget}
+           "completed_by_cap": caps, "budget_bytes": srv.budget,
+           "target_met_fraction": len(met) / max(1, len(done)),
+           "rounds_per_request": {"median": float(sorted(rounds)[len(rounds) // 2]) if rounds else None,
+                                  "max": max(rounds) if rounds else None},
+           "example": [{"n": r.n_dens, "delta": r.delta, "cap": r.cap, "target": r.target, "E_corr": r.energy,
+                        "sigma": r.sigma, "per_order": r.per_order, "latency_s": r.latency} for r in done[:3]]}
     print(json.dumps(out))
     be.close()
 

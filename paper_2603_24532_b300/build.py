@@ -11,8 +11,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmbpt.so")
-SOURCES = ["mbpt_runtime.cu", "mbpt_host.cpp"]
-HEADERS = ["mbpt_device.cuh", "mbpt_internal.h", os.path.join("..", "..", "include", "mbpt.h")]
+SOURCES = ["mbpt_runtime.cu", "mbpt_host.cpp", "mbpt_k_misc.cu", "mbpt_k_iterate_256x2.cu",
+           "mbpt_k_iterate_128x4.cu", "mbpt_k_iterate_256x1.cu", "mbpt_k_iterate_128x3.cu"]
+HEADERS = ["mbpt_device.cuh", "mbpt_kernels.cuh", "mbpt_kernels.h", "mbpt_internal.h",
+           os.path.join("..", "..", "include", "mbpt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,15 +36,32 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit in parallel (the kernel shapes are separate units), then link."""
     if not force and not _stale():
         return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+    import concurrent.futures
+    import tempfile
+    tag = "%d" % os.getpid()
+    odir = tempfile.mkdtemp(prefix="mbpt_build_")
+
+    def compile_one(src):
+        obj = os.path.join(odir, os.path.basename(src) + ".o")
+        cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", "-o", obj,
+               os.path.join(CSRC, src)]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        subprocess.check_call(cmd)
+        return obj
+
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB + ".tmp" + tag
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp] + objs)
     os.replace(tmp, LIB)
+    for o in objs:
+        os.remove(o)
+    os.rmdir(odir)
     return LIB
 
 

@@ -179,12 +179,25 @@ __device__ __forceinline__ void vertex_pot_f64(const DiagRec& R, double Px, doub
 //  s: sample index within the iteration, t: iteration, sid: stream id, (k0,k1): key
 //  x_out (optional): the mapped point in [0,1]^d
 // ---------------------------------------------------------------------------
-template <int N, int PREC>
+// Axes of chord c: map 0 gives every chord (k, cos t, phi) on axes 3c..3c+2.  Map 1 (rotational
+// invariance, Sec. III.C) puts chord 0 on the z axis (k only, axis 0) and chord 1 in the xz plane
+// (k, cos t on axes 1, 2); chords c >= 2 use axes 3c-3..3c-1.  The fixed angles integrate to
+// 4 pi x 2 pi, folded into pref with the other constant Jacobian factors.
+template <int MAPK>
+__device__ __forceinline__ constexpr int chord_axis(int c) {
+    return MAPK == 0 ? 3 * c : (c == 0 ? 0 : (c == 1 ? 1 : 3 * c - 3));
+}
+template <int MAPK>
+__device__ __forceinline__ constexpr int chord_kind(int c) {   // 0 full direction, 1 z axis, 2 xz plane
+    return MAPK == 0 ? 0 : (c == 0 ? 1 : (c == 1 ? 2 : 0));
+}
+
+template <int N, int PREC, int MAPK>
 __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* __restrict__ gs, uint32_t s,
                                                  uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1,
                                                  double* x_out) {
     constexpr int L = N + 1;          // chords
-    constexpr int D = 3 * L;          // dimensions
+    constexpr int D = 3 * L - 3 * MAPK;   // dimensions
     constexpr int NL = 2 * N;         // lines
     constexpr int NBLK = (D + 3) / 4; // Philox blocks
     SampleOut o;
@@ -243,26 +256,50 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         jv = zero_bin ? 0.0 : __longlong_as_double(__double_as_longlong(widen_pos_normal(mp)) + ((long long)ex << 52));
 #pragma unroll
         for (int c = 0; c < L; ++c) {
-            const float x0 = xf[3 * c], x1 = xf[3 * c + 1], x2 = xf[3 * c + 2];
-            const float k = fmaf(R.chord_rng_f[c], x0, R.chord_lo_f[c]);
-            const float ct = fmaf(2.0f, x1, -1.0f);
-            const float sq = sqrtf(fmaf(-x1, x1, x1));
-            const float a = fmaf(-x2, x2, x2);
-            const float b = x2 - 0.5f;
-            const float bb = b * b;
-            const float mm = fmaf(a, a, bb);
-            const float rr = __frcp_rn(mm);
-            const float R2 = 2.0f * sq * rr;
-            const float nx = R2 * fmaf(a, a, -bb), ny = R2 * ((a + a) * b), nz = ct;
+            const int ax = chord_axis<MAPK>(c), kind = chord_kind<MAPK>(c);
+            const float k = fmaf(R.chord_rng_f[c], xf[ax], R.chord_lo_f[c]);
             const double kd = widen_f(k);
-            K[0][c] = kd * widen_f(nx);      // exact: 24-bit x 24-bit
-            K[1][c] = kd * widen_f(ny);
-            K[2][c] = kd * widen_f(nz);
-            U[c] = fma(K[0][c], K[0][c], fma(K[1][c], K[1][c], K[2][c] * K[2][c]));
-            lf[0][c] = k * nx;
-            lf[1][c] = k * ny;
-            lf[2][c] = k * nz;
-            jc *= widen_f(k * k * ((0.5f - a) * rr));
+            if (kind == 1) {
+                K[0][c] = 0.0;
+                K[1][c] = 0.0;
+                K[2][c] = kd;
+                U[c] = kd * kd;
+                lf[0][c] = 0.0f;
+                lf[1][c] = 0.0f;
+                lf[2][c] = k;
+                jc *= widen_f(k * k);
+            } else if (kind == 2) {
+                const float x1 = xf[ax + 1];
+                const float ct = fmaf(2.0f, x1, -1.0f);
+                const float st = 2.0f * sqrtf(fmaf(-x1, x1, x1));
+                K[0][c] = kd * widen_f(st);
+                K[1][c] = 0.0;
+                K[2][c] = kd * widen_f(ct);
+                U[c] = fma(K[0][c], K[0][c], K[2][c] * K[2][c]);
+                lf[0][c] = k * st;
+                lf[1][c] = 0.0f;
+                lf[2][c] = k * ct;
+                jc *= widen_f(k * k);
+            } else {
+                const float x1 = xf[ax + 1], x2 = xf[ax + 2];
+                const float ct = fmaf(2.0f, x1, -1.0f);
+                const float sq = sqrtf(fmaf(-x1, x1, x1));
+                const float a = fmaf(-x2, x2, x2);
+                const float b = x2 - 0.5f;
+                const float bb = b * b;
+                const float mm = fmaf(a, a, bb);
+                const float rr = __frcp_rn(mm);
+                const float R2 = 2.0f * sq * rr;
+                const float nx = R2 * fmaf(a, a, -bb), ny = R2 * ((a + a) * b), nz = ct;
+                K[0][c] = kd * widen_f(nx);      // exact: 24-bit x 24-bit
+                K[1][c] = kd * widen_f(ny);
+                K[2][c] = kd * widen_f(nz);
+                U[c] = fma(K[0][c], K[0][c], fma(K[1][c], K[1][c], K[2][c] * K[2][c]));
+                lf[0][c] = k * nx;
+                lf[1][c] = k * ny;
+                lf[2][c] = k * nz;
+                jc *= widen_f(k * k * ((0.5f - a) * rr));
+            }
         }
     } else {
         double x[D];
@@ -281,24 +318,40 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         }
 #pragma unroll
         for (int c = 0; c < L; ++c) {
-            const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-            const double k = fma(R.chord_rng[c], x0, R.chord_lo[c]);
-            const double ct = fma(2.0, x1, -1.0);
-            const double sq = sqrt_nr(fma(-x1, x1, x1));
-            const double a = fma(-x2, x2, x2);
-            const double b = x2 - 0.5;
-            const double bb = b * b;
-            const double mm = fma(a, a, bb);
-            const double rr = rcp_nr(mm);           // mm = (1/2 - a)^2 in [1/16, 1/4]
-            const double ncos = fma(a, a, -bb);
-            const double nsin = (a + a) * b;
-            const double R2 = (k + k) * sq * rr;
-            K[0][c] = R2 * ncos;
-            K[1][c] = R2 * nsin;
-            K[2][c] = k * ct;
+            const int ax = chord_axis<MAPK>(c), kind = chord_kind<MAPK>(c);
+            const double k = fma(R.chord_rng[c], x[ax], R.chord_lo[c]);
             const double k2 = k * k;
+            if (kind == 1) {
+                K[0][c] = 0.0;
+                K[1][c] = 0.0;
+                K[2][c] = k;
+                jc *= k2;
+            } else if (kind == 2) {
+                const double x1 = x[ax + 1];
+                const double ct = fma(2.0, x1, -1.0);
+                const double sq = sqrt_nr(fma(-x1, x1, x1));
+                K[0][c] = (k + k) * sq;
+                K[1][c] = 0.0;
+                K[2][c] = k * ct;
+                jc *= k2;
+            } else {
+                const double x1 = x[ax + 1], x2 = x[ax + 2];
+                const double ct = fma(2.0, x1, -1.0);
+                const double sq = sqrt_nr(fma(-x1, x1, x1));
+                const double a = fma(-x2, x2, x2);
+                const double b = x2 - 0.5;
+                const double bb = b * b;
+                const double mm = fma(a, a, bb);
+                const double rr = rcp_nr(mm);           // mm = (1/2 - a)^2 in [1/16, 1/4]
+                const double ncos = fma(a, a, -bb);
+                const double nsin = (a + a) * b;
+                const double R2 = (k + k) * sq * rr;
+                K[0][c] = R2 * ncos;
+                K[1][c] = R2 * nsin;
+                K[2][c] = k * ct;
+                jc *= k2 * ((0.5 - a) * rr);
+            }
             U[c] = k2;
-            jc *= k2 * ((0.5 - a) * rr);
             if (PREC != MBPT_FP64) {
                 lf[0][c] = narrow_trunc(K[0][c]);
                 lf[1][c] = narrow_trunc(K[1][c]);
@@ -306,6 +359,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
             }
         }
     }
+
     // --- tree lines from momentum conservation: k = k_a + k_b - k_c
 #pragma unroll
     for (int j = 0; j < N - 1; ++j) {
@@ -443,8 +497,12 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         S = sum;
     }
 
-    // --- weight: w = pref * J_vegas * J_chords * S / prod_m D~_m
-    if (PREC == MBPT_FP64) o.w = (R.pref * (jv * jc) * S) / Dprod;
+    // --- weight: w = pref * J_vegas * J_chords * S / prod_m D~_m.  A spin sum that is exactly zero
+    // (asymmetric matter: every line passes its step for some species, but no species assignment
+    // is consistent along the loops, e.g. a hole and a particle of equal momentum in different
+    // species) gives zero; the cut of such a pair can have D = 0, so the division is skipped.
+    if (!nonzero(S)) o.w = 0.0;
+    else if (PREC == MBPT_FP64) o.w = (R.pref * (jv * jc) * S) / Dprod;
     else o.w = (R.pref * (jv * jc) * S) * rcp_scaled(Dprod);
     return o;
 }

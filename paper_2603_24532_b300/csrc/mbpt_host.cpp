@@ -272,8 +272,8 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
     if (ph.kF_n > 0.0 && ph.kF_n < kfmin) kfmin = ph.kF_n;
     if (ph.kF_p > 0.0 && ph.kF_p < kfmin) kfmin = ph.kF_p;
     if (!(ph.K_max > kfmax) || !(ph.hbar2_over_m > 0.0) || !(ph.Lambda > 0.0) || !(ph.m_pi >= 0.0) ||
-        ph.reg_power < 2 || ph.reg_power > 8 || (ph.reg_power & 1) || ph.map_kind != 0) {
-        set_err(err, errlen, "invalid physics parameters (K_max > kF, hbar2_over_m > 0, Lambda > 0, even reg_power 2..8, map_kind 0)");
+        ph.reg_power < 2 || ph.reg_power > 8 || (ph.reg_power & 1) || ph.map_kind < 0 || ph.map_kind > 1) {
+        set_err(err, errlen, "invalid physics parameters (K_max > kF, hbar2_over_m > 0, Lambda > 0, even reg_power 2..8, map_kind 0 or 1)");
         return MBPT_EINVAL;
     }
     if (cfg.n_bins < 2 || cfg.n_bins > MBPT_MAX_BINS || cfg.samples_per_iter < 2 ||
@@ -288,7 +288,8 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
     r->order = n;
     r->n_lines = nl;
     r->n_chords = nc;
-    r->d = 3 * nc;
+    r->map_kind = ph.map_kind;
+    r->d = 3 * nc - 3 * ph.map_kind;
     r->nb = cfg.n_bins;
     r->precision = cfg.precision;
     r->reg_half = ph.reg_power / 2;
@@ -447,10 +448,16 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
     r->regc2f = (float)(r->regc * pow(1.4426950408889634, 1.0 / r->reg_half));
     const double pi = 3.14159265358979323846;
     double dens = (ph.kF_n * ph.kF_n * ph.kF_n + ph.kF_p * ph.kF_p * ph.kF_p) / (3.0 * pi * pi);
-    // (-1)^h 2^-n_eq / n_dens * (2pi)^-3(n+1) * (2/(hbar^2/m))^(n-1) * N_b^d * prod_c 4 (range_c)
+    // (-1)^h 2^-n_eq / n_dens * (2pi)^-3(n+1) * (2/(hbar^2/m))^(n-1) * N_b^d * chord constants:
+    // 4 range_c per full chord (dcos/dx = 2, dphi/dx = 2/(1/2 - a) with the 1/(1/2 - a) per sample);
+    // with the rotational reduction 4 pi range_0 (all directions of chord 0) and
+    // 2 x 2 pi range_1 (polar angle, all azimuths of chord 1)
     double pref = ((h & 1) ? -1.0 : 1.0) / pow(2.0, neq) / pow(2.0 * pi, 3.0 * nc) / dens *
-                  pow(2.0 / ph.hbar2_over_m, n - 1) * pow((double)cfg.n_bins, 3.0 * nc);
-    for (int c = 0; c < nc; ++c) pref *= 4.0 * r->chord_rng[c];
+                  pow(2.0 / ph.hbar2_over_m, n - 1) * pow((double)cfg.n_bins, (double)r->d);
+    for (int c = 0; c < nc; ++c) {
+        if (ph.map_kind == 1 && c < 2) pref *= 4.0 * pi * r->chord_rng[c];
+        else pref *= 4.0 * r->chord_rng[c];
+    }
     r->pref = pref;
     return MBPT_OK;
 }

@@ -52,7 +52,7 @@ struct alignas(16) DiagRec {
     double pref;                                 // all constant factors of the weight
     float CSf, CY4f, mpi2_4f, regc2f;            // FP32 copies; regc2f folds in log2(e)^(1/reg_half)
     int8_t line_slot[MBPT_MAX_LINES];            // slot of each descriptor line
-    int8_t pad[4];
+    int32_t map_kind;                            // 0: full chord directions; 1: rotational reduction
 };
 
 // Per-integral running state (device).

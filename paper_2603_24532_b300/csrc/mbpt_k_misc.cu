@@ -1,0 +1,193 @@
+// Non-templated kernels of libmbpt: finalize (reduction, combination, refinement), sample dump
+// and Philox test hooks.
+#include "mbpt_kernels.cuh"
+#include "mbpt_kernels.h"
+
+namespace mbpt {
+
+// Grid refinement of one axis (Lepage 1978 with (7,1)/8 and (1,6,1)/8 smoothing):
+// dbar -> r = dbar/sum -> m = ((r-1)/ln r)^alpha -> new edges at equal shares of the
+// piecewise-linear cumulative of m.
+__device__ void refine_axis(double* grid, const double* old, const double* h, double* m, int nb, double alpha) {
+    m[0] = (7.0 * h[0] + h[1]) / 8.0;
+    for (int i = 1; i < nb - 1; ++i) m[i] = (h[i - 1] + 6.0 * h[i] + h[i + 1]) / 8.0;
+    m[nb - 1] = (h[nb - 2] + 7.0 * h[nb - 1]) / 8.0;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += m[i];
+    if (!(tot > 0.0)) return;
+    double msum = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        const double r = m[i] / tot;
+        double v;
+        if (r <= 0.0) v = 0.0;
+        else if (r >= 1.0) v = 1.0;
+        else v = pow((r - 1.0) / log(r), alpha);
+        m[i] = v;
+        msum += v;
+    }
+    const double share = msum / nb;
+    int j = 0;
+    double cum = 0.0;
+    for (int k = 1; k < nb; ++k) {
+        const double target = k * share;
+        while (j < nb - 1 && cum + m[j] < target) {
+            cum += m[j];
+            ++j;
+        }
+        double frac = m[j] > 0.0 ? (target - cum) / m[j] : 0.0;
+        if (frac > 1.0) frac = 1.0;
+        if (frac < 0.0) frac = 0.0;
+        grid[k] = old[j] + frac * (old[j + 1] - old[j]);
+    }
+    grid[0] = old[0];
+    grid[nb] = old[nb];
+}
+
+// Per integral: fixed-order reduction of the chunk slots, combination of the iteration into the
+// running estimate, convergence test and grid refinement.
+__global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkItem* __restrict__ items,
+                                                 const double* __restrict__ csum, const float* __restrict__ chist,
+                                                 double* const* __restrict__ last_hist) {
+    __shared__ double hsum[kMaxD * MBPT_MAX_BINS];
+    __shared__ double tmp[kMaxD * MBPT_MAX_BINS];
+    __shared__ double old[kMaxD * (MBPT_MAX_BINS + 1)];
+    __shared__ double red[2][8];
+    __shared__ int s_skip, s_refine;
+    const int tid = threadIdx.x;
+    for (uint32_t ii = blockIdx.x; ii < hdr->n_items; ii += gridDim.x) {
+        const WorkItem& W = items[ii];
+        DiagState* st = W.state;
+        if (tid == 0) s_skip = st->converged;
+        __syncthreads();
+        if (s_skip) {
+            __syncthreads();
+            continue;
+        }
+        double a = 0.0, b = 0.0;
+        for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x) {
+            a += csum[2 * (size_t)(W.chunk_begin + c)];
+            b += csum[2 * (size_t)(W.chunk_begin + c) + 1];
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = a;
+            red[1][tid >> 5] = b;
+        }
+        const int d = W.rec->d, nb = W.rec->nb;
+        for (int i = tid; i < d * nb; i += blockDim.x) {
+            double acc = 0.0;
+            for (uint32_t c = 0; c < W.n_chunks; ++c)
+                acc += (double)chist[(size_t)(W.chunk_begin + c) * (size_t)W.hist_stride + i];
+            hsum[i] = acc;
+            last_hist[ii][i] = acc;
+        }
+        for (int i = tid; i < d * (nb + 1); i += blockDim.x) old[i] = W.grid[i];
+        __syncthreads();
+        if (tid == 0) {
+            double A = 0.0, B = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                A += red[0][w];
+                B += red[1][w];
+            }
+            const double M = (double)W.samples;
+            const double I = A / M;
+            const double var = (B / M - I * I) / (M - 1.0);
+            const int t = st->iter;
+            if (t < kMaxIters) {
+                st->hist_mean[t] = I;
+                st->hist_var[t] = var;
+            }
+            st->last_mean = I;
+            st->last_var = var;
+            if (!isfinite(I) || !isfinite(var)) st->status = MBPT_ENUMERIC;
+            if (var > 0.0) {
+                st->sum_inv_var += 1.0 / var;
+                st->sum_mean_w += I / var;
+                st->n_used += 1;
+            }
+            double mean, sigma, chi2 = 0.0;
+            if (st->sum_inv_var > 0.0) {
+                mean = st->sum_mean_w / st->sum_inv_var;
+                sigma = sqrt(1.0 / st->sum_inv_var);
+                const int T = t + 1 < kMaxIters ? t + 1 : kMaxIters;
+                if (st->n_used > 1) {
+                    double c2 = 0.0;
+                    for (int k = 0; k < T; ++k)
+                        if (st->hist_var[k] > 0.0) {
+                            const double dd = st->hist_mean[k] - mean;
+                            c2 += dd * dd / st->hist_var[k];
+                        }
+                    chi2 = c2 / (st->n_used - 1);
+                }
+            } else {
+                mean = I;
+                sigma = 0.0;
+            }
+            st->mean = mean;
+            st->sigma = sigma;
+            st->chi2 = chi2;
+            st->n_evals += (int64_t)W.samples;
+            st->iter = t + 1;
+            const bool has_target = (W.target_rel > 0.0) || (W.target_abs > 0.0);
+            const double goal = fmax(W.target_rel * fabs(mean), W.target_abs);
+            if (has_target && st->iter >= 2 && sigma <= goal) st->converged = 1;
+            s_refine = (W.freeze_after == 0u) || ((uint32_t)st->iter < W.freeze_after);
+        }
+        __syncthreads();
+        if (s_refine && tid < d) refine_axis(W.grid + tid * (nb + 1), old + tid * (nb + 1), hsum + tid * nb,
+                                             tmp + tid * MBPT_MAX_BINS, nb, W.alpha);
+        __syncthreads();
+    }
+}
+
+// Test hook kernel: samples [first, first+count) of iteration `iter`, mapped point and weight.
+template <int N, int PREC, int MAPK>
+__device__ void dump_one(const DiagRec& R, const Grid2* gs, uint32_t s, uint32_t t, uint32_t sid, uint32_t k0,
+                         uint32_t k1, double* x, double* w) {
+    const SampleOut o = eval_sample<N, PREC, MAPK>(R, gs, s, t, sid, k0, k1, x);
+    *w = o.w;
+}
+
+__global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, const double* grid, uint64_t seed, uint32_t sid,
+                                             uint32_t iter, uint64_t first, uint64_t count, double* xo,
+                                             double* wo) {
+    __shared__ DiagRec R;
+    __shared__ Grid2 gs[kMaxD * kGridStride];
+    load_record(&R, rec);
+    __syncthreads();
+    const int prec = effective_precision(R.precision, grid, R.d, R.nb);
+    load_grid(gs, grid, R.d, R.nb, prec);
+    __syncthreads();
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint32_t s = (uint32_t)(first + i);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    double* x = xo ? xo + i * R.d : nullptr;
+    double* w = wo + i;
+    switch ((R.order * 3 + prec) * 2 + R.map_kind) {
+#define MBPT_CASE(N_, P_, M_) \
+    case (N_ * 3 + P_) * 2 + M_: dump_one<N_, P_, M_>(R, gs, s, iter, sid, k0, k1, x, w); break;
+#define MBPT_CASES(N_) \
+    MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
+    MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)
+        MBPT_CASES(2)
+        MBPT_CASES(3)
+        MBPT_CASES(4)
+        MBPT_CASES(5)
+#undef MBPT_CASES
+#undef MBPT_CASE
+        default: *w = 0.0;
+    }
+}
+
+__global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                         uint64_t count, uint32_t* out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    uint32_t o[4];
+    philox4x32_10(c0 + (uint32_t)i, c1, c2, c3, k0, k1, o);
+    for (int j = 0; j < 4; ++j) out[4 * i + j] = o[j];
+}
+
+}  // namespace mbpt

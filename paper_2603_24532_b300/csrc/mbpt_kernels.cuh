@@ -1,0 +1,194 @@
+// Device kernels of libmbpt (internal): chunk scheduling, the per-chunk sample loop, reductions,
+// refinement.  Templates and inline functions only; the __global__ entry points are defined in
+// separate translation units (one per compiled launch shape) so they build in parallel.
+#pragma once
+#include <stdint.h>
+
+#include "mbpt_device.cuh"
+#include "mbpt_internal.h"
+
+namespace mbpt {
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+template <int NW>
+struct alignas(16) ChunkSmemT {
+    DiagRec rec;
+    Grid2 grid[kMaxD * kGridStride];
+    float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
+    double red[2][NW];
+    uint32_t chunk, item, iter, skip;
+};
+using ChunkSmem = ChunkSmemT<kWarps>;
+
+__device__ __forceinline__ void load_record(DiagRec* dst, const DiagRec* src) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(DiagRec) / 16); i += blockDim.x) d[i] = s[i];
+}
+
+// The FP32 sampling map needs every bin wider than float resolution; an iteration whose grid has a
+// narrower bin samples with the FP64 map instead (decided per integral and iteration, so every chunk
+// of the integral takes the same path).  Must be called by every thread of the block.
+__device__ __forceinline__ int effective_precision(int prec, const double* grid, int d, int nb) {
+    if (prec != MBPT_MIXED) return prec;
+    int bad = 0;
+    for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
+        const int a = idx / nb, i = idx - a * nb;
+        const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
+        if (e1 > e0 && !((float)e1 > (float)e0)) bad = 1;
+    }
+    return __syncthreads_or(bad) ? MBPT_MIXED_MAP64 : prec;
+}
+
+__device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, int nb, int prec) {
+    for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
+        const int a = idx / nb, i = idx - a * nb;
+        const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
+        const double de = e1 - e0;
+        if (prec == MBPT_MIXED) {
+            // FP32 bins tile [0, 1] exactly: width = difference of the rounded edges
+            Grid4f g;
+            g.e = (float)e0;
+            g.de = (float)e1 - g.e;
+            g.pad0 = 0.0f;
+            g.pad1 = 0.0f;
+            reinterpret_cast<Grid4f*>(gs)[a * kGridStride + i] = g;
+        } else {
+            Grid2 g;
+            g.de = de;
+            g.a = (prec == MBPT_FP64) ? e0 : e0 - de;
+            gs[a * kGridStride + i] = g;
+        }
+    }
+}
+
+template <int N, int PREC, int MAPK, int NW>
+__device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
+                                          double& sw2) {
+    const DiagRec& R = S.rec;
+    const uint32_t cs = blockDim.x * (uint32_t)W.spt;
+    const uint64_t first = (uint64_t)chunk_local * cs;
+    const uint32_t t = S.iter;
+    const uint32_t k0 = (uint32_t)W.seed, k1 = (uint32_t)(W.seed >> 32);
+    float* hist = S.hist[threadIdx.x >> 5];
+    const int nb = R.nb;
+    constexpr int D = 3 * (N + 1) - 3 * MAPK;
+    for (int j = 0; j < W.spt; ++j) {
+        const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
+        if (s < W.samples) {
+            const SampleOut o = eval_sample<N, PREC, MAPK>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1, nullptr);
+            sw += o.w;
+            sw2 = fma(o.w, o.w, sw2);
+            if (nonzero(o.w)) {
+                const float wf = narrow_trunc(o.w);
+                float w2 = wf * wf;
+                if (!(w2 <= 3.0e38f)) w2 = 3.0e38f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const uint32_t i = (o.binpack[a >> 2] >> (8 * (a & 3))) & 0xffu;
+                    atomicAdd(&hist[a * nb + i], w2);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Persistent kernel: blocks take chunks (a fixed range of one integral's samples) from a global
+// counter; each chunk's sum w, sum w^2 and histogram go to the chunk's own slot, so the result of a
+// chunk does not depend on which block ran it or what else is in the batch.
+// Compiled in several launch shapes (threads per block x minimum resident blocks, i.e. a register cap);
+// the autotuner picks one per context.
+template <int TPB>
+__device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* __restrict__ items,
+                                               double* __restrict__ csum, float* __restrict__ chist) {
+    constexpr int NW = TPB / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ChunkSmemT<NW>& S = *reinterpret_cast<ChunkSmemT<NW>*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t n_items = hdr->n_items, total = hdr->total_chunks;
+    for (;;) {
+        if (tid == 0) {
+            const uint32_t c = atomicAdd(&hdr->chunk_counter, 1u);
+            uint32_t it = 0;
+            if (c < total) {
+                uint32_t lo = 0, hi = n_items;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (items[mid].chunk_begin <= c) lo = mid;
+                    else hi = mid;
+                }
+                it = lo;
+                if (c - items[it].chunk_begin >= items[it].n_chunks) atomicOr(&hdr->error, 1u);
+            }
+            S.chunk = c;
+            S.item = it;
+            S.skip = (c < total) ? (uint32_t)items[it].state->converged : 1u;
+            S.iter = (c < total) ? (uint32_t)items[it].state->iter : 0u;
+        }
+        __syncthreads();
+        const uint32_t chunk = S.chunk;
+        if (chunk >= total) break;
+        if (S.skip) {
+            __syncthreads();
+            continue;
+        }
+        const WorkItem& W = items[S.item];
+        load_record(&S.rec, W.rec);
+        __syncthreads();
+        const int d = S.rec.d, nb = S.rec.nb, order = S.rec.order;
+        const int prec = effective_precision(S.rec.precision, W.grid, d, nb);
+        load_grid(S.grid, W.grid, d, nb, prec);
+        for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
+        __syncthreads();
+        double sw = 0.0, sw2 = 0.0;
+        const uint32_t cl = chunk - W.chunk_begin;
+        switch ((order * 3 + prec) * 2 + S.rec.map_kind) {
+#define MBPT_CASE(N_, P_, M_) \
+    case (N_ * 3 + P_) * 2 + M_: run_chunk<N_, P_, M_, NW>(S, W, cl, sw, sw2); break;
+#define MBPT_CASES(N_) \
+    MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
+    MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)
+            MBPT_CASES(2)
+            MBPT_CASES(3)
+            MBPT_CASES(4)
+            MBPT_CASES(5)
+#undef MBPT_CASES
+#undef MBPT_CASE
+            default:
+                if (tid == 0) atomicOr(&hdr->error, 2u);
+        }
+        sw = warp_sum(sw);
+        sw2 = warp_sum(sw2);
+        if (lane == 0) {
+            S.red[0][warp] = sw;
+            S.red[1][warp] = sw2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < NW; ++w) {
+                a += S.red[0][w];
+                b += S.red[1][w];
+            }
+            csum[2 * (size_t)chunk] = a;
+            csum[2 * (size_t)chunk + 1] = b;
+        }
+        float* dst = chist + (size_t)chunk * (size_t)W.hist_stride;
+        for (int i = tid; i < d * nb; i += blockDim.x) {
+            float v = 0.0f;
+            for (int w = 0; w < NW; ++w) v += S.hist[w][i];
+            dst[i] = v;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace mbpt

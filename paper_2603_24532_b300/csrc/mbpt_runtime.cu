@@ -13,7 +13,8 @@
 #include <string>
 #include <vector>
 
-#include "mbpt_device.cuh"
+#include "mbpt_kernels.cuh"
+#include "mbpt_kernels.h"
 #include "mbpt_internal.h"
 
 using namespace mbpt;
@@ -98,189 +99,12 @@ struct Arena {
     }
 };
 
+}  // namespace
+
 // ---------------------------------------------------------------------------
-// Kernels
+// Context and integral objects
 // ---------------------------------------------------------------------------
-template <int NW>
-struct alignas(16) ChunkSmemT {
-    DiagRec rec;
-    Grid2 grid[kMaxD * kGridStride];
-    float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
-    double red[2][NW];
-    uint32_t chunk, item, iter, skip;
-};
-using ChunkSmem = ChunkSmemT<kWarps>;
-
-__device__ __forceinline__ void load_record(DiagRec* dst, const DiagRec* src) {
-    const uint4* s = reinterpret_cast<const uint4*>(src);
-    uint4* d = reinterpret_cast<uint4*>(dst);
-    for (int i = threadIdx.x; i < (int)(sizeof(DiagRec) / 16); i += blockDim.x) d[i] = s[i];
-}
-
-// The FP32 sampling map needs every bin wider than float resolution; an iteration whose grid has a
-// narrower bin samples with the FP64 map instead (decided per integral and iteration, so every chunk
-// of the integral takes the same path).  Must be called by every thread of the block.
-__device__ __forceinline__ int effective_precision(int prec, const double* grid, int d, int nb) {
-    if (prec != MBPT_MIXED) return prec;
-    int bad = 0;
-    for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
-        const int a = idx / nb, i = idx - a * nb;
-        const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
-        if (e1 > e0 && !((float)e1 > (float)e0)) bad = 1;
-    }
-    return __syncthreads_or(bad) ? MBPT_MIXED_MAP64 : prec;
-}
-
-__device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, int nb, int prec) {
-    for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
-        const int a = idx / nb, i = idx - a * nb;
-        const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
-        const double de = e1 - e0;
-        if (prec == MBPT_MIXED) {
-            // FP32 bins tile [0, 1] exactly: width = difference of the rounded edges
-            Grid4f g;
-            g.e = (float)e0;
-            g.de = (float)e1 - g.e;
-            g.pad0 = 0.0f;
-            g.pad1 = 0.0f;
-            reinterpret_cast<Grid4f*>(gs)[a * kGridStride + i] = g;
-        } else {
-            Grid2 g;
-            g.de = de;
-            g.a = (prec == MBPT_FP64) ? e0 : e0 - de;
-            gs[a * kGridStride + i] = g;
-        }
-    }
-}
-
-template <int N, int PREC, int NW>
-__device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
-                                          double& sw2) {
-    const DiagRec& R = S.rec;
-    const uint32_t cs = blockDim.x * (uint32_t)W.spt;
-    const uint64_t first = (uint64_t)chunk_local * cs;
-    const uint32_t t = S.iter;
-    const uint32_t k0 = (uint32_t)W.seed, k1 = (uint32_t)(W.seed >> 32);
-    float* hist = S.hist[threadIdx.x >> 5];
-    const int nb = R.nb;
-    constexpr int D = 3 * (N + 1);
-    for (int j = 0; j < W.spt; ++j) {
-        const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
-        if (s < W.samples) {
-            const SampleOut o = eval_sample<N, PREC>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1, nullptr);
-            sw += o.w;
-            sw2 = fma(o.w, o.w, sw2);
-            if (nonzero(o.w)) {
-                const float wf = narrow_trunc(o.w);
-                float w2 = wf * wf;
-                if (!(w2 <= 3.0e38f)) w2 = 3.0e38f;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const uint32_t i = (o.binpack[a >> 2] >> (8 * (a & 3))) & 0xffu;
-                    atomicAdd(&hist[a * nb + i], w2);
-                }
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Persistent kernel: blocks take chunks (a fixed range of one integral's samples) from a global
-// counter; each chunk's sum w, sum w^2 and histogram go to the chunk's own slot, so the result of a
-// chunk does not depend on which block ran it or what else is in the batch.
-// Compiled in several launch shapes (threads per block x minimum resident blocks, i.e. a register cap);
-// the autotuner picks one per context.
-template <int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_iterate_t(WorkHeader* hdr, const WorkItem* __restrict__ items,
-                                                        double* __restrict__ csum, float* __restrict__ chist) {
-    constexpr int NW = TPB / 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ChunkSmemT<NW>& S = *reinterpret_cast<ChunkSmemT<NW>*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t n_items = hdr->n_items, total = hdr->total_chunks;
-    for (;;) {
-        if (tid == 0) {
-            const uint32_t c = atomicAdd(&hdr->chunk_counter, 1u);
-            uint32_t it = 0;
-            if (c < total) {
-                uint32_t lo = 0, hi = n_items;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (items[mid].chunk_begin <= c) lo = mid;
-                    else hi = mid;
-                }
-                it = lo;
-                if (c - items[it].chunk_begin >= items[it].n_chunks) atomicOr(&hdr->error, 1u);
-            }
-            S.chunk = c;
-            S.item = it;
-            S.skip = (c < total) ? (uint32_t)items[it].state->converged : 1u;
-            S.iter = (c < total) ? (uint32_t)items[it].state->iter : 0u;
-        }
-        __syncthreads();
-        const uint32_t chunk = S.chunk;
-        if (chunk >= total) break;
-        if (S.skip) {
-            __syncthreads();
-            continue;
-        }
-        const WorkItem& W = items[S.item];
-        load_record(&S.rec, W.rec);
-        __syncthreads();
-        const int d = S.rec.d, nb = S.rec.nb, order = S.rec.order;
-        const int prec = effective_precision(S.rec.precision, W.grid, d, nb);
-        load_grid(S.grid, W.grid, d, nb, prec);
-        for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
-        __syncthreads();
-        double sw = 0.0, sw2 = 0.0;
-        const uint32_t cl = chunk - W.chunk_begin;
-        switch (order * 3 + prec) {
-            case 2 * 3 + MBPT_FP64: run_chunk<2, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 2 * 3 + MBPT_MIXED: run_chunk<2, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
-            case 2 * 3 + MBPT_MIXED_MAP64: run_chunk<2, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
-            case 3 * 3 + MBPT_FP64: run_chunk<3, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 3 * 3 + MBPT_MIXED: run_chunk<3, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
-            case 3 * 3 + MBPT_MIXED_MAP64: run_chunk<3, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
-            case 4 * 3 + MBPT_FP64: run_chunk<4, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 4 * 3 + MBPT_MIXED: run_chunk<4, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
-            case 4 * 3 + MBPT_MIXED_MAP64: run_chunk<4, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
-            case 5 * 3 + MBPT_FP64: run_chunk<5, MBPT_FP64, NW>(S, W, cl, sw, sw2); break;
-            case 5 * 3 + MBPT_MIXED: run_chunk<5, MBPT_MIXED, NW>(S, W, cl, sw, sw2); break;
-            case 5 * 3 + MBPT_MIXED_MAP64: run_chunk<5, MBPT_MIXED_MAP64, NW>(S, W, cl, sw, sw2); break;
-            default:
-                if (tid == 0) atomicOr(&hdr->error, 2u);
-        }
-        sw = warp_sum(sw);
-        sw2 = warp_sum(sw2);
-        if (lane == 0) {
-            S.red[0][warp] = sw;
-            S.red[1][warp] = sw2;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < NW; ++w) {
-                a += S.red[0][w];
-                b += S.red[1][w];
-            }
-            csum[2 * (size_t)chunk] = a;
-            csum[2 * (size_t)chunk + 1] = b;
-        }
-        float* dst = chist + (size_t)chunk * (size_t)W.hist_stride;
-        for (int i = tid; i < d * nb; i += blockDim.x) {
-            float v = 0.0f;
-            for (int w = 0; w < NW; ++w) v += S.hist[w][i];
-            dst[i] = v;
-        }
-        __syncthreads();
-    }
-}
-
+namespace {
 typedef void (*IterateFn)(WorkHeader*, const WorkItem*, double*, float*);
 struct KernelVariant {
     int tpb, minb;
@@ -288,204 +112,14 @@ struct KernelVariant {
     size_t smem;
 };
 const KernelVariant kVariants[] = {
-    {256, 2, k_iterate_t<256, 2>, sizeof(ChunkSmemT<8>)},
-    {128, 4, k_iterate_t<128, 4>, sizeof(ChunkSmemT<4>)},
-    {256, 1, k_iterate_t<256, 1>, sizeof(ChunkSmemT<8>)},
-    {128, 3, k_iterate_t<128, 3>, sizeof(ChunkSmemT<4>)},
+    {256, 2, k_iterate_256x2, sizeof(ChunkSmemT<8>)},
+    {128, 4, k_iterate_128x4, sizeof(ChunkSmemT<4>)},
+    {256, 1, k_iterate_256x1, sizeof(ChunkSmemT<8>)},
+    {128, 3, k_iterate_128x3, sizeof(ChunkSmemT<4>)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
-
-// Grid refinement of one axis (Lepage 1978 with (7,1)/8 and (1,6,1)/8 smoothing):
-// dbar -> r = dbar/sum -> m = ((r-1)/ln r)^alpha -> new edges at equal shares of the
-// piecewise-linear cumulative of m.
-__device__ void refine_axis(double* grid, const double* old, const double* h, double* m, int nb, double alpha) {
-    m[0] = (7.0 * h[0] + h[1]) / 8.0;
-    for (int i = 1; i < nb - 1; ++i) m[i] = (h[i - 1] + 6.0 * h[i] + h[i + 1]) / 8.0;
-    m[nb - 1] = (h[nb - 2] + 7.0 * h[nb - 1]) / 8.0;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += m[i];
-    if (!(tot > 0.0)) return;
-    double msum = 0.0;
-    for (int i = 0; i < nb; ++i) {
-        const double r = m[i] / tot;
-        double v;
-        if (r <= 0.0) v = 0.0;
-        else if (r >= 1.0) v = 1.0;
-        else v = pow((r - 1.0) / log(r), alpha);
-        m[i] = v;
-        msum += v;
-    }
-    const double share = msum / nb;
-    int j = 0;
-    double cum = 0.0;
-    for (int k = 1; k < nb; ++k) {
-        const double target = k * share;
-        while (j < nb - 1 && cum + m[j] < target) {
-            cum += m[j];
-            ++j;
-        }
-        double frac = m[j] > 0.0 ? (target - cum) / m[j] : 0.0;
-        if (frac > 1.0) frac = 1.0;
-        if (frac < 0.0) frac = 0.0;
-        grid[k] = old[j] + frac * (old[j + 1] - old[j]);
-    }
-    grid[0] = old[0];
-    grid[nb] = old[nb];
-}
-
-// Per integral: fixed-order reduction of the chunk slots, combination of the iteration into the
-// running estimate, convergence test and grid refinement.
-__global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkItem* __restrict__ items,
-                                                 const double* __restrict__ csum, const float* __restrict__ chist,
-                                                 double* const* __restrict__ last_hist) {
-    __shared__ double hsum[kMaxD * MBPT_MAX_BINS];
-    __shared__ double tmp[kMaxD * MBPT_MAX_BINS];
-    __shared__ double old[kMaxD * (MBPT_MAX_BINS + 1)];
-    __shared__ double red[2][8];
-    __shared__ int s_skip, s_refine;
-    const int tid = threadIdx.x;
-    for (uint32_t ii = blockIdx.x; ii < hdr->n_items; ii += gridDim.x) {
-        const WorkItem& W = items[ii];
-        DiagState* st = W.state;
-        if (tid == 0) s_skip = st->converged;
-        __syncthreads();
-        if (s_skip) {
-            __syncthreads();
-            continue;
-        }
-        double a = 0.0, b = 0.0;
-        for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x) {
-            a += csum[2 * (size_t)(W.chunk_begin + c)];
-            b += csum[2 * (size_t)(W.chunk_begin + c) + 1];
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if ((tid & 31) == 0) {
-            red[0][tid >> 5] = a;
-            red[1][tid >> 5] = b;
-        }
-        const int d = W.rec->d, nb = W.rec->nb;
-        for (int i = tid; i < d * nb; i += blockDim.x) {
-            double acc = 0.0;
-            for (uint32_t c = 0; c < W.n_chunks; ++c)
-                acc += (double)chist[(size_t)(W.chunk_begin + c) * (size_t)W.hist_stride + i];
-            hsum[i] = acc;
-            last_hist[ii][i] = acc;
-        }
-        for (int i = tid; i < d * (nb + 1); i += blockDim.x) old[i] = W.grid[i];
-        __syncthreads();
-        if (tid == 0) {
-            double A = 0.0, B = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                A += red[0][w];
-                B += red[1][w];
-            }
-            const double M = (double)W.samples;
-            const double I = A / M;
-            const double var = (B / M - I * I) / (M - 1.0);
-            const int t = st->iter;
-            if (t < kMaxIters) {
-                st->hist_mean[t] = I;
-                st->hist_var[t] = var;
-            }
-            st->last_mean = I;
-            st->last_var = var;
-            if (!isfinite(I) || !isfinite(var)) st->status = MBPT_ENUMERIC;
-            if (var > 0.0) {
-                st->sum_inv_var += 1.0 / var;
-                st->sum_mean_w += I / var;
-                st->n_used += 1;
-            }
-            double mean, sigma, chi2 = 0.0;
-            if (st->sum_inv_var > 0.0) {
-                mean = st->sum_mean_w / st->sum_inv_var;
-                sigma = sqrt(1.0 / st->sum_inv_var);
-                const int T = t + 1 < kMaxIters ? t + 1 : kMaxIters;
-                if (st->n_used > 1) {
-                    double c2 = 0.0;
-                    for (int k = 0; k < T; ++k)
-                        if (st->hist_var[k] > 0.0) {
-                            const double dd = st->hist_mean[k] - mean;
-                            c2 += dd * dd / st->hist_var[k];
-                        }
-                    chi2 = c2 / (st->n_used - 1);
-                }
-            } else {
-                mean = I;
-                sigma = 0.0;
-            }
-            st->mean = mean;
-            st->sigma = sigma;
-            st->chi2 = chi2;
-            st->n_evals += (int64_t)W.samples;
-            st->iter = t + 1;
-            const bool has_target = (W.target_rel > 0.0) || (W.target_abs > 0.0);
-            const double goal = fmax(W.target_rel * fabs(mean), W.target_abs);
-            if (has_target && st->iter >= 2 && sigma <= goal) st->converged = 1;
-            s_refine = (W.freeze_after == 0u) || ((uint32_t)st->iter < W.freeze_after);
-        }
-        __syncthreads();
-        if (s_refine && tid < d) refine_axis(W.grid + tid * (nb + 1), old + tid * (nb + 1), hsum + tid * nb,
-                                             tmp + tid * MBPT_MAX_BINS, nb, W.alpha);
-        __syncthreads();
-    }
-}
-
-// Test hook kernel: samples [first, first+count) of iteration `iter`, mapped point and weight.
-template <int N, int PREC>
-__device__ void dump_one(const DiagRec& R, const Grid2* gs, uint32_t s, uint32_t t, uint32_t sid, uint32_t k0,
-                         uint32_t k1, double* x, double* w) {
-    const SampleOut o = eval_sample<N, PREC>(R, gs, s, t, sid, k0, k1, x);
-    *w = o.w;
-}
-
-__global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, const double* grid, uint64_t seed, uint32_t sid,
-                                             uint32_t iter, uint64_t first, uint64_t count, double* xo,
-                                             double* wo) {
-    __shared__ DiagRec R;
-    __shared__ Grid2 gs[kMaxD * kGridStride];
-    load_record(&R, rec);
-    __syncthreads();
-    const int prec = effective_precision(R.precision, grid, R.d, R.nb);
-    load_grid(gs, grid, R.d, R.nb, prec);
-    __syncthreads();
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const uint32_t s = (uint32_t)(first + i);
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    double* x = xo ? xo + i * R.d : nullptr;
-    double* w = wo + i;
-    switch (R.order * 3 + prec) {
-        case 2 * 3 + MBPT_FP64: dump_one<2, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 2 * 3 + MBPT_MIXED: dump_one<2, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 2 * 3 + MBPT_MIXED_MAP64: dump_one<2, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 3 * 3 + MBPT_FP64: dump_one<3, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 3 * 3 + MBPT_MIXED: dump_one<3, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 3 * 3 + MBPT_MIXED_MAP64: dump_one<3, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 4 * 3 + MBPT_FP64: dump_one<4, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 4 * 3 + MBPT_MIXED: dump_one<4, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 4 * 3 + MBPT_MIXED_MAP64: dump_one<4, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 5 * 3 + MBPT_FP64: dump_one<5, MBPT_FP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 5 * 3 + MBPT_MIXED: dump_one<5, MBPT_MIXED>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        case 5 * 3 + MBPT_MIXED_MAP64: dump_one<5, MBPT_MIXED_MAP64>(R, gs, s, iter, sid, k0, k1, x, w); break;
-        default: *w = 0.0;
-    }
-}
-
-__global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
-                         uint64_t count, uint32_t* out) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    uint32_t o[4];
-    philox4x32_10(c0 + (uint32_t)i, c1, c2, c3, k0, k1, o);
-    for (int j = 0; j < 4; ++j) out[4 * i + j] = o[j];
-}
-
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// Context and integral objects
-// ---------------------------------------------------------------------------
 struct mbpt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -1128,10 +762,10 @@ int noalloc_setup(int device, NoAllocDevice** out) {
     if (!d.ready) {
         void* p = nullptr;
         CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        CUDA_TRY(cudaFuncSetAttribute(k_iterate_t<kThreads, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CUDA_TRY(cudaFuncSetAttribute(k_iterate_256x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sizeof(ChunkSmem)));
         int per_sm = 0, sms = 0;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate_t<kThreads, 2>, kThreads,
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate_256x2, kThreads,
                                                                sizeof(ChunkSmem)));
         CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
         if (per_sm < 1) return fail(MBPT_ECUDA, "noalloc: k_iterate cannot be resident");
@@ -1239,7 +873,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     CUDA_TRY(cudaMemcpyAsync(base + off_item, &w, sizeof(w), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(base + off_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(base + off_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, s));
-    k_iterate_t<kThreads, 2><<<nd->blocks, kThreads, sizeof(ChunkSmem), s>>>((WorkHeader*)(base + off_hdr),
+    k_iterate_256x2<<<nd->blocks, kThreads, sizeof(ChunkSmem), s>>>((WorkHeader*)(base + off_hdr),
                                                              (const WorkItem*)(base + off_item),
                                                              (double*)(base + off_csum), (float*)(base + off_chist));
     CUDA_TRY(cudaGetLastError());

@@ -367,12 +367,12 @@ def state_with_grid(image: bytes, grid: np.ndarray) -> bytes:
 
 
 def physics(kF_n=1.0, kF_p=0.0, hbar2_over_m=41.47, C_S=-50.0, C_Y=-200.0, m_pi=0.7, Lam=2.0, reg_power=4,
-            K_max=None) -> mbpt_physics:
+            K_max=None, map_kind=0) -> mbpt_physics:
     """Physics point of the toy potential; K_max defaults to max kF + 3 Lambda."""
     p = mbpt_physics()
     p.kF_n, p.kF_p, p.hbar2_over_m = kF_n, kF_p, hbar2_over_m
     p.C_S, p.C_Y, p.m_pi, p.Lambda = C_S, C_Y, m_pi, Lam
-    p.reg_power, p.map_kind = reg_power, 0
+    p.reg_power, p.map_kind = reg_power, map_kind
     p.K_max = K_max if K_max is not None else max(kF_n, kF_p) + 3.0 * Lam
     return p
 

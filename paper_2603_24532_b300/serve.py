@@ -88,9 +88,10 @@ class MbptBackend:
     """The C ABI as the server's backend (all work on the GPU)."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, arena_ptr: int = 0, stream: int = 0,
-                 precision: Optional[int] = None):
+                 precision: Optional[int] = None, map_kind: int = 1):
         from . import mbpt as M
         self.M = M
+        self.map_kind = map_kind
         self.ctx = M.mbpt_ctx_create(device, arena_bytes, arena_ptr=arena_ptr, stream=stream)
         self.precision = M.MBPT_MIXED if precision is None else precision
         self._descs = {}
@@ -101,7 +102,7 @@ class MbptBackend:
         return self._descs[order]
 
     def physics(self, kF_n: float, kF_p: float):
-        return self.M.physics(kF_n=kF_n, kF_p=kF_p, K_max=max(kF_n, kF_p) + 6.0)
+        return self.M.physics(kF_n=kF_n, kF_p=kF_p, K_max=max(kF_n, kF_p) + 6.0, map_kind=self.map_kind)
 
     def cfg(self, samples: int, stream_id: int, seed: int):
         return self.M.vegas_cfg(samples=samples, seed=seed, stream_id=stream_id, precision=self.precision)

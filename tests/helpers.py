@@ -17,7 +17,7 @@ def make_desc(D: O.Diagram) -> M.mbpt_diagram_desc:
 def phys_pair(kF_n=1.0, kF_p=0.0, **kw):
     po = O.Physics(kF_n=kF_n, kF_p=kF_p, **kw)
     pm = M.physics(kF_n=kF_n, kF_p=kF_p, hbar2_over_m=po.hbar2_over_m, C_S=po.C_S, C_Y=po.C_Y, m_pi=po.m_pi,
-                   Lam=po.Lam, reg_power=po.reg_power, K_max=po.K_max)
+                   Lam=po.Lam, reg_power=po.reg_power, K_max=po.K_max, map_kind=po.map_kind)
     return po, pm
 
 
@@ -28,11 +28,11 @@ MATTER = {
 }
 
 
-def matter_pair(name, **kw):
+def matter_pair(name, map_kind=0, **kw):
     args = dict(MATTER[name])
     args.update(kw)
     kmax = max(args["kF_n"], args["kF_p"]) + 6.0
-    return phys_pair(K_max=kmax, **args)
+    return phys_pair(K_max=kmax, map_kind=map_kind, **args)
 
 
 def random_grid(d, nb, rng, strength=0.9):
@@ -48,7 +48,8 @@ def random_grid(d, nb, rng, strength=0.9):
 
 
 def oracle_dump(D, po, grid, seed, sid, t, first, count):
-    sums, hist, x, w = O.vegas_samples(0, D, po.array(), D.d, grid, seed, sid, t, first, first + count, dump=True)
+    sums, hist, x, w = O.vegas_samples(0, D, po.array(), grid.shape[0], grid, seed, sid, t, first, first + count,
+                                       dump=True)
     return x, w
 
 

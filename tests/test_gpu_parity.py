@@ -41,23 +41,24 @@ def test_philox_device_matches_oracle(ctx):
             assert list(got[i]) == want
 
 
-CASES = [(2, "pnm", 1), (2, "snm", 1), (3, "pnm", 3), (3, "snm", 3), (3, "asym", 3), (4, "pnm", 8), (4, "snm", 5),
-         (4, "asym", 5), (5, "pnm", 8), (5, "asym", 3)]
+CASES = [(2, "pnm", 1, 0), (2, "snm", 1, 0), (3, "pnm", 3, 0), (3, "snm", 3, 0), (3, "asym", 3, 0),
+         (4, "pnm", 8, 0), (4, "snm", 5, 0), (4, "asym", 5, 0), (5, "pnm", 8, 0), (5, "asym", 3, 0),
+         (2, "pnm", 1, 1), (3, "snm", 3, 1), (4, "asym", 4, 1), (5, "pnm", 5, 1)]
 
 
-@pytest.mark.parametrize("n,matter,k", CASES)
-def test_per_sample_parity_fp64(ctx, n, matter, k):
-    rng = np.random.default_rng(1000 * n + len(matter))
-    po, pm = matter_pair(matter)
+@pytest.mark.parametrize("n,matter,k,mapk", CASES)
+def test_per_sample_parity_fp64(ctx, n, matter, k, mapk):
+    rng = np.random.default_rng(1000 * n + len(matter) + 7 * mapk)
+    po, pm = matter_pair(matter, map_kind=mapk)
     count = 1536 if n >= 5 else 3072
     for D in _pick(n, k, rng):
         cfg = M.vegas_cfg(samples=1 << 16, seed=12345, stream_id=D.diagram_id + 7, precision=M.MBPT_FP64)
         g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
         try:
-            grid = random_grid(D.d, 50, rng)
+            grid = random_grid(po.dim(D), 50, rng)
             M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
             t, first = 3, 1021          # ragged offset, non-zero iteration counter
-            xg, wg = M.mbpt_dump_samples(g, t, first, count, D.d)
+            xg, wg = M.mbpt_dump_samples(g, t, first, count, po.dim(D))
             xo, wo = oracle_dump(D, po, grid, 12345, D.diagram_id + 7, t, first, count)
             assert np.max(np.abs(xg - xo)) <= 4 * EPS
             ns = near_surface(D, po, xo)
@@ -78,21 +79,22 @@ def test_per_sample_parity_fp64(ctx, n, matter, k):
 
 
 @pytest.mark.parametrize("prec", [M.MBPT_MIXED, M.MBPT_MIXED_MAP64])
-@pytest.mark.parametrize("n,matter", [(3, "pnm"), (4, "snm"), (5, "pnm"), (4, "asym")])
-def test_mixed_precision_deviation(ctx, n, matter, prec):
+@pytest.mark.parametrize("n,matter,mapk", [(3, "pnm", 0), (4, "snm", 0), (5, "pnm", 0), (4, "asym", 0),
+                                           (3, "pnm", 1), (5, "pnm", 1)])
+def test_mixed_precision_deviation(ctx, n, matter, mapk, prec):
     """Mixed modes (FP32 potentials and spin sum; FP32 or FP64 sampling map) on identical
     samples: aggregate deviation from the FP64 oracle below 1e-4 relative."""
-    rng = np.random.default_rng(7 * n)
-    po, pm = matter_pair(matter)
+    rng = np.random.default_rng(7 * n + mapk)
+    po, pm = matter_pair(matter, map_kind=mapk)
     for D in _pick(n, 3, rng):
         if O.is_anomalous(D):
             continue
         cfg = M.vegas_cfg(samples=1 << 16, seed=99, stream_id=D.diagram_id, precision=prec)
         g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
         try:
-            grid = random_grid(D.d, 50, rng, strength=0.5)
+            grid = random_grid(po.dim(D), 50, rng, strength=0.5)
             M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
-            xg, wg = M.mbpt_dump_samples(g, 0, 0, 2048, D.d)
+            xg, wg = M.mbpt_dump_samples(g, 0, 0, 2048, po.dim(D))
             xo, wo = oracle_dump(D, po, grid, 99, D.diagram_id, 0, 0, 2048)
             assert np.max(np.abs(xg - xo)) <= (4 * EPS if prec == M.MBPT_MIXED_MAP64 else 2e-7)
             ok = ~near_surface(D, po, xo, rel=1e-5 if prec == M.MBPT_MIXED else 1e-9)
@@ -135,12 +137,13 @@ def test_one_iteration_sums_histogram_and_refinement(ctx, prec):
         M.mbpt_destroy_diagram(g)
 
 
-def test_second_order_estimate_config1(ctx):
+@pytest.mark.parametrize("mapk", [0, 1])
+def test_second_order_estimate_config1(ctx, mapk):
     """Config 1: one second-order diagram, neutron matter kF = 1, 10 x 2^18 samples,
     FP64: the GPU estimate agrees with the oracle's own VEGAS run and with the
     deterministic quadrature of Eq. (2) within 3 combined standard errors."""
     import quad_pins as Q
-    po, pm = matter_pair("pnm")
+    po, pm = matter_pair("pnm", map_kind=mapk)
     pm.K_max = 7.0
     po.K_max = 7.0
     (D,) = O.enumerate_diagrams(2)
@@ -219,6 +222,27 @@ def test_anomalous_integral_is_exactly_zero(ctx):
         assert r.mean == 0.0 and r.sigma == 0.0 and r.n_iter == 2 and r.converged == 1
     finally:
         M.mbpt_destroy_diagram(g)
+
+
+@pytest.mark.parametrize("mapk", [0, 1])
+def test_anomalous_diagrams_in_asymmetric_matter_are_zero(ctx, mapk):
+    """A hole and a particle forced to equal momentum can pass their steps for different species
+    in asymmetric matter; the spin sum is then exactly zero and so is the weight (no 0/0)."""
+    po, pm = matter_pair("asym", map_kind=mapk)
+    rng = np.random.default_rng(33)
+    for D in [D for D in O.enumerate_diagrams(4) if O.is_anomalous(D)] + \
+             [D for D in O.enumerate_diagrams(5) if O.is_anomalous(D)][:20]:
+        g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=4096, precision=M.MBPT_MIXED))
+        try:
+            grid = random_grid(po.dim(D), 50, rng)
+            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+            _, w = M.mbpt_dump_samples(g, 0, 0, 4096, po.dim(D), with_x=False)
+            assert np.all(w == 0.0)
+            M.mbpt_vegas_iterate(ctx, [g], 2)
+            r = M.mbpt_estimate(g)
+            assert r.mean == 0.0 and r.sigma == 0.0 and r.status == 0
+        finally:
+            M.mbpt_destroy_diagram(g)
 
 
 def test_targets_stop_iterating(ctx):

@@ -64,6 +64,25 @@ def test_second_order_snm_vs_gauss_legendre():
     assert within(m, s, q2(-200.0, g=4))
 
 
+def test_rotational_reduction_second_order_vs_quadrature():
+    """Chord map 1 (chord 0 along z, chord 1 in the xz plane, 4 pi x 2 pi integrated out; Sec. III.C)
+    integrates the same Eq. (2) in 6 instead of 9 dimensions."""
+    (D,) = O.enumerate_diagrams(2)
+    ph = O.Physics(map_kind=1)
+    assert ph.dim(D) == 6
+    m, s, chi, _ = O.vegas(D, ph, 10, 1 << 16, seed=1)
+    assert within(m, s, q2(-200.0))
+    assert s < 3e-3 * abs(q2(-200.0))
+
+
+@pytest.mark.parametrize("i", [0, 2])
+def test_rotational_reduction_third_order_matches_full_map(i):
+    D = O.enumerate_diagrams(3)[i]
+    m0, s0, _, _ = O.vegas(D, O.Physics(map_kind=0), 12, 1 << 16, seed=11)
+    m1, s1, _, _ = O.vegas(D, O.Physics(map_kind=1), 12, 1 << 16, seed=12)
+    assert abs(m0 - m1) <= 3.0 * math.hypot(s0, s1)
+
+
 def test_planted_spin_sum_error_is_caught():
     """Dropping the direct-exchange cross term of the spin sum (a plausible
     mistake) moves the reference far outside the oracle's error bar."""
