@@ -264,6 +264,25 @@ def run_gpu(args):
         M.mbpt_destroy_diagram(g)
     vrot = world * evals_step / (float(np.mean(strot)) * 1e-3)
 
+    # ---- fourth-order batch (all 39 diagrams x kF {1.0, 1.33, 1.6} x {PNM, SNM}, 2^24 samples each,
+    # anomalous ones flagged and skipped): throughput of one batched iteration
+    g4 = []
+    for ki, kf in enumerate((1.0, 1.33, 1.6)):
+        for mi, kfp in enumerate((0.0, kf)):
+            ph = M.physics(kF_n=kf, kF_p=kfp, K_max=kf + 6.0)
+            for d in M.mbpt_generate(4):
+                if d.anomalous:
+                    continue
+                g4.append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(
+                    samples=1 << 24, seed=1 + rank, stream_id=10000 * rank + 1000 * mi + 100 * ki + d.diagram_id,
+                    precision=M.MBPT_MIXED)))
+    M.mbpt_vegas_iterate(ctx, g4, 1)
+    torch.cuda.synchronize()
+    it4, st4 = timed_steps(g4, 2)
+    for g in g4:
+        M.mbpt_destroy_diagram(g)
+    v4 = world * len(g4) * (1 << 24) / (float(np.mean(st4)) * 1e-3)
+
     # ---- FP64 batched, same workload (tuned the same way)
     g64, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
     tuned64 = autotune(ctx, g64, trials=1)["best"] if args.autotune else None
@@ -335,6 +354,9 @@ def run_gpu(args):
         "diagrams_to_0p1pct_per_s": {"batched_mixed": d_mixed, "k0_plain_fp64": d_k0,
                                      "ratio": (d_mixed / d_k0) if (d_mixed and d_k0) else None,
                                      "batched_mixed_rotational_9d": d_rot},
+        "fourth_order_batch": {"value": v4, "unit": UNIT, "integrals": len(g4), "samples_per_iter": 1 << 24,
+                               "ms_per_iteration": float(np.mean(st4)),
+                               "workload": "39 fourth-order diagrams (33 non-anomalous) x kF {1.0,1.33,1.6} x {PNM,SNM}, mixed"},
         "rotational_9d": {"value": vrot, "unit": UNIT, "kernel_ms": float(np.mean(itrot)),
                           "note": "same scan with chord 0 along z and chord 1 in the xz plane (d = 9)"},
     }

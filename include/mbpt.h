@@ -132,8 +132,10 @@ typedef struct {
  * word) and counter (s, t, stream_id, j), j = 0..ceil(d/4)-1; axis a takes word
  * a.  The grid is refined after every iteration (smoothing (7,1)/8 and
  * (1,6,1)/8, compression exponent alpha) until `freeze_after` iterations have
- * run (0 = never freeze).  The integral stops iterating once its combined
- * standard error is <= max(target_rel*|mean|, target_abs) (0, 0 = never).
+ * run (0 = never freeze).  The first `train_iters` iterations only train the
+ * grid: their estimates are recorded but not combined (PVegas' training phase,
+ * Sec. III.C).  The integral stops iterating once its combined standard error
+ * is <= max(target_rel*|mean|, target_abs) (0, 0 = never).
  */
 typedef struct {
     int32_t n_bins;            /* 2..MBPT_MAX_BINS (50 in the paper's setup) */
@@ -145,6 +147,8 @@ typedef struct {
     uint64_t samples_per_iter; /* >= 2, < 2^32 */
     double target_rel;
     double target_abs;
+    uint32_t train_iters;      /* leading iterations excluded from the combined estimate */
+    uint32_t reserved;
 } mbpt_vegas_cfg;
 
 typedef struct {
@@ -228,7 +232,7 @@ int mbpt_create_diagram(mbpt_ctx* ctx, const mbpt_diagram_desc* desc, const mbpt
                         const mbpt_vegas_cfg* cfg, mbpt_diag** out);
 int mbpt_destroy_diagram(mbpt_diag* diag);
 /*
- * Change an integral's samples per iteration, freeze point and targets for its
+ * Change an integral's samples per iteration, freeze point, training iterations and targets for its
  * next iterations (PVegas' adaptive number of samples per iteration, Sec. III.C).
  * Seed, stream id, bins, alpha and precision must be unchanged (MBPT_EINVAL).
  */

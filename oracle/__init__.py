@@ -460,14 +460,14 @@ def refine(grid: np.ndarray, hist: np.ndarray, alpha: float = 1.5) -> np.ndarray
     return out
 
 
-def combine(means: Sequence[float], variances: Sequence[float]):
+def combine(means: Sequence[float], variances: Sequence[float], skip: int = 0):
     """Inverse-variance weighted mean of the iteration estimates, its standard
     error and chi^2 per degree of freedom.  Iterations whose sample variance is
     exactly zero (an integrand that vanished on every sample) carry no weight;
     if every iteration has zero variance the last estimate is returned with
     zero error."""
-    means = np.asarray(means, dtype=np.float64)
-    variances = np.asarray(variances, dtype=np.float64)
+    means = np.asarray(means, dtype=np.float64)[skip:]
+    variances = np.asarray(variances, dtype=np.float64)[skip:]
     pos = variances > 0.0
     if not np.any(pos):
         return float(means[-1]), 0.0, 0.0

@@ -26,9 +26,10 @@ def main():
     ap.add_argument("--arena-gb", type=float, default=48.0)
     ap.add_argument("--time-limit", type=float, default=None)
     ap.add_argument("--max-iters", type=int, default=60)
+    ap.add_argument("--warm-start", action="store_true")
     a = ap.parse_args()
     be = S.MbptBackend(arena_bytes=int(a.arena_gb * (1 << 30)))
-    srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters)
+    srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters, warm_start=a.warm_start)
     trace = S.poisson_trace(a.requests, a.rate, a.seed)
     t0 = time.perf_counter()
     done = srv.run(trace, realtime=True, time_limit=a.time_limit)
@@ -43,6 +44,7 @@ def main():
            "diagrams_per_s": n_int / wall, "evals_per_s": srv.evals / wall, "rounds": srv.rounds,
            "completed_by_cap": caps, "budget_bytes": srv.budget,
            "target_met_fraction": len(met) / max(1, len(done)),
+           "warm_start": a.warm_start, "warm_started_integrals": srv.warm_starts,
            "rounds_per_request": {"median": float(sorted(rounds)[len(rounds) // 2]) if rounds else None,
                                   "max": max(rounds) if rounds else None},
            "example": [{"n": r.n_dens, "delta": r.delta, "cap": r.cap, "target": r.target, "E_corr": r.energy,

@@ -84,7 +84,8 @@ struct alignas(16) WorkItem {
     double alpha, target_rel, target_abs;
     int32_t spt;           // samples per thread per chunk
     int32_t hist_stride;   // floats per chunk histogram slot
-    int32_t pad0, pad1;
+    uint32_t train_iters;  // leading iterations not combined into the estimate
+    int32_t pad1;
 };
 
 struct alignas(16) WorkHeader {

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
             st->last_mean = I;
             st->last_var = var;
             if (!isfinite(I) || !isfinite(var)) st->status = MBPT_ENUMERIC;
-            if (var > 0.0) {
+            const bool training = (uint32_t)t < W.train_iters;   // grid training only
+            if (var > 0.0 && !training) {
                 st->sum_inv_var += 1.0 / var;
                 st->sum_mean_w += I / var;
                 st->n_used += 1;
@@ -113,13 +114,16 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
                 const int T = t + 1 < kMaxIters ? t + 1 : kMaxIters;
                 if (st->n_used > 1) {
                     double c2 = 0.0;
-                    for (int k = 0; k < T; ++k)
+                    for (int k = (int)W.train_iters; k < T; ++k)
                         if (st->hist_var[k] > 0.0) {
                             const double dd = st->hist_mean[k] - mean;
                             c2 += dd * dd / st->hist_var[k];
                         }
                     chi2 = c2 / (st->n_used - 1);
                 }
+            } else if (training) {
+                mean = I;                        // no combined estimate yet
+                sigma = (double)INFINITY;
             } else {
                 mean = I;
                 sigma = 0.0;
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
             st->iter = t + 1;
             const bool has_target = (W.target_rel > 0.0) || (W.target_abs > 0.0);
             const double goal = fmax(W.target_rel * fabs(mean), W.target_abs);
-            if (has_target && st->iter >= 2 && sigma <= goal) st->converged = 1;
+            if (has_target && (uint32_t)st->iter >= W.train_iters + 2u && sigma <= goal) st->converged = 1;
             s_refine = (W.freeze_after == 0u) || ((uint32_t)st->iter < W.freeze_after);
         }
         __syncthreads();

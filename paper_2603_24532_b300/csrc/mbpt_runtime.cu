@@ -491,7 +491,7 @@ int mbpt_set_config(mbpt_diag* g, const mbpt_vegas_cfg* cfg) {
     const mbpt_vegas_cfg& o = g->cfg;
     if (cfg->n_bins != o.n_bins || cfg->precision != o.precision || cfg->seed != o.seed ||
         cfg->stream_id != o.stream_id || cfg->alpha != o.alpha)
-        return fail(MBPT_EINVAL, "set_config: only samples_per_iter, freeze_after and the targets may change");
+        return fail(MBPT_EINVAL, "set_config: only samples_per_iter, freeze_after, train_iters and the targets may change");
     if (cfg->samples_per_iter < 2 || cfg->samples_per_iter >= (1ull << 32) || !(cfg->target_rel >= 0.0) ||
         !(cfg->target_abs >= 0.0))
         return fail(MBPT_EINVAL, "set_config: invalid samples or targets");
@@ -499,6 +499,7 @@ int mbpt_set_config(mbpt_diag* g, const mbpt_vegas_cfg* cfg) {
     g->cfg.freeze_after = cfg->freeze_after;
     g->cfg.target_rel = cfg->target_rel;
     g->cfg.target_abs = cfg->target_abs;
+    g->cfg.train_iters = cfg->train_iters;
     return MBPT_OK;
 }
 
@@ -547,6 +548,7 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         w.alpha = g->cfg.alpha;
         w.target_rel = g->cfg.target_rel;
         w.target_abs = g->cfg.target_abs;
+        w.train_iters = g->cfg.train_iters;
         w.hist_stride = stride;
         chunk += w.n_chunks;
         if (chunk >= (1ull << 31)) return fail(MBPT_EINVAL, "vegas_iterate: batch too large");

@@ -114,6 +114,7 @@ class mbpt_vegas_cfg(ctypes.Structure):
         ("stream_id", ctypes.c_uint32), ("freeze_after", ctypes.c_uint32),
         ("samples_per_iter", ctypes.c_uint64),
         ("target_rel", ctypes.c_double), ("target_abs", ctypes.c_double),
+        ("train_iters", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -378,10 +379,11 @@ def physics(kF_n=1.0, kF_p=0.0, hbar2_over_m=41.47, C_S=-50.0, C_Y=-200.0, m_pi=
 
 
 def vegas_cfg(samples=1 << 18, seed=1, stream_id=0, precision=MBPT_FP64, n_bins=50, alpha=1.5, freeze_after=0,
-              target_rel=0.0, target_abs=0.0) -> mbpt_vegas_cfg:
+              target_rel=0.0, target_abs=0.0, train_iters=0) -> mbpt_vegas_cfg:
     c = mbpt_vegas_cfg()
     c.n_bins, c.precision, c.alpha = n_bins, precision, alpha
     c.seed, c.stream_id, c.freeze_after = seed, stream_id, freeze_after
     c.samples_per_iter = samples
     c.target_rel, c.target_abs = target_rel, target_abs
+    c.train_iters = train_iters
     return c

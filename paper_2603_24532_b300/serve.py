@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import math
 import time
+from collections import OrderedDict
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence
 
@@ -78,6 +79,7 @@ class Integral:
     cfg: object = None
     samples: int = 0
     evals: int = 0
+    warm: bool = False
     mean: float = 0.0
     sigma: float = float("inf")
     n_iter: int = 0
@@ -128,6 +130,19 @@ class MbptBackend:
     def estimate_many(self, handles: Sequence):
         return [(r.mean, r.sigma, r.n_iter) for r in self.M.mbpt_estimate_batch(list(handles))]
 
+    def get_grid(self, h):
+        img = self.M.mbpt_get_state(h)
+        d = int(np.frombuffer(img, dtype=np.int32, count=2, offset=8)[0])
+        nb = int(np.frombuffer(img, dtype=np.int32, count=2, offset=8)[1])
+        return self.M.state_grid(img, d, nb)
+
+    def set_grid(self, h, grid):
+        self.M.mbpt_set_state(h, self.M.state_with_grid(self.M.mbpt_get_state(h), grid))
+
+    def set_train(self, h, cfg, iters: int):
+        cfg.train_iters = int(iters)
+        self.M.mbpt_set_config(h, cfg)
+
     def set_samples(self, h, cfg, samples: int):
         cfg.samples_per_iter = int(samples)
         self.M.mbpt_set_config(h, cfg)
@@ -139,6 +154,35 @@ class MbptBackend:
         self.M.mbpt_ctx_destroy(self.ctx)
 
 
+class GridCache:
+    """Trained VEGAS grids of finished integrals, keyed by (order, diagram, asymmetry), for warm
+    starts at neighbouring densities (Sec. III.C: importance-sampling distributions propagate in
+    density for changes up to about 0.02 fm^-3)."""
+
+    def __init__(self, window: float = 0.02, max_entries: int = 50000):
+        self.window = window
+        self.max_entries = max_entries
+        self.entries: "OrderedDict[tuple, np.ndarray]" = OrderedDict()
+
+    def put(self, order: int, did: int, delta: float, n_dens: float, grid) -> None:
+        if grid is None:
+            return
+        key = (order, did, round(delta, 6), round(n_dens, 6))
+        self.entries[key] = grid
+        self.entries.move_to_end(key)
+        while len(self.entries) > self.max_entries:
+            self.entries.popitem(last=False)
+
+    def get(self, order: int, did: int, delta: float, n_dens: float):
+        best, best_d = None, None
+        for (o, d, dl, n), g in self.entries.items():
+            if o == order and d == did and dl == round(delta, 6):
+                dist = abs(n - n_dens)
+                if dist <= self.window and (best_d is None or dist < best_d):
+                    best, best_d = g, dist
+        return best
+
+
 SAMPLES_BY_ORDER = {2: 1 << 16, 3: 1 << 16, 4: 1 << 16, 5: 1 << 16}   # pilot iteration
 MIN_SAMPLES, MAX_SAMPLES = 1 << 14, 1 << 21
 
@@ -146,9 +190,12 @@ MIN_SAMPLES, MAX_SAMPLES = 1 << 14, 1 << 21
 class Server:
     def __init__(self, backend, budget_bytes: int = 40 << 30, max_integrals: int = 1 << 16,
                  samples_by_order: Optional[Dict[int, int]] = None, min_iters: int = 3, max_iters: int = 60,
-                 seed: int = 1, clock: Callable[[], float] = time.perf_counter, adaptive: bool = True):
+                 seed: int = 1, clock: Callable[[], float] = time.perf_counter, adaptive: bool = True,
+                 warm_start: bool = False, warm_window: float = 0.02):
         self.b = backend
         self.adaptive = adaptive
+        self.cache = GridCache(warm_window) if warm_start else None
+        self.warm_starts = 0
         self.budget = budget_bytes
         self.max_integrals = max_integrals
         self.samples = dict(SAMPLES_BY_ORDER if samples_by_order is None else samples_by_order)
@@ -204,7 +251,18 @@ class Server:
             try:
                 for order, d, phys, cfg, nb in plan:
                     h = self.b.create(d, phys, cfg)
-                    created.append(Integral(req, order, d.diagram_id, h, nb, cfg, self.samples[order]))
+                    it = Integral(req, order, d.diagram_id, h, nb, cfg, self.samples[order])
+                    created.append(it)
+                    if self.cache is not None and hasattr(self.b, "set_grid"):
+                        g = self.cache.get(order, d.diagram_id, req.delta, req.n_dens)
+                        if g is not None:
+                            # half the donor's bin structure, half uniform, plus one training iteration
+                            # that is not combined (abbreviated retraining)
+                            u = np.linspace(0.0, 1.0, g.shape[1])[None, :]
+                            self.b.set_grid(h, 0.5 * g + 0.5 * u)
+                            if hasattr(self.b, "set_train"):
+                                self.b.set_train(h, it.cfg, 1)
+                            it.warm = True
             except MemoryError:
                 # the arena refused (its scratch competes with integral state): roll back, retry later
                 for it in created:
@@ -238,7 +296,8 @@ class Server:
                 it.evals += it.samples
                 if (it.n_iter >= self.min_iters and it.sigma <= req.budget) or it.n_iter >= self.max_iters:
                     it.done = True
-                elif self.adaptive and hasattr(self.b, "set_samples") and it.sigma > 0.0 and req.budget > 0.0:
+                elif (self.adaptive and hasattr(self.b, "set_samples") and 0.0 < it.sigma < float("inf")
+                      and req.budget > 0.0):
                     # samples still needed if sigma ~ 1/sqrt(evaluations), spread over a few iterations
                     need = it.evals * ((it.sigma / req.budget) ** 2 - 1.0)
                     left = max(1, self.min_iters - it.n_iter, 4)
@@ -254,6 +313,9 @@ class Server:
                     req.per_order[order] = sum(it.mean for it in req.integrals if it.order == order)
                 req.completed = now
                 for it in req.integrals:
+                    if self.cache is not None and hasattr(self.b, "get_grid"):
+                        self.cache.put(it.order, it.diagram_id, req.delta, req.n_dens, self.b.get_grid(it.handle))
+                    self.warm_starts += int(it.warm)
                     self.b.destroy(it.handle)
                     self.used_bytes -= it.bytes
                 self.n_integrals -= len(req.integrals)

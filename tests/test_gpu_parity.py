@@ -257,6 +257,27 @@ def test_targets_stop_iterating(ctx):
         M.mbpt_destroy_diagram(g)
 
 
+def test_training_iterations_are_not_combined(ctx):
+    """With train_iters = 2 the first two iterations refine the grid but do not enter the
+    combined estimate (oracle combination with skip = 2 on the recorded history)."""
+    po, pm = matter_pair("pnm")
+    D = O.enumerate_diagrams(3)[2]
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=1 << 15, train_iters=2))
+    try:
+        M.mbpt_vegas_iterate(ctx, [g], 1)
+        assert np.isinf(M.mbpt_estimate(g).sigma)
+        M.mbpt_vegas_iterate(ctx, [g], 4)
+        r = M.mbpt_estimate(g)
+        img = M.mbpt_get_state(g)
+        hm = np.frombuffer(img, dtype=np.float64, count=5, offset=M.STATE_HEADER_BYTES + 7 * 8 + 8 + 16)
+        hv = np.frombuffer(img, dtype=np.float64, count=5,
+                           offset=M.STATE_HEADER_BYTES + 7 * 8 + 8 + 16 + 8 * M.MAX_ITERS)
+        m, s, chi = O.combine(hm, hv, skip=2)
+        assert r.n_iter == 5 and r.mean == pytest.approx(m, rel=1e-12) and r.sigma == pytest.approx(s, rel=1e-12)
+    finally:
+        M.mbpt_destroy_diagram(g)
+
+
 def test_freeze_keeps_grid(ctx):
     po, pm = matter_pair("pnm")
     D = O.enumerate_diagrams(3)[0]

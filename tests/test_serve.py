@@ -65,6 +65,22 @@ class FakeBackend:
         del self.live[h]
 
 
+def test_grid_cache_nearest_within_window():
+    c = S.GridCache(window=0.02)
+    c.put(4, 7, 0.5, 0.10, "g10")
+    c.put(4, 7, 0.5, 0.13, "g13")
+    c.put(4, 7, 0.25, 0.11, "other-delta")
+    c.put(3, 7, 0.5, 0.11, "other-order")
+    assert c.get(4, 7, 0.5, 0.105) == "g10"
+    assert c.get(4, 7, 0.5, 0.125) == "g13"
+    assert c.get(4, 7, 0.5, 0.16) is None          # outside the window
+    assert c.get(4, 8, 0.5, 0.10) is None          # other diagram
+    small = S.GridCache(max_entries=2)
+    for i in range(3):
+        small.put(2, 0, 0.0, 0.05 + i, i)
+    assert len(small.entries) == 2 and small.get(2, 0, 0.0, 0.05) is None
+
+
 def test_fermi_momenta():
     kn, kp = S.fermi_momenta(0.16, 0.0)
     assert kn == pytest.approx(kp) and kn == pytest.approx((3 * math.pi ** 2 * 0.08) ** (1 / 3))
@@ -161,6 +177,26 @@ def test_result_same_alone_and_in_mix_gpu():
             alone = S.Server(be, samples_by_order=small, max_iters=30).run([S.Request(**_req(r))], realtime=False)
             assert (alone[0].energy, alone[0].sigma, dict(alone[0].per_order)) == mixd[r.rid]
             assert alone[0].energy < 0.0
+    finally:
+        be.close()
+
+
+@pytest.mark.gpu
+def test_warm_start_seeds_grid_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    be = S.MbptBackend(arena_bytes=1 << 30)
+    try:
+        small = {2: 1 << 15, 3: 1 << 16, 4: 1 << 16}
+        cold = S.Server(be, samples_by_order=small, max_iters=40)
+        r_cold = cold.run([S.Request(0.121, 0.5, 3, 0.003, rid=2)], realtime=False)[0]
+        srv = S.Server(be, samples_by_order=small, max_iters=40, warm_start=True)
+        srv.run([S.Request(0.110, 0.5, 3, 0.003, rid=1)], realtime=False)
+        r_warm = srv.run([S.Request(0.121, 0.5, 3, 0.003, rid=2)], realtime=False)[-1]
+        assert srv.warm_starts == 4                       # 1 + 3 integrals seeded from n = 0.110
+        assert abs(r_warm.energy - r_cold.energy) <= 3 * math.hypot(r_warm.sigma, r_cold.sigma)
+        assert r_warm.sigma <= r_warm.target * abs(r_warm.energy) * 1.2
     finally:
         be.close()
 
