@@ -136,6 +136,14 @@ typedef struct {
  * grid: their estimates are recorded but not combined (PVegas' training phase,
  * Sec. III.C).  The integral stops iterating once its combined standard error
  * is <= max(target_rel*|mean|, target_abs) (0, 0 = never).
+ *
+ * Denominator regulator (Sec. III.A): with n_shifts = 3 every sample also
+ * evaluates the integrand with each energy denominator D_m replaced by
+ * D_m - shift[k] (D_m < 0 on the integration domain, so the shift moves the
+ * pole away), and the quadratic through the three components extrapolated to
+ * zero shift, sum_k L_k w_k with the Lagrange weights L_k of the three shifts;
+ * all four are accumulated and combined like the main estimate (the grid still
+ * adapts to the unshifted integrand).  Read them with mbpt_estimate_shifts.
  */
 typedef struct {
     int32_t n_bins;            /* 2..MBPT_MAX_BINS (50 in the paper's setup) */
@@ -148,7 +156,8 @@ typedef struct {
     double target_rel;
     double target_abs;
     uint32_t train_iters;      /* leading iterations excluded from the combined estimate */
-    uint32_t reserved;
+    uint32_t n_shifts;         /* 0, or 3: denominator regulator components (below) */
+    double shift[3];           /* MeV, positive and distinct */
 } mbpt_vegas_cfg;
 
 typedef struct {
@@ -253,6 +262,9 @@ int mbpt_vegas_iterate(mbpt_ctx* ctx, mbpt_diag* const* diags, int k, int n_iter
 int mbpt_estimate(const mbpt_diag* diag, mbpt_result* out);
 /* The same for k integrals of one context with a single synchronisation; out[i] for diags[i]. */
 int mbpt_estimate_batch(mbpt_diag* const* diags, int k, mbpt_result* out);
+/* Regulator components: mean[k], sigma[k] for shift k = 0..2 and, at index 3, the
+ * extrapolation to zero shift.  MBPT_EINVAL if the integral has no shifts. */
+int mbpt_estimate_shifts(const mbpt_diag* diag, double mean[4], double sigma[4]);
 
 /*
  * Checkpoint: the grid, the iteration history and counters as a host byte

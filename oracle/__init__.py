@@ -96,6 +96,13 @@ def lib():
                                                ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                                P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                                P(ctypes.c_double)]
+            L.oracle_vegas_samples_group.restype = None
+            L.oracle_vegas_samples_group.argtypes = [ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double),
+                                                     P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                                     P(ctypes.c_double), ctypes.c_uint64, ctypes.c_uint32,
+                                                     ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                                     P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                                     P(ctypes.c_double)]
             L.oracle_refine.restype = None
             L.oracle_refine.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int, ctypes.c_double,
                                         P(ctypes.c_double)]
@@ -320,10 +327,11 @@ class Physics:
     reg_power: int = 4
     K_max: float = 7.0
     map_kind: int = 0
+    shift: float = 0.0      # denominator shift s (MeV): D_m -> D_m - s, the regulator of Sec. III.A
 
     def array(self) -> np.ndarray:
         return np.asarray([self.kF_n, self.kF_p, self.hbar2_over_m, self.C_S, self.C_Y, self.m_pi, self.Lam,
-                           float(self.reg_power), self.K_max, float(self.map_kind)], dtype=np.float64)
+                           float(self.reg_power), self.K_max, float(self.map_kind), self.shift], dtype=np.float64)
 
     def dim(self, D: "Diagram") -> int:
         """integration dimension of diagram D under this chord map"""
@@ -396,19 +404,62 @@ class IterationResult:
         return (self.sum_w2 / self.n - self.mean ** 2) / (self.n - 1)
 
 
-def vegas_samples(kind: int, D: Optional[Diagram], ph_arr: np.ndarray, d: int, grid: np.ndarray, seed: int,
+def hole_chords(D: Diagram) -> int:
+    """Number of loop momenta that are hole momenta (integrated over the Fermi ball): the
+    particle-hole composition of the integration domain.  Grouping key of Sec. III.A (reading): at
+    orders 2-5 it takes 1, 2, 4, 5 distinct values, the N_grp column of Table I."""
+    return int(sum(D.hole(l) for l in D.chords))
+
+
+@dataclass
+class Group:
+    """Sum of same-order diagrams integrated as one integrand (Sec. III.A): f(x) = sum_m scale_m f_m(x),
+    every member through its own chord map at the same point x."""
+    members: List[Diagram]
+    scales: List[float]
+
+    @property
+    def n(self) -> int:
+        return self.members[0].n
+
+    @property
+    def d(self) -> int:
+        return self.members[0].d
+
+
+def groups(n: int, skip_anomalous: bool = True) -> dict:
+    """Diagrams of order n grouped by hole_chords (unit scales), key -> Group."""
+    out = {}
+    for D in enumerate_diagrams(n):
+        if skip_anomalous and is_anomalous(D):
+            continue
+        out.setdefault(hole_chords(D), []).append(D)
+    return {k: Group(v, [1.0] * len(v)) for k, v in sorted(out.items())}
+
+
+def group_integrand(G: Group, ph: Physics, x: np.ndarray) -> float:
+    return float(sum(c * integrand(D, ph, x) for D, c in zip(G.members, G.scales)))
+
+
+def vegas_samples(kind: int, D, ph_arr: np.ndarray, d: int, grid: np.ndarray, seed: int,
                   sid: int, t: int, s_begin: int, s_end: int, dump: bool = False):
     L = lib()
     nb = grid.shape[1] - 1
     grid = np.ascontiguousarray(grid, dtype=np.float64)
     sums = np.zeros(2)
     hist = np.zeros(d * nb)
-    info = D.info if D is not None else np.zeros(L.oracle_info_ints(), dtype=np.int32)
     cnt = s_end - s_begin
     dx = np.zeros(cnt * d) if dump else None
     dw = np.zeros(cnt) if dump else None
-    L.oracle_vegas_samples(kind, _ip(info), _dp(ph_arr), d, nb, _dp(grid), seed, sid, t, s_begin, s_end,
-                           _dp(sums), _dp(hist), _dp(dx), _dp(dw))
+    if isinstance(D, Group):
+        infos = np.ascontiguousarray(np.concatenate([m.info for m in D.members]), dtype=np.int32)
+        sc = np.ascontiguousarray(D.scales, dtype=np.float64)
+        L.oracle_vegas_samples_group(len(D.members), _ip(infos), _dp(sc), _dp(ph_arr), d, nb, _dp(grid), seed, sid,
+                                     t, s_begin, s_end, _dp(sums), _dp(hist), _dp(dx), _dp(dw))
+    else:
+        info = D.info if D is not None else np.zeros(L.oracle_info_ints(), dtype=np.int32)
+        L.oracle_vegas_samples(kind, _ip(info), _dp(ph_arr), d, nb, _dp(grid), seed, sid, t, s_begin, s_end,
+                               _dp(sums), _dp(hist), _dp(dx), _dp(dw))
     if dump:
         return sums, hist.reshape(d, nb), dx.reshape(cnt, d), dw
     return sums, hist.reshape(d, nb)

@@ -229,6 +229,8 @@ int oracle_derive(int n, const int* lines, const int* ports, const int* chords, 
  *   ph[6] Lambda (fm^-1), ph[7] regulator exponent (even integer),
  *   ph[8] K_max: upper end of the radial range of particle chords (fm^-1)
  *   ph[9] chord map: 0 full directions, 1 rotational reduction (see chord_momenta)
+ *   ph[10] denominator shift s (MeV): every D_m below is replaced by D_m - s
+ *          (the regulator of Sec. III.A; 0 = the diagram itself)
  * The potential is V(p, p') = [C_S + C_Y / (|p - p'|^2 + m_pi^2)]
  *                             * exp(-(|p|/Lambda)^r - (|p'|/Lambda)^r).
  * ------------------------------------------------------------------------- */
@@ -480,6 +482,7 @@ double oracle_integrand_momenta(const int* info, const double* ph, const double*
             mag += eps;
         }
         if (!(D < 0.0)) return 0.0;   /* only on a measure-zero set */
+        D -= ph[10];
         dprod *= D;
         condsum += mag / fabs(D);
     }
@@ -571,10 +574,10 @@ static double test_integrand(int kind, const double* ph, const double* x, int d)
     return f;
 }
 
-void oracle_vegas_samples(int kind, const int* info, const double* ph, int d, int nb,
-                          const double* grid, uint64_t seed, uint32_t sid, uint32_t t,
-                          uint64_t s_begin, uint64_t s_end,
-                          double* sums, double* hist, double* dump_x, double* dump_w) {
+static void vegas_samples_impl(int kind, int n_members, const int* info, const double* scale,
+                               const double* ph, int d, int nb, const double* grid, uint64_t seed,
+                               uint32_t sid, uint32_t t, uint64_t s_begin, uint64_t s_end, double* sums,
+                               double* hist, double* dump_x, double* dump_w) {
     double sw = 0.0, sw2 = 0.0;
     for (uint64_t s = s_begin; s < s_end; ++s) {
         uint32_t words[4 * ((O_MAXC * 3 + 3) / 4 + 1)];
@@ -598,8 +601,13 @@ void oracle_vegas_samples(int kind, const int* info, const double* ph, int d, in
             bin[a] = i;
         }
         double f;
-        if (kind == 0) f = oracle_integrand(info, ph, x, NULL);
-        else if (kind == 1) f = oracle_first_order_integrand(ph, x);
+        if (kind == 0) {
+            /* a group integrand is the plain sum of its members' integrands at the same point,
+             * each through its own chord map (Sec. III.A, grouped evaluation) */
+            f = 0.0;
+            for (int m = 0; m < n_members; ++m)
+                f += scale[m] * oracle_integrand(info + (size_t)m * OI_END, ph, x, NULL);
+        } else if (kind == 1) f = oracle_first_order_integrand(ph, x);
         else f = test_integrand(kind, ph, x, d);
         double w = jac * f;
         sw += w;
@@ -614,6 +622,25 @@ void oracle_vegas_samples(int kind, const int* info, const double* ph, int d, in
     }
     sums[0] += sw;
     sums[1] += sw2;
+}
+
+void oracle_vegas_samples(int kind, const int* info, const double* ph, int d, int nb,
+                          const double* grid, uint64_t seed, uint32_t sid, uint32_t t,
+                          uint64_t s_begin, uint64_t s_end,
+                          double* sums, double* hist, double* dump_x, double* dump_w) {
+    const double one = 1.0;
+    vegas_samples_impl(kind, 1, info, &one, ph, d, nb, grid, seed, sid, t, s_begin, s_end, sums, hist, dump_x,
+                       dump_w);
+}
+
+/* The same for the sum of n_members diagrams (infos: n_members consecutive info blocks), member m
+ * scaled by scale[m]. */
+void oracle_vegas_samples_group(int n_members, const int* infos, const double* scale, const double* ph, int d,
+                                int nb, const double* grid, uint64_t seed, uint32_t sid, uint32_t t,
+                                uint64_t s_begin, uint64_t s_end, double* sums, double* hist, double* dump_x,
+                                double* dump_w) {
+    vegas_samples_impl(0, n_members, infos, scale, ph, d, nb, grid, seed, sid, t, s_begin, s_end, sums, hist,
+                       dump_x, dump_w);
 }
 
 /*

@@ -138,6 +138,7 @@ constexpr int kGridStride = MBPT_MAX_BINS;   // bins per axis row in shared memo
 struct SampleOut {
     double w;              // J_vegas * f(x)
     uint32_t binpack[5];   // bin index of axis a in byte (a & 3) of word a >> 2
+    double wc[kComp];      // regulator components (shifted denominators, extrapolation); if n_shifts
 };
 
 // V(p, p') for one vertex, FP32, from P = 2p and P' = 2p'.
@@ -192,7 +193,9 @@ __device__ __forceinline__ constexpr int chord_kind(int c) {   // 0 full directi
     return MAPK == 0 ? 0 : (c == 0 ? 1 : (c == 1 ? 2 : 0));
 }
 
-template <int N, int PREC, int MAPK>
+// REG: the integral carries the denominator regulator (a separate instantiation, so that the
+// registers of the plain integrand are not spent on it).
+template <int N, int PREC, int MAPK, bool REG>
 __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* __restrict__ gs, uint32_t s,
                                                  uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1,
                                                  double* x_out) {
@@ -391,11 +394,16 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
     else live = (okn == all);
     if (!live) {
         o.w = 0.0;
+        if (REG) {
+#pragma unroll
+            for (int k = 0; k < kComp; ++k) o.wc[k] = 0.0;
+        }
         return o;
     }
 
     // --- energy denominators (FP64): D~_m = D~_{m-1} + sum over the four lines of vertex m
     double Dprod = 1.0;
+    double Dcut[(REG && N > 1) ? N - 1 : 1];
     {
         double Dm = 0.0;
 #pragma unroll
@@ -406,6 +414,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
                 if (m == 0 && k == 0) Dm = uv;
                 else Dm += uv;
             }
+            if (REG) Dcut[m] = Dm;
             Dprod = (m == 0) ? Dm : Dprod * Dm;
         }
     }
@@ -504,6 +513,22 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
     if (!nonzero(S)) o.w = 0.0;
     else if (PREC == MBPT_FP64) o.w = (R.pref * (jv * jc) * S) / Dprod;
     else o.w = (R.pref * (jv * jc) * S) * rcp_scaled(Dprod);
+    // --- denominator regulator: every D~_m -> D~_m - eta_k (pole moved away from the domain), and
+    // the quadratic through the three components evaluated at zero shift
+    if constexpr (REG) {
+        const double num = nonzero(S) ? R.pref * (jv * jc) * S : 0.0;
+        double ext = 0.0;
+#pragma unroll
+        for (int k = 0; k < kShifts; ++k) {
+            double P = 1.0;
+#pragma unroll
+            for (int m = 0; m < N - 1; ++m) P *= (Dcut[m] - R.eta[k]);
+            const double wk = nonzero(num) ? ((PREC == MBPT_FP64) ? num / P : num * rcp_scaled(P)) : 0.0;
+            o.wc[k] = wk;
+            ext = fma(R.lag[k], wk, ext);
+        }
+        o.wc[kShifts] = ext;
+    }
     return o;
 }
 

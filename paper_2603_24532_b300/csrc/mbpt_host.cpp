@@ -283,6 +283,21 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         set_err(err, errlen, "invalid VEGAS configuration");
         return MBPT_EINVAL;
     }
+    if (cfg.n_shifts != 0 && cfg.n_shifts != (uint32_t)kShifts) {
+        set_err(err, errlen, "n_shifts must be 0 or 3");
+        return MBPT_EINVAL;
+    }
+    if (cfg.n_shifts) {
+        for (int k = 0; k < kShifts; ++k)
+            if (!(cfg.shift[k] > 0.0) || !(cfg.shift[k] < 1e6)) {
+                set_err(err, errlen, "regulator shifts must be positive (MeV)");
+                return MBPT_EINVAL;
+            }
+        if (cfg.shift[0] == cfg.shift[1] || cfg.shift[0] == cfg.shift[2] || cfg.shift[1] == cfg.shift[2]) {
+            set_err(err, errlen, "regulator shifts must be distinct");
+            return MBPT_EINVAL;
+        }
+    }
     memset(r, 0, sizeof(*r));
     int n = d.order, nl = d.n_lines, nc = d.n_chords;
     r->order = n;
@@ -459,6 +474,15 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         else pref *= 4.0 * r->chord_rng[c];
     }
     r->pref = pref;
+    // denominator regulator: D_m - shift in D~ units (D = (hbar^2/2m) D~), Lagrange weights at 0
+    r->n_shifts = (int32_t)cfg.n_shifts;
+    for (int k = 0; k < kShifts; ++k) {
+        r->eta[k] = cfg.n_shifts ? cfg.shift[k] / (0.5 * ph.hbar2_over_m) : 0.0;
+        double L = 1.0;
+        for (int j = 0; j < kShifts; ++j)
+            if (j != k) L *= (0.0 - cfg.shift[j]) / (cfg.shift[k] - cfg.shift[j]);
+        r->lag[k] = cfg.n_shifts ? L : 0.0;
+    }
     return MBPT_OK;
 }
 

@@ -12,6 +12,9 @@ constexpr int kMaxTerms = 1 << MBPT_MAX_DEVICE_ORDER;    // 32 spin-sum terms
 constexpr int kMaxLoops = MBPT_MAX_DEVICE_ORDER + 1;     // loops of one term: at most n+1
 constexpr int kMaxIters = 512;                           // iteration history kept per integral
 constexpr int kThreads = 256;                            // threads per block of the iterate kernel
+constexpr int kShifts = 3;                               // denominator-regulator components
+constexpr int kComp = kShifts + 1;                       // ... plus their extrapolation to zero shift
+constexpr int kSumStride = 2 + 2 * kComp;                // doubles per chunk-sum slot
 constexpr int kWarps = kThreads / 32;
 
 // Compiled, device-resident description of one integral (diagram x physics x VEGAS setup).
@@ -53,6 +56,10 @@ struct alignas(16) DiagRec {
     float CSf, CY4f, mpi2_4f, regc2f;            // FP32 copies; regc2f folds in log2(e)^(1/reg_half)
     int8_t line_slot[MBPT_MAX_LINES];            // slot of each descriptor line
     int32_t map_kind;                            // 0: full chord directions; 1: rotational reduction
+    int32_t n_shifts;                            // 0 or kShifts
+    int32_t pad_s;
+    double eta[kShifts];                         // shifts in units of hbar^2/2m (D~ units)
+    double lag[kShifts];                         // Lagrange weights of the quadratic at zero shift
 };
 
 // Per-integral running state (device).
@@ -68,6 +75,8 @@ struct alignas(16) DiagState {
     int32_t n_used;         // iterations entering the weighted mean
     double hist_mean[kMaxIters];
     double hist_var[kMaxIters];
+    // regulator components (shift 0..2, extrapolation): running inverse-variance sums and estimates
+    double comp_inv_var[kComp], comp_mean_w[kComp], comp_mean[kComp], comp_sigma[kComp];
 };
 
 // One entry of the batch work table.

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
     __shared__ double tmp[kMaxD * MBPT_MAX_BINS];
     __shared__ double old[kMaxD * (MBPT_MAX_BINS + 1)];
     __shared__ double red[2][8];
+    __shared__ double redq[2 * kComp][8];
     __shared__ int s_skip, s_refine;
     const int tid = threadIdx.x;
     for (uint32_t ii = blockIdx.x; ii < hdr->n_items; ii += gridDim.x) {
@@ -65,8 +66,18 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
         }
         double a = 0.0, b = 0.0;
         for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x) {
-            a += csum[2 * (size_t)(W.chunk_begin + c)];
-            b += csum[2 * (size_t)(W.chunk_begin + c) + 1];
+            a += csum[kSumStride * (size_t)(W.chunk_begin + c)];
+            b += csum[kSumStride * (size_t)(W.chunk_begin + c) + 1];
+        }
+        const int nsh = W.rec->n_shifts;
+        if (nsh) {
+            for (int q = 0; q < 2 * kComp; ++q) {
+                double v = 0.0;
+                for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x)
+                    v += csum[kSumStride * (size_t)(W.chunk_begin + c) + 2 + q];
+                v = warp_sum(v);
+                if ((tid & 31) == 0) redq[q][tid >> 5] = v;
+            }
         }
         a = warp_sum(a);
         b = warp_sum(b);
@@ -76,9 +87,19 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
         }
         const int d = W.rec->d, nb = W.rec->nb;
         for (int i = tid; i < d * nb; i += blockDim.x) {
-            double acc = 0.0;
-            for (uint32_t c = 0; c < W.n_chunks; ++c)
-                acc += (double)chist[(size_t)(W.chunk_begin + c) * (size_t)W.hist_stride + i];
+            // eight independent partial sums (memory-level parallelism), combined in a fixed order
+            const float* col = chist + (size_t)W.chunk_begin * (size_t)W.hist_stride + i;
+            const size_t st = (size_t)W.hist_stride;
+            // FP32 partial sums (each over n_chunks/8 slots), widened and combined in FP64
+            float p[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            uint32_t c = 0;
+            for (; c + 8 <= W.n_chunks; c += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) p[u] += col[(size_t)(c + u) * st];
+            }
+            for (; c < W.n_chunks; ++c) p[0] += col[(size_t)c * st];
+            const double acc = ((widen_f(p[0]) + widen_f(p[1])) + (widen_f(p[2]) + widen_f(p[3]))) +
+                               ((widen_f(p[4]) + widen_f(p[5])) + (widen_f(p[6]) + widen_f(p[7])));
             hsum[i] = acc;
             last_hist[ii][i] = acc;
         }
@@ -131,6 +152,29 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
             st->mean = mean;
             st->sigma = sigma;
             st->chi2 = chi2;
+            if (nsh) {
+                // regulator components: same combination as the main estimate
+                for (int q = 0; q < kComp; ++q) {
+                    double Aq = 0.0, Bq = 0.0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                        Aq += redq[2 * q][w];
+                        Bq += redq[2 * q + 1][w];
+                    }
+                    const double Iq = Aq / M;
+                    const double vq = (Bq / M - Iq * Iq) / (M - 1.0);
+                    if (vq > 0.0 && !training) {
+                        st->comp_inv_var[q] += 1.0 / vq;
+                        st->comp_mean_w[q] += Iq / vq;
+                    }
+                    if (st->comp_inv_var[q] > 0.0) {
+                        st->comp_mean[q] = st->comp_mean_w[q] / st->comp_inv_var[q];
+                        st->comp_sigma[q] = sqrt(1.0 / st->comp_inv_var[q]);
+                    } else {
+                        st->comp_mean[q] = Iq;
+                        st->comp_sigma[q] = training ? (double)INFINITY : 0.0;
+                    }
+                }
+            }
             st->n_evals += (int64_t)W.samples;
             st->iter = t + 1;
             const bool has_target = (W.target_rel > 0.0) || (W.target_abs > 0.0);
@@ -149,7 +193,7 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
 template <int N, int PREC, int MAPK>
 __device__ void dump_one(const DiagRec& R, const Grid2* gs, uint32_t s, uint32_t t, uint32_t sid, uint32_t k0,
                          uint32_t k1, double* x, double* w) {
-    const SampleOut o = eval_sample<N, PREC, MAPK>(R, gs, s, t, sid, k0, k1, x);
+    const SampleOut o = eval_sample<N, PREC, MAPK, false>(R, gs, s, t, sid, k0, k1, x);
     *w = o.w;
 }
 

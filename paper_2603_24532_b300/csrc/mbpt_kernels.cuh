@@ -17,7 +17,9 @@ struct alignas(16) ChunkSmemT {
     DiagRec rec;
     Grid2 grid[kMaxD * kGridStride];
     float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
+    double cacc[2 * kComp][NW * 32];         // per-thread sums of the regulator components
     double red[2][NW];
+    double redc[2 * kComp][NW];
     uint32_t chunk, item, iter, skip;
 };
 using ChunkSmem = ChunkSmemT<kWarps>;
@@ -64,7 +66,7 @@ __device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, 
     }
 }
 
-template <int N, int PREC, int MAPK, int NW>
+template <int N, int PREC, int MAPK, bool REG, int NW>
 __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
     const DiagRec& R = S.rec;
@@ -78,9 +80,16 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     for (int j = 0; j < W.spt; ++j) {
         const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
         if (s < W.samples) {
-            const SampleOut o = eval_sample<N, PREC, MAPK>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1, nullptr);
+            const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1, nullptr);
             sw += o.w;
             sw2 = fma(o.w, o.w, sw2);
+            if constexpr (REG) {
+#pragma unroll
+                for (int c = 0; c < kComp; ++c) {
+                    S.cacc[2 * c][threadIdx.x] += o.wc[c];
+                    S.cacc[2 * c + 1][threadIdx.x] = fma(o.wc[c], o.wc[c], S.cacc[2 * c + 1][threadIdx.x]);
+                }
+            }
             if (nonzero(o.w)) {
                 const float wf = narrow_trunc(o.w);
                 float w2 = wf * wf;
@@ -147,20 +156,23 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
         const int prec = effective_precision(S.rec.precision, W.grid, d, nb);
         load_grid(S.grid, W.grid, d, nb, prec);
         for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
+        for (int c = 0; c < 2 * kComp; ++c) S.cacc[c][tid] = 0.0;
         __syncthreads();
         double sw = 0.0, sw2 = 0.0;
         const uint32_t cl = chunk - W.chunk_begin;
-        switch ((order * 3 + prec) * 2 + S.rec.map_kind) {
-#define MBPT_CASE(N_, P_, M_) \
-    case (N_ * 3 + P_) * 2 + M_: run_chunk<N_, P_, M_, NW>(S, W, cl, sw, sw2); break;
+        switch (((order * 3 + prec) * 2 + S.rec.map_kind) * 2 + (S.rec.n_shifts ? 1 : 0)) {
+#define MBPT_CASE(N_, P_, M_, R_) \
+    case ((N_ * 3 + P_) * 2 + M_) * 2 + R_: run_chunk<N_, P_, M_, (R_ != 0), NW>(S, W, cl, sw, sw2); break;
+#define MBPT_CASE2(N_, P_, M_) MBPT_CASE(N_, P_, M_, 0) MBPT_CASE(N_, P_, M_, 1)
 #define MBPT_CASES(N_) \
-    MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
-    MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)
+    MBPT_CASE2(N_, MBPT_FP64, 0) MBPT_CASE2(N_, MBPT_MIXED, 0) MBPT_CASE2(N_, MBPT_MIXED_MAP64, 0) \
+    MBPT_CASE2(N_, MBPT_FP64, 1) MBPT_CASE2(N_, MBPT_MIXED, 1) MBPT_CASE2(N_, MBPT_MIXED_MAP64, 1)
             MBPT_CASES(2)
             MBPT_CASES(3)
             MBPT_CASES(4)
             MBPT_CASES(5)
 #undef MBPT_CASES
+#undef MBPT_CASE2
 #undef MBPT_CASE
             default:
                 if (tid == 0) atomicOr(&hdr->error, 2u);
@@ -172,14 +184,27 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             S.red[1][warp] = sw2;
         }
         __syncthreads();
+        if (S.rec.n_shifts) {
+            for (int c = 0; c < 2 * kComp; ++c) {
+                const double v = warp_sum(S.cacc[c][tid]);
+                if (lane == 0) S.redc[c][warp] = v;
+            }
+        }
+        __syncthreads();
         if (tid == 0) {
             double a = 0.0, b = 0.0;
             for (int w = 0; w < NW; ++w) {
                 a += S.red[0][w];
                 b += S.red[1][w];
             }
-            csum[2 * (size_t)chunk] = a;
-            csum[2 * (size_t)chunk + 1] = b;
+            csum[kSumStride * (size_t)chunk] = a;
+            csum[kSumStride * (size_t)chunk + 1] = b;
+            if (S.rec.n_shifts)
+                for (int c = 0; c < 2 * kComp; ++c) {
+                    double v = 0.0;
+                    for (int w = 0; w < NW; ++w) v += S.redc[c][w];
+                    csum[kSumStride * (size_t)chunk + 2 + c] = v;
+                }
         }
         float* dst = chist + (size_t)chunk * (size_t)W.hist_stride;
         for (int i = tid; i < d * nb; i += blockDim.x) {

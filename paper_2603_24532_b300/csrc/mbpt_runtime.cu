@@ -195,10 +195,10 @@ int ensure_batch_buffers(mbpt_ctx* c, size_t n_items, size_t n_chunks, size_t hi
     if (n_chunks > c->chunks_cap) {
         size_t cap = std::max(n_chunks, c->chunks_cap + c->chunks_cap / 2);
         c->arena.release(c->d_csum);
-        c->d_csum = (double*)c->arena.alloc(sizeof(double) * 2 * cap);
+        c->d_csum = (double*)c->arena.alloc(sizeof(double) * kSumStride * cap);
         if (!c->d_csum) {
             cap = n_chunks;
-            c->d_csum = (double*)c->arena.alloc(sizeof(double) * 2 * cap);
+            c->d_csum = (double*)c->arena.alloc(sizeof(double) * kSumStride * cap);
         }
         if (!c->d_csum) {
             c->chunks_cap = 0;
@@ -490,7 +490,8 @@ int mbpt_set_config(mbpt_diag* g, const mbpt_vegas_cfg* cfg) {
     if (!g || !cfg || !g->ctx || !g->ctx->diags.count(g)) return fail(MBPT_EINVAL, "set_config: bad argument");
     const mbpt_vegas_cfg& o = g->cfg;
     if (cfg->n_bins != o.n_bins || cfg->precision != o.precision || cfg->seed != o.seed ||
-        cfg->stream_id != o.stream_id || cfg->alpha != o.alpha)
+        cfg->stream_id != o.stream_id || cfg->alpha != o.alpha || cfg->n_shifts != o.n_shifts ||
+        (o.n_shifts && (cfg->shift[0] != o.shift[0] || cfg->shift[1] != o.shift[1] || cfg->shift[2] != o.shift[2])))
         return fail(MBPT_EINVAL, "set_config: only samples_per_iter, freeze_after, train_iters and the targets may change");
     if (cfg->samples_per_iter < 2 || cfg->samples_per_iter >= (1ull << 32) || !(cfg->target_rel >= 0.0) ||
         !(cfg->target_abs >= 0.0))
@@ -621,6 +622,23 @@ int mbpt_estimate_batch(mbpt_diag* const* diags, int k, mbpt_result* out) {
         out[i].n_evals = s.n_evals;
         out[i].converged = s.converged;
         out[i].status = s.status;
+    }
+    return MBPT_OK;
+}
+
+int mbpt_estimate_shifts(const mbpt_diag* g, double mean[4], double sigma[4]) {
+    if (!g || !mean || !sigma || !g->ctx) return fail(MBPT_EINVAL, "estimate_shifts: NULL argument");
+    if (!g->cfg.n_shifts) return fail(MBPT_EINVAL, "estimate_shifts: the integral has no regulator shifts");
+    mbpt_ctx* c = g->ctx;
+    DeviceGuard dg(c->device);
+    int st = check_device_error(c);
+    if (st) return st;
+    double buf[4 * kComp];
+    CUDA_TRY(cudaMemcpyAsync(buf, g->d_state->comp_inv_var, sizeof(buf), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < kComp; ++q) {
+        mean[q] = buf[2 * kComp + q];
+        sigma[q] = buf[3 * kComp + q];
     }
     return MBPT_OK;
 }
@@ -788,8 +806,8 @@ __global__ void __launch_bounds__(256) k_reduce_noalloc(const WorkItem* __restri
     const int tid = threadIdx.x;
     double a = 0.0, b = 0.0;
     for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x) {
-        a += csum[2 * (size_t)c];
-        b += csum[2 * (size_t)c + 1];
+        a += csum[kSumStride * (size_t)c];
+        b += csum[kSumStride * (size_t)c + 1];
     }
     a = warp_sum(a);
     b = warp_sum(b);
@@ -821,6 +839,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
                                             const mbpt_vegas_cfg* cfg, uint32_t iter, const double* grid,
                                             double* out, void* cuda_stream) {
     if (!desc || !ph || !cfg || !grid || !out) return fail(MBPT_EINVAL, "iteration_noalloc: NULL argument");
+    if (cfg->n_shifts) return fail(MBPT_EINVAL, "iteration_noalloc: denominator regulator not supported here");
     if (device < 0 || device >= kNoAllocMaxDevices) return fail(MBPT_EINVAL, "iteration_noalloc: bad device");
     DiagRec rec;
     char err[256] = {0};
@@ -834,10 +853,10 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t off_hdr = 0, off_item = up(sizeof(WorkHeader)), off_rec = off_item + up(sizeof(WorkItem));
     const size_t off_state = off_rec + up(sizeof(DiagRec)), off_csum = off_state + up(sizeof(DiagState));
-    const size_t off_chist = off_csum + up(sizeof(double) * 2 * n_chunks);
+    const size_t off_chist = off_csum + up(sizeof(double) * kSumStride * n_chunks);
     const size_t need = off_chist + sizeof(float) * nh * n_chunks;
     if (need > kNoAllocScratchBytes) {
-        const uint64_t per_chunk = 16 + 4 * nh;
+        const uint64_t per_chunk = 8 * kSumStride + 4 * nh;
         const uint64_t max_chunks = (kNoAllocScratchBytes - off_csum - 512) / per_chunk;
         return fail(MBPT_EINVAL, "iteration_noalloc: " + std::to_string(cfg->samples_per_iter) +
                                      " samples need " + std::to_string(need) + " bytes of scratch, more than the " +

@@ -114,7 +114,8 @@ class mbpt_vegas_cfg(ctypes.Structure):
         ("stream_id", ctypes.c_uint32), ("freeze_after", ctypes.c_uint32),
         ("samples_per_iter", ctypes.c_uint64),
         ("target_rel", ctypes.c_double), ("target_abs", ctypes.c_double),
-        ("train_iters", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("train_iters", ctypes.c_uint32), ("n_shifts", ctypes.c_uint32),
+        ("shift", ctypes.c_double * 3),
     ]
 
 
@@ -161,6 +162,7 @@ def lib():
             "mbpt_vegas_iterate": [vp, P(vp), ctypes.c_int, ctypes.c_int],
             "mbpt_estimate": [vp, P(mbpt_result)],
             "mbpt_estimate_batch": [P(vp), ctypes.c_int, P(mbpt_result)],
+            "mbpt_estimate_shifts": [vp, P(ctypes.c_double), P(ctypes.c_double)],
             "mbpt_get_state": [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
             "mbpt_set_state": [vp, vp, ctypes.c_size_t],
             "mbpt_dump_samples": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P(ctypes.c_double),
@@ -286,6 +288,14 @@ def mbpt_estimate(diag) -> mbpt_result:
     return r
 
 
+def mbpt_estimate_shifts(diag):
+    """(mean[4], sigma[4]): the three shifted integrals and their extrapolation to zero shift."""
+    mean = np.zeros(4)
+    sigma = np.zeros(4)
+    check(lib().mbpt_estimate_shifts(diag, _dp(mean), _dp(sigma)))
+    return mean, sigma
+
+
 def mbpt_estimate_batch(diags: Sequence) -> List[mbpt_result]:
     k = len(diags)
     if k == 0:
@@ -338,7 +348,8 @@ def mbpt_vegas_iteration_noalloc(device: int, desc: mbpt_diagram_desc, phys: mbp
 # ---------------------------------------------------------------------------
 STATE_HEADER_BYTES = 24
 MAX_ITERS = 512
-DIAGSTATE_BYTES = 7 * 8 + 8 + 4 * 4 + 2 * MAX_ITERS * 8
+N_COMP = 4
+DIAGSTATE_BYTES = 7 * 8 + 8 + 4 * 4 + 2 * MAX_ITERS * 8 + 4 * N_COMP * 8
 
 
 def state_grid(image: bytes, d: int, nb: int) -> np.ndarray:
@@ -379,11 +390,17 @@ def physics(kF_n=1.0, kF_p=0.0, hbar2_over_m=41.47, C_S=-50.0, C_Y=-200.0, m_pi=
 
 
 def vegas_cfg(samples=1 << 18, seed=1, stream_id=0, precision=MBPT_FP64, n_bins=50, alpha=1.5, freeze_after=0,
-              target_rel=0.0, target_abs=0.0, train_iters=0) -> mbpt_vegas_cfg:
+              target_rel=0.0, target_abs=0.0, train_iters=0, shifts=None) -> mbpt_vegas_cfg:
     c = mbpt_vegas_cfg()
     c.n_bins, c.precision, c.alpha = n_bins, precision, alpha
     c.seed, c.stream_id, c.freeze_after = seed, stream_id, freeze_after
     c.samples_per_iter = samples
     c.target_rel, c.target_abs = target_rel, target_abs
     c.train_iters = train_iters
+    if shifts:
+        if len(shifts) != 3:
+            raise ValueError("the denominator regulator takes exactly three shifts")
+        c.n_shifts = 3
+        for k, v in enumerate(shifts):
+            c.shift[k] = float(v)
     return c

@@ -32,9 +32,14 @@ def main():
     ap.add_argument("--oracle-integrals", type=int, default=48)
     ap.add_argument("--oracle-samples", type=int, default=1 << 16)
     ap.add_argument("--map-kind", type=int, default=0)
+    ap.add_argument("--dedup-mirrors", action="store_true",
+                    help="one integral per pair of mirror (complex-conjugate) diagrams, counted twice")
     a = ap.parse_args()
     ctx = M.mbpt_ctx_create(0, 16 << 30)
     descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
+    if a.dedup_mirrors:
+        descs = [d for d in descs if d.diagram_id <= d.mirror_id]
+    mult = {d.diagram_id: (2 if (a.dedup_mirrors and d.mirror_id != d.diagram_id) else 1) for d in descs}
     kfs = (1.0, 1.33, 1.6)
     gs, meta = [], []
     for ki, kf in enumerate(kfs):
@@ -50,8 +55,8 @@ def main():
     res = M.mbpt_estimate_batch(gs)
     for ki, kf in enumerate(kfs):
         idx = [i for i, (k, _) in enumerate(meta) if k == kf]
-        order_sum = abs(sum(res[i].mean for i in idx))
-        floor = a.target * order_sum / math.sqrt(len(idx))
+        order_sum = abs(sum(mult[meta[i][1].diagram_id] * res[i].mean for i in idx))
+        floor = a.target * order_sum / math.sqrt(sum(mult[meta[i][1].diagram_id] ** 2 for i in idx))
         for i in idx:
             cfg = M.vegas_cfg(samples=a.samples, seed=1, stream_id=1000 * ki + meta[i][1].diagram_id,
                               precision=M.MBPT_MIXED, target_rel=a.target, target_abs=floor)
@@ -72,8 +77,9 @@ def main():
     per_kf = {}
     for ki, kf in enumerate(kfs):
         idx = [i for i, (k, _) in enumerate(meta) if k == kf]
-        per_kf[str(kf)] = {"E5_sum": float(sum(res[i].mean for i in idx)),
-                           "sigma": float(math.sqrt(sum(res[i].sigma ** 2 for i in idx)))}
+        per_kf[str(kf)] = {"E5_sum": float(sum(mult[meta[i][1].diagram_id] * res[i].mean for i in idx)),
+                           "sigma": float(math.sqrt(sum((mult[meta[i][1].diagram_id] * res[i].sigma) ** 2
+                                                        for i in idx)))}
 
     # per-diagram deviation of the mixed evaluation from the FP64 oracle on identical samples
     dev = None
@@ -103,7 +109,8 @@ def main():
                              "same grid and counters"}
     out = {"workload": "all 840 fifth-order diagrams (668 non-anomalous) x kF {1.0, 1.33, 1.6}, PNM, mixed, "
                        "to %.2g relative (or iteration cap %d)" % (a.target, a.max_iters),
-           "integrals": len(gs), "samples_per_iter": a.samples, "map_kind": a.map_kind, "wall_s": wall,
+           "integrals": len(gs), "dedup_mirrors": a.dedup_mirrors, "samples_per_iter": a.samples,
+           "map_kind": a.map_kind, "wall_s": wall,
            "iterations": iters, "evals": evals, "evals_per_s": evals / wall, "converged": int(conv),
            "median_rel_err": float(np.median(rel)) if rel else None, "per_kF": per_kf,
            "oracle_deviation": dev}

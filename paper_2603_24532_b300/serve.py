@@ -80,6 +80,7 @@ class Integral:
     samples: int = 0
     evals: int = 0
     warm: bool = False
+    mult: int = 1
     mean: float = 0.0
     sigma: float = float("inf")
     n_iter: int = 0
@@ -90,18 +91,31 @@ class MbptBackend:
     """The C ABI as the server's backend (all work on the GPU)."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, arena_ptr: int = 0, stream: int = 0,
-                 precision: Optional[int] = None, map_kind: int = 1):
+                 precision: Optional[int] = None, map_kind: int = 1, dedup_mirrors: bool = True):
         from . import mbpt as M
         self.M = M
         self.map_kind = map_kind
+        self.dedup_mirrors = dedup_mirrors
         self.ctx = M.mbpt_ctx_create(device, arena_bytes, arena_ptr=arena_ptr, stream=stream)
         self.precision = M.MBPT_MIXED if precision is None else precision
         self._descs = {}
 
     def diagrams(self, order: int):
+        """Non-anomalous diagrams; with mirror deduplication one representative per pair of
+        complex-conjugate (time- and arrow-reversed) diagrams, whose integrands are equal sample by
+        sample for a real symmetric potential, each with its multiplicity (1 or 2): the N_eff
+        diagrams of Table I."""
         if order not in self._descs:
-            self._descs[order] = [d for d in self.M.mbpt_generate(order) if not d.anomalous]
+            ds = [d for d in self.M.mbpt_generate(order) if not d.anomalous]
+            if self.dedup_mirrors:
+                ds = [d for d in ds if d.diagram_id <= d.mirror_id]
+            self._descs[order] = ds
         return self._descs[order]
+
+    def multiplicity(self, desc) -> int:
+        if not self.dedup_mirrors:
+            return 1
+        return 1 if desc.mirror_id == desc.diagram_id else 2
 
     def physics(self, kF_n: float, kF_p: float):
         return self.M.physics(kF_n=kF_n, kF_p=kF_p, K_max=max(kF_n, kF_p) + 6.0, map_kind=self.map_kind)
@@ -251,7 +265,8 @@ class Server:
             try:
                 for order, d, phys, cfg, nb in plan:
                     h = self.b.create(d, phys, cfg)
-                    it = Integral(req, order, d.diagram_id, h, nb, cfg, self.samples[order])
+                    it = Integral(req, order, d.diagram_id, h, nb, cfg, self.samples[order],
+                                  mult=self.b.multiplicity(d) if hasattr(self.b, "multiplicity") else 1)
                     created.append(it)
                     if self.cache is not None and hasattr(self.b, "set_grid"):
                         g = self.cache.get(order, d.diagram_id, req.delta, req.n_dens)
@@ -286,10 +301,12 @@ class Server:
         still = []
         for req in self.active:
             req.rounds += 1
-            e_sum = sum(it.mean for it in req.integrals)
+            e_sum = sum(it.mult * it.mean for it in req.integrals)
             if req.budget is None:
                 # per-integral error budget from the first (pilot) estimate of the request's sum
-                req.budget = req.target * abs(e_sum) / math.sqrt(len(req.integrals))
+                # (a representative of a mirror pair counts twice)
+                n_eff = sum(it.mult ** 2 for it in req.integrals)
+                req.budget = req.target * abs(e_sum) / math.sqrt(n_eff)
             for it in req.integrals:
                 if it.done:
                     continue
@@ -308,9 +325,9 @@ class Server:
                         it.samples = nxt
             if all(it.done for it in req.integrals):
                 req.energy = e_sum
-                req.sigma = math.sqrt(sum(it.sigma ** 2 for it in req.integrals))
+                req.sigma = math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals))
                 for order in range(2, req.cap + 1):
-                    req.per_order[order] = sum(it.mean for it in req.integrals if it.order == order)
+                    req.per_order[order] = sum(it.mult * it.mean for it in req.integrals if it.order == order)
                 req.completed = now
                 for it in req.integrals:
                     if self.cache is not None and hasattr(self.b, "get_grid"):

@@ -42,12 +42,13 @@ def first_order_contact(kF, g, C_S):
     return C_S * n * (g - 1) / (2.0 * g)
 
 
-def second_order(kF, g, hbar2_over_m, C_S, C_Y, m_pi, Lam, r=4, n_rad=12, n_ang=10, pmax=8.0, cross=True):
+def second_order(kF, g, hbar2_over_m, C_S, C_Y, m_pi, Lam, r=4, n_rad=12, n_ang=10, pmax=8.0, cross=True,
+                 shift=0.0):
     """E^(2)/N = (1/n) (1/4) sum_spins int d^3k_i d^3k_j d^3k_a/(2pi)^9 |<ab|V|ij>|^2 / D
     with P = (k_i + k_j)/2, p = (k_i - k_j)/2, p' = (k_a - k_b)/2 (Jacobian 8),
     D = (hbar^2/m)(p^2 - p'^2), spin sum g^2 (V_d^2 + V_e^2) - 2 g V_d V_e.
     P along z, p in the xz-plane; holes need P^2 + p^2 + 2Pp|cos t_p| < kF^2,
-    particles P^2 + p'^2 - 2Pp'|cos t'| >= kF^2."""
+    particles P^2 + p'^2 - 2Pp'|cos t'| >= kF^2.  shift s replaces D by D - s."""
     n = g * kF ** 3 / (6.0 * math.pi ** 2)
     Pn, Pw = gl(0.0, kF, n_rad)
     total = 0.0
@@ -102,7 +103,7 @@ def second_order(kF, g, hbar2_over_m, C_S, C_Y, m_pi, Lam, r=4, n_rad=12, n_ang=
             vd = (C_S + C_Y / (qd2 + m_pi ** 2)) * reg
             ve = (C_S + C_Y / (qe2 + m_pi ** 2)) * reg
             S = g * g * (vd ** 2 + ve ** 2) - (2.0 * g * vd * ve if cross else 0.0)
-            Dn = hbar2_over_m * (p ** 2 - PP ** 2)
+            Dn = hbar2_over_m * (p ** 2 - PP ** 2) - shift
             W = (wct[:, None, None, None] * (pp_w * pp_nodes ** 2)[None, :, None, None]
                  * wctp[None, :, :, None] * phw[None, None, None, :])
             inner = float(np.sum(W * S / Dn)) * 4.0

@@ -278,6 +278,62 @@ def test_training_iterations_are_not_combined(ctx):
         M.mbpt_destroy_diagram(g)
 
 
+@pytest.mark.parametrize("prec", [M.MBPT_FP64, M.MBPT_MIXED])
+def test_denominator_regulator_components(ctx, prec):
+    """Regulator of Sec. III.A: each sample also evaluates the integrand with every energy
+    denominator D_m replaced by D_m - s_k; after one iteration each component's mean and error
+    match the oracle's iteration with that shift (same grid, same counters), the fourth component
+    is the quadratic extrapolation sum_k L_k I_k to s = 0, and the main estimate is unchanged."""
+    import dataclasses
+    rng = np.random.default_rng(12)
+    po, pm = matter_pair("pnm")
+    D = O.enumerate_diagrams(4)[7]
+    shifts = (3.0, 6.0, 9.0)
+    M_s = 30000 + 77
+    grid = random_grid(D.d, 50, rng, strength=0.4)
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=M_s, seed=4, stream_id=21, precision=prec,
+                                                                 shifts=shifts))
+    g0 = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=M_s, seed=4, stream_id=21, precision=prec))
+    try:
+        for h in (g, g0):
+            M.mbpt_set_state(h, M.state_with_grid(M.mbpt_get_state(h), grid))
+        M.mbpt_vegas_iterate(ctx, [g, g0], 1)
+        r, r0 = M.mbpt_estimate(g), M.mbpt_estimate(g0)
+        assert r.last_mean == r0.last_mean and r.last_sigma == r0.last_sigma
+        mean, sigma = M.mbpt_estimate_shifts(g)
+        rel = 1e-11 if prec == M.MBPT_FP64 else 1e-4
+        refs = [O.vegas_iteration(D, dataclasses.replace(po, shift=s), grid, 4, 21, 0, M_s) for s in shifts]
+        for k in range(3):
+            assert mean[k] == pytest.approx(refs[k].mean, rel=rel)
+            assert sigma[k] == pytest.approx(np.sqrt(refs[k].var_of_mean), rel=10 * rel)
+        lag = [np.prod([(0.0 - shifts[j]) / (shifts[k] - shifts[j]) for j in range(3) if j != k]) for k in range(3)]
+        ext = sum(L * ref.mean for L, ref in zip(lag, refs))
+        scale = sum(abs(L * ref.mean) for L, ref in zip(lag, refs))
+        assert abs(mean[3] - ext) <= rel * scale
+        # shifts move every denominator away from zero: each component smaller than the last
+        assert abs(refs[2].mean) < abs(refs[1].mean) < abs(refs[0].mean)
+        with pytest.raises(M.MbptError):
+            M.mbpt_estimate_shifts(g0)
+        M.mbpt_vegas_iterate(ctx, [g], 3)
+        mean, sigma = M.mbpt_estimate_shifts(g)
+        assert np.all(np.isfinite(mean)) and np.all(sigma > 0) and np.all(np.isfinite(sigma))
+    finally:
+        M.mbpt_destroy_diagram(g)
+        M.mbpt_destroy_diagram(g0)
+
+
+def test_denominator_regulator_rejects_bad_shifts(ctx):
+    po, pm = matter_pair("pnm")
+    D = O.enumerate_diagrams(3)[0]
+    for sh in ((0.0, 1.0, 2.0), (1.0, 1.0, 2.0), (-1.0, 1.0, 2.0)):
+        with pytest.raises(M.MbptError):
+            M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=1000, shifts=sh))
+    cfg = M.vegas_cfg(samples=1000, shifts=(1.0, 2.0, 3.0))
+    cfg.n_shifts = 2
+    with pytest.raises(M.MbptError):
+        M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
+
+
 def test_freeze_keeps_grid(ctx):
     po, pm = matter_pair("pnm")
     D = O.enumerate_diagrams(3)[0]

@@ -64,6 +64,42 @@ def test_second_order_snm_vs_gauss_legendre():
     assert within(m, s, q2(-200.0, g=4))
 
 
+def test_shifted_denominator_second_order_vs_quadrature():
+    """Denominator regulator (Sec. III.A): with D -> D - s the oracle's second-order VEGAS estimate
+    matches the relative-coordinate quadrature with the same shift; the shift only moves D away from
+    its pole (|E(s)| < |E(0)|); and the quadratic through three shifts, evaluated at s = 0, lands much
+    closer to the unshifted energy than the smallest shift does."""
+    (D,) = O.enumerate_diagrams(2)
+    shifts = (2.0, 4.0, 6.0)
+    qs = [Q.second_order(1.0, 2, 41.47, -50.0, -200.0, 0.7, 2.0, n_rad=10, n_ang=10, shift=s) for s in shifts]
+    q0 = q2(-200.0)
+    assert abs(qs[0]) < abs(q0) and abs(qs[2]) < abs(qs[1]) < abs(qs[0])
+    m, s, chi, _ = O.vegas(D, O.Physics(shift=shifts[1]), 10, 1 << 16, seed=1)
+    assert within(m, s, qs[1])
+    assert s < 5e-3 * abs(qs[1])
+    lag = [np.prod([(0.0 - shifts[j]) / (shifts[k] - shifts[j]) for j in range(3) if j != k]) for k in range(3)]
+    ext = float(np.dot(lag, qs))
+    assert abs(ext - q0) < 0.2 * abs(qs[0] - q0)
+
+
+def test_shifted_denominator_per_sample():
+    """At every sample the shifted integrand is the unshifted one times D/(D - s) for the single
+    second-order cut: same sign, smaller magnitude (D < 0 on the whole domain)."""
+    (D,) = O.enumerate_diagrams(2)
+    rng = np.random.default_rng(8)
+    ph0, ph1 = O.Physics(), O.Physics(shift=5.0)
+    nz = 0
+    for _ in range(400):
+        x = rng.random(D.d)
+        f0, f1 = O.integrand(D, ph0, x), O.integrand(D, ph1, x)
+        if f0 == 0.0:
+            assert f1 == 0.0
+            continue
+        nz += 1
+        assert np.sign(f1) == np.sign(f0) and abs(f1) < abs(f0)
+    assert nz > 20
+
+
 def test_rotational_reduction_second_order_vs_quadrature():
     """Chord map 1 (chord 0 along z, chord 1 in the xz plane, 4 pi x 2 pi integrated out; Sec. III.C)
     integrates the same Eq. (2) in 6 instead of 9 dimensions."""

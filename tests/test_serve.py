@@ -182,6 +182,30 @@ def test_result_same_alone_and_in_mix_gpu():
 
 
 @pytest.mark.gpu
+def test_mirror_dedup_gives_the_same_request_energy_gpu():
+    """One representative per mirror pair, counted twice, reproduces the full diagram sum: the
+    pair's integrals are equal sample by sample, so with the representatives' streams the two
+    servers agree to the statistical error of the non-shared integrals."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    small = {2: 1 << 15, 3: 1 << 16, 4: 1 << 16}
+    full = S.MbptBackend(arena_bytes=1 << 30, dedup_mirrors=False)
+    ded = S.MbptBackend(arena_bytes=1 << 30, dedup_mirrors=True)
+    try:
+        assert len(full.diagrams(4)) == 33 and len(ded.diagrams(4)) == 27
+        assert sum(ded.multiplicity(d) for d in ded.diagrams(4)) == 33
+        req = dict(n_dens=0.16, delta=0.0, cap=4, target=0.01, arrival=0.0, rid=3)
+        a = S.Server(full, samples_by_order=small, max_iters=40).run([S.Request(**req)], realtime=False)[0]
+        b = S.Server(ded, samples_by_order=small, max_iters=40).run([S.Request(**req)], realtime=False)[0]
+        assert len(b.integrals) == 1 + 3 + 27 and len(a.integrals) == 1 + 3 + 33
+        assert abs(a.energy - b.energy) <= 3 * math.hypot(a.sigma, b.sigma)
+    finally:
+        full.close()
+        ded.close()
+
+
+@pytest.mark.gpu
 def test_warm_start_seeds_grid_gpu():
     import torch
     if not torch.cuda.is_available():
