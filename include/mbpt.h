@@ -71,6 +71,7 @@ typedef enum {
 #define MBPT_MAX_LINES 12
 #define MBPT_MAX_CHORDS 7
 #define MBPT_MAX_BINS 64
+#define MBPT_MAX_GROUP 1024       /* members of one group integral */
 
 /* descriptor flags */
 #define MBPT_FLAG_ANOMALOUS   1   /* a hole and a particle forced to equal momentum: zero at T = 0 */
@@ -186,6 +187,14 @@ typedef struct {
  */
 int mbpt_generate(int order, mbpt_diagram_desc* out, int cap, int* count);
 
+/*
+ * Grouping key of a descriptor (grouped evaluation, Sec. III.A and Table I's N_grp): the number of
+ * its loop momenta (chords) that are hole lines, i.e. how many integration momenta lie in the Fermi
+ * ball.  Diagrams of one order with equal keys share the integration domain; at orders 2..5 the key
+ * takes 1, 2, 4 and 5 distinct values.  MBPT_EINVAL for a NULL argument or bad chord index.
+ */
+int mbpt_hole_chords(const mbpt_diagram_desc* desc, int* out);
+
 /* ---- context ------------------------------------------------------------- */
 
 /*
@@ -200,6 +209,8 @@ int mbpt_ctx_destroy(mbpt_ctx* ctx);
 int mbpt_ctx_mem(const mbpt_ctx* ctx, size_t* used, size_t* largest_free);
 /* Device bytes one integral with this descriptor and configuration needs. */
 int mbpt_diag_bytes(const mbpt_diagram_desc* desc, const mbpt_vegas_cfg* cfg, size_t* bytes);
+/* The same for a group integral of k members (mbpt_create_group); the members' order is that of descs[0]. */
+int mbpt_group_bytes(const mbpt_diagram_desc* descs, int k, const mbpt_vegas_cfg* cfg, size_t* bytes);
 
 /*
  * Launch shape of mbpt_vegas_iterate.  The sample-evaluation kernel is compiled
@@ -239,6 +250,19 @@ int mbpt_ctx_stream(const mbpt_ctx* ctx, void** cuda_stream);
  */
 int mbpt_create_diagram(mbpt_ctx* ctx, const mbpt_diagram_desc* desc, const mbpt_physics* physics,
                         const mbpt_vegas_cfg* cfg, mbpt_diag** out);
+/*
+ * Grouped evaluation (Sec. III.A): one integral whose integrand is the sum of k diagrams of the same
+ * order, member m scaled by scale[m] (NULL: all 1; e.g. 2 for one diagram standing for a mirror
+ * pair), every member mapped through its own chord map from the same sampled point x, so that one
+ * VEGAS grid adapts to the sum and the members' fluctuations are correlated.  One physics point and
+ * configuration for all members; the result (mbpt_estimate, the regulator components, the state
+ * image) is that of the sum.  Each sample costs k integrand evaluations; a chunk holds
+ * kGroupSlots / (1 + 4 if regulated) samples per thread.  MBPT_EINVAL for k outside
+ * 1..MBPT_MAX_GROUP, mixed orders, a non-finite scale or any member that create_diagram would reject.
+ * mbpt_dump_samples of a group returns the summed weight.
+ */
+int mbpt_create_group(mbpt_ctx* ctx, const mbpt_diagram_desc* descs, int k, const double* scale,
+                      const mbpt_physics* physics, const mbpt_vegas_cfg* cfg, mbpt_diag** out);
 int mbpt_destroy_diagram(mbpt_diag* diag);
 /*
  * Change an integral's samples per iteration, freeze point, training iterations and targets for its

@@ -2,7 +2,7 @@
 continuous-batching server on one GPU and report latency percentiles and throughput.
 
     python -m paper_2603_24532_b300.bench_serve [--requests 1200] [--rate 20] [--seed 7]
-        [--budget-gb 40] [--time-limit 300]
+        [--budget-gb 40] [--time-limit 300] [--warm-start] [--grouped]
 
 Requests (seed 7, exponential gaps of mean 1/rate): n ~ U[0.04, 0.20] fm^-3, delta from
 {0, 0.25, 0.5, 0.75, 1}, order cap from {2, 3, 4}, relative target from {1%, 0.3%, 0.1%};
@@ -27,8 +27,9 @@ def main():
     ap.add_argument("--time-limit", type=float, default=None)
     ap.add_argument("--max-iters", type=int, default=60)
     ap.add_argument("--warm-start", action="store_true")
+    ap.add_argument("--grouped", action="store_true", help="one integral per (order, particle-hole group)")
     a = ap.parse_args()
-    be = S.MbptBackend(arena_bytes=int(a.arena_gb * (1 << 30)))
+    be = S.MbptBackend(arena_bytes=int(a.arena_gb * (1 << 30)), grouped=a.grouped)
     srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters, warm_start=a.warm_start)
     trace = S.poisson_trace(a.requests, a.rate, a.seed)
     t0 = time.perf_counter()
@@ -44,7 +45,7 @@ def main():
            "diagrams_per_s": n_int / wall, "evals_per_s": srv.evals / wall, "rounds": srv.rounds,
            "completed_by_cap": caps, "budget_bytes": srv.budget,
            "target_met_fraction": len(met) / max(1, len(done)),
-           "warm_start": a.warm_start, "warm_started_integrals": srv.warm_starts,
+           "warm_start": a.warm_start, "warm_started_integrals": srv.warm_starts, "grouped": a.grouped,
            "rounds_per_request": {"median": float(sorted(rounds)[len(rounds) // 2]) if rounds else None,
                                   "max": max(rounds) if rounds else None},
            "example": [{"n": r.n_dens, "delta": r.delta, "cap": r.cap, "target": r.target, "E_corr": r.energy,

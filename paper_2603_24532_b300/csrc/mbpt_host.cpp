@@ -510,3 +510,17 @@ extern "C" int mbpt_generate(int order, mbpt_diagram_desc* out, int cap, int* co
     }
     return MBPT_OK;
 }
+
+extern "C" int mbpt_hole_chords(const mbpt_diagram_desc* d, int* out) {
+    if (!d || !out || d->n_chords < 0 || d->n_chords > MBPT_MAX_CHORDS || d->n_lines < 0 ||
+        d->n_lines > MBPT_MAX_LINES)
+        return MBPT_EINVAL;
+    int h = 0;
+    for (int c = 0; c < d->n_chords; ++c) {
+        const int l = d->chord_line[c];
+        if (l < 0 || l >= d->n_lines) return MBPT_EINVAL;
+        h += d->line_src[l] > d->line_dst[l];   // src above dst in time: a hole line
+    }
+    *out = h;
+    return MBPT_OK;
+}

@@ -15,6 +15,8 @@ constexpr int kThreads = 256;                            // threads per block of
 constexpr int kShifts = 3;                               // denominator-regulator components
 constexpr int kComp = kShifts + 1;                       // ... plus their extrapolation to zero shift
 constexpr int kSumStride = 2 + 2 * kComp;                // doubles per chunk-sum slot
+// grouped evaluation: per-thread shared-memory slots holding per-sample sums over the members
+constexpr int kGroupSlots = 8;
 constexpr int kWarps = kThreads / 32;
 
 // Compiled, device-resident description of one integral (diagram x physics x VEGAS setup).
@@ -94,7 +96,7 @@ struct alignas(16) WorkItem {
     int32_t spt;           // samples per thread per chunk
     int32_t hist_stride;   // floats per chunk histogram slot
     uint32_t train_iters;  // leading iterations not combined into the estimate
-    int32_t pad1;
+    uint32_t n_members;    // records at rec[0..n_members): > 1 is a group integral (sum of the members)
 };
 
 struct alignas(16) WorkHeader {

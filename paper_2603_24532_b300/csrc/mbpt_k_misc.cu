@@ -87,19 +87,8 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
         }
         const int d = W.rec->d, nb = W.rec->nb;
         for (int i = tid; i < d * nb; i += blockDim.x) {
-            // eight independent partial sums (memory-level parallelism), combined in a fixed order
-            const float* col = chist + (size_t)W.chunk_begin * (size_t)W.hist_stride + i;
-            const size_t st = (size_t)W.hist_stride;
-            // FP32 partial sums (each over n_chunks/8 slots), widened and combined in FP64
-            float p[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            uint32_t c = 0;
-            for (; c + 8 <= W.n_chunks; c += 8) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) p[u] += col[(size_t)(c + u) * st];
-            }
-            for (; c < W.n_chunks; ++c) p[0] += col[(size_t)c * st];
-            const double acc = ((widen_f(p[0]) + widen_f(p[1])) + (widen_f(p[2]) + widen_f(p[3]))) +
-                               ((widen_f(p[4]) + widen_f(p[5])) + (widen_f(p[6]) + widen_f(p[7])));
+            const double acc = hist_column_sum(chist + (size_t)W.chunk_begin * (size_t)W.hist_stride + i,
+                                               (size_t)W.hist_stride, W.n_chunks);
             hsum[i] = acc;
             last_hist[ii][i] = acc;
         }
@@ -197,36 +186,46 @@ __device__ void dump_one(const DiagRec& R, const Grid2* gs, uint32_t s, uint32_t
     *w = o.w;
 }
 
-__global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, const double* grid, uint64_t seed, uint32_t sid,
-                                             uint32_t iter, uint64_t first, uint64_t count, double* xo,
-                                             double* wo) {
+__global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members, const double* grid, uint64_t seed,
+                                             uint32_t sid, uint32_t iter, uint64_t first, uint64_t count,
+                                             double* xo, double* wo) {
     __shared__ DiagRec R;
     __shared__ Grid2 gs[kMaxD * kGridStride];
     load_record(&R, rec);
     __syncthreads();
     const int prec = effective_precision(R.precision, grid, R.d, R.nb);
     load_grid(gs, grid, R.d, R.nb, prec);
-    __syncthreads();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+    const bool active = i < count;
     const uint32_t s = (uint32_t)(first + i);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    double* x = xo ? xo + i * R.d : nullptr;
-    double* w = wo + i;
-    switch ((R.order * 3 + prec) * 2 + R.map_kind) {
+    double* x = (xo && active) ? xo + i * R.d : nullptr;
+    double acc = 0.0;
+    // a group integral: the sum of its members' weights at the same point
+    for (int m = 0; m < n_members; ++m) {
+        if (m > 0) load_record(&R, rec + m);
+        __syncthreads();
+        double w = 0.0;
+        if (active) {
+            switch ((R.order * 3 + prec) * 2 + R.map_kind) {
 #define MBPT_CASE(N_, P_, M_) \
-    case (N_ * 3 + P_) * 2 + M_: dump_one<N_, P_, M_>(R, gs, s, iter, sid, k0, k1, x, w); break;
+    case (N_ * 3 + P_) * 2 + M_: dump_one<N_, P_, M_>(R, gs, s, iter, sid, k0, k1, m == 0 ? x : nullptr, &w); break;
 #define MBPT_CASES(N_) \
     MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
     MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)
-        MBPT_CASES(2)
-        MBPT_CASES(3)
-        MBPT_CASES(4)
-        MBPT_CASES(5)
+                MBPT_CASES(2)
+                MBPT_CASES(3)
+                MBPT_CASES(4)
+                MBPT_CASES(5)
 #undef MBPT_CASES
 #undef MBPT_CASE
-        default: *w = 0.0;
+                default: w = 0.0;
+            }
+        }
+        acc = (m == 0) ? w : acc + w;
+        __syncthreads();
     }
+    if (active) wo[i] = acc;
 }
 
 __global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,

@@ -18,6 +18,7 @@ struct alignas(16) ChunkSmemT {
     Grid2 grid[kMaxD * kGridStride];
     float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
     double cacc[2 * kComp][NW * 32];         // per-thread sums of the regulator components
+    double gacc[kGroupSlots][NW * 32];       // group integrals: per-sample sums over the members
     double red[2][NW];
     double redc[2 * kComp][NW];
     uint32_t chunk, item, iter, skip;
@@ -66,6 +67,45 @@ __device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, 
     }
 }
 
+// Histogram of w^2 over the sample's bins (warp-private FP32 bins; clamped below FLT_MAX).
+template <int D>
+__device__ __forceinline__ void hist_add(float* hist, int nb, const uint32_t* binpack, double w) {
+    const float wf = narrow_trunc(w);
+    float w2 = wf * wf;
+    if (!(w2 <= 3.0e38f)) w2 = 3.0e38f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const uint32_t i = (binpack[a >> 2] >> (8 * (a & 3))) & 0xffu;
+        atomicAdd(&hist[a * nb + i], w2);
+    }
+}
+
+// Bin indices of sample s alone (the same integer map as eval_sample: i = floor((u + 1/2) 2^-32 nb)).
+template <int D>
+__device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1,
+                                            uint32_t nb, uint32_t* binpack) {
+    constexpr int NBLK = (D + 3) / 4;
+#pragma unroll
+    for (int w = 0; w < 5; ++w) binpack[w] = 0;
+#pragma unroll
+    for (int j = 0; j < NBLK; ++j) {
+        uint32_t u[4];
+        philox4x32_10(s, t, sid, (uint32_t)j, k0, k1, u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int a = 4 * j + q;
+            if (a < D) {
+                const uint32_t i = (uint32_t)(((2ull * (uint64_t)u[q] + 1ull) * (uint64_t)nb) >> 33);
+                binpack[a >> 2] |= i << (8 * (a & 3));
+            }
+        }
+    }
+}
+
+// One chunk: samples first + j*blockDim + tid, j < spt.  A group integral (n_members > 1) evaluates
+// every member at each sample, member by member with the record swapped in shared memory, summing
+// the weights per sample in gacc (spt x (1 + regulator components) <= kGroupSlots slots per thread);
+// sums, squares and the histogram then see the group's integrand.
 template <int N, int PREC, int MAPK, bool REG, int NW>
 __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
@@ -77,10 +117,32 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     float* hist = S.hist[threadIdx.x >> 5];
     const int nb = R.nb;
     constexpr int D = 3 * (N + 1) - 3 * MAPK;
-    for (int j = 0; j < W.spt; ++j) {
-        const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
-        if (s < W.samples) {
-            const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1, nullptr);
+    constexpr int PER = REG ? 1 + kComp : 1;        // group slots per sample
+    const int nm = (int)W.n_members;
+    const bool grp = nm > 1;
+    for (int m = 0; m < nm; ++m) {
+        if (m > 0) {
+            __syncthreads();
+            load_record(&S.rec, W.rec + m);
+            __syncthreads();
+        }
+        for (int j = 0; j < W.spt; ++j) {
+            const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
+            if (s >= W.samples) continue;
+            const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1,
+                                                                nullptr);
+            if (grp) {
+                double* a = &S.gacc[j * PER][threadIdx.x];
+                a[0] = (m == 0) ? o.w : a[0] + o.w;
+                if constexpr (REG) {
+#pragma unroll
+                    for (int c = 0; c < kComp; ++c) {
+                        double& v = S.gacc[j * PER + 1 + c][threadIdx.x];
+                        v = (m == 0) ? o.wc[c] : v + o.wc[c];
+                    }
+                }
+                continue;
+            }
             sw += o.w;
             sw2 = fma(o.w, o.w, sw2);
             if constexpr (REG) {
@@ -90,18 +152,44 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
                     S.cacc[2 * c + 1][threadIdx.x] = fma(o.wc[c], o.wc[c], S.cacc[2 * c + 1][threadIdx.x]);
                 }
             }
-            if (nonzero(o.w)) {
-                const float wf = narrow_trunc(o.w);
-                float w2 = wf * wf;
-                if (!(w2 <= 3.0e38f)) w2 = 3.0e38f;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const uint32_t i = (o.binpack[a >> 2] >> (8 * (a & 3))) & 0xffu;
-                    atomicAdd(&hist[a * nb + i], w2);
-                }
-            }
+            if (nonzero(o.w)) hist_add<D>(hist, nb, o.binpack, o.w);
         }
     }
+    if (!grp) return;
+    for (int j = 0; j < W.spt; ++j) {
+        const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
+        if (s >= W.samples) continue;
+        const double w = S.gacc[j * PER][threadIdx.x];
+        sw += w;
+        sw2 = fma(w, w, sw2);
+        if constexpr (REG) {
+#pragma unroll
+            for (int c = 0; c < kComp; ++c) {
+                const double v = S.gacc[j * PER + 1 + c][threadIdx.x];
+                S.cacc[2 * c][threadIdx.x] += v;
+                S.cacc[2 * c + 1][threadIdx.x] = fma(v, v, S.cacc[2 * c + 1][threadIdx.x]);
+            }
+        }
+        if (nonzero(w)) {
+            uint32_t bp[5];
+            sample_bins<D>((uint32_t)s, t, W.stream_id, k0, k1, (uint32_t)nb, bp);
+            hist_add<D>(hist, nb, bp, w);
+        }
+    }
+}
+
+// Sum over n chunk slots of one histogram entry (col[c * stride]): eight FP32 partial sums
+// (independent loads in flight), widened and combined in FP64 in a fixed order.
+__device__ __forceinline__ double hist_column_sum(const float* __restrict__ col, size_t stride, uint32_t n) {
+    float p[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    uint32_t c = 0;
+    for (; c + 8 <= n; c += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) p[u] += col[(size_t)(c + u) * stride];
+    }
+    for (; c < n; ++c) p[0] += col[(size_t)c * stride];
+    return ((widen_f(p[0]) + widen_f(p[1])) + (widen_f(p[2]) + widen_f(p[3]))) +
+           ((widen_f(p[4]) + widen_f(p[5])) + (widen_f(p[6]) + widen_f(p[7])));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -3,6 +3,8 @@
 // reduction, iteration combination and grid refinement) and the C ABI.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -155,13 +157,14 @@ struct mbpt_diag {
     double* d_grid = nullptr;
     double* d_last_hist = nullptr;
     int d = 0, nb = 0;
+    int n_members = 1;        // > 1: group integral, d_rec holds n_members records
 };
 
 namespace {
 
-size_t state_block_bytes(int d, int nb) {
+size_t state_block_bytes(int d, int nb, int n_members = 1) {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return up(sizeof(DiagRec)) + up(sizeof(DiagState)) + up(sizeof(double) * d * (nb + 1)) +
+    return up(sizeof(DiagRec) * (size_t)n_members) + up(sizeof(DiagState)) + up(sizeof(double) * d * (nb + 1)) +
            up(sizeof(double) * d * nb);
 }
 
@@ -395,6 +398,15 @@ int mbpt_diag_bytes(const mbpt_diagram_desc* desc, const mbpt_vegas_cfg* cfg, si
     return MBPT_OK;
 }
 
+int mbpt_group_bytes(const mbpt_diagram_desc* descs, int k, const mbpt_vegas_cfg* cfg, size_t* bytes) {
+    if (!descs || !cfg || !bytes) return fail(MBPT_EINVAL, "group_bytes: NULL argument");
+    if (k < 1 || k > MBPT_MAX_GROUP) return fail(MBPT_EINVAL, "group_bytes: member count must be 1..MBPT_MAX_GROUP");
+    if (descs[0].n_chords < 1 || descs[0].n_chords > MBPT_MAX_CHORDS || cfg->n_bins < 2 || cfg->n_bins > MBPT_MAX_BINS)
+        return fail(MBPT_EINVAL, "group_bytes: invalid sizes");
+    *bytes = state_block_bytes(3 * descs[0].n_chords, cfg->n_bins, k);
+    return MBPT_OK;
+}
+
 int mbpt_kernel_variants(int* tpb, int* minb, int cap, int* count) {
     if (!count) return fail(MBPT_EINVAL, "kernel_variants: NULL count");
     *count = kNumVariants;
@@ -438,39 +450,49 @@ int mbpt_ctx_get_launch(const mbpt_ctx* c, int order, int* tpb, int* minb, int* 
     return MBPT_OK;
 }
 
-int mbpt_create_diagram(mbpt_ctx* c, const mbpt_diagram_desc* desc, const mbpt_physics* ph,
-                        const mbpt_vegas_cfg* cfg, mbpt_diag** out) {
-    if (!c || !desc || !ph || !cfg || !out) return fail(MBPT_EINVAL, "create_diagram: NULL argument");
-    DiagRec rec;
+static int create_integral(mbpt_ctx* c, const mbpt_diagram_desc* descs, int k, const double* scale,
+                           const mbpt_physics* ph, const mbpt_vegas_cfg* cfg, mbpt_diag** out, const char* who) {
+    std::vector<DiagRec> recs((size_t)k);
     char err[256] = {0};
-    int st = compile_record(*desc, *ph, *cfg, &rec, err, sizeof(err));
-    if (st) return fail(st, std::string("create_diagram: ") + err);
+    for (int m = 0; m < k; ++m) {
+        int st = compile_record(descs[m], *ph, *cfg, &recs[m], err, sizeof(err));
+        if (st) return fail(st, std::string(who) + ": member " + std::to_string(m) + ": " + err);
+        if (recs[m].order != recs[0].order)
+            return fail(MBPT_EINVAL, std::string(who) + ": members must have the same order");
+        if (scale) {
+            if (!std::isfinite(scale[m])) return fail(MBPT_EINVAL, std::string(who) + ": non-finite member scale");
+            recs[m].pref *= scale[m];
+        }
+    }
     DeviceGuard dg(c->device);
-    const int d = rec.d, nb = rec.nb;
-    char* blk = (char*)c->arena.alloc(state_block_bytes(d, nb));
-    if (!blk) return fail(MBPT_ENOMEM, "create_diagram: arena exhausted");
+    const int d = recs[0].d, nb = recs[0].nb;
+    char* blk = (char*)c->arena.alloc(state_block_bytes(d, nb, k));
+    if (!blk) return fail(MBPT_ENOMEM, std::string(who) + ": arena exhausted");
     mbpt_diag* g = new (std::nothrow) mbpt_diag();
     if (!g) {
         c->arena.release(blk);
-        return fail(MBPT_ENOMEM, "create_diagram: host allocation");
+        return fail(MBPT_ENOMEM, std::string(who) + ": host allocation");
     }
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t rec_bytes = up(sizeof(DiagRec) * (size_t)k);
     g->ctx = c;
-    g->desc = *desc;
+    g->desc = descs[0];
     g->phys = *ph;
     g->cfg = *cfg;
     g->d = d;
     g->nb = nb;
+    g->n_members = k;
     g->d_rec = (DiagRec*)blk;
-    g->d_state = (DiagState*)(blk + up(sizeof(DiagRec)));
-    g->d_grid = (double*)(blk + up(sizeof(DiagRec)) + up(sizeof(DiagState)));
+    g->d_state = (DiagState*)(blk + rec_bytes);
+    g->d_grid = (double*)(blk + rec_bytes + up(sizeof(DiagState)));
     g->d_last_hist = (double*)((char*)g->d_grid + up(sizeof(double) * d * (nb + 1)));
     std::vector<double> grid((size_t)d * (nb + 1));
     for (int a = 0; a < d; ++a)
         for (int i = 0; i <= nb; ++i) grid[(size_t)a * (nb + 1) + i] = (double)i / nb;
     DiagState s0;
     memset(&s0, 0, sizeof(s0));
-    cudaError_t e = cudaMemcpyAsync(g->d_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(g->d_rec, recs.data(), sizeof(DiagRec) * (size_t)k, cudaMemcpyHostToDevice,
+                                    c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->d_grid, grid.data(), sizeof(double) * grid.size(), cudaMemcpyHostToDevice, c->stream);
@@ -479,11 +501,24 @@ int mbpt_create_diagram(mbpt_ctx* c, const mbpt_diagram_desc* desc, const mbpt_p
     if (e != cudaSuccess) {
         c->arena.release(blk);
         delete g;
-        return fail(MBPT_ECUDA, std::string("create_diagram upload: ") + cudaGetErrorString(e));
+        return fail(MBPT_ECUDA, std::string(who) + " upload: " + cudaGetErrorString(e));
     }
     c->diags.insert(g);
     *out = g;
     return MBPT_OK;
+}
+
+int mbpt_create_diagram(mbpt_ctx* c, const mbpt_diagram_desc* desc, const mbpt_physics* ph,
+                        const mbpt_vegas_cfg* cfg, mbpt_diag** out) {
+    if (!c || !desc || !ph || !cfg || !out) return fail(MBPT_EINVAL, "create_diagram: NULL argument");
+    return create_integral(c, desc, 1, nullptr, ph, cfg, out, "create_diagram");
+}
+
+int mbpt_create_group(mbpt_ctx* c, const mbpt_diagram_desc* descs, int k, const double* scale,
+                      const mbpt_physics* ph, const mbpt_vegas_cfg* cfg, mbpt_diag** out) {
+    if (!c || !descs || !ph || !cfg || !out) return fail(MBPT_EINVAL, "create_group: NULL argument");
+    if (k < 1 || k > MBPT_MAX_GROUP) return fail(MBPT_EINVAL, "create_group: member count must be 1..MBPT_MAX_GROUP");
+    return create_integral(c, descs, k, scale, ph, cfg, out, "create_group");
 }
 
 int mbpt_set_config(mbpt_diag* g, const mbpt_vegas_cfg* cfg) {
@@ -541,7 +576,9 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         w.samples = g->cfg.samples_per_iter;
         w.seed = g->cfg.seed;
         w.stream_id = g->cfg.stream_id;
-        w.spt = c->spt[g->desc.order];
+        w.n_members = (uint32_t)g->n_members;
+        // a group keeps per-sample member sums in kGroupSlots shared-memory slots per thread
+        w.spt = g->n_members > 1 ? kGroupSlots / (g->cfg.n_shifts ? 1 + kComp : 1) : c->spt[g->desc.order];
         const uint64_t cs = (uint64_t)kVariants[c->variant].tpb * (uint64_t)w.spt;
         w.n_chunks = (uint32_t)((w.samples + cs - 1) / cs);
         w.chunk_begin = (uint32_t)chunk;
@@ -718,8 +755,8 @@ int mbpt_dump_samples(mbpt_diag* g, int64_t iter, int64_t first, int64_t count, 
         return fail(MBPT_ENOMEM, "dump_samples: arena exhausted");
     }
     const int blocks = (int)((count + 255) / 256);
-    k_dump<<<blocks, 256, 0, c->stream>>>(g->d_rec, g->d_grid, g->cfg.seed, g->cfg.stream_id, (uint32_t)iter,
-                                          (uint64_t)first, (uint64_t)count, dx, dw);
+    k_dump<<<blocks, 256, 0, c->stream>>>(g->d_rec, g->n_members, g->d_grid, g->cfg.seed, g->cfg.stream_id,
+                                          (uint32_t)iter, (uint64_t)first, (uint64_t)count, dx, dw);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && x)
         e = cudaMemcpyAsync(x, dx, sizeof(double) * (size_t)count * g->d, cudaMemcpyDeviceToHost, c->stream);
@@ -826,11 +863,8 @@ __global__ void __launch_bounds__(256) k_reduce_noalloc(const WorkItem* __restri
         out[1] = B;
     }
     const int nh = W.rec->d * W.rec->nb;
-    for (int i = tid; i < nh; i += blockDim.x) {
-        double acc = 0.0;
-        for (uint32_t c = 0; c < W.n_chunks; ++c) acc += (double)chist[(size_t)c * (size_t)W.hist_stride + i];
-        out[2 + i] = acc;
-    }
+    for (int i = tid; i < nh; i += blockDim.x)
+        out[2 + i] = hist_column_sum(chist + i, (size_t)W.hist_stride, W.n_chunks);   // as k_finalize
 }
 
 }  // namespace
@@ -889,6 +923,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     w.n_chunks = (uint32_t)n_chunks;
     w.alpha = cfg->alpha;
     w.spt = spt;
+    w.n_members = 1;
     w.hist_stride = (int32_t)nh;
     CUDA_TRY(cudaMemcpyAsync(base + off_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(base + off_item, &w, sizeof(w), cudaMemcpyHostToDevice, s));

@@ -157,6 +157,10 @@ def lib():
             "mbpt_ctx_last_timing": [vp, P(ctypes.c_double), P(ctypes.c_double)],
             "mbpt_ctx_stream": [vp, P(vp)],
             "mbpt_create_diagram": [vp, P(mbpt_diagram_desc), P(mbpt_physics), P(mbpt_vegas_cfg), P(vp)],
+            "mbpt_create_group": [vp, P(mbpt_diagram_desc), ctypes.c_int, P(ctypes.c_double), P(mbpt_physics),
+                                  P(mbpt_vegas_cfg), P(vp)],
+            "mbpt_hole_chords": [P(mbpt_diagram_desc), P(ctypes.c_int)],
+            "mbpt_group_bytes": [P(mbpt_diagram_desc), ctypes.c_int, P(mbpt_vegas_cfg), P(ctypes.c_size_t)],
             "mbpt_destroy_diagram": [vp],
             "mbpt_set_config": [vp, P(mbpt_vegas_cfg)],
             "mbpt_vegas_iterate": [vp, P(vp), ctypes.c_int, ctypes.c_int],
@@ -227,6 +231,13 @@ def mbpt_diag_bytes(desc: mbpt_diagram_desc, cfg: mbpt_vegas_cfg) -> int:
     return b.value
 
 
+def mbpt_group_bytes(descs: Sequence[mbpt_diagram_desc], cfg: mbpt_vegas_cfg) -> int:
+    arr = (mbpt_diagram_desc * max(1, len(descs)))(*descs)
+    b = ctypes.c_size_t()
+    check(lib().mbpt_group_bytes(arr, len(descs), ctypes.byref(cfg), ctypes.byref(b)))
+    return b.value
+
+
 def mbpt_kernel_variants():
     n = ctypes.c_int()
     check(lib().mbpt_kernel_variants(None, None, 0, ctypes.byref(n)))
@@ -267,6 +278,27 @@ def mbpt_create_diagram(ctx, desc: mbpt_diagram_desc, phys: mbpt_physics, cfg: m
     check(lib().mbpt_create_diagram(ctx, ctypes.byref(desc), ctypes.byref(phys), ctypes.byref(cfg),
                                     ctypes.byref(g)))
     return g
+
+
+def mbpt_create_group(ctx, descs: Sequence[mbpt_diagram_desc], phys: mbpt_physics, cfg: mbpt_vegas_cfg,
+                      scales: Optional[Sequence[float]] = None):
+    """One integral over the sum of same-order diagrams (member m scaled by scales[m])."""
+    k = len(descs)
+    arr = (mbpt_diagram_desc * max(1, k))(*descs)
+    sc = None
+    if scales is not None:
+        if len(scales) != k:
+            raise ValueError("one scale per member")
+        sc = (ctypes.c_double * k)(*[float(v) for v in scales])
+    g = ctypes.c_void_p()
+    check(lib().mbpt_create_group(ctx, arr, k, sc, ctypes.byref(phys), ctypes.byref(cfg), ctypes.byref(g)))
+    return g
+
+
+def mbpt_hole_chords(desc: mbpt_diagram_desc) -> int:
+    out = ctypes.c_int(0)
+    check(lib().mbpt_hole_chords(ctypes.byref(desc), ctypes.byref(out)))
+    return out.value
 
 
 def mbpt_destroy_diagram(diag):

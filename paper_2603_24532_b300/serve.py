@@ -4,7 +4,8 @@ A request asks for the correlation energy per particle sum_{k=2}^{cap} E^(k)/N o
 matter at density n (fm^-3) and isospin asymmetry delta, to a relative statistical error
 `target`.  It expands into one integral per non-anomalous Hugenholtz diagram of orders
 2..cap at kF_n = (3 pi^2 n (1 + delta)/2)^(1/3), kF_p = (3 pi^2 n (1 - delta)/2)^(1/3)
-(Sec. II; a species with zero density is absent).
+(Sec. II; a species with zero density is absent).  With a grouped backend an order expands
+instead into one integral per particle-hole group of its diagrams (Sec. III.A).
 
 The loop (one "round" per VEGAS iteration of every resident integral):
   1. admit waiting requests in arrival order while the device arena holds their integrals
@@ -87,15 +88,32 @@ class Integral:
     done: bool = False
 
 
+class GroupUnit:
+    """The diagrams of one order sharing a particle-hole composition (number of hole loop momenta),
+    integrated as one integrand (Sec. III.A); member scales carry mirror multiplicities."""
+
+    def __init__(self, order: int, key: int, descs, scales):
+        self.order = order
+        self.key = key
+        self.diagram_id = 1000 + key      # unit id within the order (stream ids, grid cache)
+        self.mirror_id = self.diagram_id
+        self.descs = list(descs)
+        self.scales = list(scales)
+
+
 class MbptBackend:
-    """The C ABI as the server's backend (all work on the GPU)."""
+    """The C ABI as the server's backend (all work on the GPU).  With grouped=True each order of a
+    request is a handful of group integrals (Table I's N_grp) instead of one integral per diagram."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, arena_ptr: int = 0, stream: int = 0,
-                 precision: Optional[int] = None, map_kind: int = 1, dedup_mirrors: bool = True):
+                 precision: Optional[int] = None, map_kind: int = 1, dedup_mirrors: bool = True,
+                 grouped: bool = False):
         from . import mbpt as M
         self.M = M
         self.map_kind = map_kind
         self.dedup_mirrors = dedup_mirrors
+        self.grouped = grouped
+        self._units = {}
         self.ctx = M.mbpt_ctx_create(device, arena_bytes, arena_ptr=arena_ptr, stream=stream)
         self.precision = M.MBPT_MIXED if precision is None else precision
         self._descs = {}
@@ -112,10 +130,25 @@ class MbptBackend:
             self._descs[order] = ds
         return self._descs[order]
 
-    def multiplicity(self, desc) -> int:
+    def units(self, order: int):
+        """What one order of a request expands into: diagrams, or groups of them."""
+        if not self.grouped:
+            return self.diagrams(order)
+        if order not in self._units:
+            by_key = {}
+            for d in self.diagrams(order):
+                by_key.setdefault(self.M.mbpt_hole_chords(d), []).append(d)
+            self._units[order] = [GroupUnit(order, k, ds, [self._mult(d) for d in ds])
+                                  for k, ds in sorted(by_key.items())]
+        return self._units[order]
+
+    def _mult(self, desc) -> int:
         if not self.dedup_mirrors:
             return 1
         return 1 if desc.mirror_id == desc.diagram_id else 2
+
+    def multiplicity(self, unit) -> int:
+        return 1 if isinstance(unit, GroupUnit) else self._mult(unit)
 
     def physics(self, kF_n: float, kF_p: float):
         return self.M.physics(kF_n=kF_n, kF_p=kF_p, K_max=max(kF_n, kF_p) + 6.0, map_kind=self.map_kind)
@@ -124,10 +157,14 @@ class MbptBackend:
         return self.M.vegas_cfg(samples=samples, seed=seed, stream_id=stream_id, precision=self.precision)
 
     def nbytes(self, desc, cfg) -> int:
+        if isinstance(desc, GroupUnit):
+            return self.M.mbpt_group_bytes(desc.descs, cfg)
         return self.M.mbpt_diag_bytes(desc, cfg)
 
     def create(self, desc, phys, cfg):
         try:
+            if isinstance(desc, GroupUnit):
+                return self.M.mbpt_create_group(self.ctx, desc.descs, phys, cfg, scales=desc.scales)
             return self.M.mbpt_create_diagram(self.ctx, desc, phys, cfg)
         except self.M.MbptError as e:
             if e.status == self.M.MBPT_ENOMEM:
@@ -241,7 +278,7 @@ class Server:
         phys = self.b.physics(kn, kp)
         plan = []
         for order in range(2, req.cap + 1):
-            for d in self.b.diagrams(order):
+            for d in (self.b.units(order) if hasattr(self.b, "units") else self.b.diagrams(order)):
                 sid = (req.rid * 8 + order) * 1024 + d.diagram_id
                 cfg = self.b.cfg(self.samples[order], sid & 0xFFFFFFFF, self.seed)
                 plan.append((order, d, phys, cfg, self.b.nbytes(d, cfg)))

@@ -16,6 +16,15 @@ def test_table1_counts(n):
     assert len(O.enumerate_diagrams(n)) == want[n]
 
 
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_table1_group_counts(n):
+    """Grouping by the number of hole loop momenta (the particle-hole composition of the integration
+    domain) reproduces Table I's N_grp column, anomalous diagrams included or not."""
+    want = {int(r[0]): int(r[1]) for r in golden_rows("table1_groups.txt")}
+    assert len({O.hole_chords(D) for D in O.enumerate_diagrams(n)}) == want[n]
+    assert len(O.groups(n)) == want[n]
+
+
 def test_hole_distribution_and_ladders():
     h4 = collections.Counter(D.h for D in O.enumerate_diagrams(4))
     assert dict(h4) == {2: 1, 3: 7, 4: 23, 5: 7, 6: 1}

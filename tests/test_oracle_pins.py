@@ -8,6 +8,7 @@ import pytest
 
 import oracle as O
 import quad_pins as Q
+from helpers import random_grid
 
 
 def within(est, sig, ref, k=3.0):
@@ -98,6 +99,37 @@ def test_shifted_denominator_per_sample():
         nz += 1
         assert np.sign(f1) == np.sign(f0) and abs(f1) < abs(f0)
     assert nz > 20
+
+
+def test_group_iteration_is_the_sum_of_member_iterations():
+    """A group's integrand is the sum of its members' integrands at the same point (Sec. III.A):
+    on one grid and one set of counters its sum of weights is the scaled sum of the members' sums."""
+    rng = np.random.default_rng(3)
+    G = O.groups(4)[4]
+    G = O.Group(G.members[:5], [1.0, 2.0, 0.5, 1.0, 3.0])
+    ph = O.Physics(kF_n=1.2)
+    grid = random_grid(G.d, 50, rng, strength=0.5)
+    r = O.vegas_iteration(G, ph, grid, 7, 3, 2, 3000)
+    parts = [O.vegas_iteration(D, ph, grid, 7, 3, 2, 3000).sum_w for D in G.members]
+    ref = float(np.dot(G.scales, parts))
+    assert r.sum_w == pytest.approx(ref, rel=1e-12, abs=1e-12 * float(np.sum(np.abs(parts))))
+    x = rng.random(G.d)
+    assert O.group_integrand(G, ph, x) == pytest.approx(
+        sum(c * O.integrand(D, ph, x) for D, c in zip(G.members, G.scales)), rel=1e-15)
+
+
+def test_third_order_group_estimate_matches_members():
+    """The third-order group of diagrams with three hole loop momenta (hh and ph ladders/ring)
+    integrated as one integrand agrees with the sum of the separately integrated members within the
+    combined error."""
+    G = O.groups(3)[3]
+    assert len(G.members) == 2
+    ph = O.Physics()
+    mg, sg, _, _ = O.vegas(G, ph, 8, 1 << 15, seed=2, sid=5)
+    ms = [O.vegas(D, ph, 8, 1 << 15, seed=2, sid=6 + i)[:2] for i, D in enumerate(G.members)]
+    tot = sum(m for m, _ in ms)
+    st = math.sqrt(sum(s * s for _, s in ms))
+    assert within(mg, math.hypot(sg, st), tot)
 
 
 def test_rotational_reduction_second_order_vs_quadrature():
