@@ -72,6 +72,8 @@ typedef enum {
 #define MBPT_MAX_CHORDS 7
 #define MBPT_MAX_BINS 64
 #define MBPT_MAX_GROUP 1024       /* members of one group integral */
+#define MBPT_HF_KNOTS 1024        /* knots of the Hartree-Fock self-energy table */
+#define MBPT_HF_QUAD 64           /* Gauss-Legendre nodes per dimension of each knot's integral */
 
 /* descriptor flags */
 #define MBPT_FLAG_ANOMALOUS   1   /* a hole and a particle forced to equal momentum: zero at T = 0 */
@@ -117,6 +119,16 @@ typedef struct {
  * integrand (Sec. III.C, "N_dim - 3"): chord 0 along z (k only), chord 1 in the
  * xz plane (k, cos theta), the fixed angles integrated analytically (4 pi 2 pi);
  * d = 3 order.
+ * spectrum 0: free single-particle energies eps(k) = (hbar^2/2m) k^2.  spectrum 1:
+ * Hartree-Fock energies eps(k) = (hbar^2/2m) k^2 + Sigma(k) (Eq. (7)), with
+ *   Sigma(k) = (2 pi)^-3 int_{k' < kF} d^3k' [g V(p, p) - V(p, -p)],  p = (k - k')/2,
+ * g = 2 (neutron matter) or 4 (symmetric matter), tabulated once per integral at
+ * 1024 knots k_i = i h, h = 2 K_max / 1023, each by a 64 x 64-point Gauss-Legendre
+ * rule over (|k'|, cos angle), and interpolated by the cubic spline with zero slope
+ * at k = 0 and zero curvature at the last knot; Sigma = 0 beyond the last knot
+ * (the sampling-time interpolation of the paper, Sec. II).  The Hartree-Fock
+ * spectrum needs one Fermi momentum (kF_n = kF_p or kF_p = 0) and a spectrum that
+ * increases with k (MBPT_EINVAL otherwise).
  */
 typedef struct {
     double kF_n, kF_p;
@@ -125,6 +137,8 @@ typedef struct {
     int32_t reg_power;       /* even, 2..8 */
     int32_t map_kind;        /* 0 or 1 */
     double K_max;
+    int32_t spectrum;        /* 0 free, 1 Hartree-Fock */
+    int32_t reserved;        /* 0 */
 } mbpt_physics;
 
 /*
@@ -195,6 +209,14 @@ int mbpt_generate(int order, mbpt_diagram_desc* out, int cap, int* count);
  */
 int mbpt_hole_chords(const mbpt_diagram_desc* desc, int* out);
 
+/*
+ * The Hartree-Fock self-energy Sigma(k) (MeV) of the physics point's spectrum table (see
+ * mbpt_physics, spectrum 1) at n momenta k[i] (fm^-1), evaluated on the host in FP64 from the same
+ * per-interval cubic coefficients the device uses.  MBPT_EINVAL for invalid physics or two
+ * different Fermi momenta.
+ */
+int mbpt_hf_self_energy(const mbpt_physics* physics, int n, const double* k, double* sigma);
+
 /* ---- context ------------------------------------------------------------- */
 
 /*
@@ -207,7 +229,8 @@ int mbpt_ctx_create(mbpt_ctx** ctx, int device, void* arena, size_t arena_bytes,
 int mbpt_ctx_destroy(mbpt_ctx* ctx);
 /* Bytes of the arena in use and free (largest block) -- for admission control. */
 int mbpt_ctx_mem(const mbpt_ctx* ctx, size_t* used, size_t* largest_free);
-/* Device bytes one integral with this descriptor and configuration needs. */
+/* Device bytes one integral with this descriptor and configuration needs (with the Hartree-Fock
+ * spectrum, one more block of (MBPT_HF_KNOTS - 1) x 60 bytes for its table). */
 int mbpt_diag_bytes(const mbpt_diagram_desc* desc, const mbpt_vegas_cfg* cfg, size_t* bytes);
 /* The same for a group integral of k members (mbpt_create_group); the members' order is that of descs[0]. */
 int mbpt_group_bytes(const mbpt_diagram_desc* descs, int k, const mbpt_vegas_cfg* cfg, size_t* bytes);

@@ -103,6 +103,15 @@ def lib():
                                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                                      P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                                      P(ctypes.c_double)]
+            L.oracle_hf_self_energy.restype = ctypes.c_double
+            L.oracle_hf_self_energy.argtypes = [P(ctypes.c_double), ctypes.c_double, ctypes.c_int, ctypes.c_int]
+            L.oracle_spline_build.restype = None
+            L.oracle_spline_build.argtypes = [ctypes.c_int, ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double)]
+            L.oracle_spline_eval.restype = ctypes.c_double
+            L.oracle_spline_eval.argtypes = [ctypes.c_int, ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double),
+                                             ctypes.c_double]
+            L.oracle_gauss_legendre.restype = None
+            L.oracle_gauss_legendre.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)]
             L.oracle_refine.restype = None
             L.oracle_refine.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int, ctypes.c_double,
                                         P(ctypes.c_double)]
@@ -328,10 +337,19 @@ class Physics:
     K_max: float = 7.0
     map_kind: int = 0
     shift: float = 0.0      # denominator shift s (MeV): D_m -> D_m - s, the regulator of Sec. III.A
+    spectrum: int = 0       # 0 free, 1 Hartree-Fock (Eq. (7), spline of the self-energy)
+
+    def base_array(self) -> np.ndarray:
+        return np.asarray([self.kF_n, self.kF_p, self.hbar2_over_m, self.C_S, self.C_Y, self.m_pi, self.Lam,
+                           float(self.reg_power), self.K_max, float(self.map_kind), self.shift,
+                           float(self.spectrum)], dtype=np.float64)
 
     def array(self) -> np.ndarray:
-        return np.asarray([self.kF_n, self.kF_p, self.hbar2_over_m, self.C_S, self.C_Y, self.m_pi, self.Lam,
-                           float(self.reg_power), self.K_max, float(self.map_kind), self.shift], dtype=np.float64)
+        a = self.base_array()
+        if self.spectrum == 0:
+            return a
+        y, m, h = hf_table(self)
+        return np.concatenate([a, [float(len(y)), h], y, m])
 
     def dim(self, D: "Diagram") -> int:
         """integration dimension of diagram D under this chord map"""
@@ -340,6 +358,44 @@ class Physics:
     @property
     def density(self) -> float:
         return (self.kF_n ** 3 + self.kF_p ** 3) / (3.0 * math.pi ** 2)
+
+
+# The method's fixed Hartree-Fock tabulation: Sigma at HF_KNOTS knots k_i = i h, h = 2 K_max/(HF_KNOTS - 1),
+# each from an HF_QUAD x HF_QUAD Gauss-Legendre rule; cubic spline in k (zero slope at 0, zero curvature
+# at the last knot), Sigma = 0 beyond.
+HF_KNOTS = 1024
+HF_QUAD = 64
+_HF_CACHE = {}
+
+
+def hf_self_energy(ph: "Physics", k: float, n_rad: int = HF_QUAD, n_ang: int = HF_QUAD) -> float:
+    """Sigma(k) in MeV by direct quadrature (one Fermi momentum: neutron or symmetric matter)."""
+    return lib().oracle_hf_self_energy(_dp(ph.base_array()), float(k), n_rad, n_ang)
+
+
+def hf_table(ph: "Physics"):
+    """(Sigma at the knots, spline second derivatives, knot spacing)."""
+    if ph.kF_n > 0 and ph.kF_p > 0 and ph.kF_n != ph.kF_p:
+        raise ValueError("the Hartree-Fock spectrum needs one Fermi momentum (neutron or symmetric matter)")
+    key = tuple(ph.base_array()[[0, 1, 2, 3, 4, 5, 6, 7, 8]])
+    if key not in _HF_CACHE:
+        L = lib()
+        h = 2.0 * ph.K_max / (HF_KNOTS - 1)
+        base = ph.base_array()
+        y = np.array([L.oracle_hf_self_energy(_dp(base), i * h, HF_QUAD, HF_QUAD) for i in range(HF_KNOTS)])
+        m = np.zeros(HF_KNOTS)
+        L.oracle_spline_build(HF_KNOTS, h, _dp(y), _dp(m))
+        _HF_CACHE[key] = (y, m, h)
+    return _HF_CACHE[key]
+
+
+def sp_energy(ph: "Physics", k: float) -> float:
+    """Single-particle energy (MeV) of momentum k in the physics point's spectrum."""
+    kin = 0.5 * ph.hbar2_over_m * k * k
+    if ph.spectrum == 0:
+        return kin
+    y, m, h = hf_table(ph)
+    return kin + lib().oracle_spline_eval(len(y), h, _dp(y), _dp(m), float(k))
 
 
 def integrand(D: Diagram, ph: Physics, x: np.ndarray, with_cond: bool = False):

@@ -231,6 +231,11 @@ int oracle_derive(int n, const int* lines, const int* ports, const int* chords, 
  *   ph[9] chord map: 0 full directions, 1 rotational reduction (see chord_momenta)
  *   ph[10] denominator shift s (MeV): every D_m below is replaced by D_m - s
  *          (the regulator of Sec. III.A; 0 = the diagram itself)
+ *   ph[11] single-particle spectrum: 0 free, eps = (hbar^2/2m) k^2; 1 Hartree-Fock,
+ *          eps = (hbar^2/2m) k^2 + Sigma(k) (Eq. (7)) with Sigma from the cubic spline whose
+ *          knots follow: ph[12] number of knots N, ph[13] knot spacing h (knot i at k = i h),
+ *          ph[14 .. 14+N) Sigma at the knots (MeV), ph[14+N .. 14+2N) the spline's second
+ *          derivatives (oracle_spline_build); Sigma = 0 beyond the last knot
  * The potential is V(p, p') = [C_S + C_Y / (|p - p'|^2 + m_pi^2)]
  *                             * exp(-(|p|/Lambda)^r - (|p'|/Lambda)^r).
  * ------------------------------------------------------------------------- */
@@ -374,6 +379,107 @@ static double density(const double* ph) {
     return (ph[0] * ph[0] * ph[0] + ph[1] * ph[1] * ph[1]) / (3.0 * M_PI * M_PI);
 }
 
+/* ---------------------------------------------------------------------------
+ * Hartree-Fock spectrum (Eq. (7)).
+ * ------------------------------------------------------------------------- */
+
+/* Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the Legendre polynomial P_n
+ * (three-term recurrence) from the Chebyshev-like starting guess cos(pi (i + 3/4)/(n + 1/2)). */
+void oracle_gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 2; j <= n; ++j) {
+                double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* Hartree-Fock self-energy (MeV) of a nucleon of momentum k in matter with one Fermi momentum kF and
+ * g occupied labels (2 neutron matter, 4 symmetric matter), for the spin-isospin independent
+ * potential: the direct term <ij|V|ij> counts every label of j, the exchange term only j with i's
+ * label, so
+ *   Sigma(k) = (1/(2 pi)^3) int_{k' < kF} d^3k' [g V(p, p) - V(p, -p)],  p = (k - k')/2,
+ * reduced by azimuthal symmetry to 1/(4 pi^2) int_0^kF dk' k'^2 int_{-1}^{1} dc [...], with
+ * |p|^2 = (k^2 + k'^2 - 2 k k' c)/4, on n_rad x n_ang Gauss-Legendre nodes. */
+double oracle_hf_self_energy(const double* ph, double k, int n_rad, int n_ang) {
+    double kf = ph[0] > 0.0 ? ph[0] : ph[1];
+    double g = (ph[0] > 0.0 ? 2.0 : 0.0) + (ph[1] > 0.0 ? 2.0 : 0.0);
+    double xr[256], wr[256], xa[256], wa[256];
+    if (n_rad > 256 || n_ang > 256) return NAN;
+    oracle_gauss_legendre(n_rad, xr, wr);
+    oracle_gauss_legendre(n_ang, xa, wa);
+    double tot = 0.0;
+    for (int i = 0; i < n_rad; ++i) {
+        double kp = 0.5 * kf * (xr[i] + 1.0), wk = 0.5 * kf * wr[i];
+        double inner = 0.0;
+        for (int j = 0; j < n_ang; ++j) {
+            double c = xa[j];
+            double p2 = 0.25 * (k * k + kp * kp - 2.0 * k * kp * c);
+            if (p2 < 0.0) p2 = 0.0;
+            /* p along z and p' = +-p: V(p, p) has q = 0, V(p, -p) has |q|^2 = 4 p^2 */
+            double pv[3] = {0.0, 0.0, sqrt(p2)}, mv[3] = {0.0, 0.0, -sqrt(p2)};
+            inner += wa[j] * (g * vpot(ph, pv, pv) - vpot(ph, pv, mv));
+        }
+        tot += wk * kp * kp * inner;
+    }
+    return tot / (4.0 * M_PI * M_PI);
+}
+
+/* Cubic spline through y_i at k_i = i h (i < n) with zero slope at k = 0 (Sigma is even in k) and
+ * zero curvature at the last knot; m receives the second derivatives (tridiagonal system solved by
+ * forward elimination and back substitution). */
+void oracle_spline_build(int n, double h, const double* y, double* m) {
+    double c[4096], d[4096];
+    if (n < 3 || n > 4096) return;
+    /* row 0: 2 m0 + m1 = 6 (y1 - y0)/h^2; rows 1..n-2: m_{i-1} + 4 m_i + m_{i+1} = 6 (y_{i-1} - 2 y_i + y_{i+1})/h^2 */
+    double b0 = 2.0;
+    c[0] = 1.0 / b0;
+    d[0] = 6.0 * (y[1] - y[0]) / (h * h) / b0;
+    for (int i = 1; i < n - 1; ++i) {
+        double rhs = 6.0 * (y[i - 1] - 2.0 * y[i] + y[i + 1]) / (h * h);
+        double den = 4.0 - c[i - 1];
+        c[i] = 1.0 / den;
+        d[i] = (rhs - d[i - 1]) / den;
+    }
+    m[n - 1] = 0.0;
+    for (int i = n - 2; i >= 0; --i) m[i] = d[i] - c[i] * m[i + 1];
+}
+
+double oracle_spline_eval(int n, double h, const double* y, const double* m, double k) {
+    if (!(k < (n - 1) * h)) return 0.0;
+    int i = (int)floor(k / h);
+    if (i > n - 2) i = n - 2;
+    double t = k - i * h;
+    double slope = (y[i + 1] - y[i]) / h - h * (2.0 * m[i] + m[i + 1]) / 6.0;
+    return y[i] + t * slope + t * t * m[i] / 2.0 + t * t * t * (m[i + 1] - m[i]) / (6.0 * h);
+}
+
+/* Single-particle energy (MeV) of a line with |k|^2 = ksq; *mag receives |kinetic| + |Sigma| for the
+ * rounding estimate. */
+static double sp_energy(const double* ph, double ksq, double* mag) {
+    double kin = 0.5 * ph[2] * ksq;
+    if (ph[11] == 0.0) {
+        *mag = kin;
+        return kin;
+    }
+    int n = (int)ph[12];
+    double sg = oracle_spline_eval(n, ph[13], ph + 14, ph + 14 + n, sqrt(ksq));
+    *mag = kin + fabs(sg);
+    return kin + sg;
+}
+
 /*
  * oracle_integrand: the contribution of one diagram to E/N at a point
  * x in [0,1]^(3(n+1)) of the chord coordinates:
@@ -468,7 +574,6 @@ double oracle_integrand_momenta(const int* info, const double* ph, const double*
     }
     double ssum = spin_sum(&S);
     if (ssum == 0.0) return 0.0;
-    double e2m = 0.5 * ph[2];
     double dprod = 1.0, condsum = 0.0;
     for (int m = 0; m < n - 1; ++m) {
         double D = 0.0, mag = 0.0;
@@ -476,10 +581,11 @@ double oracle_integrand_momenta(const int* info, const double* ph, const double*
             int s = info[OI_SRC + l], d = info[OI_DST + l];
             int lo = s < d ? s : d, hi = s < d ? d : s;
             if (!(lo <= m && m < hi)) continue;
-            double eps = e2m * S.ksq[l];
+            double emag;
+            double eps = sp_energy(ph, S.ksq[l], &emag);
             if (line_is_hole(info, l)) D += eps;
             else D -= eps;
-            mag += eps;
+            mag += emag;
         }
         if (!(D < 0.0)) return 0.0;   /* only on a measure-zero set */
         D -= ph[10];

@@ -28,9 +28,12 @@ def main():
     ap.add_argument("--max-iters", type=int, default=60)
     ap.add_argument("--warm-start", action="store_true")
     ap.add_argument("--grouped", action="store_true", help="one integral per (order, particle-hole group)")
+    ap.add_argument("--warm-blend", type=float, default=0.5, help="weight of the donor grid in a warm start")
+    ap.add_argument("--warm-train", type=int, default=1, help="uncombined iterations after a warm start")
     a = ap.parse_args()
     be = S.MbptBackend(arena_bytes=int(a.arena_gb * (1 << 30)), grouped=a.grouped)
-    srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters, warm_start=a.warm_start)
+    srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters, warm_start=a.warm_start,
+                   warm_blend=a.warm_blend, warm_train=a.warm_train)
     trace = S.poisson_trace(a.requests, a.rate, a.seed)
     t0 = time.perf_counter()
     done = srv.run(trace, realtime=True, time_limit=a.time_limit)
@@ -46,6 +49,7 @@ def main():
            "completed_by_cap": caps, "budget_bytes": srv.budget,
            "target_met_fraction": len(met) / max(1, len(done)),
            "warm_start": a.warm_start, "warm_started_integrals": srv.warm_starts, "grouped": a.grouped,
+           "warm_blend": a.warm_blend if a.warm_start else None, "warm_train": a.warm_train if a.warm_start else None,
            "rounds_per_request": {"median": float(sorted(rounds)[len(rounds) // 2]) if rounds else None,
                                   "max": max(rounds) if rounds else None},
            "example": [{"n": r.n_dens, "delta": r.delta, "cap": r.cap, "target": r.target, "E_corr": r.energy,

@@ -193,12 +193,200 @@ __device__ __forceinline__ constexpr int chord_kind(int c) {   // 0 full directi
     return MAPK == 0 ? 0 : (c == 0 ? 1 : (c == 1 ? 2 : 0));
 }
 
+// Hartree-Fock self-energy of a line with |k|^2 = u, in units of hbar^2/2m (the spectrum table's cubic
+// on the interval of k; 0 beyond the table).  FP32 in the mixed mode, FP64 otherwise.
+template <int PREC>
+__device__ __forceinline__ double hf_sigma(const DiagRec& R, double u) {
+    const float kf = sqrtf(narrow_trunc(u));
+    const int i = (int)(kf * R.hf_hinv_f);
+    if (i >= R.hf_n) return 0.0;
+    if (PREC == MBPT_MIXED) {
+        const float* c = R.hf_tab_f + 5 * i;
+        const float t = kf - __ldg(c);
+        return widen_f(fmaf(fmaf(fmaf(__ldg(c + 4), t, __ldg(c + 3)), t, __ldg(c + 2)), t, __ldg(c + 1)));
+    } else {
+        const double* c = R.hf_tab + 5 * i;
+        const double t = sqrt_nr(u) - __ldg(c);
+        return fma(fma(fma(__ldg(c + 4), t, __ldg(c + 3)), t, __ldg(c + 2)), t, __ldg(c + 1));
+    }
+}
+
+// FP64 chord momenta, |l|^2 and chord Jacobian from an FP64 point x (FP64 and FP64-map modes, and the
+// mixed mode's samples near a Fermi surface).  k = lo + rng x0, cos(t) = 2 x1 - 1,
+// sin(t) = 2 sqrt(x1 (1 - x1)), rational azimuth a = x2 (1 - x2), b = x2 - 1/2:
+// cos(phi) = (a^2 - b^2)/(a^2 + b^2), sin(phi) = 2ab/(a^2 + b^2), dphi/dx2 = 2/(1/2 - a); Jacobian
+// k^2 (1/2 - a)/(a^2 + b^2) times the constant 4 rng folded into pref.
+template <int N, int PREC, int MAPK, int D>
+__device__ __forceinline__ void chords_fp64(const DiagRec& R, const double (&x)[D], double (&K)[3][16],
+                                            double (&U)[16], float (&lf)[3][N + 1], double& jc) {
+#pragma unroll
+    for (int c = 0; c < N + 1; ++c) {
+        const int ax = chord_axis<MAPK>(c), kind = chord_kind<MAPK>(c);
+        const double k = fma(R.chord_rng[c], x[ax], R.chord_lo[c]);
+        const double k2 = k * k;
+        if (kind == 1) {
+            K[0][c] = 0.0;
+            K[1][c] = 0.0;
+            K[2][c] = k;
+            jc *= k2;
+        } else if (kind == 2) {
+            const double x1 = x[ax + 1];
+            const double ct = fma(2.0, x1, -1.0);
+            const double sq = sqrt_nr(fma(-x1, x1, x1));
+            K[0][c] = (k + k) * sq;
+            K[1][c] = 0.0;
+            K[2][c] = k * ct;
+            jc *= k2;
+        } else {
+            const double x1 = x[ax + 1], x2 = x[ax + 2];
+            const double ct = fma(2.0, x1, -1.0);
+            const double sq = sqrt_nr(fma(-x1, x1, x1));
+            const double a = fma(-x2, x2, x2);
+            const double b = x2 - 0.5;
+            const double bb = b * b;
+            const double mm = fma(a, a, bb);
+            const double rr = rcp_nr(mm);           // mm = (1/2 - a)^2 in [1/16, 1/4]
+            const double ncos = fma(a, a, -bb);
+            const double nsin = (a + a) * b;
+            const double R2 = (k + k) * sq * rr;
+            K[0][c] = R2 * ncos;
+            K[1][c] = R2 * nsin;
+            K[2][c] = k * ct;
+            jc *= k2 * ((0.5 - a) * rr);
+        }
+        U[c] = k2;
+        if (PREC != MBPT_FP64) {
+            lf[0][c] = narrow_trunc(K[0][c]);
+            lf[1][c] = narrow_trunc(K[1][c]);
+            lf[2][c] = narrow_trunc(K[2][c]);
+        }
+    }
+}
+
+// FP32 front of a mixed-precision sample: the VEGAS map on the FP32 grid (point, bins, Jacobian as a
+// mantissa product and exponent sum, so that it cannot underflow), chord magnitudes, unit directions
+// (kind 1: along z; kind 2: in the xz plane; kind 0: rational azimuth), Jacobian factors and FP32
+// chord momenta.
+template <int N, int MAPK, int D>
+__device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __restrict__ gf, const uint32_t* u,
+                                            uint32_t nb, float (&xf)[D], uint32_t (&binpack)[5], float& mp,
+                                            int& ex, bool& zero_bin, float (&kmag)[N + 1],
+                                            float (&kdir)[3][N + 1], float (&jcf)[N + 1],
+                                            float (&lf)[3][N + 1]) {
+    mp = 1.0f;
+    ex = 0;
+    zero_bin = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const uint64_t r = (2ull * (uint64_t)u[a] + 1ull) * (uint64_t)nb;
+        const uint32_t i = (uint32_t)(r >> 33);
+        const uint32_t fb = (uint32_t)((r >> 10) & 0x7FFFFFull);          // top 23 bits of the fraction
+        const float frac = __uint_as_float(0x3F800000u | fb) - 1.0f;
+        const Grid4f g = gf[a * kGridStride + i];
+        xf[a] = fmaf(frac, g.de, g.e);
+        const uint32_t bits = __float_as_uint(g.de);
+        zero_bin |= (bits == 0u);
+        ex += (int)(bits >> 23) - 127;
+        mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+        binpack[a >> 2] |= i << (8 * (a & 3));
+    }
+#pragma unroll
+    for (int c = 0; c < N + 1; ++c) {
+        const int ax = chord_axis<MAPK>(c), kind = chord_kind<MAPK>(c);
+        const float k = fmaf(R.chord_rng_f[c], xf[ax], R.chord_lo_f[c]);
+        kmag[c] = k;
+        if (kind == 1) {
+            kdir[0][c] = 0.0f;
+            kdir[1][c] = 0.0f;
+            kdir[2][c] = 1.0f;
+            jcf[c] = k * k;
+        } else if (kind == 2) {
+            const float x1 = xf[ax + 1];
+            kdir[0][c] = 2.0f * sqrtf(fmaf(-x1, x1, x1));
+            kdir[1][c] = 0.0f;
+            kdir[2][c] = fmaf(2.0f, x1, -1.0f);
+            jcf[c] = k * k;
+        } else {
+            const float x1 = xf[ax + 1], x2 = xf[ax + 2];
+            const float ct = fmaf(2.0f, x1, -1.0f);
+            const float sq = sqrtf(fmaf(-x1, x1, x1));
+            const float a = fmaf(-x2, x2, x2);
+            const float b = x2 - 0.5f;
+            const float bb = b * b;
+            const float mm = fmaf(a, a, bb);
+            const float rr = __frcp_rn(mm);
+            const float R2 = 2.0f * sq * rr;
+            kdir[0][c] = R2 * fmaf(a, a, -bb);
+            kdir[1][c] = R2 * ((a + a) * b);
+            kdir[2][c] = ct;
+            jcf[c] = k * k * ((0.5f - a) * rr);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) lf[q][c] = k * kdir[q][c];
+    }
+}
+
+// Fermi-step pre-test in FP32 of the mixed mode.  Returns true when some line fails its step for
+// every species by more than the FP32 error bound of |k|^2: the sample is zero.  Bound: the FP32
+// chord components are within 2^-24 of the exact FP64 products that the exact path uses, a line is
+// accumulated from at most N+1 chords by fused multiply-adds with coefficients -1..1, so with
+// S_l = sum over its chords of |coefficient| |k_c|, |k_f^2 - k^2| < 2^-19 S_l^2; the margin is
+// 2^-16 S_l^2 plus 2^-20 kF^2 for the FP32 copy of kF^2.  near: some line lies within the margin plus
+// 2^-10 kF^2 of a Fermi surface (the band in which the caller places the sample with the FP64 map).
+template <int N>
+__device__ __forceinline__ bool pretest_dead(const DiagRec& R, const float (&lf)[3][N + 1],
+                                             const float (&kmag)[N + 1], bool& near) {
+    constexpr int L = N + 1;
+    bool dead = false;
+    near = false;
+#pragma unroll
+    for (int l = 0; l < 2 * N; ++l) {
+        float x, y, z, S;
+        if (l < L) {
+            x = lf[0][l];
+            y = lf[1][l];
+            z = lf[2][l];
+            S = kmag[l];
+        } else {
+            x = 0.0f;
+            y = 0.0f;
+            z = 0.0f;
+            S = 0.0f;
+#pragma unroll
+            for (int c = 0; c < L; ++c) {
+                const float cf = R.tcoef[l - L][c];
+                x = fmaf(cf, lf[0][c], x);
+                y = fmaf(cf, lf[1][c], y);
+                z = fmaf(cf, lf[2][c], z);
+                S = fmaf(fabsf(cf), kmag[c], S);
+            }
+        }
+        const float uf = fmaf(x, x, fmaf(y, y, z * z));
+        const float mg = 1.52587890625e-05f * S * S;
+        const bool hole = (R.hole_slots >> l) & 1u;
+        const float mn = fmaf(9.5367431640625e-07f, R.kf2_nf, mg);
+        const float dn = uf - R.kf2_nf;
+        bool f = hole ? (dn > mn) : (dn < -mn);
+        bool nr = fabsf(dn) <= fmaf(9.765625e-04f, R.kf2_nf, mn);
+        if (R.asym) {
+            const float mp2 = fmaf(9.5367431640625e-07f, R.kf2_pf, mg);
+            const float dp = uf - R.kf2_pf;
+            f = f && (hole ? (dp > mp2) : (dp < -mp2));
+            nr = nr || (fabsf(dp) <= fmaf(9.765625e-04f, R.kf2_pf, mp2));
+        }
+        dead |= f;
+        near |= nr;
+    }
+    return dead;
+}
+
 // REG: the integral carries the denominator regulator (a separate instantiation, so that the
 // registers of the plain integrand are not spent on it).
 template <int N, int PREC, int MAPK, bool REG>
-__device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* __restrict__ gs, uint32_t s,
-                                                 uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1,
-                                                 double* x_out) {
+__device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* __restrict__ gs,
+                                                 const double* __restrict__ grid64, uint32_t s, uint32_t t,
+                                                 uint32_t sid, uint32_t k0, uint32_t k1, double* x_out,
+                                                 bool force64 = false) {
     constexpr int L = N + 1;          // chords
     constexpr int D = 3 * L - 3 * MAPK;   // dimensions
     constexpr int NL = 2 * N;         // lines
@@ -214,10 +402,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
     // --- VEGAS map: y = (u + 1/2) 2^-32, i = floor(y nb), x = e_i + (y nb - i) de_i, J = prod nb de_i
     // (nb^d is folded into pref).  (2u+1) nb < 2^39, so the bin index and the fraction are exact
     // integer arithmetic.
-    // --- chord momenta: k = lo + rng x0, cos(t) = 2 x1 - 1, sin(t) = 2 sqrt(x1 (1 - x1)),
-    // rational azimuth a = x2 (1 - x2), b = x2 - 1/2: cos(phi) = (a^2 - b^2)/(a^2 + b^2),
-    // sin(phi) = 2ab/(a^2 + b^2), dphi/dx2 = 2/(1/2 - a).  Jacobian k^2 (1/2 - a)/(a^2+b^2) times
-    // the constant 4 rng folded into pref.
+    // --- chord momenta (chords_fp64, mixed_front)
     double K[3][16];
     double U[16];
 #pragma unroll
@@ -235,73 +420,76 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         // Sampling map in FP32.  It only decides where the sample lies: each chord momentum is the
         // exact FP64 product of an FP32 magnitude and an FP32 unit direction, so lines, steps and
         // energy denominators below are evaluated in FP64 at that point; the map's Jacobian is
-        // good to FP32 rounding (a relative weight error ~1e-7 per sample).
+        // good to FP32 rounding (a relative weight error ~1e-7 per sample).  Samples whose lines
+        // come within ~1e-3 kF^2 of a Fermi surface -- where the energy denominators can vanish and
+        // a step decision could depend on where the FP32 map rounds the point -- are placed with the
+        // FP64 map instead (the FP64 mode's point, bins unchanged).
+        // force64: the caller has already classified the sample as near a surface (mixed_classify).
         const Grid4f* gf = reinterpret_cast<const Grid4f*>(gs);
         float xf[D];
-        float mp = 1.0f;          // Jacobian prod de_i as mantissa product x 2^ex (no FP32 underflow)
+        float mp = 1.0f;
         int ex = 0;
         bool zero_bin = false;
+        float kmag[L], kdir[3][L], jcf[L];
+        bool near = force64;
+        if (!force64) mixed_front<N, MAPK, D>(R, gf, u, nb, xf, o.binpack, mp, ex, zero_bin, kmag, kdir, jcf, lf);
+        if (!force64 && pretest_dead<N>(R, lf, kmag, near)) {
+            if (x_out) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const uint64_t r = (2ull * (uint64_t)u[a] + 1ull) * (uint64_t)nb;
-            const uint32_t i = (uint32_t)(r >> 33);
-            const uint32_t fb = (uint32_t)((r >> 10) & 0x7FFFFFull);          // top 23 bits of the fraction
-            const float frac = __uint_as_float(0x3F800000u | fb) - 1.0f;
-            const Grid4f g = gf[a * kGridStride + i];
-            xf[a] = fmaf(frac, g.de, g.e);
-            const uint32_t bits = __float_as_uint(g.de);
-            zero_bin |= (bits == 0u);
-            ex += (int)(bits >> 23) - 127;
-            mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
-            o.binpack[a >> 2] |= i << (8 * (a & 3));
-            if (x_out) x_out[a] = widen_f(xf[a]);
+                for (int a = 0; a < D; ++a) x_out[a] = widen_f(xf[a]);
+            }
+            o.w = 0.0;
+            if (REG) {
+#pragma unroll
+                for (int k = 0; k < kComp; ++k) o.wc[k] = 0.0;
+            }
+            return o;
         }
-        jv = zero_bin ? 0.0 : __longlong_as_double(__double_as_longlong(widen_pos_normal(mp)) + ((long long)ex << 52));
+        if (near) {
+            double x[D];
 #pragma unroll
-        for (int c = 0; c < L; ++c) {
-            const int ax = chord_axis<MAPK>(c), kind = chord_kind<MAPK>(c);
-            const float k = fmaf(R.chord_rng_f[c], xf[ax], R.chord_lo_f[c]);
-            const double kd = widen_f(k);
-            if (kind == 1) {
-                K[0][c] = 0.0;
-                K[1][c] = 0.0;
-                K[2][c] = kd;
-                U[c] = kd * kd;
-                lf[0][c] = 0.0f;
-                lf[1][c] = 0.0f;
-                lf[2][c] = k;
-                jc *= widen_f(k * k);
-            } else if (kind == 2) {
-                const float x1 = xf[ax + 1];
-                const float ct = fmaf(2.0f, x1, -1.0f);
-                const float st = 2.0f * sqrtf(fmaf(-x1, x1, x1));
-                K[0][c] = kd * widen_f(st);
-                K[1][c] = 0.0;
-                K[2][c] = kd * widen_f(ct);
-                U[c] = fma(K[0][c], K[0][c], K[2][c] * K[2][c]);
-                lf[0][c] = k * st;
-                lf[1][c] = 0.0f;
-                lf[2][c] = k * ct;
-                jc *= widen_f(k * k);
-            } else {
-                const float x1 = xf[ax + 1], x2 = xf[ax + 2];
-                const float ct = fmaf(2.0f, x1, -1.0f);
-                const float sq = sqrtf(fmaf(-x1, x1, x1));
-                const float a = fmaf(-x2, x2, x2);
-                const float b = x2 - 0.5f;
-                const float bb = b * b;
-                const float mm = fmaf(a, a, bb);
-                const float rr = __frcp_rn(mm);
-                const float R2 = 2.0f * sq * rr;
-                const float nx = R2 * fmaf(a, a, -bb), ny = R2 * ((a + a) * b), nz = ct;
-                K[0][c] = kd * widen_f(nx);      // exact: 24-bit x 24-bit
-                K[1][c] = kd * widen_f(ny);
-                K[2][c] = kd * widen_f(nz);
-                U[c] = fma(K[0][c], K[0][c], fma(K[1][c], K[1][c], K[2][c] * K[2][c]));
-                lf[0][c] = k * nx;
-                lf[1][c] = k * ny;
-                lf[2][c] = k * nz;
-                jc *= widen_f(k * k * ((0.5f - a) * rr));
+            for (int a = 0; a < D; ++a) {
+                const uint64_t r = (2ull * (uint64_t)u[a] + 1ull) * (uint64_t)nb;
+                const uint32_t i = (uint32_t)(r >> 33);
+                const uint64_t fb = r & ((1ull << 33) - 1ull);
+                const double m = __longlong_as_double((long long)(0x3FF0000000000000ull | (fb << 19)));
+                const double e0 = grid64[a * (nb + 1) + i];
+                const double de = grid64[a * (nb + 1) + i + 1] - e0;
+                x[a] = fma(m - 1.0, de, e0);
+                jv *= de;
+                o.binpack[a >> 2] |= i << (8 * (a & 3));
+                if (x_out) x_out[a] = x[a];
+            }
+            chords_fp64<N, MBPT_MIXED, MAPK, D>(R, x, K, U, lf, jc);
+        } else {
+            if (x_out) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) x_out[a] = widen_f(xf[a]);
+            }
+            jv = zero_bin ? 0.0
+                          : __longlong_as_double(__double_as_longlong(widen_pos_normal(mp)) + ((long long)ex << 52));
+            // exact FP64 chord momenta: products of the FP32 magnitude and direction (24 x 24 bits)
+#pragma unroll
+            for (int c = 0; c < L; ++c) {
+                const int kind = chord_kind<MAPK>(c);
+                const double kd = widen_f(kmag[c]);
+                if (kind == 1) {
+                    K[0][c] = 0.0;
+                    K[1][c] = 0.0;
+                    K[2][c] = kd;
+                    U[c] = kd * kd;
+                } else if (kind == 2) {
+                    K[0][c] = kd * widen_f(kdir[0][c]);
+                    K[1][c] = 0.0;
+                    K[2][c] = kd * widen_f(kdir[2][c]);
+                    U[c] = fma(K[0][c], K[0][c], K[2][c] * K[2][c]);
+                } else {
+                    K[0][c] = kd * widen_f(kdir[0][c]);
+                    K[1][c] = kd * widen_f(kdir[1][c]);
+                    K[2][c] = kd * widen_f(kdir[2][c]);
+                    U[c] = fma(K[0][c], K[0][c], fma(K[1][c], K[1][c], K[2][c] * K[2][c]));
+                }
+                jc *= widen_f(jcf[c]);
             }
         }
     } else {
@@ -319,48 +507,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
             o.binpack[a >> 2] |= i << (8 * (a & 3));
             if (x_out) x_out[a] = x[a];
         }
-#pragma unroll
-        for (int c = 0; c < L; ++c) {
-            const int ax = chord_axis<MAPK>(c), kind = chord_kind<MAPK>(c);
-            const double k = fma(R.chord_rng[c], x[ax], R.chord_lo[c]);
-            const double k2 = k * k;
-            if (kind == 1) {
-                K[0][c] = 0.0;
-                K[1][c] = 0.0;
-                K[2][c] = k;
-                jc *= k2;
-            } else if (kind == 2) {
-                const double x1 = x[ax + 1];
-                const double ct = fma(2.0, x1, -1.0);
-                const double sq = sqrt_nr(fma(-x1, x1, x1));
-                K[0][c] = (k + k) * sq;
-                K[1][c] = 0.0;
-                K[2][c] = k * ct;
-                jc *= k2;
-            } else {
-                const double x1 = x[ax + 1], x2 = x[ax + 2];
-                const double ct = fma(2.0, x1, -1.0);
-                const double sq = sqrt_nr(fma(-x1, x1, x1));
-                const double a = fma(-x2, x2, x2);
-                const double b = x2 - 0.5;
-                const double bb = b * b;
-                const double mm = fma(a, a, bb);
-                const double rr = rcp_nr(mm);           // mm = (1/2 - a)^2 in [1/16, 1/4]
-                const double ncos = fma(a, a, -bb);
-                const double nsin = (a + a) * b;
-                const double R2 = (k + k) * sq * rr;
-                K[0][c] = R2 * ncos;
-                K[1][c] = R2 * nsin;
-                K[2][c] = k * ct;
-                jc *= k2 * ((0.5 - a) * rr);
-            }
-            U[c] = k2;
-            if (PREC != MBPT_FP64) {
-                lf[0][c] = narrow_trunc(K[0][c]);
-                lf[1][c] = narrow_trunc(K[1][c]);
-                lf[2][c] = narrow_trunc(K[2][c]);
-            }
-        }
+        chords_fp64<N, PREC, MAPK, D>(R, x, K, U, lf, jc);
     }
 
     // --- tree lines from momentum conservation: k = k_a + k_b - k_c
@@ -399,6 +546,13 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
             for (int k = 0; k < kComp; ++k) o.wc[k] = 0.0;
         }
         return o;
+    }
+
+    // --- Hartree-Fock spectrum (Eq. (7)): single-particle energy (hbar^2/2m)(|k|^2 + Sigma~(|k|)) on every
+    // line; the Fermi steps above test |k|^2 itself
+    if (R.spectrum) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) U[l] += hf_sigma<PREC>(R, U[l]);
     }
 
     // --- energy denominators (FP64): D~_m = D~_{m-1} + sum over the four lines of vertex m
@@ -530,6 +684,29 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         o.wc[kShifts] = ext;
     }
     return o;
+}
+
+// Mixed precision: class of sample s after the FP32 front and Fermi-step pre-test (Philox and FP32
+// work only): 0 zero (eval_sample would reject it), 1 live or undecided and away from every Fermi
+// surface (FP32 placement), 2 near a surface (eval_sample places it with the FP64 map).
+template <int N, int MAPK>
+__device__ __forceinline__ int mixed_classify(const DiagRec& R, const Grid2* __restrict__ gs, uint32_t s, uint32_t t,
+                                              uint32_t sid, uint32_t k0, uint32_t k1) {
+    constexpr int L = N + 1;
+    constexpr int D = 3 * L - 3 * MAPK;
+    constexpr int NBLK = (D + 3) / 4;
+    uint32_t u[4 * NBLK];
+#pragma unroll
+    for (int j = 0; j < NBLK; ++j) philox4x32_10(s, t, sid, (uint32_t)j, k0, k1, &u[4 * j]);
+    float xf[D];
+    uint32_t bp[5] = {0u, 0u, 0u, 0u, 0u};
+    float mp, kmag[L], kdir[3][L], jcf[L], lf[3][L];
+    int ex;
+    bool zero_bin, near;
+    mixed_front<N, MAPK, D>(R, reinterpret_cast<const Grid4f*>(gs), u, (uint32_t)R.nb, xf, bp, mp, ex, zero_bin, kmag,
+                            kdir, jcf, lf);
+    if (pretest_dead<N>(R, lf, kmag, near)) return 0;
+    return near ? 2 : 1;
 }
 
 }  // namespace mbpt

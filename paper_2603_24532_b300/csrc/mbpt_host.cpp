@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <map>
 #include <vector>
@@ -276,6 +277,14 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         set_err(err, errlen, "invalid physics parameters (K_max > kF, hbar2_over_m > 0, Lambda > 0, even reg_power 2..8, map_kind 0 or 1)");
         return MBPT_EINVAL;
     }
+    if (ph.spectrum != 0 && ph.spectrum != 1) {
+        set_err(err, errlen, "spectrum must be 0 (free) or 1 (Hartree-Fock)");
+        return MBPT_EINVAL;
+    }
+    if (ph.spectrum == 1 && ph.kF_n > 0.0 && ph.kF_p > 0.0 && ph.kF_n != ph.kF_p) {
+        set_err(err, errlen, "the Hartree-Fock spectrum needs one Fermi momentum (neutron or symmetric matter)");
+        return MBPT_EINVAL;
+    }
     if (cfg.n_bins < 2 || cfg.n_bins > MBPT_MAX_BINS || cfg.samples_per_iter < 2 ||
         cfg.samples_per_iter >= (1ull << 32) || !(cfg.alpha >= 0.0) ||
         (cfg.precision != MBPT_FP64 && cfg.precision != MBPT_MIXED && cfg.precision != MBPT_MIXED_MAP64) || !(cfg.target_rel >= 0.0) ||
@@ -359,6 +368,9 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         ++t;
     }
     for (int l = 0; l < nl; ++l) r->line_slot[l] = (int8_t)slot_of[l];
+    for (int l = 0; l < nl; ++l)
+        if (slot_of[l] >= nc)
+            for (int c = 0; c < nc; ++c) r->tcoef[slot_of[l] - nc][c] = (float)d.line_coef[l][c];
     int h = 0;
     for (int l = 0; l < nl; ++l)
         if (d.line_src[l] > d.line_dst[l]) { r->hole_slots |= 1u << slot_of[l]; ++h; }
@@ -453,6 +465,11 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         r->kf2_n = ph.kF_n * ph.kF_n;
         r->kf2_p = ph.kF_p * ph.kF_p;
     }
+    r->kf2_nf = (float)r->kf2_n;
+    r->kf2_pf = (float)r->kf2_p;
+    r->spectrum = ph.spectrum;
+    r->hf_n = MBPT_HF_KNOTS - 1;
+    r->hf_hinv_f = (float)((MBPT_HF_KNOTS - 1) / (2.0 * ph.K_max));
     r->CS = ph.C_S;
     r->CY4 = 4.0 * ph.C_Y;
     r->mpi2_4 = 4.0 * ph.m_pi * ph.m_pi;
@@ -484,6 +501,113 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         r->lag[k] = cfg.n_shifts ? L : 0.0;
     }
     return MBPT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Hartree-Fock single-particle spectrum (Eq. (7)) for one Fermi momentum.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Gauss-Legendre rule on [-1, 1]: roots of P_n by Newton's method (P_n and P_n' from the three-term
+// recurrence), weights 2 / ((1 - x^2) P_n'(x)^2).
+void gl_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dpn = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm1 = 1.0, pn = z;
+            for (int j = 2; j <= n; ++j) {
+                const double pj = ((2 * j - 1) * z * pn - (j - 1) * pm1) / j;
+                pm1 = pn;
+                pn = pj;
+            }
+            dpn = n * (z * pn - pm1) / (z * z - 1.0);
+            const double step = pn / dpn;
+            z -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dpn * dpn);
+    }
+}
+
+}  // namespace
+
+// Sigma at the knots k_i = i h (MeV): 1/(4 pi^2) int_0^kF dk' k'^2 int_{-1}^{1} dc [g V_d - V_e] with
+// V_d = [C_S + C_Y/m_pi^2] exp(-2 (p/L)^r), V_e = [C_S + C_Y/(4p^2 + m_pi^2)] exp(-2 (p/L)^r),
+// p^2 = (k^2 + k'^2 - 2 k k' c)/4.  Then the cubic spline (zero slope at 0, zero curvature at the end)
+// as per-interval polynomials in t = k - k_i, in units of hbar^2/2m: tab[5 i .. 5 i + 4] = k_i, a, b, c, d.
+int build_hf_table(const mbpt_physics& ph, std::vector<double>& tab, char* err, size_t errlen) {
+    const int n = MBPT_HF_KNOTS, nq = MBPT_HF_QUAD;
+    const double kf = ph.kF_n > 0.0 ? ph.kF_n : ph.kF_p;
+    const double g = (ph.kF_n > 0.0 ? 2.0 : 0.0) + (ph.kF_p > 0.0 ? 2.0 : 0.0);
+    const double h = 2.0 * ph.K_max / (n - 1);
+    const double pi = 3.14159265358979323846;
+    std::vector<double> xg, wg;
+    gl_rule(nq, xg, wg);
+    const double L2 = ph.Lambda * ph.Lambda, mpi2 = ph.m_pi * ph.m_pi, rh = 0.5 * ph.reg_power;
+    std::vector<double> y(n), m(n);
+    for (int i = 0; i < n; ++i) {
+        const double k = i * h;
+        double acc = 0.0;
+        for (int a = 0; a < nq; ++a) {
+            const double kp = 0.5 * kf * (xg[a] + 1.0);
+            double inner = 0.0;
+            for (int b = 0; b < nq; ++b) {
+                double p2 = 0.25 * (k * k + kp * kp - 2.0 * k * kp * xg[b]);
+                if (p2 < 0.0) p2 = 0.0;
+                const double F = std::exp(-2.0 * std::pow(p2 / L2, rh));
+                const double vd = (ph.C_S + ph.C_Y / mpi2) * F;
+                const double ve = (ph.C_S + ph.C_Y / (4.0 * p2 + mpi2)) * F;
+                inner += wg[b] * (g * vd - ve);
+            }
+            acc += 0.5 * kf * wg[a] * kp * kp * inner;
+        }
+        y[i] = acc / (4.0 * pi * pi);
+    }
+    // spline second derivatives: 2 m0 + m1 = 6 (y1 - y0)/h^2; m_{i-1} + 4 m_i + m_{i+1} = 6 (y_{i-1} - 2 y_i + y_{i+1})/h^2;
+    // m_{n-1} = 0.  Thomas algorithm.
+    std::vector<double> cp(n), dp(n);
+    cp[0] = 0.5;
+    dp[0] = 3.0 * (y[1] - y[0]) / (h * h);
+    for (int i = 1; i < n - 1; ++i) {
+        const double den = 4.0 - cp[i - 1];
+        cp[i] = 1.0 / den;
+        dp[i] = (6.0 * (y[i - 1] - 2.0 * y[i] + y[i + 1]) / (h * h) - dp[i - 1]) / den;
+    }
+    m[n - 1] = 0.0;
+    for (int i = n - 2; i >= 0; --i) m[i] = dp[i] - cp[i] * m[i + 1];
+    const double e = 0.5 * ph.hbar2_over_m;
+    tab.assign((size_t)5 * (n - 1), 0.0);
+    double prev = -1e300;
+    for (int i = 0; i < n - 1; ++i) {
+        tab[5 * i + 0] = i * h;
+        tab[5 * i + 1] = y[i] / e;
+        tab[5 * i + 2] = ((y[i + 1] - y[i]) / h - h * (2.0 * m[i] + m[i + 1]) / 6.0) / e;
+        tab[5 * i + 3] = 0.5 * m[i] / e;
+        tab[5 * i + 4] = (m[i + 1] - m[i]) / (6.0 * h) / e;
+        const double eps = i * h * i * h + y[i] / e;    // in units of hbar^2/2m
+        if (i > 0 && !(eps > prev)) {
+            set_err(err, errlen, "the Hartree-Fock spectrum does not increase with k");
+            return MBPT_EINVAL;
+        }
+        prev = eps;
+    }
+    return MBPT_OK;
+}
+
+// Sigma(k)/(hbar^2/2m) from the table (FP64), 0 beyond the last knot.
+double hf_eval(const std::vector<double>& tab, double hinv, double k) {
+    const int nint = (int)(tab.size() / 5);
+    int i = (int)std::floor(k * hinv);
+    if (i < 0) i = 0;
+    if (i >= nint) return 0.0;
+    const double* c = &tab[5 * (size_t)i];
+    const double t = k - c[0];
+    return std::fma(std::fma(std::fma(c[4], t, c[3]), t, c[2]), t, c[1]);
 }
 
 }  // namespace mbpt
@@ -522,5 +646,20 @@ extern "C" int mbpt_hole_chords(const mbpt_diagram_desc* d, int* out) {
         h += d->line_src[l] > d->line_dst[l];   // src above dst in time: a hole line
     }
     *out = h;
+    return MBPT_OK;
+}
+
+extern "C" int mbpt_hf_self_energy(const mbpt_physics* ph, int n, const double* k, double* sigma) {
+    if (!ph || n < 0 || (n > 0 && (!k || !sigma))) return MBPT_EINVAL;
+    if (!(ph->kF_n >= 0.0) || !(ph->kF_p >= 0.0) || !(ph->kF_n > 0.0 || ph->kF_p > 0.0) ||
+        (ph->kF_n > 0.0 && ph->kF_p > 0.0 && ph->kF_n != ph->kF_p) || !(ph->K_max > 0.0) ||
+        !(ph->hbar2_over_m > 0.0) || !(ph->Lambda > 0.0) || ph->reg_power < 2)
+        return MBPT_EINVAL;
+    std::vector<double> tab;
+    char err[128];
+    int st = build_hf_table(*ph, tab, err, sizeof(err));
+    if (st) return st;
+    const double hinv = (MBPT_HF_KNOTS - 1) / (2.0 * ph->K_max), e = 0.5 * ph->hbar2_over_m;
+    for (int i = 0; i < n; ++i) sigma[i] = e * hf_eval(tab, hinv, k[i]);
     return MBPT_OK;
 }

@@ -3,6 +3,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mbpt.h"
 
 namespace mbpt {
@@ -41,6 +43,8 @@ struct alignas(16) DiagRec {
     // P_v = k_o1 - k_o2 and P'_v = k_i1 - k_i2 as chord combinations (coefficients -2..2)
     float vcoef_out[MBPT_MAX_DEVICE_ORDER][8];
     float vcoef_in[MBPT_MAX_DEVICE_ORDER][8];
+    // tree line in slot n+1+j as a chord combination (coefficients -1..1), for the FP32 step pre-test
+    float tcoef[MBPT_MAX_DEVICE_ORDER][8];
     // spin(-isospin) sum, term t: bit v of t set = vertex v taken in exchange
     float gcoef_f[kMaxTerms];                    // (-1)^L(t) g^L(t)   (one Fermi momentum)
     double gcoef_d[kMaxTerms];
@@ -59,6 +63,13 @@ struct alignas(16) DiagRec {
     int8_t line_slot[MBPT_MAX_LINES];            // slot of each descriptor line
     int32_t map_kind;                            // 0: full chord directions; 1: rotational reduction
     int32_t n_shifts;                            // 0 or kShifts
+    float kf2_nf, kf2_pf;                        // FP32 copies of kf2_n, kf2_p (Fermi-step pre-test)
+    int32_t spectrum;                            // 0 free, 1 Hartree-Fock (table below)
+    float hf_hinv_f;                             // 1 / knot spacing, FP32
+    const double* hf_tab;                        // per interval i: k_i and the cubic's a, b, c, d (D~ units)
+    const float* hf_tab_f;                       // the same in FP32 (mixed precision)
+    int32_t hf_n;                                // intervals (knots - 1)
+    int32_t pad_h;
     int32_t pad_s;
     double eta[kShifts];                         // shifts in units of hbar^2/2m (D~ units)
     double lag[kShifts];                         // Lagrange weights of the quadratic at zero shift
@@ -112,5 +123,7 @@ struct alignas(16) WorkHeader {
 int compile_record(const mbpt_diagram_desc& desc, const mbpt_physics& ph, const mbpt_vegas_cfg& cfg,
                    DiagRec* rec, char* err, size_t errlen);
 int validate_descriptor(const mbpt_diagram_desc& desc, char* err, size_t errlen);
+int build_hf_table(const mbpt_physics& ph, std::vector<double>& tab, char* err, size_t errlen);
+double hf_eval(const std::vector<double>& tab, double hinv, double k);
 
 }  // namespace mbpt

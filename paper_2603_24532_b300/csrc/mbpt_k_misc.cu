@@ -180,9 +180,9 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
 
 // Test hook kernel: samples [first, first+count) of iteration `iter`, mapped point and weight.
 template <int N, int PREC, int MAPK>
-__device__ void dump_one(const DiagRec& R, const Grid2* gs, uint32_t s, uint32_t t, uint32_t sid, uint32_t k0,
-                         uint32_t k1, double* x, double* w) {
-    const SampleOut o = eval_sample<N, PREC, MAPK, false>(R, gs, s, t, sid, k0, k1, x);
+__device__ void dump_one(const DiagRec& R, const Grid2* gs, const double* grid64, uint32_t s, uint32_t t,
+                         uint32_t sid, uint32_t k0, uint32_t k1, double* x, double* w) {
+    const SampleOut o = eval_sample<N, PREC, MAPK, false>(R, gs, grid64, s, t, sid, k0, k1, x);
     *w = o.w;
 }
 
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members,
         if (active) {
             switch ((R.order * 3 + prec) * 2 + R.map_kind) {
 #define MBPT_CASE(N_, P_, M_) \
-    case (N_ * 3 + P_) * 2 + M_: dump_one<N_, P_, M_>(R, gs, s, iter, sid, k0, k1, m == 0 ? x : nullptr, &w); break;
+    case (N_ * 3 + P_) * 2 + M_: dump_one<N_, P_, M_>(R, gs, grid, s, iter, sid, k0, k1, m == 0 ? x : nullptr, &w); break;
 #define MBPT_CASES(N_) \
     MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
     MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)

@@ -19,6 +19,8 @@ struct alignas(16) ChunkSmemT {
     float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
     double cacc[2 * kComp][NW * 32];         // per-thread sums of the regulator components
     double gacc[kGroupSlots][NW * 32];       // group integrals: per-sample sums over the members
+    uint32_t queue[NW][2][64];               // mixed precision: per-warp queues of samples past the pre-test
+                                             // (away from / near a Fermi surface)
     double red[2][NW];
     double redc[2 * kComp][NW];
     uint32_t chunk, item, iter, skip;
@@ -102,10 +104,18 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
     }
 }
 
-// One chunk: samples first + j*blockDim + tid, j < spt.  A group integral (n_members > 1) evaluates
-// every member at each sample, member by member with the record swapped in shared memory, summing
-// the weights per sample in gacc (spt x (1 + regulator components) <= kGroupSlots slots per thread);
-// sums, squares and the histogram then see the group's integrand.
+// One chunk: samples first + j*blockDim + tid, j < spt.
+//  Mixed precision (plain integrals): the FP64 pipe issues per warp instruction, so a warp whose
+//  lanes hold a mix of zero and live samples pays for the zero ones, and one whose lanes take both
+//  sampling maps pays for both.  Each warp therefore first runs the FP32 front and Fermi-step
+//  pre-test of its samples and queues the ones that may be live, by class (away from / near a
+//  Fermi surface; ballot + prefix count into 64-entry shared-memory queues); full warps of one class
+//  are then evaluated, the partial ones at the end of the chunk.  Which thread sums which sample
+//  depends only on the chunk, so results stay deterministic.
+//  A group integral (n_members > 1) evaluates every member at each sample, member by member with
+//  the record swapped in shared memory, summing the weights per sample in gacc
+//  (spt x (1 + regulator components) <= kGroupSlots slots per thread); sums, squares and the
+//  histogram then see the group's integrand.
 template <int N, int PREC, int MAPK, bool REG, int NW>
 __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
@@ -115,44 +125,92 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     const uint32_t t = S.iter;
     const uint32_t k0 = (uint32_t)W.seed, k1 = (uint32_t)(W.seed >> 32);
     float* hist = S.hist[threadIdx.x >> 5];
+    uint32_t* q = &S.queue[threadIdx.x >> 5][0][0];      // q[0..63] away from, q[64..127] near a surface
+    const uint32_t lane = threadIdx.x & 31u;
     const int nb = R.nb;
     constexpr int D = 3 * (N + 1) - 3 * MAPK;
     constexpr int PER = REG ? 1 + kComp : 1;        // group slots per sample
     const int nm = (int)W.n_members;
     const bool grp = nm > 1;
+    const bool compact = (PREC == MBPT_MIXED) && !grp;
     for (int m = 0; m < nm; ++m) {
         if (m > 0) {
             __syncthreads();
             load_record(&S.rec, W.rec + m);
             __syncthreads();
         }
-        for (int j = 0; j < W.spt; ++j) {
-            const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
-            if (s >= W.samples) continue;
-            const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, (uint32_t)s, t, W.stream_id, k0, k1,
-                                                                nullptr);
-            if (grp) {
-                double* a = &S.gacc[j * PER][threadIdx.x];
-                a[0] = (m == 0) ? o.w : a[0] + o.w;
-                if constexpr (REG) {
+        int j = 0, nq0 = 0, nq1 = 0;       // warp-uniform
+        for (;;) {
+            uint64_t s;
+            int jslot = 0;
+            bool have, use_near = false;
+            if (compact) {
+                while (nq0 < 32 && nq1 < 32 && j < W.spt) {
+                    const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
+                    const int cls =
+                        sc < W.samples ? mixed_classify<N, MAPK>(R, S.grid, (uint32_t)sc, t, W.stream_id, k0, k1) : 0;
+                    const uint32_t lt = (1u << lane) - 1u;
+                    const uint32_t b0 = __ballot_sync(0xffffffffu, cls == 1);
+                    const uint32_t b1 = __ballot_sync(0xffffffffu, cls == 2);
+                    if (cls == 1) q[nq0 + __popc(b0 & lt)] = (uint32_t)sc;
+                    if (cls == 2) q[64 + nq1 + __popc(b1 & lt)] = (uint32_t)sc;
+                    nq0 += __popc(b0);
+                    nq1 += __popc(b1);
+                    ++j;
+                }
+                if (nq1 >= 32) use_near = true;
+                else if (nq0 >= 32 || nq0 > 0) use_near = false;
+                else if (nq1 > 0) use_near = true;
+                else break;
+                __syncwarp();
+                const int cnt = use_near ? nq1 : nq0;
+                have = (int)lane < cnt;
+                s = have ? q[(use_near ? 64 : 0) + lane] : 0u;
+            } else {
+                if (j >= W.spt) break;
+                jslot = j;
+                s = first + (uint64_t)j * blockDim.x + threadIdx.x;
+                have = s < W.samples;
+                ++j;
+            }
+            if (have) {
+                const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, W.grid, (uint32_t)s, t, W.stream_id,
+                                                                    k0, k1, nullptr, use_near);
+                if (grp) {
+                    double* a = &S.gacc[jslot * PER][threadIdx.x];
+                    a[0] = (m == 0) ? o.w : a[0] + o.w;
+                    if constexpr (REG) {
 #pragma unroll
-                    for (int c = 0; c < kComp; ++c) {
-                        double& v = S.gacc[j * PER + 1 + c][threadIdx.x];
-                        v = (m == 0) ? o.wc[c] : v + o.wc[c];
+                        for (int c = 0; c < kComp; ++c) {
+                            double& v = S.gacc[jslot * PER + 1 + c][threadIdx.x];
+                            v = (m == 0) ? o.wc[c] : v + o.wc[c];
+                        }
+                    }
+                } else {
+                    if (nonzero(o.w)) {          // a zero weight leaves both sums unchanged: no FP64 work
+                        sw += o.w;
+                        sw2 = fma(o.w, o.w, sw2);
+                        hist_add<D>(hist, nb, o.binpack, o.w);
+                    }
+                    if constexpr (REG) {
+#pragma unroll
+                        for (int c = 0; c < kComp; ++c) {
+                            S.cacc[2 * c][threadIdx.x] += o.wc[c];
+                            S.cacc[2 * c + 1][threadIdx.x] = fma(o.wc[c], o.wc[c], S.cacc[2 * c + 1][threadIdx.x]);
+                        }
                     }
                 }
-                continue;
             }
-            sw += o.w;
-            sw2 = fma(o.w, o.w, sw2);
-            if constexpr (REG) {
-#pragma unroll
-                for (int c = 0; c < kComp; ++c) {
-                    S.cacc[2 * c][threadIdx.x] += o.wc[c];
-                    S.cacc[2 * c + 1][threadIdx.x] = fma(o.wc[c], o.wc[c], S.cacc[2 * c + 1][threadIdx.x]);
-                }
+            if (compact) {
+                uint32_t* qq = q + (use_near ? 64 : 0);
+                const int cnt = use_near ? nq1 : nq0;
+                const int done = cnt < 32 ? cnt : 32;
+                __syncwarp();
+                if ((int)lane < cnt - done) qq[lane] = qq[done + lane];
+                __syncwarp();
+                if (use_near) nq1 -= done;
+                else nq0 -= done;
             }
-            if (nonzero(o.w)) hist_add<D>(hist, nb, o.binpack, o.w);
         }
     }
     if (!grp) return;

@@ -158,6 +158,7 @@ struct mbpt_diag {
     double* d_last_hist = nullptr;
     int d = 0, nb = 0;
     int n_members = 1;        // > 1: group integral, d_rec holds n_members records
+    void* d_hf = nullptr;     // Hartree-Fock spectrum table (FP64 then FP32 coefficients), or null
 };
 
 namespace {
@@ -466,8 +467,35 @@ static int create_integral(mbpt_ctx* c, const mbpt_diagram_desc* descs, int k, c
     }
     DeviceGuard dg(c->device);
     const int d = recs[0].d, nb = recs[0].nb;
+    std::vector<double> hf;
+    std::vector<float> hff;
+    void* d_hf = nullptr;
+    if (ph->spectrum == 1) {
+        int st = build_hf_table(*ph, hf, err, sizeof(err));
+        if (st) return fail(st, std::string(who) + ": " + err);
+        hff.resize(hf.size());
+        for (size_t i = 0; i < hf.size(); ++i) hff[i] = (float)hf[i];
+        const size_t fb = sizeof(double) * hf.size();
+        d_hf = c->arena.alloc(fb + sizeof(float) * hff.size());
+        if (!d_hf) return fail(MBPT_ENOMEM, std::string(who) + ": arena exhausted (spectrum table)");
+        cudaError_t e1 = cudaMemcpyAsync(d_hf, hf.data(), fb, cudaMemcpyHostToDevice, c->stream);
+        if (e1 == cudaSuccess)
+            e1 = cudaMemcpyAsync((char*)d_hf + fb, hff.data(), sizeof(float) * hff.size(), cudaMemcpyHostToDevice,
+                                 c->stream);
+        if (e1 != cudaSuccess) {
+            c->arena.release(d_hf);
+            return fail(MBPT_ECUDA, std::string(who) + " spectrum upload: " + cudaGetErrorString(e1));
+        }
+        for (int m = 0; m < k; ++m) {
+            recs[m].hf_tab = (const double*)d_hf;
+            recs[m].hf_tab_f = (const float*)((char*)d_hf + fb);
+        }
+    }
     char* blk = (char*)c->arena.alloc(state_block_bytes(d, nb, k));
-    if (!blk) return fail(MBPT_ENOMEM, std::string(who) + ": arena exhausted");
+    if (!blk) {
+        c->arena.release(d_hf);
+        return fail(MBPT_ENOMEM, std::string(who) + ": arena exhausted");
+    }
     mbpt_diag* g = new (std::nothrow) mbpt_diag();
     if (!g) {
         c->arena.release(blk);
@@ -482,6 +510,7 @@ static int create_integral(mbpt_ctx* c, const mbpt_diagram_desc* descs, int k, c
     g->d = d;
     g->nb = nb;
     g->n_members = k;
+    g->d_hf = d_hf;
     g->d_rec = (DiagRec*)blk;
     g->d_state = (DiagState*)(blk + rec_bytes);
     g->d_grid = (double*)(blk + rec_bytes + up(sizeof(DiagState)));
@@ -500,6 +529,7 @@ static int create_integral(mbpt_ctx* c, const mbpt_diagram_desc* descs, int k, c
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         c->arena.release(blk);
+        c->arena.release(d_hf);
         delete g;
         return fail(MBPT_ECUDA, std::string(who) + " upload: " + cudaGetErrorString(e));
     }
@@ -546,6 +576,7 @@ int mbpt_destroy_diagram(mbpt_diag* g) {
     DeviceGuard dg(c->device);
     cudaStreamSynchronize(c->stream);   // no queued work may still reference it
     c->arena.release(g->d_rec);
+    c->arena.release(g->d_hf);
     c->diags.erase(g);
     delete g;
     return MBPT_OK;
@@ -874,6 +905,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
                                             double* out, void* cuda_stream) {
     if (!desc || !ph || !cfg || !grid || !out) return fail(MBPT_EINVAL, "iteration_noalloc: NULL argument");
     if (cfg->n_shifts) return fail(MBPT_EINVAL, "iteration_noalloc: denominator regulator not supported here");
+    if (ph->spectrum) return fail(MBPT_EINVAL, "iteration_noalloc: the Hartree-Fock spectrum is not supported here");
     if (device < 0 || device >= kNoAllocMaxDevices) return fail(MBPT_EINVAL, "iteration_noalloc: bad device");
     DiagRec rec;
     char err[256] = {0};

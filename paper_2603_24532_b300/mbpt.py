@@ -103,6 +103,7 @@ class mbpt_physics(ctypes.Structure):
         ("C_S", ctypes.c_double), ("C_Y", ctypes.c_double), ("m_pi", ctypes.c_double), ("Lambda", ctypes.c_double),
         ("reg_power", ctypes.c_int32), ("map_kind", ctypes.c_int32),
         ("K_max", ctypes.c_double),
+        ("spectrum", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -161,6 +162,7 @@ def lib():
                                   P(mbpt_vegas_cfg), P(vp)],
             "mbpt_hole_chords": [P(mbpt_diagram_desc), P(ctypes.c_int)],
             "mbpt_group_bytes": [P(mbpt_diagram_desc), ctypes.c_int, P(mbpt_vegas_cfg), P(ctypes.c_size_t)],
+            "mbpt_hf_self_energy": [P(mbpt_physics), ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)],
             "mbpt_destroy_diagram": [vp],
             "mbpt_set_config": [vp, P(mbpt_vegas_cfg)],
             "mbpt_vegas_iterate": [vp, P(vp), ctypes.c_int, ctypes.c_int],
@@ -236,6 +238,14 @@ def mbpt_group_bytes(descs: Sequence[mbpt_diagram_desc], cfg: mbpt_vegas_cfg) ->
     b = ctypes.c_size_t()
     check(lib().mbpt_group_bytes(arr, len(descs), ctypes.byref(cfg), ctypes.byref(b)))
     return b.value
+
+
+def mbpt_hf_self_energy(phys: mbpt_physics, k) -> np.ndarray:
+    """Hartree-Fock self-energy (MeV) of the physics point's spectrum table at momenta k (fm^-1)."""
+    kk = np.ascontiguousarray(np.atleast_1d(k), dtype=np.float64)
+    out = np.zeros_like(kk)
+    check(lib().mbpt_hf_self_energy(ctypes.byref(phys), len(kk), _dp(kk), _dp(out)))
+    return out
 
 
 def mbpt_kernel_variants():
@@ -411,12 +421,12 @@ def state_with_grid(image: bytes, grid: np.ndarray) -> bytes:
 
 
 def physics(kF_n=1.0, kF_p=0.0, hbar2_over_m=41.47, C_S=-50.0, C_Y=-200.0, m_pi=0.7, Lam=2.0, reg_power=4,
-            K_max=None, map_kind=0) -> mbpt_physics:
+            K_max=None, map_kind=0, spectrum=0) -> mbpt_physics:
     """Physics point of the toy potential; K_max defaults to max kF + 3 Lambda."""
     p = mbpt_physics()
     p.kF_n, p.kF_p, p.hbar2_over_m = kF_n, kF_p, hbar2_over_m
     p.C_S, p.C_Y, p.m_pi, p.Lambda = C_S, C_Y, m_pi, Lam
-    p.reg_power, p.map_kind = reg_power, map_kind
+    p.reg_power, p.map_kind, p.spectrum = reg_power, map_kind, spectrum
     p.K_max = K_max if K_max is not None else max(kF_n, kF_p) + 3.0 * Lam
     return p
 

@@ -242,10 +242,13 @@ class Server:
     def __init__(self, backend, budget_bytes: int = 40 << 30, max_integrals: int = 1 << 16,
                  samples_by_order: Optional[Dict[int, int]] = None, min_iters: int = 3, max_iters: int = 60,
                  seed: int = 1, clock: Callable[[], float] = time.perf_counter, adaptive: bool = True,
-                 warm_start: bool = False, warm_window: float = 0.02):
+                 warm_start: bool = False, warm_window: float = 0.02, warm_blend: float = 0.5,
+                 warm_train: int = 1):
         self.b = backend
         self.adaptive = adaptive
         self.cache = GridCache(warm_window) if warm_start else None
+        self.warm_blend = warm_blend          # weight of the donor grid (rest: uniform bins)
+        self.warm_train = warm_train          # leading iterations of a warm-started integral not combined
         self.warm_starts = 0
         self.budget = budget_bytes
         self.max_integrals = max_integrals
@@ -308,12 +311,12 @@ class Server:
                     if self.cache is not None and hasattr(self.b, "set_grid"):
                         g = self.cache.get(order, d.diagram_id, req.delta, req.n_dens)
                         if g is not None:
-                            # half the donor's bin structure, half uniform, plus one training iteration
-                            # that is not combined (abbreviated retraining)
+                            # the donor's bin structure blended with uniform bins, plus warm_train
+                            # training iterations that are not combined (abbreviated retraining)
                             u = np.linspace(0.0, 1.0, g.shape[1])[None, :]
-                            self.b.set_grid(h, 0.5 * g + 0.5 * u)
-                            if hasattr(self.b, "set_train"):
-                                self.b.set_train(h, it.cfg, 1)
+                            self.b.set_grid(h, self.warm_blend * g + (1.0 - self.warm_blend) * u)
+                            if self.warm_train and hasattr(self.b, "set_train"):
+                                self.b.set_train(h, it.cfg, self.warm_train)
                             it.warm = True
             except MemoryError:
                 # the arena refused (its scratch competes with integral state): roll back, retry later

@@ -17,7 +17,8 @@ def make_desc(D: O.Diagram) -> M.mbpt_diagram_desc:
 def phys_pair(kF_n=1.0, kF_p=0.0, **kw):
     po = O.Physics(kF_n=kF_n, kF_p=kF_p, **kw)
     pm = M.physics(kF_n=kF_n, kF_p=kF_p, hbar2_over_m=po.hbar2_over_m, C_S=po.C_S, C_Y=po.C_Y, m_pi=po.m_pi,
-                   Lam=po.Lam, reg_power=po.reg_power, K_max=po.K_max, map_kind=po.map_kind)
+                   Lam=po.Lam, reg_power=po.reg_power, K_max=po.K_max, map_kind=po.map_kind,
+                   spectrum=po.spectrum)
     return po, pm
 
 

@@ -14,6 +14,13 @@ import math
 import numpy as np
 
 
+def first_order_from_sigma(kF, g, sigma, n=200):
+    """E_HF/N = (g/2n) int d^3k/(2 pi)^3 theta(kF - k) Sigma(k) = (g/(4 pi^2 n)) int_0^kF k^2 Sigma(k) dk."""
+    nd = g * kF ** 3 / (6.0 * math.pi ** 2)
+    x, w = gl(0.0, kF, n)
+    return g / (4.0 * math.pi ** 2 * nd) * float(np.sum(w * x ** 2 * sigma(x)))
+
+
 def gl(a: float, b: float, n: int):
     x, w = np.polynomial.legendre.leggauss(n)
     return 0.5 * (b - a) * x + 0.5 * (b + a), 0.5 * (b - a) * w
@@ -43,12 +50,14 @@ def first_order_contact(kF, g, C_S):
 
 
 def second_order(kF, g, hbar2_over_m, C_S, C_Y, m_pi, Lam, r=4, n_rad=12, n_ang=10, pmax=8.0, cross=True,
-                 shift=0.0):
+                 shift=0.0, sigma=None):
     """E^(2)/N = (1/n) (1/4) sum_spins int d^3k_i d^3k_j d^3k_a/(2pi)^9 |<ab|V|ij>|^2 / D
     with P = (k_i + k_j)/2, p = (k_i - k_j)/2, p' = (k_a - k_b)/2 (Jacobian 8),
     D = (hbar^2/m)(p^2 - p'^2), spin sum g^2 (V_d^2 + V_e^2) - 2 g V_d V_e.
     P along z, p in the xz-plane; holes need P^2 + p^2 + 2Pp|cos t_p| < kF^2,
-    particles P^2 + p'^2 - 2Pp'|cos t'| >= kF^2.  shift s replaces D by D - s."""
+    particles P^2 + p'^2 - 2Pp'|cos t'| >= kF^2.  shift s replaces D by D - s.  sigma (a vectorised
+    function of |k|) adds a self-energy to every single-particle energy: the lines are then
+    k_i,j = P +- p, k_a,b = P +- p' and D = eps_i + eps_j - eps_a - eps_b - s."""
     n = g * kF ** 3 / (6.0 * math.pi ** 2)
     Pn, Pw = gl(0.0, kF, n_rad)
     total = 0.0
@@ -104,6 +113,15 @@ def second_order(kF, g, hbar2_over_m, C_S, C_Y, m_pi, Lam, r=4, n_rad=12, n_ang=
             ve = (C_S + C_Y / (qe2 + m_pi ** 2)) * reg
             S = g * g * (vd ** 2 + ve ** 2) - (2.0 * g * vd * ve if cross else 0.0)
             Dn = hbar2_over_m * (p ** 2 - PP ** 2) - shift
+            if sigma is not None:
+                # P along z, p in the xz plane at polar angle t_p, p' at (t', phi')
+                pz = p * CT
+                ppz = PP * CTP
+                ki = np.sqrt(np.maximum(P ** 2 + p ** 2 + 2 * P * pz, 0.0))
+                kj = np.sqrt(np.maximum(P ** 2 + p ** 2 - 2 * P * pz, 0.0))
+                ka = np.sqrt(np.maximum(P ** 2 + PP ** 2 + 2 * P * ppz, 0.0))
+                kb = np.sqrt(np.maximum(P ** 2 + PP ** 2 - 2 * P * ppz, 0.0))
+                Dn = Dn + sigma(ki) + sigma(kj) - sigma(ka) - sigma(kb)
             W = (wct[:, None, None, None] * (pp_w * pp_nodes ** 2)[None, :, None, None]
                  * wctp[None, :, :, None] * phw[None, None, None, :])
             inner = float(np.sum(W * S / Dn)) * 4.0

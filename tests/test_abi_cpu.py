@@ -73,3 +73,22 @@ def test_no_device_fails_cleanly():
         pytest.skip("a GPU is present")
     with pytest.raises(M.MbptError):
         M.mbpt_ctx_create(0, 1 << 20)
+
+
+@pytest.mark.parametrize("kfp", [0.0, 1.2])
+def test_hf_self_energy_table_matches_oracle(kfp):
+    """The product's Hartree-Fock table (its own quadrature, spline and per-interval cubics) against
+    the oracle's spline of its own knot values, at knots, between knots and beyond the table."""
+    kfn = 1.2 if kfp else 1.0
+    po = O.Physics(kF_n=kfn, kF_p=kfp, K_max=kfn + 6.0, spectrum=1)
+    pm = M.physics(kF_n=kfn, kF_p=kfp, K_max=kfn + 6.0, spectrum=1)
+    ks = np.concatenate([np.linspace(0.0, 2 * po.K_max * 0.999, 257), [0.3 * po.K_max / 1023, 2 * po.K_max + 0.5]])
+    got = M.mbpt_hf_self_energy(pm, ks)
+    ref = np.array([O.sp_energy(po, k) - 0.5 * po.hbar2_over_m * k * k for k in ks])
+    assert np.max(np.abs(got - ref)) < 1e-11
+    assert got[-1] == 0.0
+
+
+def test_hf_self_energy_rejects_two_fermi_momenta():
+    with pytest.raises(M.MbptError):
+        M.mbpt_hf_self_energy(M.physics(kF_n=1.2, kF_p=0.8, spectrum=1), [0.5])

@@ -104,7 +104,7 @@ def test_group_of_a_repeated_member_is_exactly_twice_the_diagram(ctx):
     po, pm = matter_pair("snm")
     D = O.enumerate_diagrams(4)[11]
     assert not O.is_anomalous(D)
-    cfg = M.vegas_cfg(samples=50000, seed=2, stream_id=31, precision=M.MBPT_MIXED)
+    cfg = M.vegas_cfg(samples=50000, seed=2, stream_id=31, precision=M.MBPT_MIXED_MAP64)
     tpb, minb, spt0 = M.mbpt_ctx_get_launch(ctx, 4)
     M.mbpt_ctx_set_launch(ctx, 4, 8)          # the chunk shape a group uses (8 samples per thread)
     a = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)

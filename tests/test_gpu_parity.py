@@ -106,6 +106,88 @@ def test_mixed_precision_deviation(ctx, n, matter, mapk, prec):
             M.mbpt_destroy_diagram(g)
 
 
+@pytest.mark.parametrize("n,matter,mapk", [(3, "pnm", 0), (4, "snm", 1), (4, "asym", 0), (5, "pnm", 0)])
+def test_mixed_map_near_fermi_surfaces_is_the_fp64_map(ctx, n, matter, mapk):
+    """Mixed mode places a live sample with a line within ~1e-3 kF^2 of a Fermi surface with the FP64
+    map (the oracle's point to rounding), and decides every Fermi step as the FP64 oracle does: zero
+    patterns agree except for weights below the FP32 range of the potentials."""
+    rng = np.random.default_rng(300 + 7 * n + mapk)
+    po, pm = matter_pair(matter, map_kind=mapk)
+    kf2 = [k * k for k in (po.kF_n, po.kF_p) if k > 0]
+    for D in _pick(n, 2, rng):
+        if O.is_anomalous(D):
+            continue
+        cfg = M.vegas_cfg(samples=1 << 16, seed=5, stream_id=D.diagram_id, precision=M.MBPT_MIXED)
+        g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
+        try:
+            grid = random_grid(po.dim(D), 50, rng, strength=0.5)
+            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+            xg, wg = M.mbpt_dump_samples(g, 1, 0, 4096, po.dim(D))
+            xo, wo = oracle_dump(D, po, grid, 5, D.diagram_id, 1, 0, 4096)
+            dist = np.array([min(np.min(np.abs(O.line_ksq(D, po, x) - k2)) / k2 for k2 in kf2) for x in xo])
+            band = (dist < 5e-4) & (wo != 0)
+            assert band.sum() > 0
+            assert np.max(np.abs(xg[band] - xo[band])) <= 4 * EPS
+            ok = dist > 1e-9
+            mism = ok & ((wg == 0) != (wo == 0))
+            assert np.all(wg[mism] == 0) and np.all(np.abs(wo[mism]) < 1e-20 * np.max(np.abs(wo)))
+        finally:
+            M.mbpt_destroy_diagram(g)
+
+
+@pytest.mark.parametrize("n,matter,mapk", [(2, "pnm", 0), (3, "snm", 1), (4, "pnm", 0), (5, "snm", 0)])
+def test_hartree_fock_spectrum_per_sample(ctx, n, matter, mapk):
+    """Hartree-Fock single-particle energies (Eq. (7)) in the energy denominators: FP64 per-sample
+    parity with the oracle's own tabulation and spline (tolerance widened by the conditioning of
+    each denominator, kinetic and self-energy parts counted separately), and the mixed modes within
+    the aggregate 1e-4 bound."""
+    rng = np.random.default_rng(900 + n + mapk)
+    po, pm = matter_pair(matter, map_kind=mapk, spectrum=1)
+    for D in _pick(n, 2, rng):
+        if O.is_anomalous(D):
+            continue
+        grid = random_grid(po.dim(D), 50, rng, strength=0.5)
+        xo, wo = oracle_dump(D, po, grid, 11, D.diagram_id, 2, 333, 1536)
+        ns = near_surface(D, po, xo)
+        for prec in (M.MBPT_FP64, M.MBPT_MIXED, M.MBPT_MIXED_MAP64):
+            cfg = M.vegas_cfg(samples=1 << 16, seed=11, stream_id=D.diagram_id, precision=prec)
+            g = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
+            try:
+                M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+                xg, wg = M.mbpt_dump_samples(g, 2, 333, 1536, po.dim(D))
+                if prec == M.MBPT_FP64:
+                    ok = ~ns
+                    assert np.array_equal(wg[ok] == 0.0, wo[ok] == 0.0)
+                    tol = fp64_tol(D, po, xo, wo) + 1e-15 * np.mean(np.abs(wo))
+                    assert np.all(np.abs(wg - wo)[ok] <= tol[ok])
+                    assert (wo != 0).sum() > 0
+                else:
+                    ok = ~near_surface(D, po, xo, rel=1e-5)
+                    l1 = np.sum(np.abs(wg[ok] - wo[ok])) / max(np.sum(np.abs(wo[ok])), 1e-300)
+                    assert l1 < 1e-4, l1
+            finally:
+                M.mbpt_destroy_diagram(g)
+
+
+def test_hartree_fock_spectrum_changes_the_integrand_and_rejects_asymmetric_matter(ctx):
+    po0, pm0 = matter_pair("pnm")
+    po1, pm1 = matter_pair("pnm", spectrum=1)
+    D = O.enumerate_diagrams(3)[1]
+    cfg = M.vegas_cfg(samples=1 << 14, seed=3)
+    g0 = M.mbpt_create_diagram(ctx, make_desc(D), pm0, cfg)
+    g1 = M.mbpt_create_diagram(ctx, make_desc(D), pm1, cfg)
+    try:
+        _, w0 = M.mbpt_dump_samples(g0, 0, 0, 512, D.d, with_x=False)
+        _, w1 = M.mbpt_dump_samples(g1, 0, 0, 512, D.d, with_x=False)
+        assert np.array_equal(w0 == 0, w1 == 0) and np.any(w0 != w1)
+    finally:
+        M.mbpt_destroy_diagram(g0)
+        M.mbpt_destroy_diagram(g1)
+    _, pa = matter_pair("asym", spectrum=1)
+    with pytest.raises(M.MbptError):
+        M.mbpt_create_diagram(ctx, make_desc(D), pa, cfg)
+
+
 @pytest.mark.parametrize("prec", [M.MBPT_FP64, M.MBPT_MIXED, M.MBPT_MIXED_MAP64])
 def test_one_iteration_sums_histogram_and_refinement(ctx, prec):
     """One batched iteration on a ragged sample count: sum w, sum w^2 against the

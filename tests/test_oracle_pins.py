@@ -132,6 +132,74 @@ def test_third_order_group_estimate_matches_members():
     assert within(mg, math.hypot(sg, st), tot)
 
 
+# --- Hartree-Fock spectrum (Eq. (7)) ---------------------------------------------------------
+
+def test_gauss_legendre_rule():
+    x = np.zeros(12)
+    w = np.zeros(12)
+    O.lib().oracle_gauss_legendre(12, O._dp(x), O._dp(w))
+    assert np.sum(w) == pytest.approx(2.0, rel=1e-14)
+    for deg in (2, 10, 22):                       # exact to degree 2n - 1 = 23
+        assert np.sum(w * x ** deg) == pytest.approx(2.0 / (deg + 1), rel=1e-13)
+
+
+@pytest.mark.parametrize("kfp", [0.0, 1.0])
+def test_hf_self_energy_contact_closed_form(kfp):
+    """Unregulated contact: Sigma(k) = C_S n (g - 1)/g for every k (C_S n/2 in neutron matter)."""
+    ph = O.Physics(kF_n=1.0, kF_p=kfp, C_Y=0.0, Lam=1e6)
+    g = 4 if kfp else 2
+    for k in (0.0, 0.4, 1.3, 3.0):
+        assert O.hf_self_energy(ph, k) == pytest.approx(-50.0 * ph.density * (g - 1) / g, rel=1e-12)
+
+
+@pytest.mark.parametrize("kfp", [0.0, 1.0])
+def test_hf_self_energy_integrates_to_first_order(kfp):
+    """(g/2n) sum over the Fermi sea of Sigma is the first-order energy per particle, pinned
+    independently by the 1D reduction over the relative momentum."""
+    ph = O.Physics(kF_n=1.0, kF_p=kfp, spectrum=1)
+    g = 4 if kfp else 2
+    ref = Q.first_order_full_v(1.0, g, ph.C_S, ph.C_Y, ph.m_pi, ph.Lam)
+    direct = Q.first_order_from_sigma(1.0, g, np.vectorize(lambda k: O.hf_self_energy(ph, k)), n=48)
+    spline = Q.first_order_from_sigma(1.0, g, np.vectorize(lambda k: O.sp_energy(ph, k) - 0.5 * 41.47 * k * k),
+                                      n=48)
+    assert direct == pytest.approx(ref, rel=1e-10)
+    assert spline == pytest.approx(ref, rel=1e-7)
+
+
+def test_hf_spline_between_knots():
+    """The tabulated spectrum: between knots the spline is within 1e-7 MeV of the direct quadrature,
+    and it is the cubic spline with zero slope at k = 0 and zero curvature at the end (an independent
+    spline construction on the same knots agrees to rounding)."""
+    from scipy.interpolate import CubicSpline
+    ph = O.Physics(spectrum=1)
+    y, m, h = O.hf_table(ph)
+    ks = (np.arange(0, 400, 7) + 0.5) * h
+    sp = np.array([O.sp_energy(ph, k) - 0.5 * ph.hbar2_over_m * k * k for k in ks])
+    dq = np.array([O.hf_self_energy(ph, k) for k in ks])
+    assert np.max(np.abs(sp - dq)) < 1e-7
+    cs = CubicSpline(np.arange(len(y)) * h, y, bc_type=((1, 0.0), (2, 0.0)))
+    assert np.max(np.abs(sp - cs(ks))) < 1e-12
+    assert O.sp_energy(ph, 2.0 * ph.K_max + 0.1) == pytest.approx(0.5 * ph.hbar2_over_m * (2 * ph.K_max + 0.1) ** 2)
+
+
+def test_hf_second_order_vs_quadrature():
+    """Eq. (2) with Hartree-Fock single-particle energies in the denominator: the oracle's VEGAS
+    estimate against the relative-coordinate quadrature with the same spectrum (an independent
+    spline of the oracle's knot values), and clearly apart from the free-spectrum value."""
+    from scipy.interpolate import CubicSpline
+    (D,) = O.enumerate_diagrams(2)
+    ph = O.Physics(spectrum=1)
+    y, m, h = O.hf_table(ph)
+    cs = CubicSpline(np.arange(len(y)) * h, y, bc_type=((1, 0.0), (2, 0.0)))
+    kend = (len(y) - 1) * h
+    sig = lambda k: np.where(k < kend, cs(np.minimum(k, kend)), 0.0)
+    ref = Q.second_order(1.0, 2, 41.47, -50.0, -200.0, 0.7, 2.0, n_rad=10, n_ang=10, sigma=sig)
+    mm, ss, _, _ = O.vegas(D, ph, 10, 1 << 16, seed=1)
+    assert within(mm, ss, ref)
+    assert ss < 5e-3 * abs(ref)
+    assert abs(ref - q2(-200.0)) > 5 * ss
+
+
 def test_rotational_reduction_second_order_vs_quadrature():
     """Chord map 1 (chord 0 along z, chord 1 in the xz plane, 4 pi x 2 pi integrated out; Sec. III.C)
     integrates the same Eq. (2) in 6 instead of 9 dimensions."""
