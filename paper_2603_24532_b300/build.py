@@ -11,8 +11,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmbpt.so")
-SOURCES = ["mbpt_runtime.cu", "mbpt_host.cpp", "mbpt_k_misc.cu", "mbpt_k_iterate_256x2.cu",
-           "mbpt_k_iterate_128x4.cu", "mbpt_k_iterate_256x1.cu", "mbpt_k_iterate_128x3.cu"]
+SHAPES = ["256x2", "128x4", "256x1", "128x3"]
+# the long kernel units first, so that they start as early as possible on a machine with fewer cores
+SOURCES = (["mbpt_k_iterate_%s%s.cu" % (sh, part) for sh in SHAPES for part in ("", "_reg")] +
+           ["mbpt_runtime.cu", "mbpt_host.cpp", "mbpt_k_misc.cu"])
 HEADERS = ["mbpt_device.cuh", "mbpt_kernels.cuh", "mbpt_kernels.h", "mbpt_internal.h",
            os.path.join("..", "..", "include", "mbpt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -111,12 +111,18 @@ struct alignas(16) WorkItem {
 };
 
 struct alignas(16) WorkHeader {
-    uint32_t n_items;
+    uint32_t n_items;         // all items of the batch (k_finalize)
     uint32_t total_chunks;
-    uint32_t chunk_counter;   // dynamic chunk scheduling, reset before every iterate launch
-    uint32_t error;           // non-zero: a kernel saw an out-of-range index
+    uint32_t error;           // non-zero: a kernel saw an out-of-range index or a misplaced item
+    uint32_t pad0;
     uint64_t hist_floats;     // size of the chunk histogram scratch
-    uint64_t pad;
+    // the batch is split in two parts, each run by its own k_iterate kernel: items [0, part_items[0])
+    // without the denominator regulator, then part_items[1] items with it; their chunks are
+    // [0, part_chunks[0]) and [part_chunks[0], part_chunks[0] + part_chunks[1])
+    uint32_t part_items[2];
+    uint32_t part_chunks[2];
+    uint32_t part_counter[2]; // dynamic chunk scheduling, reset before every iterate launch
+    uint32_t pad1[2];
 };
 
 // host-side helpers (mbpt_host.cpp)

@@ -12,6 +12,9 @@ namespace mbpt {
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+constexpr int kClassRounds = 16;                      // pre-test rounds between evaluation phases
+constexpr int kQueue = 2 * 31 + 32 * kClassRounds + 2;   // carried-over entries of both classes + one phase
+
 template <int NW>
 struct alignas(16) ChunkSmemT {
     DiagRec rec;
@@ -19,8 +22,8 @@ struct alignas(16) ChunkSmemT {
     float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
     double cacc[2 * kComp][NW * 32];         // per-thread sums of the regulator components
     double gacc[kGroupSlots][NW * 32];       // group integrals: per-sample sums over the members
-    uint32_t queue[NW][2][64];               // mixed precision: per-warp queues of samples past the pre-test
-                                             // (away from / near a Fermi surface)
+    uint32_t queue[NW][kQueue];              // mixed precision: per-warp stacks of samples past the pre-test
+                                             // (away from a Fermi surface from the bottom, near one from the top)
     double red[2][NW];
     double redc[2 * kComp][NW];
     uint32_t chunk, item, iter, skip;
@@ -105,15 +108,17 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 }
 
 // One chunk: samples first + j*blockDim + tid, j < spt.
-//  Mixed precision (plain integrals): the FP64 pipe issues per warp instruction, so a warp whose
+//  Mixed precision: the FP64 pipe issues per warp instruction, so a warp whose
 //  lanes hold a mix of zero and live samples pays for the zero ones, and one whose lanes take both
-//  sampling maps pays for both.  Each warp therefore first runs the FP32 front and Fermi-step
-//  pre-test of its samples and queues the ones that may be live, by class (away from / near a
-//  Fermi surface; ballot + prefix count into 64-entry shared-memory queues); full warps of one class
-//  are then evaluated, the partial ones at the end of the chunk.  Which thread sums which sample
-//  depends only on the chunk, so results stay deterministic.
+//  sampling maps pays for both.  Each warp therefore alternates two phases, each a tight loop over
+//  its own code: kClassRounds rounds of the FP32 front and Fermi-step pre-test, pushing the samples
+//  that may be live onto one of two shared-memory stacks by class (away from / near a Fermi
+//  surface; ballot + prefix count), then full warps of one class popped and evaluated until fewer
+//  than 32 of each remain; the partial warps are evaluated at the end of the chunk.  Which thread
+//  sums which sample depends only on the chunk, so results stay deterministic.
 //  A group integral (n_members > 1) evaluates every member at each sample, member by member with
-//  the record swapped in shared memory, summing the weights per sample in gacc
+//  the record swapped in shared memory (in mixed precision each member's samples pass through the
+//  classification above), adding the weights per sample into gacc, zeroed per chunk
 //  (spt x (1 + regulator components) <= kGroupSlots slots per thread); sums, squares and the
 //  histogram then see the group's integrand.
 template <int N, int PREC, int MAPK, bool REG, int NW>
@@ -125,50 +130,55 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     const uint32_t t = S.iter;
     const uint32_t k0 = (uint32_t)W.seed, k1 = (uint32_t)(W.seed >> 32);
     float* hist = S.hist[threadIdx.x >> 5];
-    uint32_t* q = &S.queue[threadIdx.x >> 5][0][0];      // q[0..63] away from, q[64..127] near a surface
+    uint32_t* q = S.queue[threadIdx.x >> 5];
     const uint32_t lane = threadIdx.x & 31u;
     const int nb = R.nb;
     constexpr int D = 3 * (N + 1) - 3 * MAPK;
     constexpr int PER = REG ? 1 + kComp : 1;        // group slots per sample
     const int nm = (int)W.n_members;
     const bool grp = nm > 1;
-    const bool compact = (PREC == MBPT_MIXED) && !grp;
+    const bool compact = (PREC == MBPT_MIXED);
     for (int m = 0; m < nm; ++m) {
         if (m > 0) {
             __syncthreads();
             load_record(&S.rec, W.rec + m);
             __syncthreads();
         }
-        int j = 0, nq0 = 0, nq1 = 0;       // warp-uniform
+        int j = 0, nf = 0, nn = 0;       // warp-uniform: next round, stack heights (far, near)
+        bool drain = false;
         for (;;) {
             uint64_t s;
-            int jslot = 0;
-            bool have, use_near = false;
+                    bool have, use_near = false;
+            int cnt = 0;
             if (compact) {
-                while (nq0 < 32 && nq1 < 32 && j < W.spt) {
-                    const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
-                    const int cls =
-                        sc < W.samples ? mixed_classify<N, MAPK>(R, S.grid, (uint32_t)sc, t, W.stream_id, k0, k1) : 0;
-                    const uint32_t lt = (1u << lane) - 1u;
-                    const uint32_t b0 = __ballot_sync(0xffffffffu, cls == 1);
-                    const uint32_t b1 = __ballot_sync(0xffffffffu, cls == 2);
-                    if (cls == 1) q[nq0 + __popc(b0 & lt)] = (uint32_t)sc;
-                    if (cls == 2) q[64 + nq1 + __popc(b1 & lt)] = (uint32_t)sc;
-                    nq0 += __popc(b0);
-                    nq1 += __popc(b1);
-                    ++j;
+                if (!drain && nf < 32 && nn < 32) {
+                    const int jend = (j + kClassRounds < W.spt) ? j + kClassRounds : W.spt;
+                    for (; j < jend; ++j) {
+                        const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
+                        const int cls = sc < W.samples
+                                            ? mixed_classify<N, MAPK>(R, S.grid, (uint32_t)sc, t, W.stream_id, k0, k1)
+                                            : 0;
+                        const uint32_t lt = (1u << lane) - 1u;
+                        const uint32_t b0 = __ballot_sync(0xffffffffu, cls == 1);
+                        const uint32_t b1 = __ballot_sync(0xffffffffu, cls == 2);
+                        if (cls == 1) q[nf + __popc(b0 & lt)] = (uint32_t)sc;
+                        if (cls == 2) q[kQueue - 1 - (nn + __popc(b1 & lt))] = (uint32_t)sc;
+                        nf += __popc(b0);
+                        nn += __popc(b1);
+                    }
+                    if (j >= W.spt) drain = true;
+                    __syncwarp();
                 }
-                if (nq1 >= 32) use_near = true;
-                else if (nq0 >= 32 || nq0 > 0) use_near = false;
-                else if (nq1 > 0) use_near = true;
-                else break;
-                __syncwarp();
-                const int cnt = use_near ? nq1 : nq0;
+                if (nf >= 32) cnt = 32;
+                else if (nn >= 32) { cnt = 32; use_near = true; }
+                else if (drain && nf > 0) cnt = nf;
+                else if (drain && nn > 0) { cnt = nn; use_near = true; }
+                else if (drain) break;
+                else continue;
                 have = (int)lane < cnt;
-                s = have ? q[(use_near ? 64 : 0) + lane] : 0u;
+                s = !have ? 0u : (use_near ? q[kQueue - 1 - (nn - cnt + (int)lane)] : q[nf - cnt + (int)lane]);
             } else {
                 if (j >= W.spt) break;
-                jslot = j;
                 s = first + (uint64_t)j * blockDim.x + threadIdx.x;
                 have = s < W.samples;
                 ++j;
@@ -177,14 +187,14 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
                 const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, W.grid, (uint32_t)s, t, W.stream_id,
                                                                     k0, k1, nullptr, use_near);
                 if (grp) {
-                    double* a = &S.gacc[jslot * PER][threadIdx.x];
-                    a[0] = (m == 0) ? o.w : a[0] + o.w;
+                    // the sample's slot belongs to the lane of this warp that owns it in the chunk layout
+                    // (sample first + js * blockDim + own); each slot gets one add per member
+                    const uint32_t off = (uint32_t)(s - first);
+                    const int js = (int)(off / blockDim.x), own = (int)(off - (uint32_t)js * blockDim.x);
+                    S.gacc[js * PER][own] += o.w;
                     if constexpr (REG) {
 #pragma unroll
-                        for (int c = 0; c < kComp; ++c) {
-                            double& v = S.gacc[jslot * PER + 1 + c][threadIdx.x];
-                            v = (m == 0) ? o.wc[c] : v + o.wc[c];
-                        }
+                        for (int c = 0; c < kComp; ++c) S.gacc[js * PER + 1 + c][own] += o.wc[c];
                     }
                 } else {
                     if (nonzero(o.w)) {          // a zero weight leaves both sums unchanged: no FP64 work
@@ -202,18 +212,14 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
                 }
             }
             if (compact) {
-                uint32_t* qq = q + (use_near ? 64 : 0);
-                const int cnt = use_near ? nq1 : nq0;
-                const int done = cnt < 32 ? cnt : 32;
-                __syncwarp();
-                if ((int)lane < cnt - done) qq[lane] = qq[done + lane];
-                __syncwarp();
-                if (use_near) nq1 -= done;
-                else nq0 -= done;
+                if (use_near) nn -= cnt;
+                else nf -= cnt;
+                __syncwarp();                  // popped slots may be pushed again by the next phase
             }
         }
     }
     if (!grp) return;
+    __syncwarp();                              // slots were filled by the warp's lanes
     for (int j = 0; j < W.spt; ++j) {
         const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
         if (s >= W.samples) continue;
@@ -261,20 +267,24 @@ __device__ __forceinline__ double warp_sum(double v) {
 // chunk does not depend on which block ran it or what else is in the batch.
 // Compiled in several launch shapes (threads per block x minimum resident blocks, i.e. a register cap);
 // the autotuner picks one per context.
-template <int TPB>
+// PART 0 runs the batch's integrals without the denominator regulator, PART 1 those with it (separate
+// kernels, so that each carries only its own instantiations).
+template <int TPB, int PART>
 __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* __restrict__ items,
                                                double* __restrict__ csum, float* __restrict__ chist) {
     constexpr int NW = TPB / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ChunkSmemT<NW>& S = *reinterpret_cast<ChunkSmemT<NW>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t n_items = hdr->n_items, total = hdr->total_chunks;
+    const uint32_t item0 = PART ? hdr->part_items[0] : 0u, n_items = hdr->part_items[PART];
+    const uint32_t chunk0 = PART ? hdr->part_chunks[0] : 0u, total = hdr->part_chunks[PART];
     for (;;) {
         if (tid == 0) {
-            const uint32_t c = atomicAdd(&hdr->chunk_counter, 1u);
-            uint32_t it = 0;
-            if (c < total) {
-                uint32_t lo = 0, hi = n_items;
+            const uint32_t cl = atomicAdd(&hdr->part_counter[PART], 1u);
+            uint32_t it = item0;
+            if (cl < total) {
+                const uint32_t c = chunk0 + cl;
+                uint32_t lo = item0, hi = item0 + n_items;
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (items[mid].chunk_begin <= c) lo = mid;
@@ -282,15 +292,18 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
                 }
                 it = lo;
                 if (c - items[it].chunk_begin >= items[it].n_chunks) atomicOr(&hdr->error, 1u);
+                if ((items[it].rec->n_shifts != 0) != (PART != 0)) atomicOr(&hdr->error, 4u);
             }
-            S.chunk = c;
+            S.chunk = (cl < total) ? chunk0 + cl : 0xFFFFFFFFu;
             S.item = it;
-            S.skip = (c < total) ? (uint32_t)items[it].state->converged : 1u;
-            S.iter = (c < total) ? (uint32_t)items[it].state->iter : 0u;
+            S.skip = (cl < total) ? (uint32_t)items[it].state->converged |
+                                        (uint32_t)((items[it].rec->n_shifts != 0) != (PART != 0))
+                                  : 1u;
+            S.iter = (cl < total) ? (uint32_t)items[it].state->iter : 0u;
         }
         __syncthreads();
         const uint32_t chunk = S.chunk;
-        if (chunk >= total) break;
+        if (chunk == 0xFFFFFFFFu) break;
         if (S.skip) {
             __syncthreads();
             continue;
@@ -303,22 +316,21 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
         load_grid(S.grid, W.grid, d, nb, prec);
         for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
         for (int c = 0; c < 2 * kComp; ++c) S.cacc[c][tid] = 0.0;
+        for (int c = 0; c < kGroupSlots; ++c) S.gacc[c][tid] = 0.0;
         __syncthreads();
         double sw = 0.0, sw2 = 0.0;
         const uint32_t cl = chunk - W.chunk_begin;
-        switch (((order * 3 + prec) * 2 + S.rec.map_kind) * 2 + (S.rec.n_shifts ? 1 : 0)) {
-#define MBPT_CASE(N_, P_, M_, R_) \
-    case ((N_ * 3 + P_) * 2 + M_) * 2 + R_: run_chunk<N_, P_, M_, (R_ != 0), NW>(S, W, cl, sw, sw2); break;
-#define MBPT_CASE2(N_, P_, M_) MBPT_CASE(N_, P_, M_, 0) MBPT_CASE(N_, P_, M_, 1)
+        switch ((order * 3 + prec) * 2 + S.rec.map_kind) {
+#define MBPT_CASE(N_, P_, M_) \
+    case (N_ * 3 + P_) * 2 + M_: run_chunk<N_, P_, M_, (PART != 0), NW>(S, W, cl, sw, sw2); break;
 #define MBPT_CASES(N_) \
-    MBPT_CASE2(N_, MBPT_FP64, 0) MBPT_CASE2(N_, MBPT_MIXED, 0) MBPT_CASE2(N_, MBPT_MIXED_MAP64, 0) \
-    MBPT_CASE2(N_, MBPT_FP64, 1) MBPT_CASE2(N_, MBPT_MIXED, 1) MBPT_CASE2(N_, MBPT_MIXED_MAP64, 1)
+    MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
+    MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)
             MBPT_CASES(2)
             MBPT_CASES(3)
             MBPT_CASES(4)
             MBPT_CASES(5)
 #undef MBPT_CASES
-#undef MBPT_CASE2
 #undef MBPT_CASE
             default:
                 if (tid == 0) atomicOr(&hdr->error, 2u);
@@ -330,7 +342,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             S.red[1][warp] = sw2;
         }
         __syncthreads();
-        if (S.rec.n_shifts) {
+        if (PART) {
             for (int c = 0; c < 2 * kComp; ++c) {
                 const double v = warp_sum(S.cacc[c][tid]);
                 if (lane == 0) S.redc[c][warp] = v;
@@ -345,7 +357,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             }
             csum[kSumStride * (size_t)chunk] = a;
             csum[kSumStride * (size_t)chunk + 1] = b;
-            if (S.rec.n_shifts)
+            if (PART)
                 for (int c = 0; c < 2 * kComp; ++c) {
                     double v = 0.0;
                     for (int w = 0; w < NW; ++w) v += S.redc[c][w];

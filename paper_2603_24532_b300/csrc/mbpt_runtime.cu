@@ -110,14 +110,14 @@ namespace {
 typedef void (*IterateFn)(WorkHeader*, const WorkItem*, double*, float*);
 struct KernelVariant {
     int tpb, minb;
-    IterateFn fn;
+    IterateFn fn, fn_reg;      // batch part without / with the denominator regulator
     size_t smem;
 };
 const KernelVariant kVariants[] = {
-    {256, 2, k_iterate_256x2, sizeof(ChunkSmemT<8>)},
-    {128, 4, k_iterate_128x4, sizeof(ChunkSmemT<4>)},
-    {256, 1, k_iterate_256x1, sizeof(ChunkSmemT<8>)},
-    {128, 3, k_iterate_128x3, sizeof(ChunkSmemT<4>)},
+    {256, 2, k_iterate_256x2, k_iterate_256x2_reg, sizeof(ChunkSmemT<8>)},
+    {128, 4, k_iterate_128x4, k_iterate_128x4_reg, sizeof(ChunkSmemT<4>)},
+    {256, 1, k_iterate_256x1, k_iterate_256x1_reg, sizeof(ChunkSmemT<8>)},
+    {128, 3, k_iterate_128x3, k_iterate_128x3_reg, sizeof(ChunkSmemT<4>)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 }  // namespace
@@ -130,7 +130,8 @@ struct mbpt_ctx {
     Arena arena;
     int sms = 0;
     int variant = 0;                       // index into kVariants
-    int variant_blocks[kNumVariants] = {0};  // persistent grid of each k_iterate variant
+    int variant_blocks[kNumVariants] = {0};      // persistent grid of each k_iterate variant
+    int variant_blocks_reg[kNumVariants] = {0};  // ... and of its regulated part
     int finalize_blocks = 0;
     int spt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};
     // batch buffers (arena)
@@ -234,10 +235,13 @@ int capture_graph(mbpt_ctx* c) {
     if (c->graph) return MBPT_OK;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(&c->d_hdr->chunk_counter, 0, sizeof(uint32_t), c->stream);
+    cudaMemsetAsync(c->d_hdr->part_counter, 0, 2 * sizeof(uint32_t), c->stream);
     cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal);
     const KernelVariant& kv = kVariants[c->variant];
+    // the regulated part's blocks exit at once when it is empty
     kv.fn<<<c->variant_blocks[c->variant], kv.tpb, kv.smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist);
+    kv.fn_reg<<<c->variant_blocks_reg[c->variant], kv.tpb, kv.smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
+                                                                                 c->d_chist);
     cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal);
     k_finalize<<<c->finalize_blocks, 256, 0, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist,
                                                          c->d_last_hist);
@@ -324,16 +328,20 @@ int mbpt_ctx_create(mbpt_ctx** out, int device, void* arena, size_t arena_bytes,
     }
     for (int v = 0; v < kNumVariants; ++v) {
         const KernelVariant& kv = kVariants[v];
+        int per_sm = 0, per_sm_reg = 0;
         e = cudaFuncSetAttribute(kv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem);
-        int per_sm = 0;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kv.fn_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv.fn, kv.tpb, kv.smem);
-        if (e != cudaSuccess || per_sm < 1) {
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_reg, kv.fn_reg, kv.tpb, kv.smem);
+        if (e != cudaSuccess || per_sm < 1 || per_sm_reg < 1) {
             if (c->own_stream) cudaStreamDestroy(c->stream);
             if (c->own_arena) cudaFree(base);
             delete c;
             return fail(MBPT_ECUDA, std::string("k_iterate occupancy: ") + cudaGetErrorString(e));
         }
         c->variant_blocks[v] = per_sm * c->sms;
+        c->variant_blocks_reg[v] = per_sm_reg * c->sms;
     }
     c->finalize_blocks = 2 * c->sms;
     for (int i = 0; i < 3; ++i) {
@@ -597,8 +605,16 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         if (!seen.insert(g).second) return fail(MBPT_EINVAL, "vegas_iterate: integral listed twice");
         stride = std::max(stride, g->d * g->nb);
     }
+    // integrals without the regulator first, then those with it (two kernels), each in call order
+    std::vector<mbpt_diag*> order_v;
+    order_v.reserve((size_t)k);
+    for (int part = 0; part < 2; ++part)
+        for (int i = 0; i < k; ++i)
+            if ((diags[i]->cfg.n_shifts != 0) == (part != 0)) order_v.push_back(diags[i]);
+    uint32_t part_items[2] = {0, 0}, part_chunks[2] = {0, 0};
     for (int i = 0; i < k; ++i) {
-        mbpt_diag* g = diags[i];
+        mbpt_diag* g = order_v[(size_t)i];
+        const int part = g->cfg.n_shifts != 0;
         WorkItem w;
         memset(&w, 0, sizeof(w));
         w.rec = g->d_rec;
@@ -621,6 +637,8 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         w.hist_stride = stride;
         chunk += w.n_chunks;
         if (chunk >= (1ull << 31)) return fail(MBPT_EINVAL, "vegas_iterate: batch too large");
+        part_items[part] += 1;
+        part_chunks[part] += w.n_chunks;
         c->h_items.push_back(w);
         c->h_last_hist.push_back(g->d_last_hist);
     }
@@ -631,6 +649,10 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
     h.n_items = (uint32_t)k;
     h.total_chunks = (uint32_t)chunk;
     h.hist_floats = (uint64_t)chunk * (uint64_t)stride;
+    for (int p = 0; p < 2; ++p) {
+        h.part_items[p] = part_items[p];
+        h.part_chunks[p] = part_chunks[p];
+    }
     CUDA_TRY(cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(WorkItem) * k, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_last_hist, c->h_last_hist.data(), sizeof(double*) * k, cudaMemcpyHostToDevice,
                              c->stream));
@@ -940,6 +962,8 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     h.n_items = 1;
     h.total_chunks = (uint32_t)n_chunks;
     h.hist_floats = (uint64_t)nh * n_chunks;
+    h.part_items[0] = 1;
+    h.part_chunks[0] = (uint32_t)n_chunks;
     DiagState s0;
     memset(&s0, 0, sizeof(s0));
     s0.iter = (int32_t)iter;

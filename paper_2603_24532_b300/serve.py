@@ -25,6 +25,7 @@ its request, so a request's result is the same alone and in a mix.
 """
 from __future__ import annotations
 
+import bisect
 import math
 import time
 from collections import OrderedDict
@@ -208,30 +209,43 @@ class MbptBackend:
 class GridCache:
     """Trained VEGAS grids of finished integrals, keyed by (order, diagram, asymmetry), for warm
     starts at neighbouring densities (Sec. III.C: importance-sampling distributions propagate in
-    density for changes up to about 0.02 fm^-3)."""
+    density for changes up to about 0.02 fm^-3).  Each key keeps its densities sorted, so a lookup
+    is a bisection; the oldest entries are evicted beyond max_entries."""
 
     def __init__(self, window: float = 0.02, max_entries: int = 50000):
         self.window = window
         self.max_entries = max_entries
-        self.entries: "OrderedDict[tuple, np.ndarray]" = OrderedDict()
+        self.entries: "OrderedDict[tuple, np.ndarray]" = OrderedDict()    # insertion order, for eviction
+        self._by_key: Dict[tuple, List[float]] = {}
 
     def put(self, order: int, did: int, delta: float, n_dens: float, grid) -> None:
         if grid is None:
             return
-        key = (order, did, round(delta, 6), round(n_dens, 6))
+        k = (order, did, round(delta, 6))
+        n = round(n_dens, 6)
+        key = k + (n,)
+        if key not in self.entries:
+            bisect.insort(self._by_key.setdefault(k, []), n)
         self.entries[key] = grid
         self.entries.move_to_end(key)
         while len(self.entries) > self.max_entries:
-            self.entries.popitem(last=False)
+            old, _ = self.entries.popitem(last=False)
+            lst = self._by_key[old[:3]]
+            lst.pop(bisect.bisect_left(lst, old[3]))
 
     def get(self, order: int, did: int, delta: float, n_dens: float):
+        k = (order, did, round(delta, 6))
+        lst = self._by_key.get(k)
+        if not lst:
+            return None
+        i = bisect.bisect_left(lst, n_dens)
         best, best_d = None, None
-        for (o, d, dl, n), g in self.entries.items():
-            if o == order and d == did and dl == round(delta, 6):
-                dist = abs(n - n_dens)
+        for j in (i - 1, i):
+            if 0 <= j < len(lst):
+                dist = abs(lst[j] - n_dens)
                 if dist <= self.window and (best_d is None or dist < best_d):
-                    best, best_d = g, dist
-        return best
+                    best, best_d = lst[j], dist
+        return None if best is None else self.entries[k + (best,)]
 
 
 SAMPLES_BY_ORDER = {2: 1 << 16, 3: 1 << 16, 4: 1 << 16, 5: 1 << 16}   # pilot iteration
