@@ -58,6 +58,22 @@ def dist_env():
     return rank, world, local
 
 
+def slowest_rank_ms(dist, t_ms: float, device) -> float:
+    """The step time of the job: the maximum over ranks (every rank holds its own replicas, so the
+    job's throughput is all ranks' units over the slowest rank's time)."""
+    if dist is None:
+        return t_ms
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: float, t_ms: float) -> float:
+    """Whole-job throughput (weak scaling: every rank processes the same units)."""
+    return world * units_per_rank / (t_ms * 1e-3)
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
@@ -184,13 +200,9 @@ def run_gpu(args):
     ms_it, ms_step = timed_steps(gs, args.steps)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_step = float(np.mean(ms_step))
-    if dist:
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = slowest_rank_ms(dist, float(np.mean(ms_step)), dev)
     evals_step = n_int * SAMPLES
-    value = world * evals_step / (t_step * 1e-3)
+    value = job_value(world, evals_step, t_step)
     res_mixed = [M.mbpt_estimate(g) for g in gs]
 
     # live-sample fraction on the adapted grids (for the algorithmic FP64 work per sample)
@@ -369,7 +381,7 @@ def run_gpu(args):
                                      "(grids and records; chunk slots stay in L2), not proportional to samples"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,   # per step: k_iterate, its regulated part (empty here), k_finalize
         "clocks": clk,
         "fp64_batched": {"value": v64, "unit": UNIT, "kernel_ms": float(np.mean(it64)), "launch": tuned64},
         "k0_plain_fp64_per_diagram": {"value": vk0, "unit": UNIT, "launches_per_step": 2 * n_int},

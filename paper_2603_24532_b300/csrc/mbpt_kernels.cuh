@@ -116,11 +116,11 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  surface; ballot + prefix count), then full warps of one class popped and evaluated until fewer
 //  than 32 of each remain; the partial warps are evaluated at the end of the chunk.  Which thread
 //  sums which sample depends only on the chunk, so results stay deterministic.
-//  A group integral (n_members > 1) evaluates every member at each sample, member by member with
-//  the record swapped in shared memory (in mixed precision each member's samples pass through the
-//  classification above), adding the weights per sample into gacc, zeroed per chunk
-//  (spt x (1 + regulator components) <= kGroupSlots slots per thread); sums, squares and the
-//  histogram then see the group's integrand.
+//  A group integral (n_members > 1) evaluates every member at each sample with the direct loop
+//  (routing groups through the phases above costs the plain path registers: a 1.2 KB stack frame
+//  instead of 120 B), member by member with the record swapped in shared memory, adding the weights
+//  per sample into gacc, zeroed per chunk (spt x (1 + regulator components) <= kGroupSlots slots per
+//  thread); sums, squares and the histogram then see the group's integrand.
 template <int N, int PREC, int MAPK, bool REG, int NW>
 __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
@@ -137,7 +137,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     constexpr int PER = REG ? 1 + kComp : 1;        // group slots per sample
     const int nm = (int)W.n_members;
     const bool grp = nm > 1;
-    const bool compact = (PREC == MBPT_MIXED);
+    const bool compact = (PREC == MBPT_MIXED) && !grp;   // groups: direct loop (fewer live registers)
     for (int m = 0; m < nm; ++m) {
         if (m > 0) {
             __syncthreads();
