@@ -88,7 +88,7 @@ def main():
         import oracle as O
         rng = np.random.default_rng(5)
         pick = rng.choice(len(gs), size=min(a.oracle_integrals, len(gs)), replace=False)
-        devs = []
+        devs, l1, cancel = [], [], []
         Os = O.enumerate_diagrams(5)
         for i in pick:
             kf, d = meta[i]
@@ -100,13 +100,22 @@ def main():
             _, wg = M.mbpt_dump_samples(gs[i], 99, 0, a.oracle_samples, dd, with_x=False)
             ref = O.vegas_iteration(D, po, grid, 1, 1000 * kfs.index(kf) + d.diagram_id, 99, a.oracle_samples)
             # sums of w/J-independent scale: E5 order sum per sample is mean(w) ~ E5/N_int
+            _, _, _, wo = O.vegas_samples(0, D, po.array(), dd, grid, 1, 1000 * kfs.index(kf) + d.diagram_id, 99,
+                                          0, a.oracle_samples, dump=True)
             scale = max(abs(ref.sum_w), 1e-3 * abs(per_kf[str(kf)]["E5_sum"]) * a.oracle_samples, 1e-300)
             devs.append(abs(np.sum(wg) - ref.sum_w) / scale)
+            l1.append(np.sum(np.abs(wg - wo)) / max(np.sum(np.abs(wo)), 1e-300))
+            cancel.append(np.sum(np.abs(wo)) / max(abs(ref.sum_w), 1e-300))
         devs = np.array(devs)
+        worst = int(np.argmax(devs))
         dev = {"integrals": int(len(devs)), "samples_each": a.oracle_samples, "max": float(devs.max()),
                "median": float(np.median(devs)), "frac_below_1e-4": float(np.mean(devs < 1e-4)),
                "definition": "|sum w_mixed - sum w_oracle| / max(|sum w_oracle|, 1e-3 |E5 order sum| M), "
-                             "same grid and counters"}
+                             "same grid and counters",
+               "l1_max": float(max(l1)), "l1_median": float(np.median(l1)),
+               "l1_definition": "sum |w_mixed - w_oracle| / sum |w_oracle| per integral",
+               "worst_cancellation": float(cancel[worst]),
+               "cancellation_definition": "sum |w| / |sum w| of the integral with the largest deviation"}
     out = {"workload": "all 840 fifth-order diagrams (668 non-anomalous) x kF {1.0, 1.33, 1.6}, PNM, mixed, "
                        "to %.2g relative (or iteration cap %d)" % (a.target, a.max_iters),
            "integrals": len(gs), "dedup_mirrors": a.dedup_mirrors, "samples_per_iter": a.samples,
