@@ -141,6 +141,27 @@ struct SampleOut {
     double wc[kComp];      // regulator components (shifted denominators, extrapolation); if n_shifts
 };
 
+// V(p, p) and Delta = V(p, p') - V(p, -p') for one vertex, FP32, from P = 2p and P' = 2p'.  The
+// difference is formed without cancellation: the contact parts cancel exactly and
+// 1/(|P-P'|^2 + 4m^2) - 1/(|P+P'|^2 + 4m^2) = 4 P.P' / ((|P-P'|^2 + 4m^2)(|P+P'|^2 + 4m^2)), so Delta keeps
+// FP32 relative accuracy where V_d and V_e nearly agree (small momentum transfer), the region in which
+// the exchange cancellation of the spin sum is strongest.
+__device__ __forceinline__ void vertex_pot_delta_f32(const DiagRec& R, float Px, float Py, float Pz, float Qx, float Qy,
+                                                     float Qz, float& vd, float& dl) {
+    const float pp = fmaf(Px, Px, fmaf(Py, Py, Pz * Pz));
+    const float qq = fmaf(Qx, Qx, fmaf(Qy, Qy, Qz * Qz));
+    const float pq = fmaf(Px, Qx, fmaf(Py, Qy, Pz * Qz));
+    const float s = pp + qq;
+    const float rd = __fdividef(1.0f, fmaf(-2.0f, pq, s) + R.mpi2_4f);   // 1/(|P - P'|^2 + 4 m^2)
+    const float re = __fdividef(1.0f, fmaf(2.0f, pq, s) + R.mpi2_4f);    // 1/(|P + P'|^2 + 4 m^2)
+    const float a = pp * R.regc2f, b = qq * R.regc2f;
+    float ah = a, bh = b;
+    for (int i = 1; i < R.reg_half; ++i) { ah *= a; bh *= b; }
+    const float F = exp2f(-(ah + bh));
+    vd = fmaf(R.CY4f, rd, R.CSf) * F;
+    dl = (R.CY4f * 4.0f * pq) * (rd * re) * F;
+}
+
 // V(p, p') for one vertex, FP32, from P = 2p and P' = 2p'.
 __device__ __forceinline__ void vertex_pot_f32(const DiagRec& R, float Px, float Py, float Pz, float Qx, float Qy,
                                                float Qz, float& vd, float& ve) {
@@ -466,6 +487,15 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
 #pragma unroll
                 for (int a = 0; a < D; ++a) x_out[a] = widen_f(xf[a]);
             }
+            // VEGAS and chord Jacobians together as one FP32 mantissa product and an exponent sum
+            // (no FP64 work, no FP32 underflow); a zero or subnormal factor gives a zero weight
+#pragma unroll
+            for (int c = 0; c < L; ++c) {
+                const uint32_t bits = __float_as_uint(jcf[c]);
+                zero_bin |= (bits & 0x7F800000u) == 0u;
+                ex += (int)(bits >> 23) - 127;
+                mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+            }
             jv = zero_bin ? 0.0
                           : __longlong_as_double(__double_as_longlong(widen_pos_normal(mp)) + ((long long)ex << 52));
             // exact FP64 chord momenta: products of the FP32 magnitude and direction (24 x 24 bits)
@@ -489,7 +519,6 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
                     K[2][c] = kd * widen_f(kdir[2][c]);
                     U[c] = fma(K[0][c], K[0][c], fma(K[1][c], K[1][c], K[2][c] * K[2][c]));
                 }
-                jc *= widen_f(jcf[c]);
             }
         }
     } else {
@@ -592,18 +621,21 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
                 P[q] = p;
                 Q[q] = qq;
             }
-            float vd, ve;
-            vertex_pot_f32(R, P[0], P[1], P[2], Q[0], Q[1], Q[2], vd, ve);
+            // one Fermi momentum: products of V_d and Delta with the difference-form table;
+            // asymmetric matter (per-sample loop factors): products of V_d and V_e
+            float vd, v2;
+            if (!R.asym) vertex_pot_delta_f32(R, P[0], P[1], P[2], Q[0], Q[1], Q[2], vd, v2);
+            else vertex_pot_f32(R, P[0], P[1], P[2], Q[0], Q[1], Q[2], vd, v2);
 #pragma unroll
             for (int j = 0; j < (1 << v); ++j) {
-                prod[j + (1 << v)] = prod[j] * ve;
+                prod[j + (1 << v)] = prod[j] * v2;
                 prod[j] *= vd;
             }
         }
         float sum = 0.0f;
         if (!R.asym) {
 #pragma unroll
-            for (int tt = 0; tt < (1 << N); ++tt) sum = fmaf(R.gcoef_f[tt], prod[tt], sum);
+            for (int tt = 0; tt < (1 << N); ++tt) sum = fmaf(R.gdel_f[tt], prod[tt], sum);
         } else {
 #pragma unroll
             for (int tt = 0; tt < (1 << N); ++tt) {

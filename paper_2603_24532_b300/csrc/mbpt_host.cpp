@@ -456,6 +456,13 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         r->gcoef_d[term] = c;
         r->gcoef_f[term] = (float)c;
     }
+    // difference form: superset sums of the coefficients, signed by the subset size (exact integers)
+    for (int a = 0; a < (1 << n); ++a) {
+        double acc = 0.0;
+        for (int term = 0; term < (1 << n); ++term)
+            if ((term & a) == a) acc += r->gcoef_d[term];
+        r->gdel_f[a] = (float)((__builtin_popcount(a) & 1) ? -acc : acc);
+    }
     // --- physics
     if (sym) {
         double kf = ph.kF_n > 0.0 ? ph.kF_n : ph.kF_p;

@@ -47,6 +47,9 @@ struct alignas(16) DiagRec {
     float tcoef[MBPT_MAX_DEVICE_ORDER][8];
     // spin(-isospin) sum, term t: bit v of t set = vertex v taken in exchange
     float gcoef_f[kMaxTerms];                    // (-1)^L(t) g^L(t)   (one Fermi momentum)
+    // the same sum with V_e = V_d - Delta at every vertex: term A (bit v set = factor Delta_v, else V_d)
+    // carries (-1)^|A| sum over the terms t whose exchange set contains A of gcoef(t)
+    float gdel_f[kMaxTerms];
     double gcoef_d[kMaxTerms];
     float gsign_f[kMaxTerms];                    // (-1)^L(t)           (per-loop species sums)
     int32_t nloops[kMaxTerms];
