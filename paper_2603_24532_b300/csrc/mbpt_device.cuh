@@ -284,16 +284,15 @@ __device__ __forceinline__ void chords_fp64(const DiagRec& R, const double (&x)[
     }
 }
 
-// FP32 front of a mixed-precision sample: the VEGAS map on the FP32 grid (point, bins, Jacobian as a
-// mantissa product and exponent sum, so that it cannot underflow), chord magnitudes, unit directions
-// (kind 1: along z; kind 2: in the xz plane; kind 0: rational azimuth), Jacobian factors and FP32
-// chord momenta.
+// FP32 front of a mixed-precision sample: the VEGAS map on the FP32 grid (point, bins), chord
+// magnitudes, unit directions (kind 1: along z; kind 2: in the xz plane; kind 0: rational azimuth) and
+// FP32 chord momenta; the VEGAS and chord Jacobians as one mantissa product and exponent sum (so that
+// it cannot underflow; a zero or subnormal factor sets zero_bin).
 template <int N, int MAPK, int D>
 __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __restrict__ gf, const uint32_t* u,
                                             uint32_t nb, float (&xf)[D], uint32_t (&binpack)[5], float& mp,
                                             int& ex, bool& zero_bin, float (&kmag)[N + 1],
-                                            float (&kdir)[3][N + 1], float (&jcf)[N + 1],
-                                            float (&lf)[3][N + 1]) {
+                                            float (&kdir)[3][N + 1], float (&lf)[3][N + 1]) {
     mp = 1.0f;
     ex = 0;
     zero_bin = false;
@@ -316,17 +315,18 @@ __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __re
         const int ax = chord_axis<MAPK>(c), kind = chord_kind<MAPK>(c);
         const float k = fmaf(R.chord_rng_f[c], xf[ax], R.chord_lo_f[c]);
         kmag[c] = k;
+        float jc;
         if (kind == 1) {
             kdir[0][c] = 0.0f;
             kdir[1][c] = 0.0f;
             kdir[2][c] = 1.0f;
-            jcf[c] = k * k;
+            jc = k * k;
         } else if (kind == 2) {
             const float x1 = xf[ax + 1];
             kdir[0][c] = 2.0f * sqrtf(fmaf(-x1, x1, x1));
             kdir[1][c] = 0.0f;
             kdir[2][c] = fmaf(2.0f, x1, -1.0f);
-            jcf[c] = k * k;
+            jc = k * k;
         } else {
             const float x1 = xf[ax + 1], x2 = xf[ax + 2];
             const float ct = fmaf(2.0f, x1, -1.0f);
@@ -340,10 +340,14 @@ __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __re
             kdir[0][c] = R2 * fmaf(a, a, -bb);
             kdir[1][c] = R2 * ((a + a) * b);
             kdir[2][c] = ct;
-            jcf[c] = k * k * ((0.5f - a) * rr);
+            jc = k * k * ((0.5f - a) * rr);
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) lf[q][c] = k * kdir[q][c];
+        const uint32_t jb = __float_as_uint(jc);
+        zero_bin |= (jb & 0x7F800000u) == 0u;
+        ex += (int)(jb >> 23) - 127;
+        mp *= __uint_as_float((jb & 0x7FFFFFu) | 0x3F800000u);
     }
 }
 
@@ -451,9 +455,9 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         float mp = 1.0f;
         int ex = 0;
         bool zero_bin = false;
-        float kmag[L], kdir[3][L], jcf[L];
+        float kmag[L], kdir[3][L];
         bool near = force64;
-        if (!force64) mixed_front<N, MAPK, D>(R, gf, u, nb, xf, o.binpack, mp, ex, zero_bin, kmag, kdir, jcf, lf);
+        if (!force64) mixed_front<N, MAPK, D>(R, gf, u, nb, xf, o.binpack, mp, ex, zero_bin, kmag, kdir, lf);
         if (!force64 && pretest_dead<N>(R, lf, kmag, near)) {
             if (x_out) {
 #pragma unroll
@@ -487,15 +491,8 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
 #pragma unroll
                 for (int a = 0; a < D; ++a) x_out[a] = widen_f(xf[a]);
             }
-            // VEGAS and chord Jacobians together as one FP32 mantissa product and an exponent sum
-            // (no FP64 work, no FP32 underflow); a zero or subnormal factor gives a zero weight
-#pragma unroll
-            for (int c = 0; c < L; ++c) {
-                const uint32_t bits = __float_as_uint(jcf[c]);
-                zero_bin |= (bits & 0x7F800000u) == 0u;
-                ex += (int)(bits >> 23) - 127;
-                mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
-            }
+            // VEGAS and chord Jacobians together (mixed_front): one FP32 mantissa product and an exponent
+            // sum, no FP64 work
             jv = zero_bin ? 0.0
                           : __longlong_as_double(__double_as_longlong(widen_pos_normal(mp)) + ((long long)ex << 52));
             // exact FP64 chord momenta: products of the FP32 magnitude and direction (24 x 24 bits)
@@ -732,11 +729,11 @@ __device__ __forceinline__ int mixed_classify(const DiagRec& R, const Grid2* __r
     for (int j = 0; j < NBLK; ++j) philox4x32_10(s, t, sid, (uint32_t)j, k0, k1, &u[4 * j]);
     float xf[D];
     uint32_t bp[5] = {0u, 0u, 0u, 0u, 0u};
-    float mp, kmag[L], kdir[3][L], jcf[L], lf[3][L];
+    float mp, kmag[L], kdir[3][L], lf[3][L];
     int ex;
     bool zero_bin, near;
     mixed_front<N, MAPK, D>(R, reinterpret_cast<const Grid4f*>(gs), u, (uint32_t)R.nb, xf, bp, mp, ex, zero_bin, kmag,
-                            kdir, jcf, lf);
+                            kdir, lf);
     if (pretest_dead<N>(R, lf, kmag, near)) return 0;
     return near ? 2 : 1;
 }

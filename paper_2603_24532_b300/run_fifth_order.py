@@ -32,9 +32,12 @@ def main():
     ap.add_argument("--oracle-integrals", type=int, default=48)
     ap.add_argument("--oracle-samples", type=int, default=1 << 16)
     ap.add_argument("--map-kind", type=int, default=0)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "map64", "fp64"],
+                    help="mixed: FP32 sampling map; map64: FP64 map, FP32 potentials and spin sums")
     ap.add_argument("--dedup-mirrors", action="store_true",
                     help="one integral per pair of mirror (complex-conjugate) diagrams, counted twice")
     a = ap.parse_args()
+    prec = {"mixed": M.MBPT_MIXED, "map64": M.MBPT_MIXED_MAP64, "fp64": M.MBPT_FP64}[a.precision]
     ctx = M.mbpt_ctx_create(0, 16 << 30)
     descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
     if a.dedup_mirrors:
@@ -45,7 +48,7 @@ def main():
     for ki, kf in enumerate(kfs):
         ph = M.physics(kF_n=kf, K_max=kf + 6.0, map_kind=a.map_kind)
         for d in descs:
-            cfg = M.vegas_cfg(samples=a.samples, seed=1, stream_id=1000 * ki + d.diagram_id, precision=M.MBPT_MIXED,
+            cfg = M.vegas_cfg(samples=a.samples, seed=1, stream_id=1000 * ki + d.diagram_id, precision=prec,
                               target_rel=a.target)
             gs.append(M.mbpt_create_diagram(ctx, d, ph, cfg))
             meta.append((kf, d))
@@ -59,7 +62,7 @@ def main():
         floor = a.target * order_sum / math.sqrt(sum(mult[meta[i][1].diagram_id] ** 2 for i in idx))
         for i in idx:
             cfg = M.vegas_cfg(samples=a.samples, seed=1, stream_id=1000 * ki + meta[i][1].diagram_id,
-                              precision=M.MBPT_MIXED, target_rel=a.target, target_abs=floor)
+                              precision=prec, target_rel=a.target, target_abs=floor)
             M.mbpt_set_config(gs[i], cfg)
     evals = 2 * a.samples * len(gs)
     iters = 2
@@ -116,8 +119,8 @@ def main():
                "l1_definition": "sum |w_mixed - w_oracle| / sum |w_oracle| per integral",
                "worst_cancellation": float(cancel[worst]),
                "cancellation_definition": "sum |w| / |sum w| of the integral with the largest deviation"}
-    out = {"workload": "all 840 fifth-order diagrams (668 non-anomalous) x kF {1.0, 1.33, 1.6}, PNM, mixed, "
-                       "to %.2g relative (or iteration cap %d)" % (a.target, a.max_iters),
+    out = {"workload": "all 840 fifth-order diagrams (668 non-anomalous) x kF {1.0, 1.33, 1.6}, PNM, %s, "
+                       "to %.2g relative (or iteration cap %d)" % (a.precision, a.target, a.max_iters),
            "integrals": len(gs), "dedup_mirrors": a.dedup_mirrors, "samples_per_iter": a.samples,
            "map_kind": a.map_kind, "wall_s": wall,
            "iterations": iters, "evals": evals, "evals_per_s": evals / wall, "converged": int(conv),
