@@ -38,11 +38,11 @@ WORKLOAD = "third-order Hugenholtz diagrams (pp, hh, ph), pure neutron matter, k
 # FP64 operations per sample of an order-3 integral, mixed precision (FP32 sampling map), in the
 # formulation of csrc/mbpt_device.cuh.  A sample that fails a Fermi step by more than the FP32 error
 # bound is rejected by the FP32 pre-test with no FP64 work.  A live sample: chord momenta 3 products
-# + |l|^2 3 + Jacobian 1 = 7 per chord (28), tree lines 6 sums + |k|^2 3 = 9 per line (18), energy
-# denominators (7 sums, 1 product), weight (4 products), Newton reciprocal of the denominator
-# product (4), sum w and sum w^2 (2) = 64.  (Samples inside the pre-test margin that the exact test
-# then rejects cost 46; they are a ~1e-4 fraction.)
-FP64_OPS_LIVE = 64.0
+# + |l|^2 3 = 6 per chord (24; the chord Jacobians are part of the FP32 mantissa product of the VEGAS
+# Jacobian), tree lines 6 sums + |k|^2 3 = 9 per line (18), energy denominators (7 sums, 1 product),
+# weight (4 products), Newton reciprocal of the denominator product (4), sum w and sum w^2 (2) = 60.
+# (About 1 % of samples lie near a Fermi surface and are placed with the FP64 map instead.)
+FP64_OPS_LIVE = 60.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_iterate_256x2 launch on the 30 x 2^20 profiling case
 # (profiles/k_iterate_third_order_scan.md): records and grids; not proportional to samples
 TRAFFIC_BYTES = 834560

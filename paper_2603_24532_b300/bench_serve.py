@@ -30,10 +30,12 @@ def main():
     ap.add_argument("--grouped", action="store_true", help="one integral per (order, particle-hole group)")
     ap.add_argument("--warm-blend", type=float, default=0.5, help="weight of the donor grid in a warm start")
     ap.add_argument("--warm-train", type=int, default=1, help="uncombined iterations after a warm start")
+    ap.add_argument("--log", default=None, help="JSONL file: one record per finished integral and request")
     a = ap.parse_args()
     be = S.MbptBackend(arena_bytes=int(a.arena_gb * (1 << 30)), grouped=a.grouped)
+    logf = open(a.log, "w") if a.log else None
     srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters, warm_start=a.warm_start,
-                   warm_blend=a.warm_blend, warm_train=a.warm_train)
+                   warm_blend=a.warm_blend, warm_train=a.warm_train, log=logf)
     trace = S.poisson_trace(a.requests, a.rate, a.seed)
     t0 = time.perf_counter()
     done = srv.run(trace, realtime=True, time_limit=a.time_limit)
@@ -55,6 +57,8 @@ def main():
            "example": [{"n": r.n_dens, "delta": r.delta, "cap": r.cap, "target": r.target, "E_corr": r.energy,
                         "sigma": r.sigma, "per_order": r.per_order, "latency_s": r.latency} for r in done[:3]]}
     print(json.dumps(out))
+    if logf:
+        logf.close()
     be.close()
 
 

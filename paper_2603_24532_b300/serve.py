@@ -26,6 +26,7 @@ its request, so a request's result is the same alone and in a mix.
 from __future__ import annotations
 
 import bisect
+import json
 import math
 import time
 from collections import OrderedDict
@@ -63,6 +64,7 @@ class Request:
     integrals: list = field(default_factory=list)
     budget: Optional[float] = None
     rounds: int = 0
+    cancelled: bool = False
 
     @property
     def latency(self) -> Optional[float]:
@@ -257,8 +259,9 @@ class Server:
                  samples_by_order: Optional[Dict[int, int]] = None, min_iters: int = 3, max_iters: int = 60,
                  seed: int = 1, clock: Callable[[], float] = time.perf_counter, adaptive: bool = True,
                  warm_start: bool = False, warm_window: float = 0.02, warm_blend: float = 0.5,
-                 warm_train: int = 1):
+                 warm_train: int = 1, log=None):
         self.b = backend
+        self.log = log                        # optional text stream: one JSON record per finished integral / request
         self.adaptive = adaptive
         self.cache = GridCache(warm_window) if warm_start else None
         self.warm_blend = warm_blend          # weight of the donor grid (rest: uniform bins)
@@ -344,6 +347,31 @@ class Server:
             self.n_integrals += len(plan)
             self.active.append(req)
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a request: waiting, it leaves the queue; admitted, its integrals are destroyed
+        and their arena bytes return to the budget.  It completes with energy None.  False if the
+        request is unknown or already finished."""
+        for q in (self.waiting, self.active):
+            for req in q:
+                if req.rid == rid:
+                    q.remove(req)
+                    for it in req.integrals:
+                        self.b.destroy(it.handle)
+                        self.used_bytes -= it.bytes
+                    self.n_integrals -= len(req.integrals)
+                    req.integrals = []
+                    req.energy = None
+                    req.completed = self.clock()
+                    req.cancelled = True
+                    self.done.append(req)
+                    self._log({"event": "cancelled", "rid": rid})
+                    return True
+        return False
+
+    def _log(self, rec: dict) -> None:
+        if self.log is not None:
+            self.log.write(json.dumps(rec) + "\n")
+
     def _retire_and_complete(self, now: float):
         live = [it for req in self.active for it in req.integrals if not it.done]
         if hasattr(self.b, "estimate_many"):
@@ -383,6 +411,13 @@ class Server:
                 for order in range(2, req.cap + 1):
                     req.per_order[order] = sum(it.mult * it.mean for it in req.integrals if it.order == order)
                 req.completed = now
+                for it in req.integrals:
+                    self._log({"event": "integral", "rid": req.rid, "order": it.order, "diagram": it.diagram_id,
+                               "mult": it.mult, "mean": it.mean, "sigma": it.sigma, "iterations": it.n_iter,
+                               "evals": it.evals, "warm": it.warm})
+                self._log({"event": "request", "rid": req.rid, "n": req.n_dens, "delta": req.delta, "cap": req.cap,
+                           "target": req.target, "energy": req.energy, "sigma": req.sigma,
+                           "per_order": req.per_order, "rounds": req.rounds, "latency_s": req.latency})
                 for it in req.integrals:
                     if self.cache is not None and hasattr(self.b, "get_grid"):
                         self.cache.put(it.order, it.diagram_id, req.delta, req.n_dens, self.b.get_grid(it.handle))

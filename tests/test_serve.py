@@ -278,3 +278,32 @@ def test_warm_start_seeds_grid_gpu():
 
 def _req(r):
     return dict(n_dens=r.n_dens, delta=r.delta, cap=r.cap, target=r.target, arrival=0.0, rid=r.rid)
+
+
+def test_cancel_frees_slots_and_logs():
+    """A cancelled request leaves the queue or releases its integrals' bytes; the JSONL log records
+    finished integrals, finished requests and the cancellation."""
+    import io
+    import json as _json
+    log = io.StringIO()
+    be = FakeBackend()
+    srv = S.Server(be, clock=iter(range(10 ** 6)).__next__, log=log)
+    trace = S.poisson_trace(4)
+    for r in trace:
+        srv.submit(r)
+    srv.step()                                   # admits all four, one round
+    used = srv.used_bytes
+    victim = srv.active[1]
+    n_int = len(victim.integrals)
+    assert srv.cancel(victim.rid)
+    assert srv.used_bytes == used - 25_000 * n_int and len(be.live) == sum(len(r.integrals) for r in srv.active)
+    assert not srv.cancel(victim.rid) and not srv.cancel(999)
+    while srv.step():
+        pass
+    done = {r.rid: r for r in srv.done}
+    assert done[victim.rid].cancelled and done[victim.rid].energy is None
+    assert all(r.energy is not None for k, r in done.items() if k != victim.rid)
+    recs = [_json.loads(line) for line in log.getvalue().splitlines()]
+    kinds = [r["event"] for r in recs]
+    assert kinds.count("request") == 3 and kinds.count("cancelled") == 1
+    assert kinds.count("integral") == sum(len(r.integrals) for k, r in done.items() if k != victim.rid)
