@@ -288,8 +288,12 @@ __device__ __forceinline__ void chords_fp64(const DiagRec& R, const double (&x)[
 // magnitudes, unit directions (kind 1: along z; kind 2: in the xz plane; kind 0: rational azimuth) and
 // FP32 chord momenta; the VEGAS and chord Jacobians as one mantissa product and exponent sum (so that
 // it cannot underflow; a zero or subnormal factor sets zero_bin).
-template <int N, int MAPK, int D>
-__device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __restrict__ gf, const uint32_t* u,
+// GRID selects the shared-memory grid: 0 the FP32 grid of the mixed mode (e, de); 1 the FP64 grid of
+// the FP64 mode (x = a + frac de); 2 the FP64 grid of the FP64-map mode (x = a + (1 + frac) de).  With
+// an FP64 grid the point is an FP32 approximation of the one the exact path uses (for the pre-test
+// only), and the Jacobian outputs are not computed.
+template <int N, int MAPK, int D, int GRID = 0>
+__device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid2* __restrict__ gs, const uint32_t* u,
                                             uint32_t nb, float (&xf)[D], uint32_t (&binpack)[5], float& mp,
                                             int& ex, bool& zero_bin, float (&kmag)[N + 1],
                                             float (&kdir)[3][N + 1], float (&lf)[3][N + 1]) {
@@ -302,12 +306,17 @@ __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __re
         const uint32_t i = (uint32_t)(r >> 33);
         const uint32_t fb = (uint32_t)((r >> 10) & 0x7FFFFFull);          // top 23 bits of the fraction
         const float frac = __uint_as_float(0x3F800000u | fb) - 1.0f;
-        const Grid4f g = gf[a * kGridStride + i];
-        xf[a] = fmaf(frac, g.de, g.e);
-        const uint32_t bits = __float_as_uint(g.de);
-        zero_bin |= (bits == 0u);
-        ex += (int)(bits >> 23) - 127;
-        mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+        if constexpr (GRID == 0) {
+            const Grid4f g = reinterpret_cast<const Grid4f*>(gs)[a * kGridStride + i];
+            xf[a] = fmaf(frac, g.de, g.e);
+            const uint32_t bits = __float_as_uint(g.de);
+            zero_bin |= (bits == 0u);
+            ex += (int)(bits >> 23) - 127;
+            mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+        } else {
+            const Grid2 g = gs[a * kGridStride + i];
+            xf[a] = fmaf(GRID == 1 ? frac : 1.0f + frac, narrow_trunc(g.de), narrow_trunc(g.a));
+        }
         binpack[a >> 2] |= i << (8 * (a & 3));
     }
 #pragma unroll
@@ -344,10 +353,12 @@ __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __re
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) lf[q][c] = k * kdir[q][c];
-        const uint32_t jb = __float_as_uint(jc);
-        zero_bin |= (jb & 0x7F800000u) == 0u;
-        ex += (int)(jb >> 23) - 127;
-        mp *= __uint_as_float((jb & 0x7FFFFFu) | 0x3F800000u);
+        if constexpr (GRID == 0) {
+            const uint32_t jb = __float_as_uint(jc);
+            zero_bin |= (jb & 0x7F800000u) == 0u;
+            ex += (int)(jb >> 23) - 127;
+            mp *= __uint_as_float((jb & 0x7FFFFFu) | 0x3F800000u);
+        }
     }
 }
 
@@ -358,7 +369,13 @@ __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid4f* __re
 // S_l = sum over its chords of |coefficient| |k_c|, |k_f^2 - k^2| < 2^-19 S_l^2; the margin is
 // 2^-16 S_l^2 plus 2^-20 kF^2 for the FP32 copy of kF^2.  near: some line lies within the margin plus
 // 2^-10 kF^2 of a Fermi surface (the band in which the caller places the sample with the FP64 map).
-template <int N>
+// SLACK (FP64 and FP64-map modes, whose exact path places the sample with the FP64 map): the FP32
+// point differs from the FP64 one by < 2^-20 per axis, which moves a chord magnitude by
+// < 2^-18 (rng + k) and its unit direction by < 2^-7 (the sin(theta) = 2 sqrt(x1 (1 - x1)) factor is
+// only 1/2-Hoelder: a change d of x1 moves it by < 2 sqrt(d)), so the line moves by
+// < 2^-6.9 S_l + 2^-18 Q_l with Q_l = sum of |coefficient| rng_c, and |k|^2 by < 2^-5.9 S_l^2 +
+// 2^-17 S_l Q_l + (that)^2; the margin adds 2^-5 S_l^2 + 2^-16 S_l Q_l.
+template <int N, bool SLACK = false>
 __device__ __forceinline__ bool pretest_dead(const DiagRec& R, const float (&lf)[3][N + 1],
                                              const float (&kmag)[N + 1], bool& near) {
     constexpr int L = N + 1;
@@ -367,11 +384,13 @@ __device__ __forceinline__ bool pretest_dead(const DiagRec& R, const float (&lf)
 #pragma unroll
     for (int l = 0; l < 2 * N; ++l) {
         float x, y, z, S;
+        float Q = 0.0f;
         if (l < L) {
             x = lf[0][l];
             y = lf[1][l];
             z = lf[2][l];
             S = kmag[l];
+            if (SLACK) Q = R.chord_rng_f[l];
         } else {
             x = 0.0f;
             y = 0.0f;
@@ -384,10 +403,12 @@ __device__ __forceinline__ bool pretest_dead(const DiagRec& R, const float (&lf)
                 y = fmaf(cf, lf[1][c], y);
                 z = fmaf(cf, lf[2][c], z);
                 S = fmaf(fabsf(cf), kmag[c], S);
+                if (SLACK) Q = fmaf(fabsf(cf), R.chord_rng_f[c], Q);
             }
         }
         const float uf = fmaf(x, x, fmaf(y, y, z * z));
-        const float mg = 1.52587890625e-05f * S * S;
+        float mg = 1.52587890625e-05f * S * S;
+        if (SLACK) mg = fmaf(0.03125f * S, S, fmaf(1.52587890625e-05f * S, Q, mg));
         const bool hole = (R.hole_slots >> l) & 1u;
         const float mn = fmaf(9.5367431640625e-07f, R.kf2_nf, mg);
         const float dn = uf - R.kf2_nf;
@@ -449,15 +470,14 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         // come within ~1e-3 kF^2 of a Fermi surface -- where the energy denominators can vanish and
         // a step decision could depend on where the FP32 map rounds the point -- are placed with the
         // FP64 map instead (the FP64 mode's point, bins unchanged).
-        // force64: the caller has already classified the sample as near a surface (mixed_classify).
-        const Grid4f* gf = reinterpret_cast<const Grid4f*>(gs);
+        // force64: the caller has already classified the sample as near a surface (sample_class).
         float xf[D];
         float mp = 1.0f;
         int ex = 0;
         bool zero_bin = false;
         float kmag[L], kdir[3][L];
         bool near = force64;
-        if (!force64) mixed_front<N, MAPK, D>(R, gf, u, nb, xf, o.binpack, mp, ex, zero_bin, kmag, kdir, lf);
+        if (!force64) mixed_front<N, MAPK, D>(R, gs, u, nb, xf, o.binpack, mp, ex, zero_bin, kmag, kdir, lf);
         if (!force64 && pretest_dead<N>(R, lf, kmag, near)) {
             if (x_out) {
 #pragma unroll
@@ -715,15 +735,18 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
     return o;
 }
 
-// Mixed precision: class of sample s after the FP32 front and Fermi-step pre-test (Philox and FP32
-// work only): 0 zero (eval_sample would reject it), 1 live or undecided and away from every Fermi
-// surface (FP32 placement), 2 near a surface (eval_sample places it with the FP64 map).
-template <int N, int MAPK>
-__device__ __forceinline__ int mixed_classify(const DiagRec& R, const Grid2* __restrict__ gs, uint32_t s, uint32_t t,
-                                              uint32_t sid, uint32_t k0, uint32_t k1) {
+// Class of sample s after an FP32 front and Fermi-step pre-test (Philox and FP32 work only):
+// 0 zero (eval_sample would find it zero), 1 live or undecided (mixed mode: and away from every Fermi
+// surface, FP32 placement), 2 (mixed mode) near a surface, placed with the FP64 map.  In the FP64 and
+// FP64-map modes the pre-test works on an FP32 approximation of the FP64 point, with the extra
+// margin for the difference, and every survivor is class 1.
+template <int N, int MAPK, int PREC>
+__device__ __forceinline__ int sample_class(const DiagRec& R, const Grid2* __restrict__ gs, uint32_t s, uint32_t t,
+                                            uint32_t sid, uint32_t k0, uint32_t k1) {
     constexpr int L = N + 1;
     constexpr int D = 3 * L - 3 * MAPK;
     constexpr int NBLK = (D + 3) / 4;
+    constexpr int GRID = PREC == MBPT_MIXED ? 0 : (PREC == MBPT_FP64 ? 1 : 2);
     uint32_t u[4 * NBLK];
 #pragma unroll
     for (int j = 0; j < NBLK; ++j) philox4x32_10(s, t, sid, (uint32_t)j, k0, k1, &u[4 * j]);
@@ -732,10 +755,9 @@ __device__ __forceinline__ int mixed_classify(const DiagRec& R, const Grid2* __r
     float mp, kmag[L], kdir[3][L], lf[3][L];
     int ex;
     bool zero_bin, near;
-    mixed_front<N, MAPK, D>(R, reinterpret_cast<const Grid4f*>(gs), u, (uint32_t)R.nb, xf, bp, mp, ex, zero_bin, kmag,
-                            kdir, lf);
-    if (pretest_dead<N>(R, lf, kmag, near)) return 0;
-    return near ? 2 : 1;
+    mixed_front<N, MAPK, D, GRID>(R, gs, u, (uint32_t)R.nb, xf, bp, mp, ex, zero_bin, kmag, kdir, lf);
+    if (pretest_dead<N, GRID != 0>(R, lf, kmag, near)) return 0;
+    return (GRID == 0 && near) ? 2 : 1;
 }
 
 }  // namespace mbpt

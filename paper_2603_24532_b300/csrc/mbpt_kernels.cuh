@@ -108,9 +108,9 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 }
 
 // One chunk: samples first + j*blockDim + tid, j < spt.
-//  Mixed precision: the FP64 pipe issues per warp instruction, so a warp whose
-//  lanes hold a mix of zero and live samples pays for the zero ones, and one whose lanes take both
-//  sampling maps pays for both.  Each warp therefore alternates two phases, each a tight loop over
+//  Plain integrals, every precision: the FP64 pipe issues per warp instruction, so a warp whose
+//  lanes hold a mix of zero and live samples pays for the zero ones, and (mixed mode) one whose lanes
+//  take both sampling maps pays for both.  Each warp therefore alternates two phases, each a tight loop over
 //  its own code: kClassRounds rounds of the FP32 front and Fermi-step pre-test, pushing the samples
 //  that may be live onto one of two shared-memory stacks by class (away from / near a Fermi
 //  surface; ballot + prefix count), then full warps of one class popped and evaluated until fewer
@@ -137,7 +137,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     constexpr int PER = REG ? 1 + kComp : 1;        // group slots per sample
     const int nm = (int)W.n_members;
     const bool grp = nm > 1;
-    const bool compact = (PREC == MBPT_MIXED) && !grp;   // groups: direct loop (fewer live registers)
+    const bool compact = !grp;   // groups: direct loop (fewer live registers)
     for (int m = 0; m < nm; ++m) {
         if (m > 0) {
             __syncthreads();
@@ -156,7 +156,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
                     for (; j < jend; ++j) {
                         const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
                         const int cls = sc < W.samples
-                                            ? mixed_classify<N, MAPK>(R, S.grid, (uint32_t)sc, t, W.stream_id, k0, k1)
+                                            ? sample_class<N, MAPK, PREC>(R, S.grid, (uint32_t)sc, t, W.stream_id, k0, k1)
                                             : 0;
                         const uint32_t lt = (1u << lane) - 1u;
                         const uint32_t b0 = __ballot_sync(0xffffffffu, cls == 1);
