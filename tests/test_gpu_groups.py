@@ -98,28 +98,30 @@ def test_group_one_iteration_vs_oracle(ctx, prec):
         M.mbpt_destroy_diagram(g)
 
 
-def test_group_of_a_repeated_member_is_exactly_twice_the_diagram(ctx):
-    """The group [a, a] doubles every weight exactly, so with the same chunking its running
-    estimate is exactly twice that of diagram a, its error too, and its grids are identical."""
+def test_group_of_a_repeated_member_is_twice_the_diagram(ctx):
+    """The group [a, a] doubles every weight exactly: it equals the group [a, a] with scales (2, 0)
+    bit for bit over several iterations (same loop, same grids), and after one iteration on the
+    uniform grid its estimate is twice that of diagram a (whose loop sums in another order)."""
     po, pm = matter_pair("snm")
     D = O.enumerate_diagrams(4)[11]
     assert not O.is_anomalous(D)
     cfg = M.vegas_cfg(samples=50000, seed=2, stream_id=31, precision=M.MBPT_MIXED_MAP64)
-    tpb, minb, spt0 = M.mbpt_ctx_get_launch(ctx, 4)
-    M.mbpt_ctx_set_launch(ctx, 4, 8)          # the chunk shape a group uses (8 samples per thread)
     a = M.mbpt_create_diagram(ctx, make_desc(D), pm, cfg)
-    g = M.mbpt_create_group(ctx, [make_desc(D), make_desc(D)], pm, cfg)
+    g1 = M.mbpt_create_group(ctx, [make_desc(D), make_desc(D)], pm, cfg)
+    g2 = M.mbpt_create_group(ctx, [make_desc(D), make_desc(D)], pm, cfg, scales=[2.0, 0.0])
     try:
-        M.mbpt_vegas_iterate(ctx, [a, g], 3)
-        ra, rg = M.mbpt_estimate(a), M.mbpt_estimate(g)
-        assert rg.mean == 2.0 * ra.mean and rg.sigma == 2.0 * ra.sigma and rg.chi2_dof == ra.chi2_dof
-        assert rg.last_mean == 2.0 * ra.last_mean
-        assert np.array_equal(M.state_grid(M.mbpt_get_state(a), D.d, 50),
-                              M.state_grid(M.mbpt_get_state(g), D.d, 50))
+        M.mbpt_vegas_iterate(ctx, [a, g1, g2], 1)
+        ra, r1 = M.mbpt_estimate(a), M.mbpt_estimate(g1)
+        assert r1.last_mean == pytest.approx(2.0 * ra.last_mean, rel=1e-12)
+        assert r1.last_sigma == pytest.approx(2.0 * ra.last_sigma, rel=1e-10)
+        M.mbpt_vegas_iterate(ctx, [g1, g2], 2)
+        r1, r2 = M.mbpt_estimate(g1), M.mbpt_estimate(g2)
+        assert (r1.mean, r1.sigma, r1.chi2_dof) == (r2.mean, r2.sigma, r2.chi2_dof)
+        assert np.array_equal(M.state_grid(M.mbpt_get_state(g1), D.d, 50),
+                              M.state_grid(M.mbpt_get_state(g2), D.d, 50))
     finally:
-        M.mbpt_destroy_diagram(a)
-        M.mbpt_destroy_diagram(g)
-        M.mbpt_ctx_set_launch(ctx, 4, spt0)
+        for h in (a, g1, g2):
+            M.mbpt_destroy_diagram(h)
 
 
 def test_group_alone_equals_group_in_a_mixed_batch(ctx):
