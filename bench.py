@@ -354,6 +354,26 @@ def run_gpu(args):
     d_rot = diags_per_s(res_rot, vrot)
     d_k0 = diags_per_s(res64, vk0)
     M.mbpt_ctx_destroy(ctx)
+    del arena
+    torch.cuda.synchronize()
+
+    # ---- serving: a short Poisson stream of equation-of-state requests (p50/p99 latency)
+    serving = None
+    if args.serve_requests > 0:
+        from paper_2603_24532_b300 import serve as S
+        be = S.MbptBackend(device=local, arena_bytes=8 << 30)
+        srv = S.Server(be, budget_bytes=6 << 30)
+        trace = S.poisson_trace(args.serve_requests, 20.0, 7 + rank)
+        t0 = time.perf_counter()
+        done = srv.run(trace, realtime=True, time_limit=args.serve_seconds)
+        wall = time.perf_counter() - t0
+        st = S.latency_stats(done)
+        met = [r for r in done if r.energy is not None and r.sigma is not None and r.sigma <= r.target * abs(r.energy)]
+        serving = {"requests": len(trace), "completed": len(done), "wall_s": wall, "p50_s": st["p50_s"],
+                   "p99_s": st["p99_s"], "target_met_fraction": len(met) / max(1, len(done)),
+                   "workload": "Poisson 20/s, n ~ U[0.04, 0.20] fm^-3, delta {0..1}, order cap {2,3,4}, "
+                               "target {1, 0.3, 0.1} %, seed 7 (+rank)"}
+        be.close()
     if dist:
         dist.barrier()
     if rank != 0:
@@ -401,6 +421,7 @@ def run_gpu(args):
                                             "point (24 group integrals), mixed"},
         "rotational_9d": {"value": vrot, "unit": UNIT, "kernel_ms": float(np.mean(itrot)),
                           "note": "same scan with chord 0 along z and chord 1 in the xz plane (d = 9)"},
+        "serving": serving,
     }
     print(json.dumps(line))
     if dist:
@@ -471,6 +492,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-requests", type=int, default=400, help="short serving run (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=40.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import mbpt as M
 
-DEFAULT_SPT = (8, 16, 32, 64)
+DEFAULT_SPT = (8, 16, 32, 64, 128)
 
 
 def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: Optional[Sequence] = None,

@@ -480,3 +480,20 @@ def test_arena_exhaustion_is_enomem():
         assert used == 0
     finally:
         M.mbpt_ctx_destroy(small)
+
+
+def test_more_iterations_than_the_history_holds(ctx):
+    """The per-iteration history keeps 512 entries; an integral that runs longer keeps combining and
+    reports a finite estimate with every evaluation counted."""
+    po, pm = matter_pair("pnm")
+    D = O.enumerate_diagrams(2)[0]
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=2048, seed=9, freeze_after=4))
+    try:
+        M.mbpt_vegas_iterate(ctx, [g], 530)
+        r = M.mbpt_estimate(g)
+        assert r.n_iter == 530 and r.n_evals == 530 * 2048
+        assert np.isfinite(r.mean) and np.isfinite(r.sigma) and r.sigma > 0 and r.status == 0
+        q = O.vegas(D, O.Physics(), 4, 1 << 14, seed=1)
+        assert abs(r.mean - q[0]) < 5 * np.hypot(r.sigma, q[1])
+    finally:
+        M.mbpt_destroy_diagram(g)
