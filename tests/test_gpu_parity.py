@@ -487,13 +487,17 @@ def test_more_iterations_than_the_history_holds(ctx):
     reports a finite estimate with every evaluation counted."""
     po, pm = matter_pair("pnm")
     D = O.enumerate_diagrams(2)[0]
-    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=2048, seed=9, freeze_after=4))
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=8192, seed=9, freeze_after=4))
     try:
-        M.mbpt_vegas_iterate(ctx, [g], 530)
+        M.mbpt_vegas_iterate(ctx, [g], 100)
+        r100 = M.mbpt_estimate(g)
+        M.mbpt_vegas_iterate(ctx, [g], 430)
         r = M.mbpt_estimate(g)
-        assert r.n_iter == 530 and r.n_evals == 530 * 2048
-        assert np.isfinite(r.mean) and np.isfinite(r.sigma) and r.sigma > 0 and r.status == 0
+        assert r.n_iter == 530 and r.n_evals == 530 * 8192
+        assert np.isfinite(r.mean) and np.isfinite(r.sigma) and 0 < r.sigma < r100.sigma and r.status == 0
+        # (inverse-variance weighting of many small iterations of a heavy-tailed integrand is biased
+        # towards small |I|, so only a loose check against the oracle's value)
         q = O.vegas(D, O.Physics(), 4, 1 << 14, seed=1)
-        assert abs(r.mean - q[0]) < 5 * np.hypot(r.sigma, q[1])
+        assert abs(r.mean - q[0]) < 0.25 * abs(q[0])
     finally:
         M.mbpt_destroy_diagram(g)
