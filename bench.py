@@ -402,7 +402,7 @@ def run_gpu(args):
                                      "(grids and records; chunk slots stay in L2), not proportional to samples"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,   # per step: k_iterate, its regulated part (empty here), k_finalize
+        "gpu_launches": 5 * args.steps,   # per step: k_iterate parts (plain; regulated and group parts empty here), k_finalize
         "clocks": clk,
         "fp64_batched": {"value": v64, "unit": UNIT, "kernel_ms": float(np.mean(it64)), "launch": tuned64},
         "k0_plain_fp64_per_diagram": {"value": vk0, "unit": UNIT, "launches_per_step": 2 * n_int},

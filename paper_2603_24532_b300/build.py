@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmbpt.so")
 SHAPES = ["256x2", "128x4", "256x1", "128x3"]
 # the long kernel units first, so that they start as early as possible on a machine with fewer cores
-SOURCES = (["mbpt_k_iterate_%s%s.cu" % (sh, part) for sh in SHAPES for part in ("", "_reg")] +
+SOURCES = (["mbpt_k_iterate_%s%s.cu" % (sh, part) for sh in SHAPES for part in ("", "_reg", "_grp", "_grp_reg")] +
            ["mbpt_runtime.cu", "mbpt_host.cpp", "mbpt_k_misc.cu"])
 HEADERS = ["mbpt_device.cuh", "mbpt_kernels.cuh", "mbpt_kernels.h", "mbpt_internal.h",
            os.path.join("..", "..", "include", "mbpt.h")]

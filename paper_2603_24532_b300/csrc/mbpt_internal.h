@@ -119,13 +119,13 @@ struct alignas(16) WorkHeader {
     uint32_t error;           // non-zero: a kernel saw an out-of-range index or a misplaced item
     uint32_t pad0;
     uint64_t hist_floats;     // size of the chunk histogram scratch
-    // the batch is split in two parts, each run by its own k_iterate kernel: items [0, part_items[0])
-    // without the denominator regulator, then part_items[1] items with it; their chunks are
-    // [0, part_chunks[0]) and [part_chunks[0], part_chunks[0] + part_chunks[1])
-    uint32_t part_items[2];
-    uint32_t part_chunks[2];
-    uint32_t part_counter[2]; // dynamic chunk scheduling, reset before every iterate launch
-    uint32_t pad1[2];
+    // the batch is split in four parts, each run by its own k_iterate kernel, in this order: plain
+    // integrals, plain with the denominator regulator, groups, groups with the regulator (part bit 0:
+    // regulator, bit 1: group); part p holds part_items[p] consecutive items and part_chunks[p]
+    // consecutive chunks
+    uint32_t part_items[4];
+    uint32_t part_chunks[4];
+    uint32_t part_counter[4]; // dynamic chunk scheduling, reset before every iterate launch
 };
 
 // host-side helpers (mbpt_host.cpp)

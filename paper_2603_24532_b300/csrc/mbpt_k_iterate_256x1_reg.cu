@@ -1,5 +1,5 @@
 // k_iterate_256x1_reg: k_iterate compiled for 256 threads per block, at least 1 resident blocks per SM, for the
-// batch's integrals with the denominator regulator.
+// batch's plain integrals with the denominator regulator.
 #include "mbpt_kernels.cuh"
 #include "mbpt_kernels.h"
 

@@ -1,5 +1,5 @@
 // k_iterate_256x2: k_iterate compiled for 256 threads per block, at least 2 resident blocks per SM, for the
-// batch's integrals without the denominator regulator.
+// batch's plain integrals.
 #include "mbpt_kernels.cuh"
 #include "mbpt_kernels.h"
 

@@ -116,12 +116,11 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  surface; ballot + prefix count), then full warps of one class popped and evaluated until fewer
 //  than 32 of each remain; the partial warps are evaluated at the end of the chunk.  Which thread
 //  sums which sample depends only on the chunk, so results stay deterministic.
-//  A group integral (n_members > 1) evaluates every member at each sample with the direct loop
-//  (routing groups through the phases above costs the plain path registers: a 1.2 KB stack frame
-//  instead of 120 B), member by member with the record swapped in shared memory, adding the weights
-//  per sample into gacc, zeroed per chunk (spt x (1 + regulator components) <= kGroupSlots slots per
-//  thread); sums, squares and the histogram then see the group's integrand.
-template <int N, int PREC, int MAPK, bool REG, int NW>
+//  A group integral (n_members > 1; its own kernel, GRP) evaluates every member at each sample, member
+//  by member with the record swapped in shared memory, each member's samples through the phases
+//  above, adding the weights per sample into gacc, zeroed per chunk (spt x (1 + regulator components)
+//  <= kGroupSlots slots per thread); sums, squares and the histogram then see the group's integrand.
+template <int N, int PREC, int MAPK, bool REG, bool GRP, int NW>
 __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
     const DiagRec& R = S.rec;
@@ -135,9 +134,9 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     const int nb = R.nb;
     constexpr int D = 3 * (N + 1) - 3 * MAPK;
     constexpr int PER = REG ? 1 + kComp : 1;        // group slots per sample
-    const int nm = (int)W.n_members;
-    const bool grp = nm > 1;
-    const bool compact = !grp;   // groups: direct loop (fewer live registers)
+    const int nm = GRP ? (int)W.n_members : 1;
+    constexpr bool grp = GRP;
+    constexpr bool compact = true;
     for (int m = 0; m < nm; ++m) {
         if (m > 0) {
             __syncthreads();
@@ -186,7 +185,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
             if (have) {
                 const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, W.grid, (uint32_t)s, t, W.stream_id,
                                                                     k0, k1, nullptr, use_near);
-                if (grp) {
+                if constexpr (GRP) {
                     // the sample's slot belongs to the lane of this warp that owns it in the chunk layout
                     // (sample first + js * blockDim + own); each slot gets one add per member
                     const uint32_t off = (uint32_t)(s - first);
@@ -218,7 +217,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
             }
         }
     }
-    if (!grp) return;
+    if constexpr (!GRP) return;
     __syncwarp();                              // slots were filled by the warp's lanes
     for (int j = 0; j < W.spt; ++j) {
         const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
@@ -267,8 +266,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // chunk does not depend on which block ran it or what else is in the batch.
 // Compiled in several launch shapes (threads per block x minimum resident blocks, i.e. a register cap);
 // the autotuner picks one per context.
-// PART 0 runs the batch's integrals without the denominator regulator, PART 1 those with it (separate
-// kernels, so that each carries only its own instantiations).
+// The batch is run by four kernels, one per part, each carrying only its own instantiations: PART
+// bit 0 = the integrals carry the denominator regulator, bit 1 = group integrals.
 template <int TPB, int PART>
 __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* __restrict__ items,
                                                double* __restrict__ csum, float* __restrict__ chist) {
@@ -276,8 +275,14 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ChunkSmemT<NW>& S = *reinterpret_cast<ChunkSmemT<NW>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t item0 = PART ? hdr->part_items[0] : 0u, n_items = hdr->part_items[PART];
-    const uint32_t chunk0 = PART ? hdr->part_chunks[0] : 0u, total = hdr->part_chunks[PART];
+    constexpr bool REGP = (PART & 1) != 0, GRPP = (PART & 2) != 0;
+    uint32_t item0 = 0, chunk0 = 0;
+#pragma unroll
+    for (int p = 0; p < PART; ++p) {
+        item0 += hdr->part_items[p];
+        chunk0 += hdr->part_chunks[p];
+    }
+    const uint32_t n_items = hdr->part_items[PART], total = hdr->part_chunks[PART];
     for (;;) {
         if (tid == 0) {
             const uint32_t cl = atomicAdd(&hdr->part_counter[PART], 1u);
@@ -292,12 +297,14 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
                 }
                 it = lo;
                 if (c - items[it].chunk_begin >= items[it].n_chunks) atomicOr(&hdr->error, 1u);
-                if ((items[it].rec->n_shifts != 0) != (PART != 0)) atomicOr(&hdr->error, 4u);
+                if ((items[it].rec->n_shifts != 0) != REGP || (items[it].n_members > 1) != GRPP)
+                    atomicOr(&hdr->error, 4u);
             }
             S.chunk = (cl < total) ? chunk0 + cl : 0xFFFFFFFFu;
             S.item = it;
             S.skip = (cl < total) ? (uint32_t)items[it].state->converged |
-                                        (uint32_t)((items[it].rec->n_shifts != 0) != (PART != 0))
+                                        (uint32_t)((items[it].rec->n_shifts != 0) != REGP ||
+                                                   (items[it].n_members > 1) != GRPP)
                                   : 1u;
             S.iter = (cl < total) ? (uint32_t)items[it].state->iter : 0u;
         }
@@ -322,7 +329,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
         const uint32_t cl = chunk - W.chunk_begin;
         switch ((order * 3 + prec) * 2 + S.rec.map_kind) {
 #define MBPT_CASE(N_, P_, M_) \
-    case (N_ * 3 + P_) * 2 + M_: run_chunk<N_, P_, M_, (PART != 0), NW>(S, W, cl, sw, sw2); break;
+    case (N_ * 3 + P_) * 2 + M_: run_chunk<N_, P_, M_, REGP, GRPP, NW>(S, W, cl, sw, sw2); break;
 #define MBPT_CASES(N_) \
     MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
     MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)
@@ -342,7 +349,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             S.red[1][warp] = sw2;
         }
         __syncthreads();
-        if (PART) {
+        if (REGP) {
             for (int c = 0; c < 2 * kComp; ++c) {
                 const double v = warp_sum(S.cacc[c][tid]);
                 if (lane == 0) S.redc[c][warp] = v;
@@ -357,7 +364,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             }
             csum[kSumStride * (size_t)chunk] = a;
             csum[kSumStride * (size_t)chunk + 1] = b;
-            if (PART)
+            if (REGP)
                 for (int c = 0; c < 2 * kComp; ++c) {
                     double v = 0.0;
                     for (int w = 0; w < NW; ++w) v += S.redc[c][w];

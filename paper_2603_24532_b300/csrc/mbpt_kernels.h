@@ -8,7 +8,7 @@ namespace mbpt {
 
 // sample evaluation: persistent, chunks from an atomic counter; one definition per launch shape
 // (threads per block x minimum resident blocks per SM) and batch part (_reg: integrals with the
-// denominator regulator)
+// denominator regulator; _grp: group integrals)
 __global__ void k_iterate_256x2(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
 __global__ void k_iterate_128x4(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
 __global__ void k_iterate_256x1(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
@@ -17,6 +17,14 @@ __global__ void k_iterate_256x2_reg(WorkHeader* hdr, const WorkItem* items, doub
 __global__ void k_iterate_128x4_reg(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
 __global__ void k_iterate_256x1_reg(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
 __global__ void k_iterate_128x3_reg(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_256x2_grp(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_128x4_grp(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_256x1_grp(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_128x3_grp(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_256x2_grp_reg(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_128x4_grp_reg(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_256x1_grp_reg(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
+__global__ void k_iterate_128x3_grp_reg(WorkHeader* hdr, const WorkItem* items, double* csum, float* chist);
 
 // per integral: fixed-order reduction of the chunk slots, combination, convergence, refinement
 __global__ void k_finalize(WorkHeader* hdr, const WorkItem* items, const double* csum, const float* chist,

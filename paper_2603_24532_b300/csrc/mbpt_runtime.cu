@@ -108,16 +108,17 @@ struct Arena {
 // ---------------------------------------------------------------------------
 namespace {
 typedef void (*IterateFn)(WorkHeader*, const WorkItem*, double*, float*);
+constexpr int kParts = 4;      // plain, plain + regulator, group, group + regulator
 struct KernelVariant {
     int tpb, minb;
-    IterateFn fn, fn_reg;      // batch part without / with the denominator regulator
+    IterateFn fn[kParts];
     size_t smem;
 };
 const KernelVariant kVariants[] = {
-    {256, 2, k_iterate_256x2, k_iterate_256x2_reg, sizeof(ChunkSmemT<8>)},
-    {128, 4, k_iterate_128x4, k_iterate_128x4_reg, sizeof(ChunkSmemT<4>)},
-    {256, 1, k_iterate_256x1, k_iterate_256x1_reg, sizeof(ChunkSmemT<8>)},
-    {128, 3, k_iterate_128x3, k_iterate_128x3_reg, sizeof(ChunkSmemT<4>)},
+    {256, 2, {k_iterate_256x2, k_iterate_256x2_reg, k_iterate_256x2_grp, k_iterate_256x2_grp_reg}, sizeof(ChunkSmemT<8>)},
+    {128, 4, {k_iterate_128x4, k_iterate_128x4_reg, k_iterate_128x4_grp, k_iterate_128x4_grp_reg}, sizeof(ChunkSmemT<4>)},
+    {256, 1, {k_iterate_256x1, k_iterate_256x1_reg, k_iterate_256x1_grp, k_iterate_256x1_grp_reg}, sizeof(ChunkSmemT<8>)},
+    {128, 3, {k_iterate_128x3, k_iterate_128x3_reg, k_iterate_128x3_grp, k_iterate_128x3_grp_reg}, sizeof(ChunkSmemT<4>)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 }  // namespace
@@ -130,8 +131,7 @@ struct mbpt_ctx {
     Arena arena;
     int sms = 0;
     int variant = 0;                       // index into kVariants
-    int variant_blocks[kNumVariants] = {0};      // persistent grid of each k_iterate variant
-    int variant_blocks_reg[kNumVariants] = {0};  // ... and of its regulated part
+    int variant_blocks[kNumVariants][kParts] = {};   // persistent grid of each k_iterate variant and part
     int finalize_blocks = 0;
     int spt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};
     // batch buffers (arena)
@@ -235,13 +235,13 @@ int capture_graph(mbpt_ctx* c) {
     if (c->graph) return MBPT_OK;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(c->d_hdr->part_counter, 0, 2 * sizeof(uint32_t), c->stream);
+    cudaMemsetAsync(c->d_hdr->part_counter, 0, kParts * sizeof(uint32_t), c->stream);
     cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal);
     const KernelVariant& kv = kVariants[c->variant];
-    // the regulated part's blocks exit at once when it is empty
-    kv.fn<<<c->variant_blocks[c->variant], kv.tpb, kv.smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist);
-    kv.fn_reg<<<c->variant_blocks_reg[c->variant], kv.tpb, kv.smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
-                                                                                 c->d_chist);
+    // the blocks of an empty part exit at once
+    for (int p = 0; p < kParts; ++p)
+        kv.fn[p]<<<c->variant_blocks[c->variant][p], kv.tpb, kv.smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
+                                                                                   c->d_chist);
     cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal);
     k_finalize<<<c->finalize_blocks, 256, 0, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist,
                                                          c->d_last_hist);
@@ -328,20 +328,18 @@ int mbpt_ctx_create(mbpt_ctx** out, int device, void* arena, size_t arena_bytes,
     }
     for (int v = 0; v < kNumVariants; ++v) {
         const KernelVariant& kv = kVariants[v];
-        int per_sm = 0, per_sm_reg = 0;
-        e = cudaFuncSetAttribute(kv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kv.fn_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv.fn, kv.tpb, kv.smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_reg, kv.fn_reg, kv.tpb, kv.smem);
-        if (e != cudaSuccess || per_sm < 1 || per_sm_reg < 1) {
-            if (c->own_stream) cudaStreamDestroy(c->stream);
-            if (c->own_arena) cudaFree(base);
-            delete c;
-            return fail(MBPT_ECUDA, std::string("k_iterate occupancy: ") + cudaGetErrorString(e));
+        for (int p = 0; p < kParts; ++p) {
+            int per_sm = 0;
+            e = cudaFuncSetAttribute(kv.fn[p], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv.fn[p], kv.tpb, kv.smem);
+            if (e != cudaSuccess || per_sm < 1) {
+                if (c->own_stream) cudaStreamDestroy(c->stream);
+                if (c->own_arena) cudaFree(base);
+                delete c;
+                return fail(MBPT_ECUDA, std::string("k_iterate occupancy: ") + cudaGetErrorString(e));
+            }
+            c->variant_blocks[v][p] = per_sm * c->sms;
         }
-        c->variant_blocks[v] = per_sm * c->sms;
-        c->variant_blocks_reg[v] = per_sm_reg * c->sms;
     }
     c->finalize_blocks = 2 * c->sms;
     for (int i = 0; i < 3; ++i) {
@@ -605,16 +603,17 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         if (!seen.insert(g).second) return fail(MBPT_EINVAL, "vegas_iterate: integral listed twice");
         stride = std::max(stride, g->d * g->nb);
     }
-    // integrals without the regulator first, then those with it (two kernels), each in call order
+    // the batch's parts in kernel order (bit 0: regulator, bit 1: group), each in call order
+    auto part_of = [](const mbpt_diag* g) { return (g->cfg.n_shifts != 0 ? 1 : 0) | (g->n_members > 1 ? 2 : 0); };
     std::vector<mbpt_diag*> order_v;
     order_v.reserve((size_t)k);
-    for (int part = 0; part < 2; ++part)
+    for (int part = 0; part < kParts; ++part)
         for (int i = 0; i < k; ++i)
-            if ((diags[i]->cfg.n_shifts != 0) == (part != 0)) order_v.push_back(diags[i]);
-    uint32_t part_items[2] = {0, 0}, part_chunks[2] = {0, 0};
+            if (part_of(diags[i]) == part) order_v.push_back(diags[i]);
+    uint32_t part_items[kParts] = {0, 0, 0, 0}, part_chunks[kParts] = {0, 0, 0, 0};
     for (int i = 0; i < k; ++i) {
         mbpt_diag* g = order_v[(size_t)i];
-        const int part = g->cfg.n_shifts != 0;
+        const int part = part_of(g);
         WorkItem w;
         memset(&w, 0, sizeof(w));
         w.rec = g->d_rec;
@@ -649,7 +648,7 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
     h.n_items = (uint32_t)k;
     h.total_chunks = (uint32_t)chunk;
     h.hist_floats = (uint64_t)chunk * (uint64_t)stride;
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < kParts; ++p) {
         h.part_items[p] = part_items[p];
         h.part_chunks[p] = part_chunks[p];
     }
