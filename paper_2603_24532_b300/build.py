@@ -27,6 +27,9 @@ def nvcc() -> str:
     return "nvcc"
 
 
+OBJDIR = os.path.join(HERE, "_build")
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
@@ -38,32 +41,35 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit in parallel (the kernel shapes are separate units), then link."""
+    """Compile the translation units in parallel (the kernel shapes and batch parts are separate units)
+    and link.  Objects are kept in _build/: a unit is recompiled when it, or any header, is newer than
+    its object (or with force)."""
     if not force and not _stale():
         return LIB
     import concurrent.futures
-    import tempfile
-    tag = "%d" % os.getpid()
-    odir = tempfile.mkdtemp(prefix="mbpt_build_")
+    os.makedirs(OBJDIR, exist_ok=True)
+    newest_header = max(os.path.getmtime(os.path.join(CSRC, h)) for h in HEADERS)
 
     def compile_one(src):
-        obj = os.path.join(odir, os.path.basename(src) + ".o")
-        cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", "-o", obj,
-               os.path.join(CSRC, src)]
+        obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+        path = os.path.join(CSRC, src)
+        if (not force and os.path.exists(obj) and os.path.getmtime(obj) > os.path.getmtime(path)
+                and os.path.getmtime(obj) > newest_header):
+            return obj
+        tmp = obj + ".tmp%d" % os.getpid()
+        cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", "-o", tmp, path]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.check_call(cmd)
+        os.replace(tmp, obj)
         return obj
 
     workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
     with concurrent.futures.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp" + tag
+    tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp] + objs)
     os.replace(tmp, LIB)
-    for o in objs:
-        os.remove(o)
-    os.rmdir(odir)
     return LIB
 
 

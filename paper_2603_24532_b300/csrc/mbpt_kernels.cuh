@@ -12,23 +12,28 @@ namespace mbpt {
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-constexpr int kClassRounds = 16;                      // pre-test rounds between evaluation phases
-constexpr int kQueue = 2 * 31 + 32 * kClassRounds + 2;   // carried-over entries of both classes + one phase
+// pre-test rounds between evaluation phases (longer phases keep the instruction cache warmer; the
+// group + regulator part has the least shared memory to spare), and the per-warp stack length:
+// carried-over entries of both classes plus one phase
+__host__ __device__ constexpr int class_rounds(int part) { return part == 3 ? 16 : 32; }
+__host__ __device__ constexpr int queue_len(int part) { return 2 * 31 + 32 * class_rounds(part) + 2; }
 
-template <int NW>
+// Shared memory of one k_iterate block; the regulator and group arrays exist only in their parts
+// (PART bit 0: regulator, bit 1: group), which leaves the plain kernel room for long pre-test phases.
+template <int NW, int PART = 0>
 struct alignas(16) ChunkSmemT {
     DiagRec rec;
     Grid2 grid[kMaxD * kGridStride];
     float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
-    double cacc[2 * kComp][NW * 32];         // per-thread sums of the regulator components
-    double gacc[kGroupSlots][NW * 32];       // group integrals: per-sample sums over the members
-    uint32_t queue[NW][kQueue];              // mixed precision: per-warp stacks of samples past the pre-test
+    double cacc[(PART & 1) ? 2 * kComp : 1][NW * 32];   // per-thread sums of the regulator components
+    double gacc[(PART & 2) ? kGroupSlots : 1][NW * 32];  // group integrals: per-sample sums over the members
+    uint32_t queue[NW][queue_len(PART)];     // per-warp stacks of samples past the pre-test
                                              // (away from a Fermi surface from the bottom, near one from the top)
     double red[2][NW];
-    double redc[2 * kComp][NW];
+    double redc[(PART & 1) ? 2 * kComp : 1][NW];
     uint32_t chunk, item, iter, skip;
 };
-using ChunkSmem = ChunkSmemT<kWarps>;
+using ChunkSmem = ChunkSmemT<kWarps, 0>;
 
 __device__ __forceinline__ void load_record(DiagRec* dst, const DiagRec* src) {
     const uint4* s = reinterpret_cast<const uint4*>(src);
@@ -111,7 +116,7 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  Plain integrals, every precision: the FP64 pipe issues per warp instruction, so a warp whose
 //  lanes hold a mix of zero and live samples pays for the zero ones, and (mixed mode) one whose lanes
 //  take both sampling maps pays for both.  Each warp therefore alternates two phases, each a tight loop over
-//  its own code: kClassRounds rounds of the FP32 front and Fermi-step pre-test, pushing the samples
+//  its own code: class_rounds() rounds of the FP32 front and Fermi-step pre-test, pushing the samples
 //  that may be live onto one of two shared-memory stacks by class (away from / near a Fermi
 //  surface; ballot + prefix count), then full warps of one class popped and evaluated until fewer
 //  than 32 of each remain; the partial warps are evaluated at the end of the chunk.  Which thread
@@ -121,7 +126,7 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  above, adding the weights per sample into gacc, zeroed per chunk (spt x (1 + regulator components)
 //  <= kGroupSlots slots per thread); sums, squares and the histogram then see the group's integrand.
 template <int N, int PREC, int MAPK, bool REG, bool GRP, int NW>
-__device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
+__device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 2 : 0)>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
     const DiagRec& R = S.rec;
     const uint32_t cs = blockDim.x * (uint32_t)W.spt;
@@ -134,9 +139,14 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
     const int nb = R.nb;
     constexpr int D = 3 * (N + 1) - 3 * MAPK;
     constexpr int PER = REG ? 1 + kComp : 1;        // group slots per sample
+    constexpr int kRounds = class_rounds((REG ? 1 : 0) | (GRP ? 2 : 0));
+    constexpr int kQ = queue_len((REG ? 1 : 0) | (GRP ? 2 : 0));
+    // (the plain kernels keep the direct loop as a runtime branch that never runs: with the loop
+    // structure fixed at compile time their register allocation is worse -- measured 1 KB stack
+    // frame instead of 120 B, and 2 % slower)
     const int nm = GRP ? (int)W.n_members : 1;
     constexpr bool grp = GRP;
-    constexpr bool compact = true;
+    const bool compact = GRP || W.n_members <= 1;
     for (int m = 0; m < nm; ++m) {
         if (m > 0) {
             __syncthreads();
@@ -151,7 +161,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
             int cnt = 0;
             if (compact) {
                 if (!drain && nf < 32 && nn < 32) {
-                    const int jend = (j + kClassRounds < W.spt) ? j + kClassRounds : W.spt;
+                    const int jend = (j + kRounds < W.spt) ? j + kRounds : W.spt;
                     for (; j < jend; ++j) {
                         const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
                         const int cls = sc < W.samples
@@ -161,7 +171,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
                         const uint32_t b0 = __ballot_sync(0xffffffffu, cls == 1);
                         const uint32_t b1 = __ballot_sync(0xffffffffu, cls == 2);
                         if (cls == 1) q[nf + __popc(b0 & lt)] = (uint32_t)sc;
-                        if (cls == 2) q[kQueue - 1 - (nn + __popc(b1 & lt))] = (uint32_t)sc;
+                        if (cls == 2) q[kQ - 1 - (nn + __popc(b1 & lt))] = (uint32_t)sc;
                         nf += __popc(b0);
                         nn += __popc(b1);
                     }
@@ -175,7 +185,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW>& S, const WorkItem& W, 
                 else if (drain) break;
                 else continue;
                 have = (int)lane < cnt;
-                s = !have ? 0u : (use_near ? q[kQueue - 1 - (nn - cnt + (int)lane)] : q[nf - cnt + (int)lane]);
+                s = !have ? 0u : (use_near ? q[kQ - 1 - (nn - cnt + (int)lane)] : q[nf - cnt + (int)lane]);
             } else {
                 if (j >= W.spt) break;
                 s = first + (uint64_t)j * blockDim.x + threadIdx.x;
@@ -273,7 +283,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
                                                double* __restrict__ csum, float* __restrict__ chist) {
     constexpr int NW = TPB / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ChunkSmemT<NW>& S = *reinterpret_cast<ChunkSmemT<NW>*>(smem_raw);
+    ChunkSmemT<NW, PART>& S = *reinterpret_cast<ChunkSmemT<NW, PART>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr bool REGP = (PART & 1) != 0, GRPP = (PART & 2) != 0;
     uint32_t item0 = 0, chunk0 = 0;
@@ -322,8 +332,10 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
         const int prec = effective_precision(S.rec.precision, W.grid, d, nb);
         load_grid(S.grid, W.grid, d, nb, prec);
         for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
-        for (int c = 0; c < 2 * kComp; ++c) S.cacc[c][tid] = 0.0;
-        for (int c = 0; c < kGroupSlots; ++c) S.gacc[c][tid] = 0.0;
+        if constexpr (REGP)
+            for (int c = 0; c < 2 * kComp; ++c) S.cacc[c][tid] = 0.0;
+        if constexpr (GRPP)
+            for (int c = 0; c < kGroupSlots; ++c) S.gacc[c][tid] = 0.0;
         __syncthreads();
         double sw = 0.0, sw2 = 0.0;
         const uint32_t cl = chunk - W.chunk_begin;
@@ -349,7 +361,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             S.red[1][warp] = sw2;
         }
         __syncthreads();
-        if (REGP) {
+        if constexpr (REGP) {
             for (int c = 0; c < 2 * kComp; ++c) {
                 const double v = warp_sum(S.cacc[c][tid]);
                 if (lane == 0) S.redc[c][warp] = v;
@@ -364,7 +376,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             }
             csum[kSumStride * (size_t)chunk] = a;
             csum[kSumStride * (size_t)chunk + 1] = b;
-            if (REGP)
+            if constexpr (REGP)
                 for (int c = 0; c < 2 * kComp; ++c) {
                     double v = 0.0;
                     for (int w = 0; w < NW; ++w) v += S.redc[c][w];

@@ -112,14 +112,16 @@ constexpr int kParts = 4;      // plain, plain + regulator, group, group + regul
 struct KernelVariant {
     int tpb, minb;
     IterateFn fn[kParts];
-    size_t smem;
+    size_t smem[kParts];
 };
+#define MBPT_SMEM(NW) {sizeof(ChunkSmemT<NW, 0>), sizeof(ChunkSmemT<NW, 1>), sizeof(ChunkSmemT<NW, 2>), sizeof(ChunkSmemT<NW, 3>)}
 const KernelVariant kVariants[] = {
-    {256, 2, {k_iterate_256x2, k_iterate_256x2_reg, k_iterate_256x2_grp, k_iterate_256x2_grp_reg}, sizeof(ChunkSmemT<8>)},
-    {128, 4, {k_iterate_128x4, k_iterate_128x4_reg, k_iterate_128x4_grp, k_iterate_128x4_grp_reg}, sizeof(ChunkSmemT<4>)},
-    {256, 1, {k_iterate_256x1, k_iterate_256x1_reg, k_iterate_256x1_grp, k_iterate_256x1_grp_reg}, sizeof(ChunkSmemT<8>)},
-    {128, 3, {k_iterate_128x3, k_iterate_128x3_reg, k_iterate_128x3_grp, k_iterate_128x3_grp_reg}, sizeof(ChunkSmemT<4>)},
+    {256, 2, {k_iterate_256x2, k_iterate_256x2_reg, k_iterate_256x2_grp, k_iterate_256x2_grp_reg}, MBPT_SMEM(8)},
+    {128, 4, {k_iterate_128x4, k_iterate_128x4_reg, k_iterate_128x4_grp, k_iterate_128x4_grp_reg}, MBPT_SMEM(4)},
+    {256, 1, {k_iterate_256x1, k_iterate_256x1_reg, k_iterate_256x1_grp, k_iterate_256x1_grp_reg}, MBPT_SMEM(8)},
+    {128, 3, {k_iterate_128x3, k_iterate_128x3_reg, k_iterate_128x3_grp, k_iterate_128x3_grp_reg}, MBPT_SMEM(4)},
 };
+#undef MBPT_SMEM
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 }  // namespace
 
@@ -240,8 +242,8 @@ int capture_graph(mbpt_ctx* c) {
     const KernelVariant& kv = kVariants[c->variant];
     // the blocks of an empty part exit at once
     for (int p = 0; p < kParts; ++p)
-        kv.fn[p]<<<c->variant_blocks[c->variant][p], kv.tpb, kv.smem, c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
-                                                                                   c->d_chist);
+        kv.fn[p]<<<c->variant_blocks[c->variant][p], kv.tpb, kv.smem[p], c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
+                                                                                      c->d_chist);
     cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal);
     k_finalize<<<c->finalize_blocks, 256, 0, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist,
                                                          c->d_last_hist);
@@ -330,8 +332,9 @@ int mbpt_ctx_create(mbpt_ctx** out, int device, void* arena, size_t arena_bytes,
         const KernelVariant& kv = kVariants[v];
         for (int p = 0; p < kParts; ++p) {
             int per_sm = 0;
-            e = cudaFuncSetAttribute(kv.fn[p], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv.fn[p], kv.tpb, kv.smem);
+            e = cudaFuncSetAttribute(kv.fn[p], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem[p]);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv.fn[p], kv.tpb, kv.smem[p]);
             if (e != cudaSuccess || per_sm < 1) {
                 if (c->own_stream) cudaStreamDestroy(c->stream);
                 if (c->own_arena) cudaFree(base);

@@ -136,11 +136,12 @@ _lib = None
 
 
 def lib():
-    """Load the in-tree libmbpt.so (building it first if it is missing or stale)."""
+    """Load the in-tree libmbpt.so (building it first if it is missing), or the library named by the
+    MBPT_LIBRARY environment variable (another build of the same sources)."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if not os.path.exists(path) or os.environ.get("MBPT_REBUILD"):
+        path = os.environ.get("MBPT_LIBRARY") or _build.LIB
+        if path == _build.LIB and (not os.path.exists(path) or os.environ.get("MBPT_REBUILD")):
             _build.build()
         L = ctypes.CDLL(path)
         P = ctypes.POINTER
