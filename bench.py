@@ -45,7 +45,7 @@ WORKLOAD = "third-order Hugenholtz diagrams (pp, hh, ph), pure neutron matter, k
 FP64_OPS_LIVE = 60.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_iterate_256x2 launch on the 30 x 2^20 profiling case
 # (profiles/k_iterate_third_order_scan.md): records and grids; not proportional to samples
-TRAFFIC_BYTES = 390656
+TRAFFIC_BYTES = 974336
 # nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second
 FP64_PEAK_NOMINAL = 1.25e12 / 2.0
 # measured DFMA issue rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu)
