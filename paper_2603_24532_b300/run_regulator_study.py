@@ -1,4 +1,4 @@
-"""Denominator-regulator study (Sec. III.A): every fourth-order diagram of neutron matter at one density,
+"""Denominator-regulator study (Sec. III.A): every fourth-order diagram of neutron (or symmetric) matter at one density,
 integrated with three energy-denominator shifts and their quadratic extrapolation to zero shift beside
 the unregulated estimate, on identical samples.  Mirror partners (equal integrals by symmetry) measure
 how far each estimate can be trusted: their difference in units of the combined error.
@@ -27,10 +27,11 @@ def main():
     ap.add_argument("--shifts", type=float, nargs=3, default=(1.0, 2.0, 3.0))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--map-kind", type=int, default=0)
+    ap.add_argument("--snm", action="store_true", help="symmetric matter (kF_p = kF_n) instead of neutron matter")
     a = ap.parse_args()
     prec = M.MBPT_MIXED if a.precision == "mixed" else M.MBPT_FP64
     ctx = M.mbpt_ctx_create(0, 4 << 30)
-    ph = M.physics(kF_n=a.kf, K_max=a.kf + 6.0, map_kind=a.map_kind)
+    ph = M.physics(kF_n=a.kf, kF_p=a.kf if a.snm else 0.0, K_max=a.kf + 6.0, map_kind=a.map_kind)
     descs = [d for d in M.mbpt_generate(4) if not d.anomalous]
     gs = [M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=a.samples, seed=7, stream_id=d.diagram_id,
                                                         precision=prec, shifts=a.shifts, train_iters=2))
@@ -58,8 +59,9 @@ def main():
     tot_sig = {"mean": float(math.sqrt(sum(r["sigma"] ** 2 for r in rows.values()))),
                "extrapolated": float(math.sqrt(sum(r["extrapolated_sigma"] ** 2 for r in rows.values())))}
     chi2 = [r["chi2"] for r in rows.values()]
-    out = {"workload": "33 non-anomalous fourth-order diagrams, PNM kF %.2f, %s, %d x %d samples (2 training), "
-                       "shifts %s MeV" % (a.kf, a.precision, a.iters, a.samples, list(a.shifts)),
+    out = {"workload": "33 non-anomalous fourth-order diagrams, %s kF %.2f, %s, %d x %d samples (2 training), "
+                       "shifts %s MeV" % ("SNM" if a.snm else "PNM", a.kf, a.precision, a.iters, a.samples,
+                                          list(a.shifts)),
            "E4_unregulated": tot["mean"], "sigma_unregulated": tot_sig["mean"],
            "E4_extrapolated": tot["extrapolated"], "sigma_extrapolated": tot_sig["extrapolated"],
            "E4_shifted": [float(sum(r["shifted"][k] for r in rows.values())) for k in range(3)],
