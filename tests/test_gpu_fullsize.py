@@ -133,3 +133,30 @@ def test_fifth_order_all_diagrams_shape(ctx):
         if O.is_anomalous(s[0]):
             assert res[i].last_mean == 0.0 and res[i].last_sigma == 0.0
         assert np.isfinite(res[i].last_mean)
+
+
+@pytest.mark.parametrize("prec", [M.MBPT_MIXED, M.MBPT_MIXED_MAP64, M.MBPT_FP64])
+def test_batched_sum_equals_every_sample_dumped(ctx, prec):
+    """The batched iteration (FP32 pre-test, compacted evaluation) against the sum of every sample
+    evaluated individually (no pre-test), for all 33 live fourth-order diagrams of symmetric matter at
+    kF = 1.6 on adapted grids: a live sample the pre-test wrongly dropped would show here."""
+    po, pm = _pair(1.6, 1.6)
+    Ds = [D for D in O.enumerate_diagrams(4) if not O.is_anomalous(D)]
+    n = 1 << 18
+    gs = [M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=n, seed=3, stream_id=70 + D.diagram_id,
+                                                                   precision=prec)) for D in Ds]
+    try:
+        M.mbpt_vegas_iterate(ctx, gs, 4)                    # adapt the grids
+        pre = [M.mbpt_get_state(g) for g in gs]
+        M.mbpt_vegas_iterate(ctx, gs, 1)
+        res = M.mbpt_estimate_batch(gs)
+        for g, D, img, r in zip(gs, Ds, pre, res):
+            post = M.mbpt_get_state(g)
+            M.mbpt_set_state(g, img)
+            _, w = M.mbpt_dump_samples(g, 4, 0, n, D.d, with_x=False)
+            M.mbpt_set_state(g, post)
+            s = float(np.sum(w))
+            assert s / n == pytest.approx(r.last_mean, rel=1e-10, abs=1e-12 * float(np.sum(np.abs(w))) / n), D.diagram_id
+    finally:
+        for g in gs:
+            M.mbpt_destroy_diagram(g)
