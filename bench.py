@@ -216,14 +216,15 @@ def run_gpu(args):
     it_ms = float(np.mean(ms_it))
     achieved = ops * evals_step / (it_ms * 1e-3)
 
-    # ---- e2e through the public API: per step H2D of the work table inside mbpt_vegas_iterate and a
-    # D2H read of every integral's estimate
-    h2d = n_int * (96 + 8) + 32
+    # ---- e2e through the public API: per step H2D of the work table inside mbpt_vegas_iterate (a
+    # 96-byte item and an 8-byte histogram pointer per integral, an 80-byte header) and a D2H read of
+    # every integral's estimate with one synchronisation (80 bytes each, and the 4-byte error word)
+    h2d = n_int * (96 + 8) + 80
     d2h = n_int * 80 + 4
     t0 = time.perf_counter()
     for _ in range(args.steps):
         M.mbpt_vegas_iterate(ctx, gs, 1)
-        _ = [M.mbpt_estimate(g).mean for g in gs]
+        _ = [r.mean for r in M.mbpt_estimate_batch(gs)]
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_value = world * evals_step / e2e_s
     # ---- precision: mixed modes vs FP64 on identical counters and grids, paired over several
