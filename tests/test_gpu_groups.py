@@ -180,3 +180,27 @@ def test_group_errors(ctx):
         M.mbpt_create_group(ctx, [d3, d3], pm, cfg, scales=[1.0, float("nan")])
     g = M.mbpt_create_group(ctx, [d3], pm, cfg)                 # one member: a plain integral
     M.mbpt_destroy_diagram(g)
+
+
+def test_group_with_hartree_fock_spectrum_and_regulator(ctx):
+    """The three options together: a group integral in the Hartree-Fock spectrum with denominator
+    shifts; its plain estimate and each shifted component after one iteration equal the oracle's
+    group iteration with the same spectrum and shift (FP64)."""
+    rng = np.random.default_rng(21)
+    po, pm = matter_pair("snm", spectrum=1)
+    G = _group(3, 3, 2)
+    shifts = (1.5, 3.0, 4.5)
+    M_s = 8000 + 3
+    g = _create(ctx, G, pm, M.vegas_cfg(samples=M_s, seed=8, stream_id=41, precision=M.MBPT_FP64, shifts=shifts))
+    try:
+        grid = random_grid(G.d, 50, rng, strength=0.4)
+        M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+        M.mbpt_vegas_iterate(ctx, [g], 1)
+        assert M.mbpt_estimate(g).last_mean == pytest.approx(O.vegas_iteration(G, po, grid, 8, 41, 0, M_s).mean,
+                                                             rel=1e-11)
+        mean, _ = M.mbpt_estimate_shifts(g)
+        for k, s in enumerate(shifts):
+            ref = O.vegas_iteration(G, dataclasses.replace(po, shift=s), grid, 8, 41, 0, M_s)
+            assert mean[k] == pytest.approx(ref.mean, rel=1e-11)
+    finally:
+        M.mbpt_destroy_diagram(g)
