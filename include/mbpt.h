@@ -78,6 +78,7 @@ typedef enum {
 /* descriptor flags */
 #define MBPT_FLAG_ANOMALOUS   1   /* a hole and a particle forced to equal momentum: zero at T = 0 */
 #define MBPT_FLAG_SELF_MIRROR 2   /* equal to its own time-and-arrow reversal */
+#define MBPT_FLAG_REPEATED_DENOMINATOR 4   /* two cuts with the same energy denominator (a 1/D^2 factor) */
 
 /*
  * One Hugenholtz diagram with two-body vertices (Sec. II, Table I).

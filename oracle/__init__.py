@@ -460,6 +460,22 @@ class IterationResult:
         return (self.sum_w2 / self.n - self.mean ** 2) / (self.n - 1)
 
 
+def has_repeated_denominator(D: Diagram) -> bool:
+    """Two cuts whose energy denominators are the same function of the loop momenta (a squared
+    denominator, e.g. a self-energy insertion).  D_m = sum_h |k_h|^2 - sum_p |k_p|^2 with
+    k_l = sum_c C_lc l_c is the quadratic form sum_l s_l C_l C_l^T (s = +1 hole, -1 particle) in the
+    loop momenta: compare the integer matrices."""
+    C = D.coef().astype(np.int64)
+    forms = []
+    for m in range(D.n - 1):
+        Q = np.zeros((C.shape[1], C.shape[1]), dtype=np.int64)
+        for l, (a, b) in enumerate(D.lines):
+            if min(a, b) <= m < max(a, b):
+                Q += (1 if D.hole(l) else -1) * np.outer(C[l], C[l])
+        forms.append(Q.tobytes())
+    return len(set(forms)) < len(forms)
+
+
 def hole_chords(D: Diagram) -> int:
     """Number of loop momenta that are hole momenta (integrated over the Fermi ball): the
     particle-hole composition of the integration domain.  Grouping key of Sec. III.A (reading): at

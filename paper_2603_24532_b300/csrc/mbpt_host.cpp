@@ -186,6 +186,27 @@ bool anomalous(const mbpt_diagram_desc& d) {
     return false;
 }
 
+// Two cuts whose energy denominators are the same function of the loop momenta.  With
+// k_l = sum_c coef_lc l_c, D~_m = sum_{lines of cut m} (+1 hole, -1 particle) |k_l|^2 is the quadratic form
+// Q_m[c][c'] = sum_l s_l coef_lc coef_lc' in the loop momenta; equal integer matrices mean equal
+// denominators, and the weight carries 1/D^2 (e.g. a self-energy insertion between the two cuts).
+bool repeated_denominator(const mbpt_diagram_desc& d) {
+    const int n = d.order, nl = d.n_lines, nc = d.n_chords;
+    std::vector<std::vector<int>> Q((size_t)(n > 1 ? n - 1 : 0), std::vector<int>((size_t)(nc * nc), 0));
+    for (int m = 0; m < n - 1; ++m)
+        for (int l = 0; l < nl; ++l) {
+            const int lo = std::min(d.line_src[l], d.line_dst[l]), hi = std::max(d.line_src[l], d.line_dst[l]);
+            if (!(lo <= m && m < hi)) continue;
+            const int sgn = d.line_src[l] > d.line_dst[l] ? 1 : -1;
+            for (int a = 0; a < nc; ++a)
+                for (int b = 0; b < nc; ++b) Q[(size_t)m][(size_t)(a * nc + b)] += sgn * d.line_coef[l][a] * d.line_coef[l][b];
+        }
+    for (int a = 0; a < n - 1; ++a)
+        for (int b = a + 1; b < n - 1; ++b)
+            if (Q[(size_t)a] == Q[(size_t)b]) return true;
+    return false;
+}
+
 Mat mirror(int n, const Mat& A) {
     Mat M{};
     for (int i = 0; i < n; ++i)
@@ -637,6 +658,7 @@ extern "C" int mbpt_generate(int order, mbpt_diagram_desc* out, int cap, int* co
         int flags = 0;
         if (anomalous(out[k])) flags |= MBPT_FLAG_ANOMALOUS;
         if (out[k].mirror_id == k) flags |= MBPT_FLAG_SELF_MIRROR;
+        if (repeated_denominator(out[k])) flags |= MBPT_FLAG_REPEATED_DENOMINATOR;
         out[k].flags = flags;
     }
     return MBPT_OK;

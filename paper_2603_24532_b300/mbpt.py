@@ -29,6 +29,7 @@ MAX_CHORDS = 7
 MAX_BINS = 64
 FLAG_ANOMALOUS = 1
 FLAG_SELF_MIRROR = 2
+FLAG_REPEATED_DENOMINATOR = 4
 
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDEVICE", -5: "ETIMEOUT", -6: "ENUMERIC",
            -7: "EBUSY"}
@@ -73,6 +74,10 @@ class mbpt_diagram_desc(ctypes.Structure):
     @property
     def anomalous(self) -> bool:
         return bool(self.flags & FLAG_ANOMALOUS)
+
+    @property
+    def repeated_denominator(self) -> bool:
+        return bool(self.flags & FLAG_REPEATED_DENOMINATOR)
 
     @classmethod
     def from_lists(cls, order, lines, ports, chords, coef, diagram_id=-1, mirror_id=-1, flags=0):

@@ -50,10 +50,19 @@ def main():
     per_point = {}
     for kf, kfp, mi, ki in points:
         idx = [i for i, m in enumerate(meta) if m[0] == kf and m[1] == kfp]
+        rep = [i for i in idx if meta[i][3].repeated_denominator]
+        rest = [i for i in idx if not meta[i][3].repeated_denominator]
         per_point["%s kF=%.2f" % ("SNM" if kfp else "PNM", kf)] = {
             "E4": float(sum(res[i].mean for i in idx)),
             "sigma": float(math.sqrt(sum(res[i].sigma ** 2 for i in idx))),
-            "max_chi2_dof": float(max(res[i].chi2_dof for i in idx))}
+            "max_chi2_dof": float(max(res[i].chi2_dof for i in idx)),
+            "repeated_denominator": {"integrals": len(rep), "sum": float(sum(res[i].mean for i in rep)),
+                                     "sigma": float(math.sqrt(sum(res[i].sigma ** 2 for i in rep))),
+                                     "max_chi2_dof": float(max(res[i].chi2_dof for i in rep))},
+            "others": {"integrals": len(rest), "sum": float(sum(res[i].mean for i in rest)),
+                       "sigma": float(math.sqrt(sum(res[i].sigma ** 2 for i in rest))),
+                       "max_chi2_dof": float(max(res[i].chi2_dof for i in rest)),
+                       "median_chi2_dof": float(np.median([res[i].chi2_dof for i in rest]))}}
 
     dev = None
     if a.oracle_integrals > 0:

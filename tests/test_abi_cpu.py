@@ -46,6 +46,7 @@ def test_generator_matches_oracle_enumeration(n):
         assert d.mirror_id == idx[O.mirror_matrix(D.A)]
         assert bool(d.flags & M.FLAG_SELF_MIRROR) == (O.mirror_matrix(D.A) == D.A)
         assert M.mbpt_hole_chords(d) == O.hole_chords(D)
+        assert d.repeated_denominator == O.has_repeated_denominator(D)
 
 
 def test_generator_argument_errors():

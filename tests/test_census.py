@@ -89,3 +89,28 @@ def test_momentum_conservation_rows():
                 e = np.zeros(n + 1, dtype=int)
                 e[c] = 1
                 assert (C[l] == e).all()
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_repeated_denominators(n):
+    """Diagrams with two cuts carrying the same energy denominator (a 1/D^2 factor): the symbolic
+    criterion (equal quadratic forms of the cuts in the loop momenta) agrees with evaluating every
+    cut's denominator at random loop momenta; 0, 4 and 124 diagrams at orders 3, 4, 5 (64 of the 124
+    at fifth order are not anomalous)."""
+    rng = np.random.default_rng(n)
+    count = 0
+    for D in O.enumerate_diagrams(n):
+        C = D.coef()
+        k = rng.normal(size=(D.n + 1, 3))
+        lines = C @ k
+        ksq = np.sum(lines ** 2, axis=1)
+        Ds = []
+        for m in range(D.n - 1):
+            Ds.append(sum((ksq[l] if D.hole(l) else -ksq[l]) for l, (a, b) in enumerate(D.lines)
+                          if min(a, b) <= m < max(a, b)))
+        numeric = any(abs(Ds[a] - Ds[b]) < 1e-9 * (1 + abs(Ds[a])) for a in range(len(Ds)) for b in range(a))
+        assert numeric == O.has_repeated_denominator(D), D.diagram_id
+        count += numeric
+    assert count == {3: 0, 4: 4, 5: 124}[n]
+    if n == 5:
+        assert sum(O.has_repeated_denominator(D) and not O.is_anomalous(D) for D in O.enumerate_diagrams(5)) == 64
