@@ -8,23 +8,27 @@ namespace mbpt {
 // Grid refinement of one axis (Lepage 1978 with (7,1)/8 and (1,6,1)/8 smoothing):
 // dbar -> r = dbar/sum -> m = ((r-1)/ln r)^alpha -> new edges at equal shares of the
 // piecewise-linear cumulative of m.
-__device__ void refine_axis(double* grid, const double* old, const double* h, double* m, int nb, double alpha) {
-    m[0] = (7.0 * h[0] + h[1]) / 8.0;
-    for (int i = 1; i < nb - 1; ++i) m[i] = (h[i - 1] + 6.0 * h[i] + h[i + 1]) / 8.0;
-    m[nb - 1] = (h[nb - 2] + 7.0 * h[nb - 1]) / 8.0;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += m[i];
-    if (!(tot > 0.0)) return;
+// Grid refinement (Lepage 1978), split so that the per-bin work runs on the whole block:
+//  refine_weights (thread per bin): smoothing (7,1)/8, (1,6,1)/8, (1,7)/8 of the bin's w^2 sums, then,
+//   once the axis total is known, the compressed importance m = ((r - 1)/ln r)^alpha of r = smoothed/total;
+//  refine_rebin (thread per axis): new edges that give every bin an equal share of sum m, by linear
+//   interpolation inside the old bins.  Totals are summed in bin order, as a sequential refinement would.
+__device__ __forceinline__ double refine_smooth(const double* h, int i, int nb) {
+    if (i == 0) return (7.0 * h[0] + h[1]) / 8.0;
+    if (i == nb - 1) return (h[nb - 2] + 7.0 * h[nb - 1]) / 8.0;
+    return (h[i - 1] + 6.0 * h[i] + h[i + 1]) / 8.0;
+}
+
+__device__ __forceinline__ double refine_importance(double smoothed, double tot, double alpha) {
+    const double r = smoothed / tot;
+    if (r <= 0.0) return 0.0;
+    if (r >= 1.0) return 1.0;
+    return pow((r - 1.0) / log(r), alpha);
+}
+
+__device__ void refine_rebin(double* grid, const double* old, const double* m, int nb) {
     double msum = 0.0;
-    for (int i = 0; i < nb; ++i) {
-        const double r = m[i] / tot;
-        double v;
-        if (r <= 0.0) v = 0.0;
-        else if (r >= 1.0) v = 1.0;
-        else v = pow((r - 1.0) / log(r), alpha);
-        m[i] = v;
-        msum += v;
-    }
+    for (int i = 0; i < nb; ++i) msum += m[i];
     const double share = msum / nb;
     int j = 0;
     double cum = 0.0;
@@ -53,6 +57,7 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
     __shared__ double old[kMaxD * (MBPT_MAX_BINS + 1)];
     __shared__ double red[2][8];
     __shared__ double redq[2 * kComp][8];
+    __shared__ double axis_tot[kMaxD];
     __shared__ int s_skip, s_refine;
     const int tid = threadIdx.x;
     for (uint32_t ii = blockIdx.x; ii < hdr->n_items; ii += gridDim.x) {
@@ -172,8 +177,28 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
             s_refine = (W.freeze_after == 0u) || ((uint32_t)st->iter < W.freeze_after);
         }
         __syncthreads();
-        if (s_refine && tid < d) refine_axis(W.grid + tid * (nb + 1), old + tid * (nb + 1), hsum + tid * nb,
-                                             tmp + tid * MBPT_MAX_BINS, nb, W.alpha);
+        if (s_refine) {
+            for (int idx = tid; idx < d * nb; idx += blockDim.x) {
+                const int a = idx / nb, i = idx - a * nb;
+                tmp[a * MBPT_MAX_BINS + i] = refine_smooth(hsum + a * nb, i, nb);
+            }
+            __syncthreads();
+            if (tid < d) {
+                double tot = 0.0;
+                for (int i = 0; i < nb; ++i) tot += tmp[tid * MBPT_MAX_BINS + i];
+                axis_tot[tid] = tot;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < d * nb; idx += blockDim.x) {
+                const int a = idx / nb, i = idx - a * nb;
+                if (axis_tot[a] > 0.0)
+                    tmp[a * MBPT_MAX_BINS + i] = refine_importance(tmp[a * MBPT_MAX_BINS + i], axis_tot[a], W.alpha);
+            }
+            __syncthreads();
+            // an axis without weight keeps its grid
+            if (tid < d && axis_tot[tid] > 0.0)
+                refine_rebin(W.grid + tid * (nb + 1), old + tid * (nb + 1), tmp + tid * MBPT_MAX_BINS, nb);
+        }
         __syncthreads();
     }
 }
