@@ -5,7 +5,7 @@
  * nuclear equation of state up to fifth order").
  *
  * What the library computes (Sec. II, Eqs. (2)-(6); Sec. III.C):
- *   for a diagram G of order n (n = 2..5 vertices, 2n lines, n+1 loop momenta)
+ *   for a diagram G of order n (n = 2..6 vertices, 2n lines, n+1 loop momenta)
  *   and a physics point (Fermi momenta kF_n, kF_p, potential V(p,p')),
  *     E_G/N = (1/n_dens) (-1)^(h+l0) 2^(-n_eq)
  *             sum_{spins, isospins} int prod_c d^3l_c/(2pi)^3
@@ -66,11 +66,13 @@ typedef enum {
     MBPT_MIXED_MAP64 = 2  /* as MBPT_MIXED but with the sampling map in FP64 */
 } mbpt_precision;
 
-#define MBPT_MAX_ORDER 6          /* generator; the device path runs 2..5 */
-#define MBPT_MAX_DEVICE_ORDER 5
+#define MBPT_MAX_ORDER 6          /* generator */
+#define MBPT_MAX_DEVICE_ORDER 6   /* the device path runs 2..6 (Table I's sixth order: d = 21) */
 #define MBPT_MAX_LINES 12
 #define MBPT_MAX_CHORDS 7
 #define MBPT_MAX_BINS 64
+#define MBPT_MAX_GRID_CELLS 1152  /* d x n_bins of one integral (grid and histograms stay in shared
+                                     memory): at most 64 bins up to d = 18, 54 at d = 21 */
 #define MBPT_MAX_GROUP 1024       /* members of one group integral */
 #define MBPT_HF_KNOTS 1024        /* knots of the Hartree-Fock self-energy table */
 #define MBPT_HF_QUAD 64           /* Gauss-Legendre nodes per dimension of each knot's integral */
@@ -162,7 +164,8 @@ typedef struct {
  * adapts to the unshifted integrand).  Read them with mbpt_estimate_shifts.
  */
 typedef struct {
-    int32_t n_bins;            /* 2..MBPT_MAX_BINS (50 in the paper's setup) */
+    int32_t n_bins;            /* 2..MBPT_MAX_BINS and d x n_bins <= MBPT_MAX_GRID_CELLS (50 in the
+                                  paper's setup) */
     int32_t precision;         /* mbpt_precision */
     double alpha;              /* grid compression exponent, 1.5 */
     uint64_t seed;
@@ -205,8 +208,8 @@ int mbpt_generate(int order, mbpt_diagram_desc* out, int cap, int* count);
 /*
  * Grouping key of a descriptor (grouped evaluation, Sec. III.A and Table I's N_grp): the number of
  * its loop momenta (chords) that are hole lines, i.e. how many integration momenta lie in the Fermi
- * ball.  Diagrams of one order with equal keys share the integration domain; at orders 2..5 the key
- * takes 1, 2, 4 and 5 distinct values.  MBPT_EINVAL for a NULL argument or bad chord index.
+ * ball.  Diagrams of one order with equal keys share the integration domain; at orders 2..6 the key
+ * takes 1, 2, 4, 5 and 6 distinct values.  MBPT_EINVAL for a NULL argument or bad chord index.
  */
 int mbpt_hole_chords(const mbpt_diagram_desc* desc, int* out);
 
@@ -268,7 +271,7 @@ int mbpt_ctx_stream(const mbpt_ctx* ctx, void** cuda_stream);
  * Validate and compile a descriptor for a physics point into a device-resident
  * integral with a uniform VEGAS grid.  Returns MBPT_EINVAL for an invalid
  * descriptor (ports not matching lines, chords not completing a spanning tree,
- * line_coef violating momentum conservation, order outside 2..5), invalid
+ * line_coef violating momentum conservation, order outside 2..6), invalid
  * physics (kF < 0, both kF zero, K_max <= kF, odd reg_power) or configuration,
  * and MBPT_ENOMEM when the arena cannot hold its state.
  */

@@ -18,7 +18,7 @@ DEFAULT_SPT = (8, 16, 32, 64, 128)
 
 
 def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: Optional[Sequence] = None,
-             trials: int = 2, orders: Iterable[int] = (2, 3, 4, 5)) -> Dict:
+             trials: int = 2, orders: Iterable[int] = (2, 3, 4, 5, 6)) -> Dict:
     if not diags:
         raise ValueError("autotune needs a non-empty batch")
     states = [M.mbpt_get_state(g) for g in diags]

@@ -132,12 +132,11 @@ struct Grid4f {
     float e, de, pad0, pad1;
 };
 
-constexpr int kGridStride = MBPT_MAX_BINS;   // bins per axis row in shared memory
 
 // Result of one sample.
 struct SampleOut {
     double w;              // J_vegas * f(x)
-    uint32_t binpack[5];   // bin index of axis a in byte (a & 3) of word a >> 2
+    uint32_t binpack[kBinWords];   // bin index of axis a in byte (a & 3) of word a >> 2
     double wc[kComp];      // regulator components (shifted denominators, extrapolation); if n_shifts
 };
 
@@ -294,7 +293,7 @@ __device__ __forceinline__ void chords_fp64(const DiagRec& R, const double (&x)[
 // only), and the Jacobian outputs are not computed.
 template <int N, int MAPK, int D, int GRID = 0>
 __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid2* __restrict__ gs, const uint32_t* u,
-                                            uint32_t nb, float (&xf)[D], uint32_t (&binpack)[5], float& mp,
+                                            uint32_t nb, float (&xf)[D], uint32_t (&binpack)[kBinWords], float& mp,
                                             int& ex, bool& zero_bin, float (&kmag)[N + 1],
                                             float (&kdir)[3][N + 1], float (&lf)[3][N + 1]) {
     mp = 1.0f;
@@ -307,14 +306,14 @@ __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid2* __res
         const uint32_t fb = (uint32_t)((r >> 10) & 0x7FFFFFull);          // top 23 bits of the fraction
         const float frac = __uint_as_float(0x3F800000u | fb) - 1.0f;
         if constexpr (GRID == 0) {
-            const Grid4f g = reinterpret_cast<const Grid4f*>(gs)[a * kGridStride + i];
+            const Grid4f g = reinterpret_cast<const Grid4f*>(gs)[a * grid_stride(D) + i];
             xf[a] = fmaf(frac, g.de, g.e);
             const uint32_t bits = __float_as_uint(g.de);
             zero_bin |= (bits == 0u);
             ex += (int)(bits >> 23) - 127;
             mp *= __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
         } else {
-            const Grid2 g = gs[a * kGridStride + i];
+            const Grid2 g = gs[a * grid_stride(D) + i];
             xf[a] = fmaf(GRID == 1 ? frac : 1.0f + frac, narrow_trunc(g.de), narrow_trunc(g.a));
         }
         binpack[a >> 2] |= i << (8 * (a & 3));
@@ -461,7 +460,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
     float lf[3][L];           // chord momenta in FP32 for the potentials
     double jv = 1.0, jc = 1.0;
 #pragma unroll
-    for (int w = 0; w < 5; ++w) o.binpack[w] = 0;
+    for (int w = 0; w < kBinWords; ++w) o.binpack[w] = 0;
     if (PREC == MBPT_MIXED) {
         // Sampling map in FP32.  It only decides where the sample lies: each chord momentum is the
         // exact FP64 product of an FP32 magnitude and an FP32 unit direction, so lines, steps and
@@ -546,7 +545,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
             const uint32_t i = (uint32_t)(r >> 33);
             const uint64_t fb = r & ((1ull << 33) - 1ull);
             const double m = __longlong_as_double((long long)(0x3FF0000000000000ull | (fb << 19)));   // 1 + frac
-            const Grid2 g = gs[a * kGridStride + i];
+            const Grid2 g = gs[a * grid_stride(D) + i];
             if (PREC == MBPT_FP64) x[a] = fma(m - 1.0, g.de, g.a);
             else x[a] = fma(m, g.de, g.a);
             jv *= g.de;
@@ -751,7 +750,7 @@ __device__ __forceinline__ int sample_class(const DiagRec& R, const Grid2* __res
 #pragma unroll
     for (int j = 0; j < NBLK; ++j) philox4x32_10(s, t, sid, (uint32_t)j, k0, k1, &u[4 * j]);
     float xf[D];
-    uint32_t bp[5] = {0u, 0u, 0u, 0u, 0u};
+    uint32_t bp[kBinWords] = {};
     float mp, kmag[L], kdir[3][L], lf[3][L];
     int ex;
     bool zero_bin, near;

@@ -222,7 +222,7 @@ void set_err(char* err, size_t len, const char* msg) {
 
 int validate_descriptor(const mbpt_diagram_desc& d, char* err, size_t errlen) {
     int n = d.order;
-    if (n < 2 || n > MBPT_MAX_DEVICE_ORDER) { set_err(err, errlen, "order must be 2..5"); return MBPT_EINVAL; }
+    if (n < 2 || n > MBPT_MAX_DEVICE_ORDER) { set_err(err, errlen, "order must be 2..6"); return MBPT_EINVAL; }
     int nl = d.n_lines;
     if (nl != 2 * n) { set_err(err, errlen, "n_lines must be 2*order"); return MBPT_EINVAL; }
     for (int l = 0; l < nl; ++l) {
@@ -336,6 +336,12 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
     r->map_kind = ph.map_kind;
     r->d = 3 * nc - 3 * ph.map_kind;
     r->nb = cfg.n_bins;
+    if (r->nb > grid_stride(r->d)) {
+        if (err && errlen)
+            snprintf(err, errlen, "n_bins %d too large for d = %d (at most %d: d x n_bins <= %d)", r->nb, r->d,
+                     grid_stride(r->d), kCells);
+        return MBPT_EINVAL;
+    }
     r->precision = cfg.precision;
     r->reg_half = ph.reg_power / 2;
     r->all_slots = (1u << nl) - 1u;
@@ -464,18 +470,17 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
                 bool first = d.vtx_in[v][0] == l;
                 l = (first != ex) ? d.vtx_out[v][0] : d.vtx_out[v][1];
             }
-            if (loops < kMaxLoops) r->loop_mask[term][loops] = mask;
+            if (loops < kMaxLoops) r->loop_mask[term][loops] = (uint16_t)mask;
             ++loops;
         }
         if (loops > kMaxLoops) {
             set_err(err, errlen, "internal: too many loops");
             return MBPT_EINVAL;
         }
-        r->nloops[term] = loops;
+        r->nloops[term] = (int8_t)loops;
         r->gsign_f[term] = (loops & 1) ? -1.0f : 1.0f;
         double c = ((loops & 1) ? -1.0 : 1.0) * pow(g, loops);
         r->gcoef_d[term] = c;
-        r->gcoef_f[term] = (float)c;
     }
     // difference form: superset sums of the coefficients, signed by the subset size (exact integers)
     for (int a = 0; a < (1 << n); ++a) {

@@ -9,9 +9,22 @@
 
 namespace mbpt {
 
-constexpr int kMaxD = 3 * (MBPT_MAX_DEVICE_ORDER + 1);   // 18 dimensions at order 5
-constexpr int kMaxTerms = 1 << MBPT_MAX_DEVICE_ORDER;    // 32 spin-sum terms
+constexpr int kMaxD = 3 * (MBPT_MAX_DEVICE_ORDER + 1);   // 21 dimensions at order 6
+constexpr int kMaxTerms = 1 << MBPT_MAX_DEVICE_ORDER;    // 64 spin-sum terms
 constexpr int kMaxLoops = MBPT_MAX_DEVICE_ORDER + 1;     // loops of one term: at most n+1
+constexpr int kBinWords = (kMaxD + 3) / 4;               // words of a sample's packed bin indices (8 bits per axis)
+// Shared-memory grid rows and histograms of one integral hold at most kCells = d x n_bins entries;
+// grid row a starts at a * grid_stride(d) (MBPT_MAX_BINS up to d = 18, 54 at d = 21)
+constexpr int kCells = MBPT_MAX_GRID_CELLS;
+#if defined(__CUDACC__)
+#define MBPT_HOST_DEVICE __host__ __device__
+#else
+#define MBPT_HOST_DEVICE
+#endif
+MBPT_HOST_DEVICE constexpr int grid_stride(int d) {
+    return d * MBPT_MAX_BINS <= kCells ? MBPT_MAX_BINS : kCells / d;
+}
+static_assert(18 * MBPT_MAX_BINS <= kCells, "orders 2..5 keep MBPT_MAX_BINS bins");
 constexpr int kMaxIters = 512;                           // iteration history kept per integral
 constexpr int kThreads = 256;                            // threads per block of the iterate kernel
 constexpr int kShifts = 3;                               // denominator-regulator components
@@ -46,14 +59,13 @@ struct alignas(16) DiagRec {
     // tree line in slot n+1+j as a chord combination (coefficients -1..1), for the FP32 step pre-test
     float tcoef[MBPT_MAX_DEVICE_ORDER][8];
     // spin(-isospin) sum, term t: bit v of t set = vertex v taken in exchange
-    float gcoef_f[kMaxTerms];                    // (-1)^L(t) g^L(t)   (one Fermi momentum)
+    double gcoef_d[kMaxTerms];                   // (-1)^L(t) g^L(t)   (one Fermi momentum)
     // the same sum with V_e = V_d - Delta at every vertex: term A (bit v set = factor Delta_v, else V_d)
     // carries (-1)^|A| sum over the terms t whose exchange set contains A of gcoef(t)
     float gdel_f[kMaxTerms];
-    double gcoef_d[kMaxTerms];
     float gsign_f[kMaxTerms];                    // (-1)^L(t)           (per-loop species sums)
-    int32_t nloops[kMaxTerms];
-    uint32_t loop_mask[kMaxTerms][kMaxLoops];
+    int8_t nloops[kMaxTerms];
+    uint16_t loop_mask[kMaxTerms][kMaxLoops];    // slots of each loop (2n <= 12 bits)
     // chord sampling: radial range [lo, lo + rng]
     double chord_lo[8], chord_rng[8];
     float chord_lo_f[8], chord_rng_f[8];

@@ -52,9 +52,9 @@ __device__ void refine_rebin(double* grid, const double* old, const double* m, i
 __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkItem* __restrict__ items,
                                                  const double* __restrict__ csum, const float* __restrict__ chist,
                                                  double* const* __restrict__ last_hist) {
-    __shared__ double hsum[kMaxD * MBPT_MAX_BINS];
-    __shared__ double tmp[kMaxD * MBPT_MAX_BINS];
-    __shared__ double old[kMaxD * (MBPT_MAX_BINS + 1)];
+    __shared__ double hsum[kCells];
+    __shared__ double tmp[kCells];
+    __shared__ double old[kCells + kMaxD];
     __shared__ double red[2][8];
     __shared__ double redq[2 * kComp][8];
     __shared__ double axis_tot[kMaxD];
@@ -180,24 +180,23 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
         if (s_refine) {
             for (int idx = tid; idx < d * nb; idx += blockDim.x) {
                 const int a = idx / nb, i = idx - a * nb;
-                tmp[a * MBPT_MAX_BINS + i] = refine_smooth(hsum + a * nb, i, nb);
+                tmp[idx] = refine_smooth(hsum + a * nb, i, nb);
             }
             __syncthreads();
             if (tid < d) {
                 double tot = 0.0;
-                for (int i = 0; i < nb; ++i) tot += tmp[tid * MBPT_MAX_BINS + i];
+                for (int i = 0; i < nb; ++i) tot += tmp[tid * nb + i];
                 axis_tot[tid] = tot;
             }
             __syncthreads();
             for (int idx = tid; idx < d * nb; idx += blockDim.x) {
-                const int a = idx / nb, i = idx - a * nb;
-                if (axis_tot[a] > 0.0)
-                    tmp[a * MBPT_MAX_BINS + i] = refine_importance(tmp[a * MBPT_MAX_BINS + i], axis_tot[a], W.alpha);
+                const int a = idx / nb;
+                if (axis_tot[a] > 0.0) tmp[idx] = refine_importance(tmp[idx], axis_tot[a], W.alpha);
             }
             __syncthreads();
             // an axis without weight keeps its grid
             if (tid < d && axis_tot[tid] > 0.0)
-                refine_rebin(W.grid + tid * (nb + 1), old + tid * (nb + 1), tmp + tid * MBPT_MAX_BINS, nb);
+                refine_rebin(W.grid + tid * (nb + 1), old + tid * (nb + 1), tmp + tid * nb, nb);
         }
         __syncthreads();
     }
@@ -215,7 +214,7 @@ __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members,
                                              uint32_t sid, uint32_t iter, uint64_t first, uint64_t count,
                                              double* xo, double* wo) {
     __shared__ DiagRec R;
-    __shared__ Grid2 gs[kMaxD * kGridStride];
+    __shared__ Grid2 gs[kCells];
     load_record(&R, rec);
     __syncthreads();
     const int prec = effective_precision(R.precision, grid, R.d, R.nb);
@@ -242,6 +241,7 @@ __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members,
                 MBPT_CASES(3)
                 MBPT_CASES(4)
                 MBPT_CASES(5)
+                MBPT_CASES(6)
 #undef MBPT_CASES
 #undef MBPT_CASE
                 default: w = 0.0;

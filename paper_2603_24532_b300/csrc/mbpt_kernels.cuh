@@ -23,8 +23,8 @@ __host__ __device__ constexpr int queue_len(int part) { return 2 * 31 + 32 * cla
 template <int NW, int PART = 0>
 struct alignas(16) ChunkSmemT {
     DiagRec rec;
-    Grid2 grid[kMaxD * kGridStride];
-    float hist[NW][kMaxD * MBPT_MAX_BINS];   // warp-private histograms
+    Grid2 grid[kCells];
+    float hist[NW][kCells];                  // warp-private histograms
     double cacc[(PART & 1) ? 2 * kComp : 1][NW * 32];   // per-thread sums of the regulator components
     double gacc[(PART & 2) ? kGroupSlots : 1][NW * 32];  // group integrals: per-sample sums over the members
     uint32_t queue[NW][queue_len(PART)];     // per-warp stacks of samples past the pre-test
@@ -56,6 +56,7 @@ __device__ __forceinline__ int effective_precision(int prec, const double* grid,
 }
 
 __device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, int nb, int prec) {
+    const int stride = grid_stride(d);
     for (int idx = threadIdx.x; idx < d * nb; idx += blockDim.x) {
         const int a = idx / nb, i = idx - a * nb;
         const double e0 = grid[a * (nb + 1) + i], e1 = grid[a * (nb + 1) + i + 1];
@@ -67,12 +68,12 @@ __device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, 
             g.de = (float)e1 - g.e;
             g.pad0 = 0.0f;
             g.pad1 = 0.0f;
-            reinterpret_cast<Grid4f*>(gs)[a * kGridStride + i] = g;
+            reinterpret_cast<Grid4f*>(gs)[a * stride + i] = g;
         } else {
             Grid2 g;
             g.de = de;
             g.a = (prec == MBPT_FP64) ? e0 : e0 - de;
-            gs[a * kGridStride + i] = g;
+            gs[a * stride + i] = g;
         }
     }
 }
@@ -96,7 +97,7 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
                                             uint32_t nb, uint32_t* binpack) {
     constexpr int NBLK = (D + 3) / 4;
 #pragma unroll
-    for (int w = 0; w < 5; ++w) binpack[w] = 0;
+    for (int w = 0; w < kBinWords; ++w) binpack[w] = 0;
 #pragma unroll
     for (int j = 0; j < NBLK; ++j) {
         uint32_t u[4];
@@ -145,7 +146,6 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
     // structure fixed at compile time their register allocation is worse -- measured 1 KB stack
     // frame instead of 120 B, and 2 % slower)
     const int nm = GRP ? (int)W.n_members : 1;
-    constexpr bool grp = GRP;
     const bool compact = GRP || W.n_members <= 1;
     for (int m = 0; m < nm; ++m) {
         if (m > 0) {
@@ -244,7 +244,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
             }
         }
         if (nonzero(w)) {
-            uint32_t bp[5];
+            uint32_t bp[kBinWords];
             sample_bins<D>((uint32_t)s, t, W.stream_id, k0, k1, (uint32_t)nb, bp);
             hist_add<D>(hist, nb, bp, w);
         }
@@ -331,7 +331,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
         const int d = S.rec.d, nb = S.rec.nb, order = S.rec.order;
         const int prec = effective_precision(S.rec.precision, W.grid, d, nb);
         load_grid(S.grid, W.grid, d, nb, prec);
-        for (int i = tid; i < NW * kMaxD * MBPT_MAX_BINS; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
+        for (int i = tid; i < NW * kCells; i += blockDim.x) (&S.hist[0][0])[i] = 0.0f;
         if constexpr (REGP)
             for (int c = 0; c < 2 * kComp; ++c) S.cacc[c][tid] = 0.0;
         if constexpr (GRPP)
@@ -349,6 +349,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
             MBPT_CASES(3)
             MBPT_CASES(4)
             MBPT_CASES(5)
+            MBPT_CASES(6)
 #undef MBPT_CASES
 #undef MBPT_CASE
             default:

@@ -135,7 +135,7 @@ struct mbpt_ctx {
     int variant = 0;                       // index into kVariants
     int variant_blocks[kNumVariants][kParts] = {};   // persistent grid of each k_iterate variant and part
     int finalize_blocks = 0;
-    int spt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};
+    int spt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16, 16};
     // batch buffers (arena)
     WorkHeader* d_hdr = nullptr;
     WorkItem* d_items = nullptr;
@@ -935,7 +935,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     char err[256] = {0};
     int st = compile_record(*desc, *ph, *cfg, &rec, err, sizeof(err));
     if (st) return fail(st, std::string("iteration_noalloc: ") + err);
-    static const int kSpt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16};   // as a fresh context (256 threads)
+    static const int kSpt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16, 16};   // as a fresh context (256 threads)
     const int spt = kSpt[rec.order];
     const uint64_t cs = (uint64_t)kThreads * (uint64_t)spt;
     const uint64_t n_chunks = (cfg->samples_per_iter + cs - 1) / cs;

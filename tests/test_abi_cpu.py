@@ -32,7 +32,7 @@ def test_generator_counts(n):
     assert len(M.mbpt_generate(n)) == want[n]
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 5])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
 def test_generator_matches_oracle_enumeration(n):
     ds = M.mbpt_generate(n)
     Os = O.enumerate_diagrams(n)

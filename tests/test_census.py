@@ -10,13 +10,13 @@ import oracle as O
 from conftest import golden_rows
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 5])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
 def test_table1_counts(n):
     want = {int(r[0]): int(r[1]) for r in golden_rows("table1_counts.txt")}
     assert len(O.enumerate_diagrams(n)) == want[n]
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 5])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
 def test_table1_group_counts(n):
     """Grouping by the number of hole loop momenta (the particle-hole composition of the integration
     domain) reproduces Table I's N_grp column, anomalous diagrams included or not."""
@@ -30,6 +30,9 @@ def test_hole_distribution_and_ladders():
     assert dict(h4) == {2: 1, 3: 7, 4: 23, 5: 7, 6: 1}
     h5 = collections.Counter(D.h for D in O.enumerate_diagrams(5))
     assert dict(h5) == {2: 1, 3: 21, 4: 207, 5: 382, 6: 207, 7: 21, 8: 1}
+    # sixth order: symmetric under h -> 2n + 2 - h (mirror), one all-pp and one all-hh ladder
+    h6 = collections.Counter(D.h for D in O.enumerate_diagrams(6))
+    assert dict(h6) == {2: 1, 3: 51, 4: 1194, 5: 6554, 6: 11700, 7: 6554, 8: 1194, 9: 51, 10: 1}
 
 
 def test_anomalous_and_mirror_structure():
@@ -37,7 +40,9 @@ def test_anomalous_and_mirror_structure():
     assert sum(O.is_anomalous(D) for D in O.enumerate_diagrams(3)) == 0
     assert sum(O.is_anomalous(D) for D in O.enumerate_diagrams(4)) == 6
     assert sum(O.is_anomalous(D) for D in O.enumerate_diagrams(5)) == 172
-    for n, selfm, orbits in ((4, 23, 27), (5, 84, 375)):
+    assert sum(O.is_anomalous(D) for D in O.enumerate_diagrams(6)) == 5728
+    eff = {int(r[0]): int(r[1]) for r in golden_rows("table1_eff.txt")}
+    for n, selfm, orbits in ((4, 23, 27), (5, 84, eff[5]), (6, 1046, eff[6])):
         Ds = O.enumerate_diagrams(n)
         idx = {D.A: k for k, D in enumerate(Ds)}
         assert sum(O.mirror_matrix(D.A) == D.A for D in Ds) == selfm
@@ -48,7 +53,7 @@ def test_anomalous_and_mirror_structure():
             assert Ds[idx[M]].h == D.h
             assert O.is_anomalous(Ds[idx[M]]) == O.is_anomalous(D)
         orb = {min(idx[D.A], idx[O.mirror_matrix(D.A)]) for D in Ds if not O.is_anomalous(D)}
-        # n = 5: equals N_diag^(eff) = 375 of Table I
+        # n = 5, 6: equal to N_diag^(eff) of Table I (375, 11269)
         assert len(orb) == orbits
 
 
