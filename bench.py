@@ -38,18 +38,22 @@ WORKLOAD = "third-order Hugenholtz diagrams (pp, hh, ph), pure neutron matter, k
 # FP64 operations per sample of an order-3 integral, mixed precision (FP32 sampling map), in the
 # formulation of csrc/mbpt_device.cuh.  A sample that fails a Fermi step by more than the FP32 error
 # bound is rejected by the FP32 pre-test with no FP64 work.  A live sample: chord momenta 3 products
-# + |l|^2 3 = 6 per chord (24; the chord Jacobians are part of the FP32 mantissa product of the VEGAS
-# Jacobian), tree lines 6 sums + |k|^2 3 = 9 per line (18), energy denominators (7 sums, 1 product),
-# weight (4 products), Newton reciprocal of the denominator product (4), sum w and sum w^2 (2) = 60.
+# + |l|^2 3 = 6 per chord (24; the chord Jacobians, the VEGAS Jacobian and the weight's constant factor
+# are one FP32 mantissa product), tree lines 6 sums + |k|^2 3 = 9 per line (18), energy denominators
+# (7 sums, 1 product), weight (2 products), Newton reciprocal of the denominator product (4), sum w and
+# sum w^2 (2) = 58.
 # (About 1 % of samples lie near a Fermi surface and are placed with the FP64 map instead.)
-FP64_OPS_LIVE = 60.0
+FP64_OPS_LIVE = 58.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_iterate_256x2 launch on the 30 x 2^20 profiling case
-# (profiles/k_iterate_third_order_scan.md): records and grids; not proportional to samples
-TRAFFIC_BYTES = 974336
+# (profiles/k_iterate_third_order_scan.md): records, grids and chunk slots, as many chunks (128 per integral)
+# as the benchmark launch; not proportional to samples
+TRAFFIC_BYTES = 670208
 # nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second
 FP64_PEAK_NOMINAL = 1.25e12 / 2.0
-# measured DFMA issue rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu)
+# measured DFMA rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu, profiles/pipe_peaks_b300.md),
+# FP64 thread operations per second at the SM clock of that run; scaled to the clock seen under load
 FP64_PEAK_MEASURED = 4.73e11
+FP64_PEAK_MEASURED_MHZ = 1938.5
 
 
 def dist_env():
@@ -396,11 +400,14 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e9, "peak": FP64_PEAK_NOMINAL / 1e9,
                      "unit": "FP64 Gop/s (DADD-equivalents)", "frac": achieved / FP64_PEAK_NOMINAL,
                      "peak_kind": "nominal 1.25 TFLOP/s FP64 of the recipe at 2032 MHz",
-                     "frac_of_measured_dfma": achieved / FP64_PEAK_MEASURED,
+                     "frac_of_measured_dfma": achieved / (FP64_PEAK_MEASURED * (clk.get("sm_mhz") or 2032.0)
+                                                          / FP64_PEAK_MEASURED_MHZ),
+                     "measured_dfma_note": "4.73e11 FP64 op/s at 1938 MHz, scaled to the median SM clock of the run",
                      "ops_per_sample": ops, "live_fraction": live_frac, "kernel": "k_iterate",
                      "kernel_ms": it_ms, "traffic": TRAFFIC_BYTES,
                      "traffic_note": "ncu dram read+write of one k_iterate launch on the 30 x 2^20 profiling case "
-                                     "(grids and records; chunk slots stay in L2), not proportional to samples"},
+                                     "(grids and records; the 128 chunk slots per integral, as many as in this "
+                                     "launch, stay in L2), not proportional to samples"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 5 * args.steps,   # per step: k_iterate parts (plain; regulated and group parts empty here), k_finalize

@@ -272,7 +272,8 @@ int mbpt_ctx_stream(const mbpt_ctx* ctx, void** cuda_stream);
  * integral with a uniform VEGAS grid.  Returns MBPT_EINVAL for an invalid
  * descriptor (ports not matching lines, chords not completing a spanning tree,
  * line_coef violating momentum conservation, order outside 2..6), invalid
- * physics (kF < 0, both kF zero, K_max <= kF, odd reg_power) or configuration,
+ * physics (kF < 0, both kF zero, K_max <= kF, odd reg_power) or configuration
+ * (including d x n_bins above MBPT_MAX_GRID_CELLS, i.e. more than 54 bins at order 6),
  * and MBPT_ENOMEM when the arena cannot hold its state.
  */
 int mbpt_create_diagram(mbpt_ctx* ctx, const mbpt_diagram_desc* desc, const mbpt_physics* physics,

@@ -505,15 +505,20 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
                 if (x_out) x_out[a] = x[a];
             }
             chords_fp64<N, MBPT_MIXED, MAPK, D>(R, x, K, U, lf, jc);
+            jv = R.pref * (jv * jc);
         } else {
             if (x_out) {
 #pragma unroll
                 for (int a = 0; a < D; ++a) x_out[a] = widen_f(xf[a]);
             }
-            // VEGAS and chord Jacobians together (mixed_front): one FP32 mantissa product and an exponent
-            // sum, no FP64 work
-            jv = zero_bin ? 0.0
-                          : __longlong_as_double(__double_as_longlong(widen_pos_normal(mp)) + ((long long)ex << 52));
+            // the weight's constant factor, VEGAS and chord Jacobians together (mixed_front): one FP32
+            // mantissa product and an exponent sum, no FP64 work
+            jv = (zero_bin || R.pref_mf == 0.0f)
+                     ? 0.0
+                     : __longlong_as_double(
+                                (long long)((unsigned long long)(__double_as_longlong(widen_pos_normal(mp * R.pref_mf)) +
+                                                                 ((long long)(ex + R.pref_e) << 52)) |
+                                            ((unsigned long long)R.pref_sign_hi << 32)));
             // exact FP64 chord momenta: products of the FP32 magnitude and direction (24 x 24 bits)
 #pragma unroll
             for (int c = 0; c < L; ++c) {
@@ -553,6 +558,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
             if (x_out) x_out[a] = x[a];
         }
         chords_fp64<N, PREC, MAPK, D>(R, x, K, U, lf, jc);
+        jv = R.pref * (jv * jc);
     }
 
     // --- tree lines from momentum conservation: k = k_a + k_b - k_c
@@ -708,17 +714,18 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         S = sum;
     }
 
-    // --- weight: w = pref * J_vegas * J_chords * S / prod_m D~_m.  A spin sum that is exactly zero
-    // (asymmetric matter: every line passes its step for some species, but no species assignment
-    // is consistent along the loops, e.g. a hole and a particle of equal momentum in different
-    // species) gives zero; the cut of such a pair can have D = 0, so the division is skipped.
+    // --- weight: w = pref * J_vegas * J_chords * S / prod_m D~_m, jv holding pref * J_vegas * J_chords.
+    // A spin sum that is exactly zero (asymmetric matter: every line passes its step for some species,
+    // but no species assignment is consistent along the loops, e.g. a hole and a particle of equal
+    // momentum in different species) gives zero; the cut of such a pair can have D = 0, so the
+    // division is skipped.
     if (!nonzero(S)) o.w = 0.0;
-    else if (PREC == MBPT_FP64) o.w = (R.pref * (jv * jc) * S) / Dprod;
-    else o.w = (R.pref * (jv * jc) * S) * rcp_scaled(Dprod);
+    else if (PREC == MBPT_FP64) o.w = (jv * S) / Dprod;
+    else o.w = (jv * S) * rcp_scaled(Dprod);
     // --- denominator regulator: every D~_m -> D~_m - eta_k (pole moved away from the domain), and
     // the quadratic through the three components evaluated at zero shift
     if constexpr (REG) {
-        const double num = nonzero(S) ? R.pref * (jv * jc) * S : 0.0;
+        const double num = nonzero(S) ? jv * S : 0.0;
         double ext = 0.0;
 #pragma unroll
         for (int k = 0; k < kShifts; ++k) {

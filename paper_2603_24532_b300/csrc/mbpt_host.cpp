@@ -281,6 +281,22 @@ int validate_descriptor(const mbpt_diagram_desc& d, char* err, size_t errlen) {
     return MBPT_OK;
 }
 
+void set_pref(DiagRec* r, double pref) {
+    r->pref = pref;
+    // FP32 mantissa and exponent of |pref| (far-class mixed samples fold it into the FP32 Jacobian);
+    // pref_mf = 0 for pref = 0
+    int e = 0;
+    float m = (float)(2.0 * std::frexp(std::fabs(pref), &e));   // in [1, 2] (0 for pref = 0), rounded to nearest
+    e -= 1;
+    if (m >= 2.0f) {
+        m = 1.0f;
+        e += 1;
+    }
+    r->pref_mf = m;
+    r->pref_e = pref == 0.0 ? 0 : e;
+    r->pref_sign_hi = std::signbit(pref) ? 0x80000000u : 0u;
+}
+
 int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbpt_vegas_cfg& cfg, DiagRec* r,
                    char* err, size_t errlen) {
     int st = validate_descriptor(d, err, errlen);
@@ -523,7 +539,7 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         if (ph.map_kind == 1 && c < 2) pref *= 4.0 * pi * r->chord_rng[c];
         else pref *= 4.0 * r->chord_rng[c];
     }
-    r->pref = pref;
+    set_pref(r, pref);
     // denominator regulator: D_m - shift in D~ units (D = (hbar^2/2m) D~), Lagrange weights at 0
     r->n_shifts = (int32_t)cfg.n_shifts;
     for (int k = 0; k < kShifts; ++k) {

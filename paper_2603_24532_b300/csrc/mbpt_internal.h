@@ -74,6 +74,10 @@ struct alignas(16) DiagRec {
     double CS, CY4, mpi2_4;                      // with P = 2p: V = [C_S + 4C_Y/(|P-P'|^2 + 4m_pi^2)] F
     double regc;                                 // (|P|^2 regc)^reg_half = (p/Lambda)^r
     double pref;                                 // all constant factors of the weight
+    float pref_mf;                               // |pref| = pref_mf 2^pref_e, pref_mf in [1, 2) (rounded to FP32)
+    int32_t pref_e;
+    uint32_t pref_sign_hi;                       // sign bit of pref in the high word of a double
+    int32_t pad_p;
     float CSf, CY4f, mpi2_4f, regc2f;            // FP32 copies; regc2f folds in log2(e)^(1/reg_half)
     int8_t line_slot[MBPT_MAX_LINES];            // slot of each descriptor line
     int32_t map_kind;                            // 0: full chord directions; 1: rotational reduction
@@ -144,6 +148,8 @@ struct alignas(16) WorkHeader {
 int compile_record(const mbpt_diagram_desc& desc, const mbpt_physics& ph, const mbpt_vegas_cfg& cfg,
                    DiagRec* rec, char* err, size_t errlen);
 int validate_descriptor(const mbpt_diagram_desc& desc, char* err, size_t errlen);
+// the weight's constant factor and its FP32 mantissa / exponent / sign fields
+void set_pref(DiagRec* rec, double pref);
 int build_hf_table(const mbpt_physics& ph, std::vector<double>& tab, char* err, size_t errlen);
 double hf_eval(const std::vector<double>& tab, double hinv, double k);
 

@@ -471,7 +471,7 @@ static int create_integral(mbpt_ctx* c, const mbpt_diagram_desc* descs, int k, c
             return fail(MBPT_EINVAL, std::string(who) + ": members must have the same order");
         if (scale) {
             if (!std::isfinite(scale[m])) return fail(MBPT_EINVAL, std::string(who) + ": non-finite member scale");
-            recs[m].pref *= scale[m];
+            set_pref(&recs[m], recs[m].pref * scale[m]);
         }
     }
     DeviceGuard dg(c->device);
