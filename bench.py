@@ -325,6 +325,22 @@ def run_gpu(args):
         M.mbpt_destroy_diagram(g)
     vg = world * n_member_evals / (float(np.mean(stg)) * 1e-3)
 
+    # ---- sixth order (Table I: 27300 diagrams, d = 21; the paper's proof-of-principle order): every
+    # non-anomalous diagram, one integral per mirror pair (11269), PNM kF = 1.33, 2^16 samples each
+    t6 = time.perf_counter()
+    ph6 = M.physics(kF_n=1.33, K_max=7.33)
+    g6 = [M.mbpt_create_diagram(ctx, d, ph6, M.vegas_cfg(samples=1 << 16, seed=1 + rank,
+                                                         stream_id=100000 * rank + d.diagram_id,
+                                                         precision=M.MBPT_MIXED))
+          for d in M.mbpt_generate(6) if not d.anomalous and d.diagram_id <= d.mirror_id]
+    create6_s = time.perf_counter() - t6
+    M.mbpt_vegas_iterate(ctx, g6, 1)
+    torch.cuda.synchronize()
+    it6, st6 = timed_steps(g6, 2)
+    for g in g6:
+        M.mbpt_destroy_diagram(g)
+    v6 = world * len(g6) * (1 << 16) / (float(np.mean(st6)) * 1e-3)
+
     # ---- FP64 batched, same workload (tuned the same way)
     g64, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
     tuned64 = autotune(ctx, g64, trials=1)["best"] if args.autotune else None
@@ -427,6 +443,10 @@ def run_gpu(args):
                                 "vs_per_diagram_batch": vg / v4,
                                 "workload": "the fourth_order_batch diagrams as 4 particle-hole groups per physics "
                                             "point (24 group integrals), mixed"},
+        "sixth_order_batch": {"value": v6, "unit": UNIT, "integrals": len(g6), "samples_per_iter": 1 << 16,
+                              "ms_per_iteration": float(np.mean(st6)), "create_s": create6_s,
+                              "workload": "27300 sixth-order diagrams, one integral per mirror pair of the 21572 "
+                                          "non-anomalous ones, PNM kF 1.33, d = 21, mixed"},
         "rotational_9d": {"value": vrot, "unit": UNIT, "kernel_ms": float(np.mean(itrot)),
                           "note": "same scan with chord 0 along z and chord 1 in the xz plane (d = 9)"},
         "serving": serving,

@@ -1,7 +1,7 @@
 """Sixth order on the device (Table I: 27300 diagrams, d = 21; evaluated by the paper with low
 statistics only): per-sample parity with the FP64 oracle on shared grids, the mixed modes on
-identical samples, one batched iteration against the oracle's, anomalous diagrams, and the
-shared-memory bin limit at d = 21."""
+identical samples, one batched iteration against the oracle's (single diagrams, a group, the
+denominator regulator), anomalous diagrams, and the shared-memory bin limit at d = 21."""
 import numpy as np
 import pytest
 
@@ -141,3 +141,54 @@ def test_bins_limited_by_shared_memory_at_d21(ctx, diagrams):
             assert M.mbpt_estimate(g).status == 0
         finally:
             M.mbpt_destroy_diagram(g)
+
+
+@pytest.mark.parametrize("prec", [M.MBPT_FP64, M.MBPT_MIXED])
+def test_sixth_order_group_one_iteration(ctx, diagrams, prec):
+    """A group of three sixth-order diagrams of one particle-hole composition (scales 1, -1, 2): one
+    iteration against the oracle's group iteration on the same grid and counters."""
+    po, pm = matter_pair("pnm")
+    key = sorted(O.groups(6))[2]
+    members = O.groups(6)[key].members[:3]
+    G = O.Group(members, [1.0, -1.0, 2.0])
+    rng = np.random.default_rng(68)
+    M_s = 12000 + 11
+    g = M.mbpt_create_group(ctx, [make_desc(D) for D in G.members], pm,
+                            M.vegas_cfg(samples=M_s, seed=2, stream_id=31, precision=prec), scales=G.scales)
+    try:
+        grid = random_grid(G.d, 50, rng, strength=0.5)
+        M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+        M.mbpt_vegas_iterate(ctx, [g], 1)
+        r = M.mbpt_estimate(g)
+        ref = O.vegas_iteration(G, po, grid, 2, 31, 0, M_s)
+        parts = [abs(c) * abs(O.vegas_iteration(D, po, grid, 2, 31, 0, M_s).sum_w) for D, c in
+                 zip(G.members, G.scales)]
+        rel = 1e-11 if prec == M.MBPT_FP64 else 1e-4
+        assert r.n_evals == M_s and r.status == 0
+        assert abs(r.last_mean * M_s - ref.sum_w) <= rel * max(abs(ref.sum_w), sum(parts))
+    finally:
+        M.mbpt_destroy_diagram(g)
+
+
+def test_sixth_order_regulator_components(ctx, diagrams):
+    """Denominator regulator at sixth order (five shifted denominators per sample): each component
+    of one iteration against the oracle's iteration with that shift."""
+    import dataclasses
+    po, pm = matter_pair("pnm")
+    rng = np.random.default_rng(69)
+    D = _pick(diagrams, 1, rng)[0]
+    shifts = (2.0, 4.0, 6.0)
+    M_s = 12000 + 5
+    g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=M_s, seed=6, stream_id=41,
+                                                                 precision=M.MBPT_FP64, shifts=shifts))
+    try:
+        grid = random_grid(D.d, 50, rng, strength=0.4)
+        M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+        M.mbpt_vegas_iterate(ctx, [g], 1)
+        mean, sigma = M.mbpt_estimate_shifts(g)
+        for k, sh in enumerate(shifts):
+            ref = O.vegas_iteration(D, dataclasses.replace(po, shift=sh), grid, 6, 41, 0, M_s)
+            assert mean[k] == pytest.approx(ref.mean, rel=1e-11)
+            assert sigma[k] == pytest.approx(np.sqrt(ref.var_of_mean), rel=1e-10)
+    finally:
+        M.mbpt_destroy_diagram(g)
