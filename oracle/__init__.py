@@ -10,7 +10,7 @@ Contents
 * ``build()`` compiles ``oracle.c`` with gcc into ``liboracle.so`` (ctypes).
 * ``enumerate_diagrams(n)`` -- brute-force list of the order-n Hugenholtz
   diagrams with two-body vertices (Table I of arXiv:2603.24532 counts them:
-  1, 3, 39, 840 at n = 2..5) in the canonical line/port/chord convention below.
+  1, 3, 39, 840, 27300 at n = 2..6) in the canonical line/port/chord convention below.
 * ``Diagram`` -- one diagram with the oracle's own derived quantities.
 * ``integrand`` / ``vegas_iteration`` / ``refine`` / ``combine`` -- the
   per-sample integrand, one VEGAS iteration (multi-threaded over sample ranges
@@ -479,7 +479,7 @@ def has_repeated_denominator(D: Diagram) -> bool:
 def hole_chords(D: Diagram) -> int:
     """Number of loop momenta that are hole momenta (integrated over the Fermi ball): the
     particle-hole composition of the integration domain.  Grouping key of Sec. III.A (reading): at
-    orders 2-5 it takes 1, 2, 4, 5 distinct values, the N_grp column of Table I."""
+    orders 2-6 it takes 1, 2, 4, 5, 6 distinct values, the N_grp column of Table I."""
     return int(sum(D.hole(l) for l in D.chords))
 
 
