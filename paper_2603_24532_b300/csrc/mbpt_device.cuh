@@ -46,6 +46,17 @@ __device__ __forceinline__ double sel(const double (&v)[16], int idx) {
     return r;
 }
 
+// the same over the first n_valid entries only (n_valid a constant after unrolling: tree line j reads
+// the chords and the tree lines before it)
+template <int NS>
+__device__ __forceinline__ double sel_upto(const double (&v)[16], int idx, int n_valid) {
+    double r = v[0];
+#pragma unroll
+    for (int j = 1; j < NS; ++j)
+        if (j < n_valid) r = (idx == j) ? v[j] : r;
+    return r;
+}
+
 __device__ __forceinline__ double neg_if(double x, int neg) {
     // flip the sign bit with an integer op
     long long b = __double_as_longlong(x) ^ ((long long)(neg != 0) << 63);
@@ -567,7 +578,8 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         const int ia = R.tree_a[j], ib = R.tree_b[j], ic = R.tree_c[j];
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            K[q][L + j] = (sel<NL>(K[q], ia) + sel<NL>(K[q], ib)) - sel<NL>(K[q], ic);
+            K[q][L + j] = (sel_upto<NL>(K[q], ia, L + j) + sel_upto<NL>(K[q], ib, L + j)) -
+                          sel_upto<NL>(K[q], ic, L + j);
         U[L + j] = fma(K[0][L + j], K[0][L + j], fma(K[1][L + j], K[1][L + j], K[2][L + j] * K[2][L + j]));
     }
 
