@@ -4,8 +4,8 @@ The paper has no counterpart to this call.  It exists for callers that must not
 allocate device memory once they are running -- a process whose device memory
 belongs to another allocator or a fixed budget, or a loop where cudaMalloc's
 implicit synchronisation is not acceptable.  Its scratch is one fixed device
-array shared by all calls, so the test makes two different calls in a row (the
-second smaller than the first, so stale slots of the first would show) and
+array shared by all calls, so the test makes different calls in a row (each
+smaller than the one before, so stale slots of an earlier call would show) and
 checks each against the arena-backed mbpt_vegas_iterate path on the same grid.
 This file is collected last on purpose.
 """
@@ -31,13 +31,14 @@ def _arena_path(ctx, desc, pm, cfg, grid):
         M.mbpt_destroy_diagram(g)
 
 
-def test_noalloc_matches_iterate_on_two_calls_in_a_row():
+def test_noalloc_matches_iterate_on_calls_in_a_row():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     ctx = M.mbpt_ctx_create(0, 1 << 30)
     rng = np.random.default_rng(2024)
-    cases = [  # (order, diagram index, matter, precision, samples) -- second call smaller than the first
+    cases = [  # (order, diagram index, matter, precision, samples) -- each call smaller than the one before
+        (6, 20000, "pnm", M.MBPT_MIXED, 90001),
         (4, 7, "snm", M.MBPT_MIXED, 70001),
         (3, 1, "pnm", M.MBPT_FP64, 40123),
     ]
