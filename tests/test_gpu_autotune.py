@@ -62,6 +62,13 @@ def test_all_shapes_agree_and_tuning_restores_state(ctx):
         b = res["best"]
         assert M.mbpt_ctx_get_launch(ctx, 3) == (b["threads"], b["min_blocks"], b["spt"])
         assert len(res["table"]) == 2 * len(M.mbpt_kernel_variants())
+        # per-order refinement of a mixed-order batch: one entry per (order, candidate), the chosen
+        # values left on the context, the states untouched
+        res = A.autotune(ctx, gs, spts=(16, 32), trials=1, variants=[(256, 2)], per_order=(3, 5))
+        assert [M.mbpt_get_state(g) for g in gs] == before
+        assert len(res["per_order_table"]) == 4 and set(res["per_order_spt"]) == {3, 5}
+        for o, spt in res["per_order_spt"].items():
+            assert M.mbpt_ctx_get_launch(ctx, o) == (256, 2, spt)
         # deterministic under the tuned shape
         M.mbpt_vegas_iterate(ctx, gs, 2)
         r1 = [r.as_dict() for r in M.mbpt_estimate_batch(gs)]
