@@ -57,6 +57,16 @@ __device__ __forceinline__ double sel_upto(const double (&v)[16], int idx, int n
     return r;
 }
 
+// v[idx] for idx known to lie in lo .. hi (constants after unrolling)
+template <int NS>
+__device__ __forceinline__ double sel_between(const double (&v)[16], int idx, int lo, int hi) {
+    double r = 0.0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+        if (j >= lo && j <= hi) r = (j == lo) ? v[j] : ((idx == j) ? v[j] : r);
+    return r;
+}
+
 __device__ __forceinline__ double neg_if(double x, int neg) {
     // flip the sign bit with an integer op
     long long b = __double_as_longlong(x) ^ ((long long)(neg != 0) << 63);
@@ -627,7 +637,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         for (int m = 0; m < N - 1; ++m) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const double uv = neg_if(sel<NL>(U, R.cut_slot[m][k]), R.cut_neg[m][k]);
+                const double uv = neg_if(sel_between<NL>(U, R.cut_slot[m][k], k, NL - 4 + k), R.cut_neg[m][k]);
                 if (m == 0 && k == 0) Dm = uv;
                 else Dm += uv;
             }

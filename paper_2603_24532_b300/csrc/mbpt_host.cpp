@@ -456,7 +456,12 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
         if (k != 4) {
             set_err(err, errlen, "internal: vertex without four lines");
             return MBPT_EINVAL;
-        }
+        }        // increasing slot order (distinct slots: term k lies in k .. 2n-4+k)
+        for (int a = 1; a < 4; ++a)
+            for (int b = a; b > 0 && r->cut_slot[m][b - 1] > r->cut_slot[m][b]; --b) {
+                std::swap(r->cut_slot[m][b - 1], r->cut_slot[m][b]);
+                std::swap(r->cut_neg[m][b - 1], r->cut_neg[m][b]);
+            }
     }
     // --- equivalent line pairs
     int neq = 0;

@@ -48,7 +48,7 @@ struct alignas(16) DiagRec {
     uint32_t all_slots;                          // (1 << 2n) - 1
     int8_t tree_a[MBPT_MAX_DEVICE_ORDER], tree_b[MBPT_MAX_DEVICE_ORDER], tree_c[MBPT_MAX_DEVICE_ORDER];
     // energy denominators, built cut by cut: D~_m = D~_{m-1} + sum_k sign[m][k] |k_slot[m][k]|^2
-    // over the four lines of vertex m (D~_-1 = 0); D_m = (hbar^2/2m) D~_m
+    // over the four lines of vertex m in increasing slot order (D~_-1 = 0); D_m = (hbar^2/2m) D~_m
     int8_t cut_slot[MBPT_MAX_DEVICE_ORDER][4];
     int8_t cut_neg[MBPT_MAX_DEVICE_ORDER][4];    // 1: subtract
     // vertex v = <o1 o2|V|i1 i2>: slots of o1, o2, i1, i2
