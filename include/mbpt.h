@@ -285,7 +285,7 @@ int mbpt_create_diagram(mbpt_ctx* ctx, const mbpt_diagram_desc* desc, const mbpt
  * VEGAS grid adapts to the sum and the members' fluctuations are correlated.  One physics point and
  * configuration for all members; the result (mbpt_estimate, the regulator components, the state
  * image) is that of the sum.  Each sample costs k integrand evaluations; a chunk holds
- * 8 samples per thread (1 with the regulator).  MBPT_EINVAL for k outside
+ * 16 samples per thread (3 with the regulator).  MBPT_EINVAL for k outside
  * 1..MBPT_MAX_GROUP, mixed orders, a non-finite scale or any member that create_diagram would reject.
  * mbpt_dump_samples of a group returns the summed weight.
  */

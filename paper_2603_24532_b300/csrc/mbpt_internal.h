@@ -31,7 +31,9 @@ constexpr int kShifts = 3;                               // denominator-regulato
 constexpr int kComp = kShifts + 1;                       // ... plus their extrapolation to zero shift
 constexpr int kSumStride = 2 + 2 * kComp;                // doubles per chunk-sum slot
 // grouped evaluation: per-thread shared-memory slots holding per-sample sums over the members
-constexpr int kGroupSlots = 8;
+// (one per sample; with the regulator, one per sample and component), i.e. samples per thread per chunk
+constexpr int kGroupSlotsPlain = 16;
+constexpr int kGroupSlotsReg = 15;
 constexpr int kWarps = kThreads / 32;
 
 // Compiled, device-resident description of one integral (diagram x physics x VEGAS setup).

@@ -12,10 +12,12 @@ namespace mbpt {
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-// pre-test rounds between evaluation phases (longer phases keep the instruction cache warmer; the
-// group + regulator part has the least shared memory to spare), and the per-warp stack length:
+// pre-test rounds between evaluation phases (longer phases keep the instruction cache warmer; a
+// group chunk has only as many rounds as its samples per thread, so the group parts take short
+// phases and spend the shared memory on per-sample slots), and the per-warp stack length:
 // carried-over entries of both classes plus one phase
-__host__ __device__ constexpr int class_rounds(int part) { return part == 3 ? 16 : 32; }
+__host__ __device__ constexpr int class_rounds(int part) { return part == 3 ? 4 : (part == 2 ? 16 : 32); }
+__host__ __device__ constexpr int group_slots(int part) { return part == 3 ? kGroupSlotsReg : kGroupSlotsPlain; }
 __host__ __device__ constexpr int queue_len(int part) { return 2 * 31 + 32 * class_rounds(part) + 2; }
 
 // Shared memory of one k_iterate block; the regulator and group arrays exist only in their parts
@@ -26,7 +28,7 @@ struct alignas(16) ChunkSmemT {
     Grid2 grid[kCells];
     float hist[NW][kCells];                  // warp-private histograms
     double cacc[(PART & 1) ? 2 * kComp : 1][NW * 32];   // per-thread sums of the regulator components
-    double gacc[(PART & 2) ? kGroupSlots : 1][NW * 32];  // group integrals: per-sample sums over the members
+    double gacc[(PART & 2) ? group_slots(PART) : 1][NW * 32];  // group integrals: per-sample sums over the members
     uint32_t queue[NW][queue_len(PART)];     // per-warp stacks of samples past the pre-test
                                              // (away from a Fermi surface from the bottom, near one from the top)
     double red[2][NW];
@@ -125,7 +127,7 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  A group integral (n_members > 1; its own kernel, GRP) evaluates every member at each sample, member
 //  by member with the record swapped in shared memory, each member's samples through the phases
 //  above, adding the weights per sample into gacc, zeroed per chunk (spt x (1 + regulator components)
-//  <= kGroupSlots slots per thread); sums, squares and the histogram then see the group's integrand.
+//  <= group_slots() slots per thread); sums, squares and the histogram then see the group's integrand.
 template <int N, int PREC, int MAPK, bool REG, bool GRP, int NW>
 __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 2 : 0)>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
@@ -335,7 +337,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
         if constexpr (REGP)
             for (int c = 0; c < 2 * kComp; ++c) S.cacc[c][tid] = 0.0;
         if constexpr (GRPP)
-            for (int c = 0; c < kGroupSlots; ++c) S.gacc[c][tid] = 0.0;
+            for (int c = 0; c < group_slots(PART); ++c) S.gacc[c][tid] = 0.0;
         __syncthreads();
         double sw = 0.0, sw2 = 0.0;
         const uint32_t cl = chunk - W.chunk_begin;

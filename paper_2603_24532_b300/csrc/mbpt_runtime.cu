@@ -626,8 +626,10 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         w.seed = g->cfg.seed;
         w.stream_id = g->cfg.stream_id;
         w.n_members = (uint32_t)g->n_members;
-        // a group keeps per-sample member sums in kGroupSlots shared-memory slots per thread
-        w.spt = g->n_members > 1 ? kGroupSlots / (g->cfg.n_shifts ? 1 + kComp : 1) : c->spt[g->desc.order];
+        // a group keeps per-sample member sums in shared-memory slots: 16 samples per thread, 3 with the
+        // regulator (five slots per sample)
+        w.spt = g->n_members > 1 ? (g->cfg.n_shifts ? kGroupSlotsReg / (1 + kComp) : kGroupSlotsPlain)
+                                 : c->spt[g->desc.order];
         const uint64_t cs = (uint64_t)kVariants[c->variant].tpb * (uint64_t)w.spt;
         w.n_chunks = (uint32_t)((w.samples + cs - 1) / cs);
         w.chunk_begin = (uint32_t)chunk;
