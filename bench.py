@@ -47,7 +47,7 @@ FP64_OPS_LIVE = 58.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_iterate_256x2 launch on the 30 x 2^20 profiling case
 # (profiles/k_iterate_third_order_scan.md): records, grids and chunk slots, as many chunks (128 per integral)
 # as the benchmark launch; not proportional to samples
-TRAFFIC_BYTES = 695296
+TRAFFIC_BYTES = 676608
 # nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second
 FP64_PEAK_NOMINAL = 1.25e12 / 2.0
 # measured DFMA rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu, profiles/pipe_peaks_b300.md),

@@ -132,7 +132,11 @@ template <int N, int PREC, int MAPK, bool REG, bool GRP, int NW>
 __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 2 : 0)>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
                                           double& sw2) {
     const DiagRec& R = S.rec;
-    const uint32_t cs = blockDim.x * (uint32_t)W.spt;
+    const int w_spt = W.spt;
+    const uint64_t w_samples = W.samples;
+    const uint32_t w_sid = W.stream_id;
+    const double* const w_grid = W.grid;
+    const uint32_t cs = blockDim.x * (uint32_t)w_spt;
     const uint64_t first = (uint64_t)chunk_local * cs;
     const uint32_t t = S.iter;
     const uint32_t k0 = (uint32_t)W.seed, k1 = (uint32_t)(W.seed >> 32);
@@ -163,11 +167,11 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
             int cnt = 0;
             if (compact) {
                 if (!drain && nf < 32 && nn < 32) {
-                    const int jend = (j + kRounds < W.spt) ? j + kRounds : W.spt;
+                    const int jend = (j + kRounds < w_spt) ? j + kRounds : w_spt;
                     for (; j < jend; ++j) {
                         const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
-                        const int cls = sc < W.samples
-                                            ? sample_class<N, MAPK, PREC>(R, S.grid, (uint32_t)sc, t, W.stream_id, k0, k1)
+                        const int cls = sc < w_samples
+                                            ? sample_class<N, MAPK, PREC>(R, S.grid, (uint32_t)sc, t, w_sid, k0, k1)
                                             : 0;
                         const uint32_t lt = (1u << lane) - 1u;
                         const uint32_t b0 = __ballot_sync(0xffffffffu, cls == 1);
@@ -177,7 +181,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                         nf += __popc(b0);
                         nn += __popc(b1);
                     }
-                    if (j >= W.spt) drain = true;
+                    if (j >= w_spt) drain = true;
                     __syncwarp();
                 }
                 if (nf >= 32) cnt = 32;
@@ -189,13 +193,13 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                 have = (int)lane < cnt;
                 s = !have ? 0u : (use_near ? q[kQ - 1 - (nn - cnt + (int)lane)] : q[nf - cnt + (int)lane]);
             } else {
-                if (j >= W.spt) break;
+                if (j >= w_spt) break;
                 s = first + (uint64_t)j * blockDim.x + threadIdx.x;
-                have = s < W.samples;
+                have = s < w_samples;
                 ++j;
             }
             if (have) {
-                const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, W.grid, (uint32_t)s, t, W.stream_id,
+                const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, w_grid, (uint32_t)s, t, w_sid,
                                                                     k0, k1, nullptr, use_near);
                 if constexpr (GRP) {
                     // the sample's slot belongs to the lane of this warp that owns it in the chunk layout
@@ -231,9 +235,9 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
     }
     if constexpr (!GRP) return;
     __syncwarp();                              // slots were filled by the warp's lanes
-    for (int j = 0; j < W.spt; ++j) {
+    for (int j = 0; j < w_spt; ++j) {
         const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
-        if (s >= W.samples) continue;
+        if (s >= w_samples) continue;
         const double w = S.gacc[j * PER][threadIdx.x];
         sw += w;
         sw2 = fma(w, w, sw2);
@@ -247,7 +251,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
         }
         if (nonzero(w)) {
             uint32_t bp[kBinWords];
-            sample_bins<D>((uint32_t)s, t, W.stream_id, k0, k1, (uint32_t)nb, bp);
+            sample_bins<D>((uint32_t)s, t, w_sid, k0, k1, (uint32_t)nb, bp);
             hist_add<D>(hist, nb, bp, w);
         }
     }
