@@ -1,16 +1,18 @@
 #!/usr/bin/env python3
-"""Benchmark: batched VEGAS evaluation of all third-order Hugenholtz diagrams of
-pure neutron matter over a density scan (3 diagrams x kF in {0.8, ..., 1.7} fm^-1,
-2^22 samples per integral per iteration), on one B300.
+"""Benchmark on one B300.  Headline: one batched VEGAS iteration over every non-anomalous fifth-order
+Hugenholtz diagram of pure neutron matter at kF in {1.0, 1.33, 1.6} fm^-1 (668 x 3 = 2004 integrals,
+18 dimensions, 2^20 samples per integral per iteration), mixed precision.
 
-A step is one VEGAS iteration over all 30 integrals: Philox sampling, VEGAS map,
-integrand, per-chunk sums and histograms, the fixed-order reduction, the
-combination of the iteration into each estimate and the grid refinement.
-The headline arm runs it batched (one persistent launch per iteration, CUDA
-graph) in mixed precision; the FP64 batched path and the plain per-diagram FP64
-loop run the same workload beside it.
+A step is one VEGAS iteration over all 2004 integrals: Philox sampling, VEGAS map, integrand, per-chunk
+sums and histograms, the fixed-order reduction, the combination of the iteration into each estimate and
+the grid refinement, as one persistent launch per batch part plus the finalize launch, replayed from a
+CUDA graph.  Beside it, from the same run: the same workload end to end through the C ABI, the time for
+every fifth-order integral to reach 0.5 % (or an absolute floor for near-zero diagrams), the plain
+per-diagram FP64 loop on a subset, the mixed-vs-FP64 deviation, the third-order density scan (with the
+FP64 batched path and the plain loop), the fourth-order batch and its aligned groups, the sixth-order
+batch, and the serving stream (p50/p99 latency, diagrams/s).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--profile-case fifth|third]
 """
 from __future__ import annotations
 
@@ -30,30 +32,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "integrand evals/s; diagrams to 0.1% err/s vs plain FP64 loop; p50/p99 EOS latency"
 UNIT = "integrand evals/s"
+# fifth order (headline)
+KF5 = (1.0, 1.33, 1.6)
+SAMPLES5 = 1 << 20
+ALPHA5 = 0.75
+WORKLOAD = ("all 840 fifth-order Hugenholtz diagrams (668 non-anomalous; both members of every mirror pair "
+            "evaluated) x kF {1.0, 1.33, 1.6} fm^-1, pure neutron matter, 18D, 2^20 samples/iteration, mixed")
+# third order (density scan)
 KF_SCAN = [round(0.8 + 0.1 * i, 2) for i in range(10)]
-SAMPLES = 1 << 22
-ORDER = 3
-WORKLOAD = "third-order Hugenholtz diagrams (pp, hh, ph), pure neutron matter, kF 0.8..1.7 fm^-1 (10 points), 12D, 2^22 samples/iteration"
-
-# FP64 operations per sample of an order-3 integral, mixed precision (FP32 sampling map), in the
-# formulation of csrc/mbpt_device.cuh.  A sample that fails a Fermi step by more than the FP32 error
-# bound is rejected by the FP32 pre-test with no FP64 work.  A live sample: chord momenta 3 products
-# + |l|^2 3 = 6 per chord (24; the chord Jacobians, the VEGAS Jacobian and the weight's constant factor
-# are one FP32 mantissa product), tree lines 6 sums + |k|^2 3 = 9 per line (18), energy denominators
-# (7 sums, 1 product), weight (2 products), Newton reciprocal of the denominator product (4), sum w and
-# sum w^2 (2) = 58.
-# (About 1 % of samples lie near a Fermi surface and are placed with the FP64 map instead.)
-FP64_OPS_LIVE = 58.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_iterate_256x2 launch on the 30 x 2^20 profiling case
-# (profiles/k_iterate_third_order_scan.md): records, grids and chunk slots, as many chunks (128 per integral)
-# as the benchmark launch; not proportional to samples
-TRAFFIC_BYTES = 676608
-# nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second
+SAMPLES3 = 1 << 22
+# nominal FP64 rate of the recipe (1.25 TFLOP/s, FMA = 2 flops) in FP64 instructions per second at 2032 MHz
 FP64_PEAK_NOMINAL = 1.25e12 / 2.0
-# measured DFMA rate on this machine's B300 (paper_2603_24532_b300/csrc/pipe_peaks.cu, profiles/pipe_peaks_b300.md),
-# FP64 thread operations per second at the SM clock of that run; scaled to the clock seen under load
-FP64_PEAK_MEASURED = 4.73e11
-FP64_PEAK_MEASURED_MHZ = 1938.5
+# FP64 thread operations (DADD + DMUL + DFMA, ncu) per sample of the profiled k_iterate launches
+FP64_OPS_FILE = os.path.join(ROOT, "profiles", "fp64_ops_per_sample.txt")
 
 
 def dist_env():
@@ -77,6 +68,20 @@ def slowest_rank_ms(dist, t_ms: float, device) -> float:
 def job_value(world: int, units_per_rank: float, t_ms: float) -> float:
     """Whole-job throughput (weak scaling: every rank processes the same units)."""
     return world * units_per_rank / (t_ms * 1e-3)
+
+
+def measured_fp64_ops(workload: str):
+    """FP64 thread operations per sample of a workload, from the committed ncu summary (lines
+    `<workload> <ops per sample> ...`); None if the file has no such line."""
+    try:
+        with open(FP64_OPS_FILE) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 2 and not line.startswith("#") and parts[0] == workload:
+                    return float(parts[1])
+    except OSError:
+        pass
+    return None
 
 
 class Clocks:
@@ -130,27 +135,50 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_integrals(M, ctx, precision, seed_base=1, stream_base=0, map_kind=0):
-    descs = M.mbpt_generate(ORDER)
+# ---------------------------------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------------------------------
+def fifth_order_integrals(M, ctx, precision, samples=SAMPLES5, seed=1, stream_base=0, every=1, **cfg_kw):
+    """The 2004 fifth-order integrals (or every `every`-th of them), with their (kF, descriptor)."""
+    descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
+    gs, meta = [], []
+    k = 0
+    for ki, kf in enumerate(KF5):
+        ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+        for d in descs:
+            k += 1
+            if (k - 1) % every:
+                continue
+            cfg = M.vegas_cfg(samples=samples, seed=seed, stream_id=stream_base + 1000 * ki + d.diagram_id,
+                              precision=precision, alpha=ALPHA5, **cfg_kw)
+            gs.append(M.mbpt_create_diagram(ctx, d, ph, cfg))
+            meta.append((kf, d))
+    return gs, meta
+
+
+def third_order_integrals(M, ctx, precision, seed=1, stream_base=0, map_kind=0):
+    descs = M.mbpt_generate(3)
     gs, meta = [], []
     for ki, kf in enumerate(KF_SCAN):
         ph = M.physics(kF_n=kf, kF_p=0.0, K_max=kf + 6.0, map_kind=map_kind)
         for d in descs:
             sid = stream_base + 100 * ki + d.diagram_id
-            cfg = M.vegas_cfg(samples=SAMPLES, seed=seed_base, stream_id=sid, precision=precision)
+            cfg = M.vegas_cfg(samples=SAMPLES3, seed=seed, stream_id=sid, precision=precision)
             gs.append(M.mbpt_create_diagram(ctx, d, ph, cfg))
             meta.append((kf, d.diagram_id))
     return gs, meta
 
 
-def l2_flush(torch, buf):
-    buf.add_(1)
+def destroy(M, gs):
+    for g in gs:
+        M.mbpt_destroy_diagram(g)
 
 
 def run_gpu(args):
     import torch
 
     from paper_2603_24532_b300 import mbpt as M
+    from paper_2603_24532_b300.autotune import autotune
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -159,12 +187,14 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
-    arena = torch.empty(32 << 30, dtype=torch.uint8, device=dev)   # chunk slots of the largest batch at the smallest tuned chunks
+    arena = torch.empty(32 << 30, dtype=torch.uint8, device=dev)   # room for the largest batch's chunk slots
     ctx = M.mbpt_ctx_create(local, arena.numel(), arena_ptr=arena.data_ptr())
     stream = torch.cuda.ExternalStream(M.mbpt_ctx_stream(ctx), device=dev)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)    # 256 MiB > 126 MB L2
 
     def timed_steps(gs, k, per_diagram=False):
+        """k iterations; per step the k_iterate time (events inside the graph) and the step time (events
+        around it on the context stream), with the L2 flushed before each step outside the events."""
         ms_it, ms_step = [], []
         for _ in range(k):
             with torch.cuda.stream(stream):
@@ -190,210 +220,253 @@ def run_gpu(args):
             ms_step.append(e0.elapsed_time(e1))
         return np.array(ms_it), np.array(ms_step)
 
-    from paper_2603_24532_b300.autotune import autotune
+    seed = 1 + rank
+    sbase = 100000 * rank
 
-    # ---- headline: batched, mixed precision, launch shape from the autotuner (untimed, states restored)
-    gs, meta = build_integrals(M, ctx, M.MBPT_MIXED, seed_base=1 + rank, stream_base=10000 * rank)
-    n_int = len(gs)
-    tuned = autotune(ctx, gs, trials=1)["best"] if args.autotune else None
-    timed_steps(gs, args.warmup)
+    # ================= headline: fifth order, batched, mixed ==========================================
+    # launch setting from the autotuner on every fourth integral (states restored), then the full batch
+    tuned = None
+    if args.autotune:
+        sub, _ = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase, every=4)
+        M.mbpt_vegas_iterate(ctx, sub, 2)
+        tuned = autotune(ctx, sub, spts=(8, 16, 32), trials=1)["launch"]
+        destroy(M, sub)
+    gs5, meta5 = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase)
+    n5 = len(gs5)
+    timed_steps(gs5, args.warmup)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    ms_it, ms_step = timed_steps(gs, args.steps)
+    ms_it, ms_step = timed_steps(gs5, args.steps)
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_step = slowest_rank_ms(dist, float(np.mean(ms_step)), dev)
-    evals_step = n_int * SAMPLES
+    evals_step = n5 * SAMPLES5
     value = job_value(world, evals_step, t_step)
-    res_mixed = [M.mbpt_estimate(g) for g in gs]
-
-    # live-sample fraction on the adapted grids (for the algorithmic FP64 work per sample)
-    live = []
-    for g in gs[:: max(1, n_int // 6)]:
-        _, w = M.mbpt_dump_samples(g, 10 ** 6, 0, 1 << 15, 12, with_x=False)
-        live.append(np.mean(w != 0))
-    live_frac = float(np.mean(live))
-    ops = FP64_OPS_LIVE * live_frac
     it_ms = float(np.mean(ms_it))
-    achieved = ops * evals_step / (it_ms * 1e-3)
 
-    # ---- e2e through the public API: per step H2D of the work table inside mbpt_vegas_iterate (a
-    # 96-byte item and an 8-byte histogram pointer per integral, an 80-byte header) and a D2H read of
-    # every integral's estimate with one synchronisation (80 bytes each, and the 4-byte error word)
-    h2d = n_int * (96 + 8) + 80
-    d2h = n_int * 80 + 4
+    # roofline of the dominant kernel: measured FP64 thread operations per sample (ncu) x samples per
+    # launch / its CUDA-event time, against the FP64 rate measured here with the library's DFMA loop
+    ops5 = measured_fp64_ops("fifth_order_mixed")
+    fp64_rate = M.mbpt_fp64_rate(local, M.mbpt_ctx_stream(ctx))
+    achieved = (ops5 * evals_step / (it_ms * 1e-3)) if ops5 else None
+
+    # end to end through the public API: per step the work table goes up inside mbpt_vegas_iterate
+    # (a WORK_ITEM_BYTES item and an 8-byte histogram pointer per integral, the work header) and every
+    # integral's estimate comes back with one synchronisation
+    h2d = n5 * (M.WORK_ITEM_BYTES + 8) + M.WORK_HEADER_BYTES
+    d2h = n5 * M.RESULT_BYTES + 4
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        M.mbpt_vegas_iterate(ctx, gs, 1)
-        _ = [r.mean for r in M.mbpt_estimate_batch(gs)]
+        M.mbpt_vegas_iterate(ctx, gs5, 1)
+        _ = [r.mean for r in M.mbpt_estimate_batch(gs5)]
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_value = world * evals_step / e2e_s
-    # ---- precision: mixed modes vs FP64 on identical counters and grids, paired over several
-    # iterations (each trial restores the same grid and sets the iteration counter), per integral;
-    # the scale of a near-zero diagram is 1e-3 of its order's sum
-    imgs = [M.mbpt_get_state(g) for g in gs]
-    twins = {}
-    for name, prec in (("fp64", M.MBPT_FP64), ("map64", M.MBPT_MIXED_MAP64)):
-        twins[name] = []
-        for (kf, did) in meta:
-            d = M.mbpt_generate(ORDER)[did]
-            ph = M.physics(kF_n=kf, kF_p=0.0, K_max=kf + 6.0)
-            sid = 10000 * rank + 100 * KF_SCAN.index(kf) + did
-            twins[name].append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=SAMPLES, seed=1 + rank,
-                                                                              stream_id=sid, precision=prec)))
-    sets = {"mixed": gs, "fp64": twins["fp64"], "map64": twins["map64"]}
-    trials = 6
-    means = {k: np.zeros((trials, n_int)) for k in sets}
-    t0_iter = 1000
-    for k in range(trials):
-        for name, arr in sets.items():
-            for g, img in zip(arr, imgs):
-                M.mbpt_set_state(g, M.state_with_iter(img, t0_iter + k))
-            M.mbpt_vegas_iterate(ctx, arr, 1)
-            means[name][k] = [r.last_mean for r in M.mbpt_estimate_batch(arr)]
-    ref = means["fp64"]
-    scale = np.zeros(n_int)
-    for ki in range(len(KF_SCAN)):
-        sl = slice(3 * ki, 3 * ki + 3)
-        scale[sl] = np.maximum(np.abs(ref[:, sl]).mean(axis=0), 1e-3 * abs(np.sum(ref[:, sl].mean(axis=0))))
-    precision_dev = {"definition": "paired over %d iterations on identical counters and grids: mean of "
-                                   "(I_mode - I_fp64) / max(|I_fp64|, 1e-3 |order sum|) per integral" % trials}
-    for name in ("mixed", "map64"):
-        dif = (means[name] - ref) / scale
-        mdif, se = dif.mean(axis=0), dif.std(axis=0, ddof=1) / np.sqrt(trials)
-        precision_dev[name] = {"max_abs_mean": float(np.max(np.abs(mdif))),
-                               "median_abs_mean": float(np.median(np.abs(mdif))),
-                               "max_single_iteration": float(np.max(np.abs(dif))),
-                               "max_abs_mean_over_se": float(np.max(np.abs(mdif) / np.maximum(se, 1e-300)))}
-    for arr in twins.values():
-        for g in arr:
-            M.mbpt_destroy_diagram(g)
-    for g in gs:
-        M.mbpt_destroy_diagram(g)
 
-    # ---- the same scan with the rotational reduction of the chord map (9D instead of 12D; NEXT row)
-    grot, _ = build_integrals(M, ctx, M.MBPT_MIXED, seed_base=1 + rank, stream_base=10000 * rank, map_kind=1)
-    timed_steps(grot, args.warmup)
-    itrot, strot = timed_steps(grot, max(4, args.steps // 4))
-    res_rot = M.mbpt_estimate_batch(grot)
-    for g in grot:
-        M.mbpt_destroy_diagram(g)
-    vrot = world * evals_step / (float(np.mean(strot)) * 1e-3)
+    # paired deviation of the mixed mode from FP64 (the FP64 path is parity-pinned to the oracle) on 48
+    # integrals with adapted grids, identical counters: per integral |I_mixed - I_fp64| / max(|I_fp64|,
+    # 1e-3 |E5 of its kF|)
+    res5 = M.mbpt_estimate_batch(gs5)
+    e5 = {kf: sum(r.mean for r, (k, _) in zip(res5, meta5) if k == kf) for kf in KF5}
+    rng = np.random.default_rng(5)
+    pick = sorted(rng.choice(n5, size=48, replace=False))
+    dev5, twins = [], []
+    for i in pick:
+        kf, d = meta5[i]
+        ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+        img = M.mbpt_get_state(gs5[i])
+        t64 = M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=1 << 16, seed=seed, stream_id=7,
+                                                            precision=M.MBPT_FP64, alpha=ALPHA5))
+        tmx = M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=1 << 16, seed=seed, stream_id=7,
+                                                            precision=M.MBPT_MIXED, alpha=ALPHA5))
+        for g in (t64, tmx):
+            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), M.state_grid(img, 18, 50)))
+        twins.append((t64, tmx, kf))
+    for k in range(2):
+        M.mbpt_vegas_iterate(ctx, [g for t in twins for g in t[:2]], 1)
+        r64 = M.mbpt_estimate_batch([t[0] for t in twins])
+        rmx = M.mbpt_estimate_batch([t[1] for t in twins])
+        if k == 1:
+            for a, b, (_, _, kf) in zip(r64, rmx, twins):
+                dev5.append(abs(b.last_mean - a.last_mean) / max(abs(a.last_mean), 1e-3 * abs(e5[kf]), 1e-300))
+    destroy(M, [g for t in twins for g in t[:2]])
+    destroy(M, gs5)
 
-    # ---- fourth-order batch (all 39 diagrams x kF {1.0, 1.33, 1.6} x {PNM, SNM}, 2^24 samples each,
-    # anomalous ones flagged and skipped): throughput of one batched iteration
-    g4 = []
-    for ki, kf in enumerate((1.0, 1.33, 1.6)):
-        for mi, kfp in enumerate((0.0, kf)):
-            ph = M.physics(kF_n=kf, kF_p=kfp, K_max=kf + 6.0)
-            for d in M.mbpt_generate(4):
-                if d.anomalous:
-                    continue
-                g4.append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(
-                    samples=1 << 24, seed=1 + rank, stream_id=10000 * rank + 1000 * mi + 100 * ki + d.diagram_id,
-                    precision=M.MBPT_MIXED)))
-    M.mbpt_vegas_iterate(ctx, g4, 1)
-    torch.cuda.synchronize()
-    it4, st4 = timed_steps(g4, 2)
-    for g in g4:
-        M.mbpt_destroy_diagram(g)
-    v4 = world * len(g4) * (1 << 24) / (float(np.mean(st4)) * 1e-3)
+    # time for every fifth-order integral to reach 0.5 % relative error: 3 training iterations, then the
+    # frozen-grid evaluation phase; a near-zero diagram's target is the absolute floor 0.5 % |E5| /
+    # sqrt(668) of its kF (its share of a 0.5 % error of the order's sum); at most 40 iterations
+    t0 = time.perf_counter()
+    gsc, metac = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed + 100, stream_base=sbase, train_iters=3,
+                                       combine=M.MBPT_COMBINE_POOLED, target_rel=0.005)
+    M.mbpt_vegas_iterate(ctx, gsc, 3)
+    rc = M.mbpt_estimate_batch(gsc)
+    floors = {}
+    for kf in KF5:
+        idx = [i for i, (k, _) in enumerate(metac) if k == kf]
+        floors[kf] = 0.005 * abs(sum(rc[i].last_mean for i in idx)) / math.sqrt(len(idx))
+    for g, (kf, d) in zip(gsc, metac):
+        cfg = M.vegas_cfg(samples=SAMPLES5, seed=seed + 100, stream_id=sbase + 1000 * KF5.index(kf) + d.diagram_id,
+                          precision=M.MBPT_MIXED, alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED,
+                          target_rel=0.005, target_abs=floors[kf])
+        M.mbpt_set_config(g, cfg)
+    iters, conv_evals = 3, 3 * len(gsc) * SAMPLES5
+    while iters < 40:
+        live = [g for g, r in zip(gsc, M.mbpt_estimate_batch(gsc)) if not r.converged]
+        if not live:
+            break
+        M.mbpt_vegas_iterate(ctx, live, 1)
+        conv_evals += len(live) * SAMPLES5
+        iters += 1
+    rc = M.mbpt_estimate_batch(gsc)
+    conv_s = time.perf_counter() - t0
+    n_conv = int(sum(r.converged for r in rc))
+    rel = [r.sigma / abs(r.mean) for r in rc if r.mean != 0.0]
+    e5c = {}
+    for kf in KF5:
+        idx = [i for i, (k, _) in enumerate(metac) if k == kf]
+        e5c[str(kf)] = {"E5": float(sum(rc[i].mean for i in idx)),
+                        "sigma": float(math.sqrt(sum(rc[i].sigma ** 2 for i in idx))),
+                        "floor": floors[kf]}
+    destroy(M, gsc)
 
-    # ---- the same fourth-order workload as group integrals (Sec. III.A): per physics point one integral
-    # per particle-hole group (4 groups of the 33 non-anomalous diagrams), 2^24 samples each, every
-    # sample evaluating all members: the same member evaluations per iteration as the batch above
-    gg, n_member_evals = [], 0
+    # the plain per-diagram FP64 loop on every 20th fifth-order integral: one launch per integral and
+    # iteration, default launch shape
+    launch_now = {o: M.mbpt_ctx_get_launch(ctx, o) for o in (2, 3, 4, 5, 6)}
+    layout_now = M.mbpt_ctx_get_hist_layout(ctx)
+    M.mbpt_ctx_set_kernel(ctx, 256, 2)
+    M.mbpt_ctx_set_hist_layout(ctx, M.MBPT_HIST_WARP_F32)
+    for o in (2, 3, 4, 5, 6):
+        M.mbpt_ctx_set_launch(ctx, o, 32)
+    gk5, _ = fifth_order_integrals(M, ctx, M.MBPT_FP64, seed=seed, stream_base=sbase, every=20)
+    timed_steps(gk5, 1, per_diagram=True)
+    _, stk5 = timed_steps(gk5, 2, per_diagram=True)
+    vk5 = world * len(gk5) * SAMPLES5 / (float(np.mean(stk5)) * 1e-3)
+    destroy(M, gk5)
+    M.mbpt_ctx_set_kernel(ctx, *launch_now[5][:2])
+    M.mbpt_ctx_set_hist_layout(ctx, layout_now)
+    for o, (_, _, spt) in launch_now.items():
+        M.mbpt_ctx_set_launch(ctx, o, spt)
+
+    # ================= third-order density scan (C2): mixed, FP64 batched, plain per-diagram loop ========
+    g3, m3 = third_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase)
+    tuned3 = autotune(ctx, g3, trials=1)["launch"] if args.autotune else None
+    n3 = len(g3)
+    timed_steps(g3, 3)
+    it3, st3 = timed_steps(g3, args.steps)
+    v3 = world * n3 * SAMPLES3 / (float(np.mean(st3)) * 1e-3)
+    res3 = M.mbpt_estimate_batch(g3)
+    live3 = []
+    for g in g3[:: max(1, n3 // 6)]:
+        _, w = M.mbpt_dump_samples(g, 10 ** 6, 0, 1 << 15, 12, with_x=False)
+        live3.append(np.mean(w != 0))
+    destroy(M, g3)
+    g3r, _ = third_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase, map_kind=1)
+    timed_steps(g3r, 3)
+    _, st3r = timed_steps(g3r, max(4, args.steps // 4))
+    v3r = world * n3 * SAMPLES3 / (float(np.mean(st3r)) * 1e-3)
+    res3r = M.mbpt_estimate_batch(g3r)
+    destroy(M, g3r)
+    g64, _ = third_order_integrals(M, ctx, M.MBPT_FP64, seed=seed, stream_base=sbase)
+    timed_steps(g64, 3)
+    it64, st64 = timed_steps(g64, max(4, args.steps // 2))
+    v64 = world * n3 * SAMPLES3 / (float(np.mean(st64)) * 1e-3)
+    res64 = M.mbpt_estimate_batch(g64)
+    destroy(M, g64)
+    M.mbpt_ctx_set_kernel(ctx, 256, 2)
+    M.mbpt_ctx_set_hist_layout(ctx, M.MBPT_HIST_WARP_F32)
+    for o in (2, 3, 4, 5, 6):
+        M.mbpt_ctx_set_launch(ctx, o, 32)
+    gk0, _ = third_order_integrals(M, ctx, M.MBPT_FP64, seed=seed, stream_base=sbase)
+    timed_steps(gk0, 2, per_diagram=True)
+    _, stk0 = timed_steps(gk0, max(2, args.steps // 4), per_diagram=True)
+    vk0 = world * n3 * SAMPLES3 / (float(np.mean(stk0)) * 1e-3)
+    destroy(M, gk0)
+
+    def diags_per_s(results, rate, rel_target=1e-3):
+        """Integrals brought to rel_target per second at a throughput `rate`, from each run's own variance."""
+        need = 0.0
+        for r in results:
+            if r.mean == 0.0 or r.sigma == 0.0:
+                continue
+            need += r.n_evals * (r.sigma / (rel_target * abs(r.mean))) ** 2
+        return len(results) / (need / rate) if need > 0 else None
+
+    d_mixed, d_rot, d_k0 = diags_per_s(res3, v3), diags_per_s(res3r, v3r), diags_per_s(res64, vk0)
+
+    # ================= fourth order (C3): 198 live integrals x 2^24, and the aligned groups ===============
+    M.mbpt_ctx_set_kernel(ctx, *launch_now[5][:2])
+    M.mbpt_ctx_set_hist_layout(ctx, layout_now)
+    for o, (_, _, spt) in launch_now.items():
+        M.mbpt_ctx_set_launch(ctx, o, spt)
+    g4, gg, member_evals = [], [], 0
     for ki, kf in enumerate((1.0, 1.33, 1.6)):
         for mi, kfp in enumerate((0.0, kf)):
             ph = M.physics(kF_n=kf, kF_p=kfp, K_max=kf + 6.0)
             by_key = {}
             for d in M.mbpt_generate(4):
-                if not d.anomalous:
-                    by_key.setdefault(M.mbpt_hole_chords(d), []).append(d)
+                if d.anomalous:
+                    continue
+                by_key.setdefault(M.mbpt_hole_chords(d), []).append(d)
+                g4.append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(
+                    samples=1 << 24, seed=seed, stream_id=sbase + 1000 * mi + 100 * ki + d.diagram_id,
+                    precision=M.MBPT_MIXED, alpha=1.0)))
             for key, ds in sorted(by_key.items()):
                 gg.append(M.mbpt_create_group(ctx, ds, ph, M.vegas_cfg(
-                    samples=1 << 24, seed=1 + rank, stream_id=10000 * rank + 1000 * mi + 100 * ki + 50 + key,
-                    precision=M.MBPT_MIXED)))
-                n_member_evals += len(ds) << 24
-    M.mbpt_vegas_iterate(ctx, gg, 1)
-    torch.cuda.synchronize()
-    itg, stg = timed_steps(gg, 2)
-    for g in gg:
-        M.mbpt_destroy_diagram(g)
-    vg = world * n_member_evals / (float(np.mean(stg)) * 1e-3)
+                    samples=1 << 24, seed=seed, stream_id=sbase + 1000 * mi + 100 * ki + 50 + key,
+                    precision=M.MBPT_MIXED, alpha=1.0)))
+                member_evals += len(ds) << 24
+    timed_steps(g4, 1)
+    it4, st4 = timed_steps(g4, max(5, args.steps // 4))
+    v4 = world * len(g4) * (1 << 24) / (float(np.mean(st4)) * 1e-3)
+    timed_steps(gg, 1)
+    _, stg = timed_steps(gg, max(5, args.steps // 4))
+    vg = world * member_evals / (float(np.mean(stg)) * 1e-3)
+    n4, ng = len(g4), len(gg)
+    destroy(M, g4)
+    destroy(M, gg)
 
-    # ---- sixth order (Table I: 27300 diagrams, d = 21; the paper's proof-of-principle order): every
-    # non-anomalous diagram, one integral per mirror pair (11269), PNM kF = 1.33, 2^16 samples each
+    # ================= sixth order: every non-anomalous diagram, one integral per mirror pair ============
     t6 = time.perf_counter()
     ph6 = M.physics(kF_n=1.33, K_max=7.33)
-    g6 = [M.mbpt_create_diagram(ctx, d, ph6, M.vegas_cfg(samples=1 << 16, seed=1 + rank,
-                                                         stream_id=100000 * rank + d.diagram_id,
-                                                         precision=M.MBPT_MIXED))
+    g6 = [M.mbpt_create_diagram(ctx, d, ph6, M.vegas_cfg(samples=1 << 16, seed=seed, stream_id=sbase + d.diagram_id,
+                                                         precision=M.MBPT_MIXED, alpha=0.75))
           for d in M.mbpt_generate(6) if not d.anomalous and d.diagram_id <= d.mirror_id]
     create6_s = time.perf_counter() - t6
-    M.mbpt_vegas_iterate(ctx, g6, 1)
-    torch.cuda.synchronize()
-    it6, st6 = timed_steps(g6, 2)
-    for g in g6:
-        M.mbpt_destroy_diagram(g)
+    timed_steps(g6, 1)
+    _, st6 = timed_steps(g6, 3)
     v6 = world * len(g6) * (1 << 16) / (float(np.mean(st6)) * 1e-3)
-
-    # ---- FP64 batched, same workload (tuned the same way)
-    g64, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
-    tuned64 = autotune(ctx, g64, trials=1)["best"] if args.autotune else None
-    timed_steps(g64, args.warmup)
-    it64, st64 = timed_steps(g64, args.steps)
-    res64 = [M.mbpt_estimate(g) for g in g64]
-    for g in g64:
-        M.mbpt_destroy_diagram(g)
-    v64 = world * evals_step / (float(np.mean(st64)) * 1e-3)
-
-    # ---- plain per-diagram FP64 loop: one launch per integral per iteration, default launch shape
-    M.mbpt_ctx_set_kernel(ctx, 256, 2)
-    for o in (2, 3, 4, 5):
-        M.mbpt_ctx_set_launch(ctx, o, 32)
-    gk0, _ = build_integrals(M, ctx, M.MBPT_FP64, seed_base=1 + rank, stream_base=10000 * rank)
-    timed_steps(gk0, max(1, args.warmup // 2), per_diagram=True)
-    itk0, stk0 = timed_steps(gk0, max(2, args.steps // 2), per_diagram=True)
-    for g in gk0:
-        M.mbpt_destroy_diagram(g)
-    vk0 = world * evals_step / (float(np.mean(stk0)) * 1e-3)
-
-    # ---- time to 0.1 % statistical error per integral, from each run's own variance
-    def diags_per_s(results, rate):
-        need = 0.0
-        for r in results:
-            if r.mean == 0.0 or r.sigma == 0.0:
-                continue
-            need += r.n_evals * (r.sigma / (1e-3 * abs(r.mean))) ** 2
-        return len(results) / (need / rate) if need > 0 else None
-
-    d_mixed = diags_per_s(res_mixed, value)
-    d_rot = diags_per_s(res_rot, vrot)
-    d_k0 = diags_per_s(res64, vk0)
+    n6 = len(g6)
+    destroy(M, g6)
     M.mbpt_ctx_destroy(ctx)
     del arena
     torch.cuda.synchronize()
 
-    # ---- serving: a short Poisson stream of equation-of-state requests (p50/p99 latency)
+    # ================= serving (C5): Poisson stream of equation-of-state requests ========================
     serving = None
     if args.serve_requests > 0:
         from paper_2603_24532_b300 import serve as S
-        be = S.MbptBackend(device=local, arena_bytes=8 << 30)
-        srv = S.Server(be, budget_bytes=6 << 30)
+        be = S.MbptBackend(device=local, arena_bytes=48 << 30)
+        srv = S.Server(be, budget_bytes=40 << 30)
         trace = S.poisson_trace(args.serve_requests, 20.0, 7 + rank)
         t0 = time.perf_counter()
         done = srv.run(trace, realtime=True, time_limit=args.serve_seconds)
         wall = time.perf_counter() - t0
-        st = S.latency_stats(done)
-        met = [r for r in done if r.energy is not None and r.sigma is not None and r.sigma <= r.target * abs(r.energy)]
-        serving = {"requests": len(trace), "completed": len(done), "wall_s": wall, "p50_s": st["p50_s"],
-                   "p99_s": st["p99_s"], "target_met_fraction": len(met) / max(1, len(done)),
+        fin = [r for r in done if r.energy is not None and math.isfinite(r.energy)]
+        n_int = sum(len(r.integrals) for r in fin)
+        n_diag = sum(it.mult for r in fin for it in r.integrals)
+        serving = {"requests": len(trace), "completed": len(done), "wall_s": wall,
+                   "latency_all": S.latency_stats(done), "latency_met": S.latency_stats(done, "met"),
+                   "latency_capped": S.latency_stats(done, "capped"),
+                   "p50_s": S.latency_stats(done)["p50_s"], "p99_s": S.latency_stats(done)["p99_s"],
+                   "target_met_fraction": sum(r.met for r in done) / max(1, len(done)),
+                   "capped_fraction": sum(r.capped for r in done) / max(1, len(done)),
+                   "integrals_per_s": n_int / wall, "diagrams_per_s": n_diag / wall,
+                   "evals_per_s": srv.evals / wall, "budget_bytes": srv.budget,
                    "workload": "Poisson 20/s, n ~ U[0.04, 0.20] fm^-3, delta {0..1}, order cap {2,3,4}, "
-                               "target {1, 0.3, 0.1} %, seed 7 (+rank)"}
+                               "target {1, 0.3, 0.1} %, seed 7 (+rank); 40 GB admission budget; "
+                               "diagrams/s counts a mirror-pair representative twice"}
         be.close()
     if dist:
         dist.barrier()
@@ -403,52 +476,78 @@ def run_gpu(args):
         return None
 
     cpu = cpu_baseline(budget_s=args.cpu_seconds) if world == 1 else None
+    sm_mhz = clk.get("sm_mhz") or 2032.0
+    dev5 = np.array(dev5)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "integrals": n_int, "samples_per_iter": SAMPLES,
-                   "precision": "mixed (FP32 potentials, spin sum and sampling map; FP64 line momenta, Fermi steps, energy denominators, sums, grid)",
-                   "step": "one batched VEGAS iteration over all integrals (sample, integrate, reduce, combine, refine)",
+        "config": {"workload": WORKLOAD, "integrals": n5, "samples_per_iter": SAMPLES5, "mirror_dedup": False,
+                   "precision": "mixed (FP32 potentials, spin sum and sampling map; FP64 line momenta, Fermi "
+                                "steps, energy denominators, sums, grid; FP64 map within 2^-7 kF^2 of a Fermi "
+                                "surface)",
+                   "vegas": {"bins": 50, "alpha": ALPHA5},
+                   "step": "one batched VEGAS iteration over all integrals (sample, integrate, reduce, combine, "
+                           "refine)",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "launch": tuned},
-        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e9, "peak": FP64_PEAK_NOMINAL / 1e9,
-                     "unit": "FP64 Gop/s (DADD-equivalents)", "frac": achieved / FP64_PEAK_NOMINAL,
-                     "peak_kind": "nominal 1.25 TFLOP/s FP64 of the recipe at 2032 MHz",
-                     "frac_of_measured_dfma": achieved / (FP64_PEAK_MEASURED * (clk.get("sm_mhz") or 2032.0)
-                                                          / FP64_PEAK_MEASURED_MHZ),
-                     "measured_dfma_note": "4.73e11 FP64 op/s at 1938 MHz, scaled to the median SM clock of the run",
-                     "ops_per_sample": ops, "live_fraction": live_frac, "kernel": "k_iterate",
-                     "kernel_ms": it_ms, "traffic": TRAFFIC_BYTES,
-                     "traffic_note": "ncu dram read+write of one k_iterate launch on the 30 x 2^20 profiling case "
-                                     "(grids and records; the 128 chunk slots per integral, as many as in this "
-                                     "launch, stay in L2), not proportional to samples"},
+                   "parallelism": "replicas" if world > 1 else "1 GPU", "launch": tuned},
+        "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "k_iterate (order-2..5 plain part)",
+                     "achieved": achieved / 1e9 if achieved else None, "peak": fp64_rate / 1e9,
+                     "unit": "FP64 Gop/s (thread operations)",
+                     "frac": achieved / fp64_rate if achieved else None,
+                     "peak_kind": "FP64 DFMA rate measured in this run with the library's dependency-free DFMA "
+                                  "loop (mbpt_fp64_rate)",
+                     "frac_of_nominal": achieved / (FP64_PEAK_NOMINAL * sm_mhz / 2032.0) if achieved else None,
+                     "nominal_note": "1.25 TFLOP/s FP64 of the recipe (FMA = 2) = 6.25e11 instructions/s at "
+                                     "2032 MHz, scaled to the run's median SM clock",
+                     "ops_per_sample": ops5, "ops_source": "ncu DADD + DMUL + DFMA thread instructions per "
+                                                          "sample, profiles/fp64_ops_per_sample.txt",
+                     "kernel_ms": it_ms, "traffic": None,
+                     "traffic_note": "HBM idle by design (records, grids, chunk slots); see the k_iterate "
+                                     "profile summary for dram bytes"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 5 * args.steps,   # per step: k_iterate parts (plain; regulated and group parts empty here), k_finalize
+        "gpu_launches": 2 * args.steps,   # per step: the k_iterate kernel of the plain order-2..5 part, k_finalize
         "clocks": clk,
-        "fp64_batched": {"value": v64, "unit": UNIT, "kernel_ms": float(np.mean(it64)), "launch": tuned64},
-        "k0_plain_fp64_per_diagram": {"value": vk0, "unit": UNIT, "launches_per_step": 2 * n_int},
-        "speedup_vs_k0": value / vk0,
-        "mixed_vs_fp64_deviation": precision_dev,
-        "diagrams_to_0p1pct_per_s": {"batched_mixed": d_mixed, "k0_plain_fp64": d_k0,
-                                     "ratio": (d_mixed / d_k0) if (d_mixed and d_k0) else None,
-                                     "batched_mixed_rotational_9d": d_rot},
-        "fourth_order_batch": {"value": v4, "unit": UNIT, "integrals": len(g4), "samples_per_iter": 1 << 24,
-                               "ms_per_iteration": float(np.mean(st4)),
-                               "workload": "39 fourth-order diagrams (33 non-anomalous) x kF {1.0,1.33,1.6} x {PNM,SNM}, mixed"},
-        "fourth_order_groups": {"value": vg, "unit": UNIT + " (member diagrams)", "integrals": len(gg),
+        "fifth_order_to_0p5pct": {"integrals": len(rc), "converged": n_conv, "wall_s": conv_s, "iterations": iters,
+                                  "evals": conv_evals, "median_rel_err": float(np.median(rel)) if rel else None,
+                                  "diagrams_per_s": n_conv / conv_s, "per_kF": e5c,
+                                  "k0_diagrams_per_s": n_conv / (conv_evals / vk5),
+                                  "definition": "3 training iterations then the frozen-grid evaluation phase; "
+                                                "converged: sigma <= max(0.5 % |I|, 0.5 % |E5(kF)| / sqrt(668)); "
+                                                "cap 40 iterations; k0: the same evaluations at the plain "
+                                                "per-diagram FP64 loop's rate"},
+        "k0_plain_fp64_fifth_order": {"value": vk5, "unit": UNIT, "integrals": int(math.ceil(n5 / 20)),
+                                      "note": "every 20th integral, one launch per integral and iteration"},
+        "speedup_vs_k0": value / vk5,
+        "mixed_vs_fp64_deviation": {"integrals": int(len(dev5)), "samples_each": 1 << 16,
+                                    "max": float(dev5.max()), "median": float(np.median(dev5)),
+                                    "frac_below_1e-4": float(np.mean(dev5 < 1e-4)),
+                                    "definition": "same grid and counters: |I_mixed - I_fp64| / max(|I_fp64|, "
+                                                  "1e-3 |E5 of the kF|), one iteration of 2^16 samples"},
+        "third_order_scan": {"value": v3, "unit": UNIT, "integrals": n3, "samples_per_iter": SAMPLES3,
+                             "kernel_ms": float(np.mean(it3)), "live_fraction": float(np.mean(live3)),
+                             "launch": tuned3,
+                             "fp64_batched": v64, "k0_plain_fp64_per_diagram": vk0, "speedup_vs_k0": v3 / vk0,
+                             "rotational_9d": v3r,
+                             "diagrams_to_0p1pct_per_s": {"batched_mixed": d_mixed, "k0_plain_fp64": d_k0,
+                                                          "ratio": (d_mixed / d_k0) if (d_mixed and d_k0) else None,
+                                                          "batched_mixed_rotational_9d": d_rot},
+                             "workload": "3 third-order diagrams x kF 0.8..1.7 fm^-1 (10 points), PNM, 12D, "
+                                         "2^22 samples/iteration, mixed"},
+        "fourth_order_batch": {"value": v4, "unit": UNIT, "integrals": n4, "samples_per_iter": 1 << 24,
+                               "ms_per_iteration": float(np.mean(st4)), "timed_steps": len(st4),
+                               "workload": "39 fourth-order diagrams (33 non-anomalous) x kF {1.0,1.33,1.6} x "
+                                           "{PNM,SNM}, mixed"},
+        "fourth_order_groups": {"value": vg, "unit": UNIT + " (member diagrams)", "integrals": ng,
                                 "samples_per_iter": 1 << 24, "ms_per_iteration": float(np.mean(stg)),
                                 "vs_per_diagram_batch": vg / v4,
-                                "workload": "the fourth_order_batch diagrams as 4 particle-hole groups per physics "
-                                            "point (24 group integrals), mixed"},
-        "sixth_order_batch": {"value": v6, "unit": UNIT, "integrals": len(g6), "samples_per_iter": 1 << 16,
+                                "workload": "the fourth_order_batch diagrams as 4 aligned particle-hole groups per "
+                                            "physics point (24 group integrals), mixed"},
+        "sixth_order_batch": {"value": v6, "unit": UNIT, "integrals": n6, "samples_per_iter": 1 << 16,
                               "ms_per_iteration": float(np.mean(st6)), "create_s": create6_s,
                               "workload": "27300 sixth-order diagrams, one integral per mirror pair of the 21572 "
                                           "non-anomalous ones, PNM kF 1.33, d = 21, mixed"},
-        "rotational_9d": {"value": vrot, "unit": UNIT, "kernel_ms": float(np.mean(itrot)),
-                          "note": "same scan with chord 0 along z and chord 1 in the xz plane (d = 9)"},
         "serving": serving,
     }
     print(json.dumps(line))
@@ -457,35 +556,39 @@ def run_gpu(args):
     return line
 
 
-def cpu_baseline(budget_s=12.0, steps=None):
-    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same
-    workload (every integral, the same number of samples each, uniform grid)."""
+# ---------------------------------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------------------------------
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the headline workload (every
+    one of the 2004 fifth-order integrals, the same number of samples each, uniform grid)."""
     import oracle as O
 
-    Ds = O.enumerate_diagrams(ORDER)
+    Ds = [D for D in O.enumerate_diagrams(5) if not O.is_anomalous(D)]
     cores = os.cpu_count() or 1
-    # calibrate on one integral
-    po = O.Physics(kF_n=1.2, K_max=7.2)
-    grid = O.uniform_grid(12, 50)
-    m, dt = 1 << 14, 0.0
-    while dt < 0.3 and m < (1 << 22):
+    grid = O.uniform_grid(18, 50)
+    po = O.Physics(kF_n=1.33, K_max=7.33)
+    # calibrate on a few integrals
+    m, dt = 8, 0.0
+    while dt < 0.5 and m < (1 << 16):
         m *= 2
         t0 = time.perf_counter()
-        for D in Ds:
-            O.vegas_iteration(D, po, grid, 1, 0, 0, m, threads=cores)
+        for D in Ds[:16]:
+            O.vegas_iteration(D, po, grid, 1, D.diagram_id, 0, m, threads=cores)
         dt = time.perf_counter() - t0
-    per = dt / (m * len(Ds))
-    n = int(max(1024, min(1 << 22, budget_s / (per * len(KF_SCAN) * len(Ds)))))
+    per = dt / (m * 16)
+    n = int(max(16, min(1 << 16, budget_s / (per * len(KF5) * len(Ds)))))
     t0 = time.perf_counter()
     total = 0
-    for ki, kf in enumerate(KF_SCAN):
+    for ki, kf in enumerate(KF5):
         po = O.Physics(kF_n=kf, K_max=kf + 6.0)
         for D in Ds:
-            O.vegas_iteration(D, po, grid, 1, 100 * ki + D.diagram_id, 0, n, threads=cores)
+            O.vegas_iteration(D, po, grid, 1, 1000 * ki + D.diagram_id, 0, n, threads=cores)
             total += n
     dt = time.perf_counter() - t0
     return {"value": total / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d samples of each of the 30 integrals (uniform grid, iteration 0), %.1f s" % (n, dt)}
+            "sample": "%d samples of each of the %d fifth-order integrals (uniform grid, iteration 0), %.1f s"
+                      % (n, len(KF5) * len(Ds), dt)}
 
 
 def run_reference(args):
@@ -503,7 +606,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "integrals": 30, "samples_per_iter": SAMPLES,
+            "config": {"workload": WORKLOAD, "integrals": 2004, "samples_per_iter": SAMPLES5,
                        "step": "bounded sample of one iteration of every integral on the host cores"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -511,21 +614,51 @@ def run_reference(args):
     return line
 
 
+def profile_case(args):
+    """A small case of one workload for ncu captures of k_iterate: `fifth` (the 2004 fifth-order integrals)
+    or `third` (the 30 third-order integrals), args.samples samples each, args.iters batched iterations."""
+    from paper_2603_24532_b300 import mbpt as M
+    ctx = M.mbpt_ctx_create(0, 8 << 30)
+    prec = M.MBPT_MIXED if args.precision == "mixed" else M.MBPT_FP64
+    if args.profile_case == "fifth":
+        gs, _ = fifth_order_integrals(M, ctx, prec, samples=args.samples)
+    else:
+        descs = M.mbpt_generate(3)
+        gs = []
+        for ki, kf in enumerate(KF_SCAN):
+            ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+            gs += [M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=args.samples, stream_id=100 * ki + d.diagram_id,
+                                                                 precision=prec)) for d in descs]
+    M.mbpt_vegas_iterate(ctx, gs, args.iters)
+    r = M.mbpt_estimate(gs[0])
+    it_ms, fin_ms = M.mbpt_ctx_last_timing(ctx)
+    print("%s: integrals %d samples %d iters %d: k_iterate %.3f ms, k_finalize %.3f ms, first mean %.6g +- %.2g"
+          % (args.profile_case, len(gs), args.samples, args.iters, it_ms, fin_ms, r.mean, r.sigma))
+    M.mbpt_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
-    ap.add_argument("--serve-requests", type=int, default=400, help="short serving run (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=40.0)
+    ap.add_argument("--serve-requests", type=int, default=1200, help="serving run (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=150.0)
+    ap.add_argument("--profile-case", choices=["fifth", "third"], default=None,
+                    help="run only a small case of one workload (for ncu captures)")
+    ap.add_argument("--samples", type=int, default=1 << 16, help="--profile-case: samples per integral")
+    ap.add_argument("--iters", type=int, default=3, help="--profile-case: batched iterations")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="--profile-case precision")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

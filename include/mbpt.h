@@ -155,6 +155,19 @@ typedef struct {
  * Sec. III.C).  The integral stops iterating once its combined standard error
  * is <= max(target_rel*|mean|, target_abs) (0, 0 = never).
  *
+ * Combination of the iterations (`combine`):
+ *   MBPT_COMBINE_INVVAR (0): Lepage's inverse-variance weighted mean of the iteration estimates
+ *     from iteration train_iters on, sigma = (sum 1/sigma_t^2)^(-1/2).  With heavy-tailed weights
+ *     the iterations that missed the tail have both the smaller |I_t| and the smaller sigma_t, so
+ *     this mean is biased toward them and its sigma is too small.
+ *   MBPT_COMBINE_POOLED (1): PVegas' split into a training and an evaluation phase (Sec. III.C).
+ *     The first train_iters iterations train the grid (refined after each) and are not combined;
+ *     from then on the grid is frozen and every evaluation sample carries the same weight: with
+ *     S1 = sum w, S2 = sum w^2 and N samples over all evaluation iterations, mean = S1/N and
+ *     sigma^2 = (S2/N - mean^2)/(N - 1), the plain Monte Carlo estimator of one long run on one
+ *     grid (unbiased whatever the tails).  chi2_dof compares the evaluation iterations' own
+ *     estimates with that mean.  freeze_after, if set, can only freeze earlier.
+ *
  * Denominator regulator (Sec. III.A): with n_shifts = 3 every sample also
  * evaluates the integrand with each energy denominator D_m replaced by
  * D_m - shift[k] (D_m < 0 on the integration domain, so the shift moves the
@@ -177,7 +190,16 @@ typedef struct {
     uint32_t train_iters;      /* leading iterations excluded from the combined estimate */
     uint32_t n_shifts;         /* 0, or 3: denominator regulator components (below) */
     double shift[3];           /* MeV, positive and distinct */
+    uint32_t combine;          /* MBPT_COMBINE_INVVAR or MBPT_COMBINE_POOLED (above) */
+    float near_band;           /* MBPT_MIXED: width of the band around each Fermi surface, in units of
+                                  kF^2, inside which a sample is placed with the FP64 map (the FP64
+                                  mode's point) instead of the FP32 map; 0 = the library default
+                                  (2^-10 up to fourth order, 2^-7 from fifth order on), else in
+                                  [2^-16, 1/2] */
 } mbpt_vegas_cfg;
+
+#define MBPT_COMBINE_INVVAR 0
+#define MBPT_COMBINE_POOLED 1
 
 typedef struct {
     double mean;               /* inverse-variance weighted mean over iterations (MeV) */
@@ -199,7 +221,10 @@ typedef struct {
  * adjacency matrices A (A[i][j] = lines from vertex i to j; zero diagonal,
  * row and column sums 2) sorted by their row-major entries; lines listed in
  * row-major order of A; ports in increasing line index; chords chosen by a
- * spanning forest that takes particle lines first, then hole lines.
+ * spanning forest that takes particle lines first, then hole lines, and listed
+ * hole chords first, then particle chords (each in line order), so that
+ * diagrams with equally many hole chords map a sampled point to the same loop
+ * momenta (see mbpt_create_group).
  * out may be NULL to query the count.  Returns MBPT_EINVAL for n outside 2..6
  * and MBPT_ENOMEM when cap is too small (*count still receives the count).
  */
@@ -254,6 +279,18 @@ int mbpt_ctx_set_kernel(mbpt_ctx* ctx, int threads_per_block, int min_blocks_per
 int mbpt_ctx_set_launch(mbpt_ctx* ctx, int order, int samples_per_thread);
 int mbpt_ctx_get_launch(const mbpt_ctx* ctx, int order, int* threads_per_block, int* min_blocks_per_sm,
                         int* samples_per_thread);
+/*
+ * Per-chunk histogram layout of the sample-evaluation kernel (an autotuner choice; the context starts with
+ * MBPT_HIST_WARP_F32).  MBPT_HIST_WARP_F32: every warp adds w^2 to its own FP32 bins (FP32 shared-memory
+ * atomics without contention between warps; results bitwise reproducible).  MBPT_HIST_BLOCK_F64: one FP64
+ * histogram per block (FP64 shared-memory atomics from every warp; the order of the additions, and so the
+ * last bits of the histogram and of the refined grid, can vary from run to run).  Either way a chunk's
+ * histogram is stored in FP32 and the chunks are summed in FP64 in a fixed order.
+ */
+int mbpt_ctx_set_hist_layout(mbpt_ctx* ctx, int layout);
+int mbpt_ctx_get_hist_layout(const mbpt_ctx* ctx, int* layout);
+#define MBPT_HIST_WARP_F32 0
+#define MBPT_HIST_BLOCK_F64 1
 
 /*
  * Device time of the last mbpt_vegas_iterate iteration: the sample-evaluation
@@ -281,8 +318,11 @@ int mbpt_create_diagram(mbpt_ctx* ctx, const mbpt_diagram_desc* desc, const mbpt
 /*
  * Grouped evaluation (Sec. III.A): one integral whose integrand is the sum of k diagrams of the same
  * order, member m scaled by scale[m] (NULL: all 1; e.g. 2 for one diagram standing for a mirror
- * pair), every member mapped through its own chord map from the same sampled point x, so that one
- * VEGAS grid adapts to the sum and the members' fluctuations are correlated.  One physics point and
+ * pair), evaluated at the same loop momenta: each member's chords are taken hole chords first (the
+ * order mbpt_generate lists them in; other descriptors are reordered), so members with equally many
+ * hole chords -- the grouping key, mbpt_hole_chords -- map a sampled point x to the same chord
+ * momenta.  One VEGAS grid then adapts to the sum, and the members' singular regions and
+ * fluctuations coincide and partly cancel.  One physics point and
  * configuration for all members; the result (mbpt_estimate, the regulator components, the state
  * image) is that of the sum.  Each sample costs k integrand evaluations; a chunk holds
  * 16 samples per thread (3 with the regulator).  MBPT_EINVAL for k outside
@@ -359,14 +399,32 @@ int mbpt_philox_device(mbpt_ctx* ctx, const uint32_t ctr[4], const uint32_t key[
  * need more (with 50 bins: above about 3.8e7 samples at order 5, 1.1e8 at
  * order 3) fail with MBPT_EINVAL and a message giving the limit.  The
  * first call on a device looks up the array's device address and sets kernel
- * attributes for that device; make that first call before any stream capture.
- * Calls that overlap on the GPU (different streams, or different host threads)
- * race on the shared array: serialise them.  Each call resets the parts that
- * must start at zero; the rest of the array keeps the last call's contents.
+ * attributes for that device.  Every call copies its work description from
+ * host stack memory with cudaMemcpyAsync, so no call may be captured into a
+ * CUDA graph.  Calls that overlap on the GPU (different streams, or different
+ * host threads) race on the shared array: serialise them.  Each call resets
+ * the parts that must start at zero; the rest of the array keeps the last
+ * call's contents.
+ *
+ * Errors: invalid arguments are rejected on the host (MBPT_EINVAL) before
+ * anything is queued, and out is left untouched.  Should the kernel report an
+ * error in its device error word (an out-of-range chunk or a record that no
+ * compiled case matches -- validated input does not produce one), the call has
+ * already returned, so every element of out (the sums and the histogram) is
+ * set to NaN instead.
  */
 int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc* desc, const mbpt_physics* physics,
                                  const mbpt_vegas_cfg* cfg, uint32_t iter, const double* grid, double* out,
                                  void* cuda_stream);
+
+/*
+ * Measurement helper (the paper has no counterpart): FP64 thread operations per second that a
+ * dependency-free DFMA loop (eight independent fused multiply-add chains per thread, 2048 threads per
+ * SM) reaches on `device` now, timed with CUDA events on `cuda_stream` (best of three launches after a
+ * warm-up launch; synchronises the stream).  It is the denominator of the roofline fraction of the
+ * FP64-bound sample-evaluation kernel, measured at the clock the GPU runs at.
+ */
+int mbpt_fp64_rate(int device, void* cuda_stream, double* ops_per_s);
 
 const char* mbpt_last_error(void);
 

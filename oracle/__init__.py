@@ -12,9 +12,12 @@ Contents
   diagrams with two-body vertices (Table I of arXiv:2603.24532 counts them:
   1, 3, 39, 840, 27300 at n = 2..6) in the canonical line/port/chord convention below.
 * ``Diagram`` -- one diagram with the oracle's own derived quantities.
-* ``integrand`` / ``vegas_iteration`` / ``refine`` / ``combine`` -- the
-  per-sample integrand, one VEGAS iteration (multi-threaded over sample ranges
-  with a fixed-order reduction), grid refinement and iteration combination.
+* ``integrand`` / ``vegas_iteration`` / ``refine`` / ``combine`` /
+  ``combine_pooled`` -- the per-sample integrand, one VEGAS iteration
+  (multi-threaded over sample ranges with a fixed-order reduction), grid
+  refinement, and the two iteration combinations: Lepage's inverse-variance
+  mean, and the evaluation phase of PVegas (Sec. III.C: training iterations,
+  then a frozen grid whose samples all carry the same weight).
 * ``discrete_diagram`` and ``rspt_coefficients`` -- the finite-space check of
   the diagram rules against exact Rayleigh-Schroedinger perturbation theory.
 
@@ -30,7 +33,8 @@ that follows the same written rules must produce the same lists):
    the lines entering v, each pair in increasing line index.
 4. Chords: scan particles (increasing index) then holes (increasing index),
    union-find over vertices; a line that joins two components is a tree line,
-   otherwise a chord.  Chords are listed in increasing line index.
+   otherwise a chord.  Chords are listed hole chords first, then particle
+   chords, each in increasing line index.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 (tests/test_oracle_pins.py, tests/test_oracle_rspt.py, tests/test_philox.py,
@@ -276,7 +280,9 @@ def diagram_from_matrix(A, diagram_id: int = -1) -> Diagram:
             chords.append(l)
         else:
             parent[rs] = rt
-    chords.sort()
+    # hole chords first, then particle chords, each in line order (any basis gives the same integral; with
+    # this order diagrams with equally many hole chords share the chord ranges of the loop-momentum map)
+    chords.sort(key=lambda l: (lines[l][0] < lines[l][1], l))
     D = Diagram(n=n, A=tuple(tuple(r) for r in A), lines=lines, ports=ports, chords=chords, diagram_id=diagram_id)
     derive(D)
     return D
@@ -603,19 +609,53 @@ def combine(means: Sequence[float], variances: Sequence[float], skip: int = 0):
     return mean, sigma, chi2
 
 
+def combine_pooled(sums_w: Sequence[float], sums_w2: Sequence[float], counts: Sequence[int]):
+    """PVegas' evaluation phase (Sec. III.C): the iterations ran on one frozen grid, so their samples are
+    draws from one distribution and every sample carries the same weight.  With S1 = sum w, S2 = sum w^2
+    and N samples over all of them: mean = S1/N, sigma^2 = (S2/N - mean^2)/(N - 1) -- the estimate and
+    standard error of one run of N samples.  chi^2/dof compares the iterations' own estimates with that
+    mean (each with its own variance)."""
+    s1, s2, n = float(np.sum(sums_w)), float(np.sum(sums_w2)), float(np.sum(counts))
+    mean = s1 / n
+    var = (s2 / n - mean * mean) / (n - 1.0)
+    sigma = math.sqrt(var) if var > 0.0 else 0.0
+    chi2 = 0.0
+    if len(counts) > 1:
+        c2, used = 0.0, 0
+        for a, b, m in zip(sums_w, sums_w2, counts):
+            it = a / m
+            v = (b / m - it * it) / (m - 1.0)
+            if v > 0.0:
+                c2 += (it - mean) ** 2 / v
+                used += 1
+        chi2 = c2 / (used - 1) if used > 1 else 0.0
+    return mean, sigma, chi2
+
+
 def vegas(D: Optional[Diagram], ph, n_iter: int, n_samples: int, seed: int = 1, sid: int = 0, nb: int = 50,
-          alpha: float = 1.5, threads: Optional[int] = None, kind: int = 0, d: Optional[int] = None):
-    """Full VEGAS run: iterate, refine after every iteration, combine all iterations."""
+          alpha: float = 1.5, threads: Optional[int] = None, kind: int = 0, d: Optional[int] = None,
+          train_iters: int = 0, pooled: bool = False):
+    """Full VEGAS run.  Default: refine after every iteration and combine every iteration from train_iters
+    on with inverse-variance weights (Lepage).  pooled: the first train_iters iterations train the grid
+    (refined after each) and are not combined; the grid is then frozen and the remaining iterations are
+    combined by combine_pooled."""
     if d is None:
         d = (ph.dim(D) if isinstance(ph, Physics) else D.d) if kind == 0 else 6
     grid = uniform_grid(d, nb)
-    means, vars_ = [], []
+    means, vars_, s1, s2, cnt = [], [], [], [], []
     for t in range(n_iter):
         r = vegas_iteration(D, ph, grid, seed, sid, t, n_samples, threads=threads, kind=kind)
         means.append(r.mean)
         vars_.append(r.var_of_mean)
-        grid = refine(grid, r.hist, alpha)
-    return combine(means, vars_) + (grid,)
+        if t >= train_iters:
+            s1.append(r.sum_w)
+            s2.append(r.sum_w2)
+            cnt.append(r.n)
+        if not pooled or t < train_iters:
+            grid = refine(grid, r.hist, alpha)
+    if pooled:
+        return combine_pooled(s1, s2, cnt) + (grid,)
+    return combine(means, vars_, skip=train_iters) + (grid,)
 
 
 # ----------------------------------------------------------------------------

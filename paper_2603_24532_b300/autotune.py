@@ -1,11 +1,12 @@
-"""Launch-shape autotuner for the batched VEGAS iteration.
+"""Launch autotuner for the batched VEGAS iteration.
 
 Times one iteration of the caller's own batch for every compiled kernel shape
 (threads per block x minimum resident blocks, i.e. a register cap) and every
-candidate samples-per-thread, optionally refines samples-per-thread order by
-order for a batch of several orders, restoring every integral's state (grid,
-sums, iteration counter) after each trial so tuning leaves no trace in the
-results, and leaves the fastest setting on the context.
+candidate samples-per-thread; then, on the best shape, the per-chunk histogram
+layout (warp-private FP32 bins or one block-shared FP64 histogram) and, for a
+batch of several orders, samples-per-thread order by order.  Every integral's
+state (grid, sums, iteration counter) is restored after each trial, so tuning
+leaves no trace in the results, and the fastest setting is left on the context.
 """
 from __future__ import annotations
 
@@ -30,18 +31,28 @@ def _time_batch(ctx, diags, states, trials):
     return float(np.median(ms))
 
 
+def batch_orders(states) -> list:
+    """The orders present in a batch, read from the integrals' state images (header word 4)."""
+    return sorted({int(np.frombuffer(st, dtype=np.int32, count=1, offset=16)[0]) for st in states})
+
+
 def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: Optional[Sequence] = None,
-             trials: int = 2, orders: Iterable[int] = (2, 3, 4, 5, 6),
-             per_order: Optional[Iterable[int]] = None) -> Dict:
-    """Search the kernel shape and one samples-per-thread value for all orders; then, for each order
-    in per_order (the orders present in a mixed batch), search that order's samples per thread alone
-    with the others held at their best (per_order_table, per_order_spt in the result)."""
+             trials: int = 2, orders: Iterable[int] = (2, 3, 4, 5, 6), per_order="auto",
+             layouts: Iterable[int] = (M.MBPT_HIST_WARP_F32, M.MBPT_HIST_BLOCK_F64)) -> Dict:
+    """Search the kernel shape and one samples-per-thread value for all orders; then the histogram
+    layout on that shape (layout_table; the FP64 block layout is taken only if it is faster); then, for
+    each order in per_order -- by default ("auto") the orders present when the batch has more than one --
+    that order's samples per thread alone with the others held at their best (per_order_table,
+    per_order_spt).  The result's "launch" summarises the chosen setting."""
     if not diags:
         raise ValueError("autotune needs a non-empty batch")
     spts = tuple(spts)
     orders = tuple(orders)
     states = [M.mbpt_get_state(g) for g in diags]
-    table, per_order_table, per_order_spt = [], [], {}
+    present = batch_orders(states)
+    if per_order == "auto":
+        per_order = present if len(present) > 1 else ()
+    table, per_order_table, per_order_spt, layout_table = [], [], {}, []
     try:
         for tpb, minb in (variants or M.mbpt_kernel_variants()):
             M.mbpt_ctx_set_kernel(ctx, tpb, minb)
@@ -54,6 +65,13 @@ def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: 
         M.mbpt_ctx_set_kernel(ctx, best["threads"], best["min_blocks"])
         for o in orders:
             M.mbpt_ctx_set_launch(ctx, o, best["spt"])
+        layout = M.MBPT_HIST_WARP_F32
+        for lay in layouts:
+            M.mbpt_ctx_set_hist_layout(ctx, lay)
+            layout_table.append({"layout": lay, "ms": _time_batch(ctx, diags, states, trials)})
+        if layout_table:
+            layout = min(layout_table, key=lambda r: r["ms"])["layout"]
+        M.mbpt_ctx_set_hist_layout(ctx, layout)
         for o in (per_order or ()):
             trial = []
             for spt in spts:
@@ -66,4 +84,8 @@ def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: 
     finally:
         for g, st in zip(diags, states):
             M.mbpt_set_state(g, st)
-    return {"best": best, "table": table, "per_order_table": per_order_table, "per_order_spt": per_order_spt}
+    launch = {"threads": best["threads"], "min_blocks": best["min_blocks"],
+              "spt_by_order": {o: M.mbpt_ctx_get_launch(ctx, o)[2] for o in present},
+              "hist_layout": "block_f64" if layout == M.MBPT_HIST_BLOCK_F64 else "warp_f32"}
+    return {"best": best, "table": table, "layout_table": layout_table, "per_order_table": per_order_table,
+            "per_order_spt": per_order_spt, "launch": launch}

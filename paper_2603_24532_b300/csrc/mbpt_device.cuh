@@ -388,7 +388,8 @@ __device__ __forceinline__ void mixed_front(const DiagRec& R, const Grid2* __res
 // accumulated from at most N+1 chords by fused multiply-adds with coefficients -1..1, so with
 // S_l = sum over its chords of |coefficient| |k_c|, |k_f^2 - k^2| < 2^-19 S_l^2; the margin is
 // 2^-16 S_l^2 plus 2^-20 kF^2 for the FP32 copy of kF^2.  near: some line lies within the margin plus
-// 2^-10 kF^2 of a Fermi surface (the band in which the caller places the sample with the FP64 map).
+// near_f kF^2 of a Fermi surface (the band in which the caller places the sample with the FP64 map;
+// 2^-10 up to fourth order, 2^-7 from fifth order on by default).
 // SLACK (FP64 and FP64-map modes, whose exact path places the sample with the FP64 map): the FP32
 // point differs from the FP64 one by < 2^-20 per axis, which moves a chord magnitude by
 // < 2^-18 (rng + k) and its unit direction by < 2^-7 (the sin(theta) = 2 sqrt(x1 (1 - x1)) factor is
@@ -433,12 +434,12 @@ __device__ __forceinline__ bool pretest_dead(const DiagRec& R, const float (&lf)
         const float mn = fmaf(9.5367431640625e-07f, R.kf2_nf, mg);
         const float dn = uf - R.kf2_nf;
         bool f = hole ? (dn > mn) : (dn < -mn);
-        bool nr = fabsf(dn) <= fmaf(9.765625e-04f, R.kf2_nf, mn);
+        bool nr = fabsf(dn) <= fmaf(R.near_f, R.kf2_nf, mn);
         if (R.asym) {
             const float mp2 = fmaf(9.5367431640625e-07f, R.kf2_pf, mg);
             const float dp = uf - R.kf2_pf;
             f = f && (hole ? (dp > mp2) : (dp < -mp2));
-            nr = nr || (fabsf(dp) <= fmaf(9.765625e-04f, R.kf2_pf, mp2));
+            nr = nr || (fabsf(dp) <= fmaf(R.near_f, R.kf2_pf, mp2));
         }
         dead |= f;
         near |= nr;

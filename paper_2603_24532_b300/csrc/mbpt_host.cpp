@@ -162,8 +162,11 @@ void build_desc(int n, const Mat& A, int id, mbpt_diagram_desc& d) {
         if (a == b) chord[l] = true;
         else parent[a] = b;
     }
+    // hole chords first, then particle chords, each in line order: diagrams with the same number of hole
+    // chords then map a sampled point to the same loop momenta (aligned group members)
     int nc = 0;
-    for (int l = 0; l < nl; ++l) if (chord[l]) d.chord_line[nc++] = (int8_t)l;
+    for (int l = 0; l < nl; ++l) if (chord[l] && d.line_src[l] > d.line_dst[l]) d.chord_line[nc++] = (int8_t)l;
+    for (int l = 0; l < nl; ++l) if (chord[l] && d.line_src[l] < d.line_dst[l]) d.chord_line[nc++] = (int8_t)l;
     d.n_chords = (int8_t)nc;
     route_chords(n, nl, d.line_src, d.line_dst, d.chord_line, nc, d.line_coef);
     d.diagram_id = id;
@@ -297,6 +300,25 @@ void set_pref(DiagRec* r, double pref) {
     r->pref_sign_hi = std::signbit(pref) ? 0x80000000u : 0u;
 }
 
+void hole_chords_first(mbpt_diagram_desc& d) {
+    const int nc = d.n_chords, nl = d.n_lines;
+    if (nc < 1 || nc > MBPT_MAX_CHORDS || nl < 1 || nl > MBPT_MAX_LINES) return;   // left to validation
+    for (int c = 0; c < nc; ++c)
+        if (d.chord_line[c] < 0 || d.chord_line[c] >= nl) return;
+    int perm[MBPT_MAX_CHORDS], k = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int c = 0; c < nc; ++c) {
+            const int l = d.chord_line[c];
+            const bool hole = d.line_src[l] > d.line_dst[l];
+            if (hole == (pass == 0)) perm[k++] = c;
+        }
+    const mbpt_diagram_desc o = d;
+    for (int j = 0; j < nc; ++j) {
+        d.chord_line[j] = o.chord_line[perm[j]];
+        for (int l = 0; l < nl; ++l) d.line_coef[l][j] = o.line_coef[l][perm[j]];
+    }
+}
+
 int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbpt_vegas_cfg& cfg, DiagRec* r,
                    char* err, size_t errlen) {
     int st = validate_descriptor(d, err, errlen);
@@ -331,6 +353,14 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
     }
     if (cfg.n_shifts != 0 && cfg.n_shifts != (uint32_t)kShifts) {
         set_err(err, errlen, "n_shifts must be 0 or 3");
+        return MBPT_EINVAL;
+    }
+    if (cfg.combine != MBPT_COMBINE_INVVAR && cfg.combine != MBPT_COMBINE_POOLED) {
+        set_err(err, errlen, "combine must be MBPT_COMBINE_INVVAR or MBPT_COMBINE_POOLED");
+        return MBPT_EINVAL;
+    }
+    if (!(cfg.near_band == 0.0f || (cfg.near_band >= 1.52587890625e-05f && cfg.near_band <= 0.5f))) {
+        set_err(err, errlen, "near_band must be 0 (default) or in [2^-16, 1/2]");
         return MBPT_EINVAL;
     }
     if (cfg.n_shifts) {
@@ -547,6 +577,9 @@ int compile_record(const mbpt_diagram_desc& d, const mbpt_physics& ph, const mbp
     set_pref(r, pref);
     // denominator regulator: D_m - shift in D~ units (D = (hbar^2/2m) D~), Lagrange weights at 0
     r->n_shifts = (int32_t)cfg.n_shifts;
+    // FP64-map band of the mixed mode: wider from fifth order on, where more lines (and the larger spin sums)
+    // make the weight more sensitive to where the FP32 map puts a sample near a Fermi surface
+    r->near_f = cfg.near_band != 0.0f ? cfg.near_band : (n >= 5 ? 0.0078125f : 0.0009765625f);
     for (int k = 0; k < kShifts; ++k) {
         r->eta[k] = cfg.n_shifts ? cfg.shift[k] / (0.5 * ph.hbar2_over_m) : 0.0;
         double L = 1.0;

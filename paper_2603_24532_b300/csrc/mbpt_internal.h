@@ -35,6 +35,17 @@ constexpr int kSumStride = 2 + 2 * kComp;                // doubles per chunk-su
 constexpr int kGroupSlotsPlain = 16;
 constexpr int kGroupSlotsReg = 15;
 constexpr int kWarps = kThreads / 32;
+// samples per thread of a chunk by order (index = order) for a fresh context and for the allocation-free
+// iteration, which promises the same chunking
+constexpr int kDefaultSpt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16, 16};
+// the batch is run by eight k_iterate kernels, one per part: bit 0 = the integrals carry the denominator
+// regulator, bit 1 = group integrals, bit 2 = sixth order (its instantiations have their own kernels, so that
+// their registers and stack do not weigh on the orders 2..5)
+constexpr int kParts = 8;
+constexpr int kPartReg = 1, kPartGrp = 2, kPartO6 = 4;
+// per-chunk histogram layouts of k_iterate (the autotuner picks one): warp-private FP32 bins, or one
+// block-shared FP64 histogram
+constexpr int kHistWarpF32 = 0, kHistBlockF64 = 1;
 
 // Compiled, device-resident description of one integral (diagram x physics x VEGAS setup).
 //
@@ -79,7 +90,7 @@ struct alignas(16) DiagRec {
     float pref_mf;                               // |pref| = pref_mf 2^pref_e, pref_mf in [1, 2) (rounded to FP32)
     int32_t pref_e;
     uint32_t pref_sign_hi;                       // sign bit of pref in the high word of a double
-    int32_t pad_p;
+    float near_f;                                // MBPT_MIXED: FP64-map band around a Fermi surface (units of kF^2)
     float CSf, CY4f, mpi2_4f, regc2f;            // FP32 copies; regc2f folds in log2(e)^(1/reg_half)
     int8_t line_slot[MBPT_MAX_LINES];            // slot of each descriptor line
     int32_t map_kind;                            // 0: full chord directions; 1: rotational reduction
@@ -111,7 +122,13 @@ struct alignas(16) DiagState {
     double hist_var[kMaxIters];
     // regulator components (shift 0..2, extrapolation): running inverse-variance sums and estimates
     double comp_inv_var[kComp], comp_mean_w[kComp], comp_mean[kComp], comp_sigma[kComp];
+    // evaluation phase of MBPT_COMBINE_POOLED: sum w, sum w^2 and samples over the evaluation iterations
+    double pool_s1, pool_s2, pool_n;
+    double comp_pool_s1[kComp], comp_pool_s2[kComp];
+    double pad_pool;
 };
+// the Python binding reads state images at fixed offsets (mbpt.py: STATE_HEADER_BYTES, DIAGSTATE_BYTES)
+static_assert(sizeof(DiagState) == 8496, "DiagState layout changed: update the binding's offsets");
 
 // One entry of the batch work table.
 struct alignas(16) WorkItem {
@@ -129,6 +146,9 @@ struct alignas(16) WorkItem {
     int32_t hist_stride;   // floats per chunk histogram slot
     uint32_t train_iters;  // leading iterations not combined into the estimate
     uint32_t n_members;    // records at rec[0..n_members): > 1 is a group integral (sum of the members)
+    uint32_t combine;      // MBPT_COMBINE_INVVAR or MBPT_COMBINE_POOLED
+    uint32_t hist_layout;  // kHistWarpF32 or kHistBlockF64
+    uint32_t pad_w[2];
 };
 
 struct alignas(16) WorkHeader {
@@ -137,19 +157,19 @@ struct alignas(16) WorkHeader {
     uint32_t error;           // non-zero: a kernel saw an out-of-range index or a misplaced item
     uint32_t pad0;
     uint64_t hist_floats;     // size of the chunk histogram scratch
-    // the batch is split in four parts, each run by its own k_iterate kernel, in this order: plain
-    // integrals, plain with the denominator regulator, groups, groups with the regulator (part bit 0:
-    // regulator, bit 1: group); part p holds part_items[p] consecutive items and part_chunks[p]
-    // consecutive chunks
-    uint32_t part_items[4];
-    uint32_t part_chunks[4];
-    uint32_t part_counter[4]; // dynamic chunk scheduling, reset before every iterate launch
+    // the batch is split in kParts parts, each run by its own k_iterate kernel, in part order (bits as for
+    // kParts); part p holds part_items[p] consecutive items and part_chunks[p] consecutive chunks
+    uint32_t part_items[kParts];
+    uint32_t part_chunks[kParts];
+    uint32_t part_counter[kParts];   // dynamic chunk scheduling, reset before every iterate launch
 };
 
 // host-side helpers (mbpt_host.cpp)
 int compile_record(const mbpt_diagram_desc& desc, const mbpt_physics& ph, const mbpt_vegas_cfg& cfg,
                    DiagRec* rec, char* err, size_t errlen);
 int validate_descriptor(const mbpt_diagram_desc& desc, char* err, size_t errlen);
+// reorder a descriptor's chords hole chords first (stable), permuting the columns of line_coef alike
+void hole_chords_first(mbpt_diagram_desc& desc);
 // the weight's constant factor and its FP32 mantissa / exponent / sign fields
 void set_pref(DiagRec* rec, double pref);
 int build_hf_table(const mbpt_physics& ph, std::vector<double>& tab, char* err, size_t errlen);

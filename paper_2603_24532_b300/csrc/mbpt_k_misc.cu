@@ -48,7 +48,8 @@ __device__ void refine_rebin(double* grid, const double* old, const double* m, i
 }
 
 // Per integral: fixed-order reduction of the chunk slots, combination of the iteration into the
-// running estimate, convergence test and grid refinement.
+// running estimate (inverse-variance weights, or with MBPT_COMBINE_POOLED the pooled sums of the
+// evaluation phase on the frozen grid), convergence test and grid refinement.
 __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkItem* __restrict__ items,
                                                  const double* __restrict__ csum, const float* __restrict__ chist,
                                                  double* const* __restrict__ last_hist) {
@@ -117,31 +118,61 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
             st->last_var = var;
             if (!isfinite(I) || !isfinite(var)) st->status = MBPT_ENUMERIC;
             const bool training = (uint32_t)t < W.train_iters;   // grid training only
-            if (var > 0.0 && !training) {
-                st->sum_inv_var += 1.0 / var;
-                st->sum_mean_w += I / var;
-                st->n_used += 1;
-            }
+            const bool pooled = W.combine == MBPT_COMBINE_POOLED;
             double mean, sigma, chi2 = 0.0;
-            if (st->sum_inv_var > 0.0) {
-                mean = st->sum_mean_w / st->sum_inv_var;
-                sigma = sqrt(1.0 / st->sum_inv_var);
-                const int T = t + 1 < kMaxIters ? t + 1 : kMaxIters;
-                if (st->n_used > 1) {
-                    double c2 = 0.0;
-                    for (int k = (int)W.train_iters; k < T; ++k)
-                        if (st->hist_var[k] > 0.0) {
-                            const double dd = st->hist_mean[k] - mean;
-                            c2 += dd * dd / st->hist_var[k];
-                        }
-                    chi2 = c2 / (st->n_used - 1);
+            if (pooled) {
+                // evaluation phase: every sample of every evaluation iteration carries the same weight
+                if (!training) {
+                    st->pool_s1 += A;
+                    st->pool_s2 += B;
+                    st->pool_n += M;
+                    st->n_used += 1;
                 }
-            } else if (training) {
-                mean = I;                        // no combined estimate yet
-                sigma = (double)INFINITY;
+                if (st->pool_n > 1.0) {
+                    const double N = st->pool_n;
+                    mean = st->pool_s1 / N;
+                    const double v = (st->pool_s2 / N - mean * mean) / (N - 1.0);
+                    sigma = v > 0.0 ? sqrt(v) : 0.0;
+                    const int T = t + 1 < kMaxIters ? t + 1 : kMaxIters;
+                    if (st->n_used > 1) {
+                        double c2 = 0.0;
+                        for (int k = (int)W.train_iters; k < T; ++k)
+                            if (st->hist_var[k] > 0.0) {
+                                const double dd = st->hist_mean[k] - mean;
+                                c2 += dd * dd / st->hist_var[k];
+                            }
+                        chi2 = c2 / (st->n_used - 1);
+                    }
+                } else {
+                    mean = I;                    // no evaluation iteration yet
+                    sigma = (double)INFINITY;
+                }
             } else {
-                mean = I;
-                sigma = 0.0;
+                if (var > 0.0 && !training) {
+                    st->sum_inv_var += 1.0 / var;
+                    st->sum_mean_w += I / var;
+                    st->n_used += 1;
+                }
+                if (st->sum_inv_var > 0.0) {
+                    mean = st->sum_mean_w / st->sum_inv_var;
+                    sigma = sqrt(1.0 / st->sum_inv_var);
+                    const int T = t + 1 < kMaxIters ? t + 1 : kMaxIters;
+                    if (st->n_used > 1) {
+                        double c2 = 0.0;
+                        for (int k = (int)W.train_iters; k < T; ++k)
+                            if (st->hist_var[k] > 0.0) {
+                                const double dd = st->hist_mean[k] - mean;
+                                c2 += dd * dd / st->hist_var[k];
+                            }
+                        chi2 = c2 / (st->n_used - 1);
+                    }
+                } else if (training) {
+                    mean = I;                    // no combined estimate yet
+                    sigma = (double)INFINITY;
+                } else {
+                    mean = I;
+                    sigma = 0.0;
+                }
             }
             st->mean = mean;
             st->sigma = sigma;
@@ -156,6 +187,22 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
                     }
                     const double Iq = Aq / M;
                     const double vq = (Bq / M - Iq * Iq) / (M - 1.0);
+                    if (pooled) {
+                        if (!training) {
+                            st->comp_pool_s1[q] += Aq;
+                            st->comp_pool_s2[q] += Bq;
+                        }
+                        if (st->pool_n > 1.0) {
+                            const double N = st->pool_n, mq = st->comp_pool_s1[q] / N;
+                            const double v = (st->comp_pool_s2[q] / N - mq * mq) / (N - 1.0);
+                            st->comp_mean[q] = mq;
+                            st->comp_sigma[q] = v > 0.0 ? sqrt(v) : 0.0;
+                        } else {
+                            st->comp_mean[q] = Iq;
+                            st->comp_sigma[q] = (double)INFINITY;
+                        }
+                        continue;
+                    }
                     if (vq > 0.0 && !training) {
                         st->comp_inv_var[q] += 1.0 / vq;
                         st->comp_mean_w[q] += Iq / vq;
@@ -174,7 +221,10 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
             const bool has_target = (W.target_rel > 0.0) || (W.target_abs > 0.0);
             const double goal = fmax(W.target_rel * fabs(mean), W.target_abs);
             if (has_target && (uint32_t)st->iter >= W.train_iters + 2u && sigma <= goal) st->converged = 1;
-            s_refine = (W.freeze_after == 0u) || ((uint32_t)st->iter < W.freeze_after);
+            // the grid is refined after every iteration until freeze_after iterations have run; in the
+            // pooled combination it is frozen once the training iterations are done
+            s_refine = ((W.freeze_after == 0u) || ((uint32_t)st->iter < W.freeze_after)) &&
+                       (!pooled || (uint32_t)st->iter <= W.train_iters);
         }
         __syncthreads();
         if (s_refine) {
@@ -251,6 +301,29 @@ __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members,
         __syncthreads();
     }
     if (active) wo[i] = acc;
+}
+
+// FP64 throughput probe for the roofline denominator: every thread runs eight independent chains
+// a <- a * b + c (no dependency between consecutive DFMAs of one chain's neighbours), so the FP64 pipe, not
+// latency, bounds the loop.  The sink store never happens (the chains stay positive) but keeps the loop.
+__device__ double g_dfma_sink;
+
+__global__ void __launch_bounds__(256) k_dfma_rate(int iters) {
+    const double b = 0.9999999, c = 1.0e-7;
+    double a0 = 1.0 + 1e-9 * threadIdx.x, a1 = a0 + 0.1, a2 = a0 + 0.2, a3 = a0 + 0.3;
+    double a4 = a0 + 0.4, a5 = a0 + 0.5, a6 = a0 + 0.6, a7 = a0 + 0.7;
+    for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, b, c);
+        a1 = fma(a1, b, c);
+        a2 = fma(a2, b, c);
+        a3 = fma(a3, b, c);
+        a4 = fma(a4, b, c);
+        a5 = fma(a5, b, c);
+        a6 = fma(a6, b, c);
+        a7 = fma(a7, b, c);
+    }
+    const double s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (s < 0.0) g_dfma_sink = s;
 }
 
 __global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,

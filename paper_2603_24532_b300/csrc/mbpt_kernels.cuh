@@ -16,17 +16,21 @@ namespace mbpt {
 // group chunk has only as many rounds as its samples per thread, so the group parts take short
 // phases and spend the shared memory on per-sample slots), and the per-warp stack length:
 // carried-over entries of both classes plus one phase
-__host__ __device__ constexpr int class_rounds(int part) { return part == 3 ? 4 : (part == 2 ? 16 : 32); }
-__host__ __device__ constexpr int group_slots(int part) { return part == 3 ? kGroupSlotsReg : kGroupSlotsPlain; }
+__host__ __device__ constexpr int class_rounds(int part) {
+    return (part & 3) == 3 ? 4 : ((part & 3) == 2 ? 16 : 32);
+}
+__host__ __device__ constexpr int group_slots(int part) { return (part & 3) == 3 ? kGroupSlotsReg : kGroupSlotsPlain; }
 __host__ __device__ constexpr int queue_len(int part) { return 2 * 31 + 32 * class_rounds(part) + 2; }
 
 // Shared memory of one k_iterate block; the regulator and group arrays exist only in their parts
-// (PART bit 0: regulator, bit 1: group), which leaves the plain kernel room for long pre-test phases.
+// (PART bit 0: regulator, bit 1: group; the sixth-order bit does not change the layout), which leaves the
+// plain kernel room for long pre-test phases.
 template <int NW, int PART = 0>
 struct alignas(16) ChunkSmemT {
     DiagRec rec;
     Grid2 grid[kCells];
-    float hist[NW][kCells];                  // warp-private histograms
+    float hist[NW][kCells];                  // warp-private FP32 histograms, or (kHistBlockF64) the first
+                                             // 8 kCells bytes hold one block-shared FP64 histogram
     double cacc[(PART & 1) ? 2 * kComp : 1][NW * 32];   // per-thread sums of the regulator components
     double gacc[(PART & 2) ? group_slots(PART) : 1][NW * 32];  // group integrals: per-sample sums over the members
     uint32_t queue[NW][queue_len(PART)];     // per-warp stacks of samples past the pre-test
@@ -36,6 +40,7 @@ struct alignas(16) ChunkSmemT {
     uint32_t chunk, item, iter, skip;
 };
 using ChunkSmem = ChunkSmemT<kWarps, 0>;
+static_assert(sizeof(double) * kCells <= sizeof(float) * 4 * kCells, "the FP64 histogram fits the FP32 ones of 4 warps");
 
 __device__ __forceinline__ void load_record(DiagRec* dst, const DiagRec* src) {
     const uint4* s = reinterpret_cast<const uint4*>(src);
@@ -80,9 +85,21 @@ __device__ __forceinline__ void load_grid(Grid2* gs, const double* grid, int d, 
     }
 }
 
-// Histogram of w^2 over the sample's bins (warp-private FP32 bins; clamped below FLT_MAX).
+// Histogram of w^2 over the sample's bins: warp-private FP32 bins (clamped below FLT_MAX), or
+// (layout kHistBlockF64) one FP64 histogram shared by the block at the start of the same array.
 template <int D>
-__device__ __forceinline__ void hist_add(float* hist, int nb, const uint32_t* binpack, double w) {
+__device__ __forceinline__ void hist_add(float* hist, float* hist_block, uint32_t layout, int nb,
+                                         const uint32_t* binpack, double w) {
+    if (layout == kHistBlockF64) {
+        double* h = reinterpret_cast<double*>(hist_block);
+        const double w2 = w * w;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const uint32_t i = (binpack[a >> 2] >> (8 * (a & 3))) & 0xffu;
+            atomicAdd(&h[a * nb + i], w2);
+        }
+        return;
+    }
     const float wf = narrow_trunc(w);
     float w2 = wf * wf;
     if (!(w2 <= 3.0e38f)) w2 = 3.0e38f;
@@ -129,8 +146,8 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  above, adding the weights per sample into gacc, zeroed per chunk (spt x (1 + regulator components)
 //  <= group_slots() slots per thread); sums, squares and the histogram then see the group's integrand.
 template <int N, int PREC, int MAPK, bool REG, bool GRP, int NW>
-__device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 2 : 0)>& S, const WorkItem& W, uint32_t chunk_local, double& sw,
-                                          double& sw2) {
+__device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 2 : 0)>& S, const WorkItem& W,
+                                          uint32_t chunk_local, double& sw, double& sw2) {
     const DiagRec& R = S.rec;
     const int w_spt = W.spt;
     const uint64_t w_samples = W.samples;
@@ -141,6 +158,8 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
     const uint32_t t = S.iter;
     const uint32_t k0 = (uint32_t)W.seed, k1 = (uint32_t)(W.seed >> 32);
     float* hist = S.hist[threadIdx.x >> 5];
+    float* hist_block = &S.hist[0][0];
+    const uint32_t layout = W.hist_layout;
     uint32_t* q = S.queue[threadIdx.x >> 5];
     const uint32_t lane = threadIdx.x & 31u;
     const int nb = R.nb;
@@ -215,7 +234,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                     if (nonzero(o.w)) {          // a zero weight leaves both sums unchanged: no FP64 work
                         sw += o.w;
                         sw2 = fma(o.w, o.w, sw2);
-                        hist_add<D>(hist, nb, o.binpack, o.w);
+                        hist_add<D>(hist, hist_block, layout, nb, o.binpack, o.w);
                     }
                     if constexpr (REG) {
 #pragma unroll
@@ -252,7 +271,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
         if (nonzero(w)) {
             uint32_t bp[kBinWords];
             sample_bins<D>((uint32_t)s, t, w_sid, k0, k1, (uint32_t)nb, bp);
-            hist_add<D>(hist, nb, bp, w);
+            hist_add<D>(hist, hist_block, layout, nb, bp, w);
         }
     }
 }
@@ -282,16 +301,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 // chunk does not depend on which block ran it or what else is in the batch.
 // Compiled in several launch shapes (threads per block x minimum resident blocks, i.e. a register cap);
 // the autotuner picks one per context.
-// The batch is run by four kernels, one per part, each carrying only its own instantiations: PART
-// bit 0 = the integrals carry the denominator regulator, bit 1 = group integrals.
+// The batch is run by kParts kernels, one per part, each carrying only its own instantiations: PART
+// bit 0 = the integrals carry the denominator regulator, bit 1 = group integrals, bit 2 = sixth order.
 template <int TPB, int PART>
 __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* __restrict__ items,
                                                double* __restrict__ csum, float* __restrict__ chist) {
     constexpr int NW = TPB / 32;
+    constexpr int LAYOUT = PART & (kPartReg | kPartGrp);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ChunkSmemT<NW, PART>& S = *reinterpret_cast<ChunkSmemT<NW, PART>*>(smem_raw);
+    ChunkSmemT<NW, LAYOUT>& S = *reinterpret_cast<ChunkSmemT<NW, LAYOUT>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr bool REGP = (PART & 1) != 0, GRPP = (PART & 2) != 0;
+    constexpr bool REGP = (PART & kPartReg) != 0, GRPP = (PART & kPartGrp) != 0, O6P = (PART & kPartO6) != 0;
+    static_assert(NW >= 4, "the FP64 block histogram overlays the FP32 histograms of four warps");
     uint32_t item0 = 0, chunk0 = 0;
 #pragma unroll
     for (int p = 0; p < PART; ++p) {
@@ -313,14 +334,16 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
                 }
                 it = lo;
                 if (c - items[it].chunk_begin >= items[it].n_chunks) atomicOr(&hdr->error, 1u);
-                if ((items[it].rec->n_shifts != 0) != REGP || (items[it].n_members > 1) != GRPP)
+                if ((items[it].rec->n_shifts != 0) != REGP || (items[it].n_members > 1) != GRPP ||
+                    (items[it].rec->order == 6) != O6P)
                     atomicOr(&hdr->error, 4u);
             }
             S.chunk = (cl < total) ? chunk0 + cl : 0xFFFFFFFFu;
             S.item = it;
             S.skip = (cl < total) ? (uint32_t)items[it].state->converged |
                                         (uint32_t)((items[it].rec->n_shifts != 0) != REGP ||
-                                                   (items[it].n_members > 1) != GRPP)
+                                                   (items[it].n_members > 1) != GRPP ||
+                                                   (items[it].rec->order == 6) != O6P)
                                   : 1u;
             S.iter = (cl < total) ? (uint32_t)items[it].state->iter : 0u;
         }
@@ -345,22 +368,30 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
         __syncthreads();
         double sw = 0.0, sw2 = 0.0;
         const uint32_t cl = chunk - W.chunk_begin;
-        switch ((order * 3 + prec) * 2 + S.rec.map_kind) {
+        const int key = (order * 3 + prec) * 2 + S.rec.map_kind;
 #define MBPT_CASE(N_, P_, M_) \
     case (N_ * 3 + P_) * 2 + M_: run_chunk<N_, P_, M_, REGP, GRPP, NW>(S, W, cl, sw, sw2); break;
 #define MBPT_CASES(N_) \
     MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
     MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)
-            MBPT_CASES(2)
-            MBPT_CASES(3)
-            MBPT_CASES(4)
-            MBPT_CASES(5)
-            MBPT_CASES(6)
+        if constexpr (O6P) {
+            switch (key) {
+                MBPT_CASES(6)
+                default:
+                    if (tid == 0) atomicOr(&hdr->error, 2u);
+            }
+        } else {
+            switch (key) {
+                MBPT_CASES(2)
+                MBPT_CASES(3)
+                MBPT_CASES(4)
+                MBPT_CASES(5)
+                default:
+                    if (tid == 0) atomicOr(&hdr->error, 2u);
+            }
+        }
 #undef MBPT_CASES
 #undef MBPT_CASE
-            default:
-                if (tid == 0) atomicOr(&hdr->error, 2u);
-        }
         sw = warp_sum(sw);
         sw2 = warp_sum(sw2);
         if (lane == 0) {
@@ -391,10 +422,15 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
                 }
         }
         float* dst = chist + (size_t)chunk * (size_t)W.hist_stride;
-        for (int i = tid; i < d * nb; i += blockDim.x) {
-            float v = 0.0f;
-            for (int w = 0; w < NW; ++w) v += S.hist[w][i];
-            dst[i] = v;
+        if (W.hist_layout == kHistBlockF64) {
+            const double* h = reinterpret_cast<const double*>(&S.hist[0][0]);
+            for (int i = tid; i < d * nb; i += blockDim.x) dst[i] = (float)h[i];
+        } else {
+            for (int i = tid; i < d * nb; i += blockDim.x) {
+                float v = 0.0f;
+                for (int w = 0; w < NW; ++w) v += S.hist[w][i];
+                dst[i] = v;
+            }
         }
         __syncthreads();
     }

@@ -108,20 +108,23 @@ struct Arena {
 // ---------------------------------------------------------------------------
 namespace {
 typedef void (*IterateFn)(WorkHeader*, const WorkItem*, double*, float*);
-constexpr int kParts = 4;      // plain, plain + regulator, group, group + regulator
+// one k_iterate kernel per batch part (kParts: regulator, group and sixth-order bits); the shared-memory
+// layout depends on the regulator and group bits only
 struct KernelVariant {
     int tpb, minb;
     IterateFn fn[kParts];
     size_t smem[kParts];
 };
-#define MBPT_SMEM(NW) {sizeof(ChunkSmemT<NW, 0>), sizeof(ChunkSmemT<NW, 1>), sizeof(ChunkSmemT<NW, 2>), sizeof(ChunkSmemT<NW, 3>)}
+#define MBPT_SMEM4(NW) sizeof(ChunkSmemT<NW, 0>), sizeof(ChunkSmemT<NW, 1>), sizeof(ChunkSmemT<NW, 2>), sizeof(ChunkSmemT<NW, 3>)
+#define MBPT_SMEM(NW) {MBPT_SMEM4(NW), MBPT_SMEM4(NW)}
 const KernelVariant kVariants[] = {
-    {256, 2, {k_iterate_256x2, k_iterate_256x2_reg, k_iterate_256x2_grp, k_iterate_256x2_grp_reg}, MBPT_SMEM(8)},
-    {128, 4, {k_iterate_128x4, k_iterate_128x4_reg, k_iterate_128x4_grp, k_iterate_128x4_grp_reg}, MBPT_SMEM(4)},
-    {256, 1, {k_iterate_256x1, k_iterate_256x1_reg, k_iterate_256x1_grp, k_iterate_256x1_grp_reg}, MBPT_SMEM(8)},
-    {128, 3, {k_iterate_128x3, k_iterate_128x3_reg, k_iterate_128x3_grp, k_iterate_128x3_grp_reg}, MBPT_SMEM(4)},
+    {256, 2, {MBPT_K_ITERATE_PARTS(256, 2)}, MBPT_SMEM(8)},
+    {128, 4, {MBPT_K_ITERATE_PARTS(128, 4)}, MBPT_SMEM(4)},
+    {256, 1, {MBPT_K_ITERATE_PARTS(256, 1)}, MBPT_SMEM(8)},
+    {128, 3, {MBPT_K_ITERATE_PARTS(128, 3)}, MBPT_SMEM(4)},
 };
 #undef MBPT_SMEM
+#undef MBPT_SMEM4
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 }  // namespace
 
@@ -135,7 +138,8 @@ struct mbpt_ctx {
     int variant = 0;                       // index into kVariants
     int variant_blocks[kNumVariants][kParts] = {};   // persistent grid of each k_iterate variant and part
     int finalize_blocks = 0;
-    int spt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16, 16};
+    int spt[MBPT_MAX_DEVICE_ORDER + 1] = {};  // samples per thread of a chunk by order (kDefaultSpt at creation)
+    int hist_layout = kHistWarpF32;          // per-chunk histogram layout of k_iterate
     // batch buffers (arena)
     WorkHeader* d_hdr = nullptr;
     WorkItem* d_items = nullptr;
@@ -144,6 +148,7 @@ struct mbpt_ctx {
     float* d_chist = nullptr;
     size_t items_cap = 0, chunks_cap = 0, hist_cap = 0;
     cudaGraphExec_t graph = nullptr;
+    unsigned graph_parts = 0;              // parts whose k_iterate kernel the captured graph launches
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // around k_iterate and k_finalize (graph nodes)
     std::set<mbpt_diag*> diags;
     std::vector<WorkItem> h_items;
@@ -233,17 +238,20 @@ int ensure_batch_buffers(mbpt_ctx* c, size_t n_items, size_t n_chunks, size_t hi
     return MBPT_OK;
 }
 
-int capture_graph(mbpt_ctx* c) {
-    if (c->graph) return MBPT_OK;
+// The iteration as a graph: reset the chunk counters, one k_iterate launch per non-empty part of the
+// batch (bit p of `parts`), k_finalize.  Re-captured when the set of non-empty parts changes.
+int capture_graph(mbpt_ctx* c, unsigned parts) {
+    if (c->graph && c->graph_parts == parts) return MBPT_OK;
+    invalidate_graph(c);
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(c->d_hdr->part_counter, 0, kParts * sizeof(uint32_t), c->stream);
     cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal);
     const KernelVariant& kv = kVariants[c->variant];
-    // the blocks of an empty part exit at once
     for (int p = 0; p < kParts; ++p)
-        kv.fn[p]<<<c->variant_blocks[c->variant][p], kv.tpb, kv.smem[p], c->stream>>>(c->d_hdr, c->d_items, c->d_csum,
-                                                                                      c->d_chist);
+        if (parts & (1u << p))
+            kv.fn[p]<<<c->variant_blocks[c->variant][p], kv.tpb, kv.smem[p], c->stream>>>(c->d_hdr, c->d_items,
+                                                                                          c->d_csum, c->d_chist);
     cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal);
     k_finalize<<<c->finalize_blocks, 256, 0, c->stream>>>(c->d_hdr, c->d_items, c->d_csum, c->d_chist,
                                                          c->d_last_hist);
@@ -256,6 +264,7 @@ int capture_graph(mbpt_ctx* c) {
         c->graph = nullptr;
         return fail(MBPT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
+    c->graph_parts = parts;
     return MBPT_OK;
 }
 
@@ -300,6 +309,7 @@ int mbpt_ctx_create(mbpt_ctx** out, int device, void* arena, size_t arena_bytes,
     mbpt_ctx* c = new (std::nothrow) mbpt_ctx();
     if (!c) return fail(MBPT_ENOMEM, "ctx_create: host allocation");
     c->device = device;
+    for (int o = 0; o <= MBPT_MAX_DEVICE_ORDER; ++o) c->spt[o] = kDefaultSpt[o];
     cudaDeviceProp p;
     cudaError_t e = cudaGetDeviceProperties(&p, device);
     if (e != cudaSuccess) {
@@ -451,6 +461,19 @@ int mbpt_ctx_set_launch(mbpt_ctx* c, int order, int spt) {
     return MBPT_OK;
 }
 
+int mbpt_ctx_set_hist_layout(mbpt_ctx* c, int layout) {
+    if (!c || (layout != MBPT_HIST_WARP_F32 && layout != MBPT_HIST_BLOCK_F64))
+        return fail(MBPT_EINVAL, "set_hist_layout: bad argument");
+    c->hist_layout = layout;
+    return MBPT_OK;
+}
+
+int mbpt_ctx_get_hist_layout(const mbpt_ctx* c, int* layout) {
+    if (!c || !layout) return fail(MBPT_EINVAL, "get_hist_layout: NULL argument");
+    *layout = c->hist_layout;
+    return MBPT_OK;
+}
+
 int mbpt_ctx_get_launch(const mbpt_ctx* c, int order, int* tpb, int* minb, int* spt) {
     if (!c || !tpb || !minb || !spt || order < 2 || order > MBPT_MAX_DEVICE_ORDER)
         return fail(MBPT_EINVAL, "get_launch: bad argument");
@@ -465,7 +488,10 @@ static int create_integral(mbpt_ctx* c, const mbpt_diagram_desc* descs, int k, c
     std::vector<DiagRec> recs((size_t)k);
     char err[256] = {0};
     for (int m = 0; m < k; ++m) {
-        int st = compile_record(descs[m], *ph, *cfg, &recs[m], err, sizeof(err));
+        // group members are aligned: hole chords first, so that all of them see the same loop momenta
+        mbpt_diagram_desc dm = descs[m];
+        if (k > 1) hole_chords_first(dm);
+        int st = compile_record(dm, *ph, *cfg, &recs[m], err, sizeof(err));
         if (st) return fail(st, std::string(who) + ": member " + std::to_string(m) + ": " + err);
         if (recs[m].order != recs[0].order)
             return fail(MBPT_EINVAL, std::string(who) + ": members must have the same order");
@@ -565,6 +591,7 @@ int mbpt_set_config(mbpt_diag* g, const mbpt_vegas_cfg* cfg) {
     const mbpt_vegas_cfg& o = g->cfg;
     if (cfg->n_bins != o.n_bins || cfg->precision != o.precision || cfg->seed != o.seed ||
         cfg->stream_id != o.stream_id || cfg->alpha != o.alpha || cfg->n_shifts != o.n_shifts ||
+        cfg->combine != o.combine || cfg->near_band != o.near_band ||
         (o.n_shifts && (cfg->shift[0] != o.shift[0] || cfg->shift[1] != o.shift[1] || cfg->shift[2] != o.shift[2])))
         return fail(MBPT_EINVAL, "set_config: only samples_per_iter, freeze_after, train_iters and the targets may change");
     if (cfg->samples_per_iter < 2 || cfg->samples_per_iter >= (1ull << 32) || !(cfg->target_rel >= 0.0) ||
@@ -606,14 +633,17 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         if (!seen.insert(g).second) return fail(MBPT_EINVAL, "vegas_iterate: integral listed twice");
         stride = std::max(stride, g->d * g->nb);
     }
-    // the batch's parts in kernel order (bit 0: regulator, bit 1: group), each in call order
-    auto part_of = [](const mbpt_diag* g) { return (g->cfg.n_shifts != 0 ? 1 : 0) | (g->n_members > 1 ? 2 : 0); };
+    // the batch's parts in kernel order (bit 0: regulator, bit 1: group, bit 2: sixth order), each in call order
+    auto part_of = [](const mbpt_diag* g) {
+        return (g->cfg.n_shifts != 0 ? kPartReg : 0) | (g->n_members > 1 ? kPartGrp : 0) |
+               (g->desc.order == 6 ? kPartO6 : 0);
+    };
     std::vector<mbpt_diag*> order_v;
     order_v.reserve((size_t)k);
     for (int part = 0; part < kParts; ++part)
         for (int i = 0; i < k; ++i)
             if (part_of(diags[i]) == part) order_v.push_back(diags[i]);
-    uint32_t part_items[kParts] = {0, 0, 0, 0}, part_chunks[kParts] = {0, 0, 0, 0};
+    uint32_t part_items[kParts] = {}, part_chunks[kParts] = {};
     for (int i = 0; i < k; ++i) {
         mbpt_diag* g = order_v[(size_t)i];
         const int part = part_of(g);
@@ -638,6 +668,8 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         w.target_rel = g->cfg.target_rel;
         w.target_abs = g->cfg.target_abs;
         w.train_iters = g->cfg.train_iters;
+        w.combine = g->cfg.combine;
+        w.hist_layout = (uint32_t)c->hist_layout;
         w.hist_stride = stride;
         chunk += w.n_chunks;
         if (chunk >= (1ull << 31)) return fail(MBPT_EINVAL, "vegas_iterate: batch too large");
@@ -661,7 +693,10 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
     CUDA_TRY(cudaMemcpyAsync(c->d_last_hist, c->h_last_hist.data(), sizeof(double*) * k, cudaMemcpyHostToDevice,
                              c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
-    st = capture_graph(c);
+    unsigned parts = 0;
+    for (int p = 0; p < kParts; ++p)
+        if (part_items[p]) parts |= 1u << p;
+    st = capture_graph(c, parts);
     if (st) return st;
     for (int it = 0; it < n_iters; ++it) CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
     CUDA_TRY(cudaGetLastError());
@@ -744,6 +779,7 @@ struct StateHeader {
     int32_t pad;
 };
 static const uint32_t kMagic = 0x4D425054u;   // "MBPT"
+static const uint32_t kStateVersion = 2u;      // 2: DiagState with the pooled evaluation-phase sums
 
 int mbpt_get_state(const mbpt_diag* g, void* buf, size_t cap, size_t* need) {
     if (!g || !need) return fail(MBPT_EINVAL, "get_state: NULL argument");
@@ -755,7 +791,7 @@ int mbpt_get_state(const mbpt_diag* g, void* buf, size_t cap, size_t* need) {
     mbpt_ctx* c = g->ctx;
     DeviceGuard dg(c->device);
     char* p = (char*)buf;
-    StateHeader h = {kMagic, 1u, g->d, g->nb, g->desc.order, 0};
+    StateHeader h = {kMagic, kStateVersion, g->d, g->nb, g->desc.order, 0};
     memcpy(p, &h, sizeof(h));
     p += sizeof(h);
     CUDA_TRY(cudaMemcpyAsync(p, g->d_state, sizeof(DiagState), cudaMemcpyDeviceToHost, c->stream));
@@ -774,7 +810,7 @@ int mbpt_set_state(mbpt_diag* g, const void* buf, size_t len) {
     if (len != bytes) return fail(MBPT_EINVAL, "set_state: wrong image size");
     StateHeader h;
     memcpy(&h, buf, sizeof(h));
-    if (h.magic != kMagic || h.version != 1u || h.d != g->d || h.nb != g->nb || h.order != g->desc.order)
+    if (h.magic != kMagic || h.version != kStateVersion || h.d != g->d || h.nb != g->nb || h.order != g->desc.order)
         return fail(MBPT_EINVAL, "set_state: image does not match this integral");
     const char* p = (const char*)buf + sizeof(h);
     DiagState s;
@@ -844,6 +880,9 @@ int mbpt_philox_device(mbpt_ctx* c, const uint32_t ctr[4], const uint32_t key[2]
 
 }  // extern "C"
 
+static_assert(sizeof(WorkItem) == 112 && sizeof(WorkHeader) == 128,
+              "work table layout changed: update the binding's transfer sizes (mbpt.py WORK_ITEM_BYTES, WORK_HEADER_BYTES)");
+
 // ---------------------------------------------------------------------------
 // Allocation-free single iteration (mbpt_vegas_iteration_noalloc).
 //
@@ -863,8 +902,11 @@ constexpr int kNoAllocMaxDevices = 64;
 struct NoAllocDevice {
     bool ready = false;
     unsigned char* ptr = nullptr;   // device address of g_noalloc_scratch on this device
-    int blocks = 0;                 // persistent grid of k_iterate
+    int blocks[2] = {0, 0};         // persistent grids of k_iterate: orders 2..5, sixth order
 };
+// the k_iterate kernels of a fresh context's default launch shape (256 threads, 2 blocks per SM) for plain
+// integrals of orders 2..5 and of the sixth order
+const IterateFn kNoAllocFn[2] = {MBPT_K_ITERATE(256, 2, 0), MBPT_K_ITERATE(256, 2, 4)};
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
@@ -876,28 +918,39 @@ int noalloc_setup(int device, NoAllocDevice** out) {
     if (!d.ready) {
         void* p = nullptr;
         CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        CUDA_TRY(cudaFuncSetAttribute(k_iterate_256x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(ChunkSmem)));
-        int per_sm = 0, sms = 0;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate_256x2, kThreads,
-                                                               sizeof(ChunkSmem)));
+        int sms = 0;
         CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-        if (per_sm < 1) return fail(MBPT_ECUDA, "noalloc: k_iterate cannot be resident");
+        for (int k = 0; k < 2; ++k) {
+            CUDA_TRY(cudaFuncSetAttribute(kNoAllocFn[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(ChunkSmem)));
+            int per_sm = 0;
+            CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kNoAllocFn[k], kThreads,
+                                                                   sizeof(ChunkSmem)));
+            if (per_sm < 1) return fail(MBPT_ECUDA, "noalloc: k_iterate cannot be resident");
+            d.blocks[k] = per_sm * sms;
+        }
         d.ptr = (unsigned char*)p;
-        d.blocks = per_sm * sms;
         d.ready = true;
     }
     *out = &d;
     return MBPT_OK;
 }
 
-// Fixed-order sums of one integral's chunk slots: out = [sum w, sum w^2, histogram d x nb].
-__global__ void __launch_bounds__(256) k_reduce_noalloc(const WorkItem* __restrict__ item,
+// Fixed-order sums of one integral's chunk slots: out = [sum w, sum w^2, histogram d x nb].  If k_iterate
+// set its error word (an out-of-range chunk, a misplaced item or a record no compiled case matches), every
+// output is NaN instead.
+__global__ void __launch_bounds__(256) k_reduce_noalloc(const WorkHeader* __restrict__ hdr,
+                                                       const WorkItem* __restrict__ item,
                                                        const double* __restrict__ csum,
                                                        const float* __restrict__ chist, double* __restrict__ out) {
     __shared__ double red[2][8];
     const WorkItem& W = *item;
     const int tid = threadIdx.x;
+    const int nh = W.rec->d * W.rec->nb;
+    if (hdr->error != 0u) {
+        for (int i = tid; i < 2 + nh; i += blockDim.x) out[i] = __longlong_as_double(0x7FF8000000000000ll);
+        return;
+    }
     double a = 0.0, b = 0.0;
     for (uint32_t c = tid; c < W.n_chunks; c += blockDim.x) {
         a += csum[kSumStride * (size_t)c];
@@ -919,7 +972,6 @@ __global__ void __launch_bounds__(256) k_reduce_noalloc(const WorkItem* __restri
         out[0] = A;
         out[1] = B;
     }
-    const int nh = W.rec->d * W.rec->nb;
     for (int i = tid; i < nh; i += blockDim.x)
         out[2 + i] = hist_column_sum(chist + i, (size_t)W.hist_stride, W.n_chunks);   // as k_finalize
 }
@@ -937,8 +989,7 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     char err[256] = {0};
     int st = compile_record(*desc, *ph, *cfg, &rec, err, sizeof(err));
     if (st) return fail(st, std::string("iteration_noalloc: ") + err);
-    static const int kSpt[MBPT_MAX_DEVICE_ORDER + 1] = {0, 0, 32, 32, 16, 16, 16};   // as a fresh context (256 threads)
-    const int spt = kSpt[rec.order];
+    const int spt = kDefaultSpt[rec.order];   // as a fresh context (256 threads)
     const uint64_t cs = (uint64_t)kThreads * (uint64_t)spt;
     const uint64_t n_chunks = (cfg->samples_per_iter + cs - 1) / cs;
     const size_t nh = (size_t)rec.d * (size_t)rec.nb;
@@ -966,8 +1017,9 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     h.n_items = 1;
     h.total_chunks = (uint32_t)n_chunks;
     h.hist_floats = (uint64_t)nh * n_chunks;
-    h.part_items[0] = 1;
-    h.part_chunks[0] = (uint32_t)n_chunks;
+    const int part = rec.order == 6 ? kPartO6 : 0;
+    h.part_items[part] = 1;
+    h.part_chunks[part] = (uint32_t)n_chunks;
     DiagState s0;
     memset(&s0, 0, sizeof(s0));
     s0.iter = (int32_t)iter;
@@ -989,12 +1041,51 @@ extern "C" int mbpt_vegas_iteration_noalloc(int device, const mbpt_diagram_desc*
     CUDA_TRY(cudaMemcpyAsync(base + off_item, &w, sizeof(w), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(base + off_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(base + off_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, s));
-    k_iterate_256x2<<<nd->blocks, kThreads, sizeof(ChunkSmem), s>>>((WorkHeader*)(base + off_hdr),
-                                                             (const WorkItem*)(base + off_item),
-                                                             (double*)(base + off_csum), (float*)(base + off_chist));
+    const int kk = part == kPartO6 ? 1 : 0;
+    kNoAllocFn[kk]<<<nd->blocks[kk], kThreads, sizeof(ChunkSmem), s>>>((WorkHeader*)(base + off_hdr),
+                                                                       (const WorkItem*)(base + off_item),
+                                                                       (double*)(base + off_csum),
+                                                                       (float*)(base + off_chist));
     CUDA_TRY(cudaGetLastError());
-    k_reduce_noalloc<<<1, 256, 0, s>>>((const WorkItem*)(base + off_item), (const double*)(base + off_csum),
-                                       (const float*)(base + off_chist), out);
+    k_reduce_noalloc<<<1, 256, 0, s>>>((const WorkHeader*)(base + off_hdr), (const WorkItem*)(base + off_item),
+                                       (const double*)(base + off_csum), (const float*)(base + off_chist), out);
     CUDA_TRY(cudaGetLastError());
+    return MBPT_OK;
+}
+
+namespace mbpt {
+__global__ void k_dfma_rate(int iters);   // mbpt_k_misc.cu
+}
+
+extern "C" int mbpt_fp64_rate(int device, void* cuda_stream, double* ops_per_s) {
+    if (!ops_per_s) return fail(MBPT_EINVAL, "fp64_rate: NULL argument");
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(MBPT_EINVAL, "fp64_rate: no such device");
+    DeviceGuard dg(device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int blocks = 8 * sms, threads = 256, iters = 4096;   // 2048 resident threads per SM
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    float best = 0.0f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // the first launch warms up
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) {
+            k_dfma_rate<<<blocks, threads, 0, s>>>(iters);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(MBPT_ECUDA, std::string("fp64_rate: ") + cudaGetErrorString(e));
+    *ops_per_s = 8.0 * (double)iters * (double)threads * (double)blocks / (1e-3 * (double)best);
     return MBPT_OK;
 }

@@ -23,6 +23,10 @@ MBPT_EBUSY = -7
 MBPT_FP64 = 0
 MBPT_MIXED = 1
 MBPT_MIXED_MAP64 = 2
+MBPT_COMBINE_INVVAR = 0
+MBPT_COMBINE_POOLED = 1
+MBPT_HIST_WARP_F32 = 0
+MBPT_HIST_BLOCK_F64 = 1
 MAX_ORDER = 6
 MAX_LINES = 12
 MAX_CHORDS = 7
@@ -122,6 +126,7 @@ class mbpt_vegas_cfg(ctypes.Structure):
         ("target_rel", ctypes.c_double), ("target_abs", ctypes.c_double),
         ("train_iters", ctypes.c_uint32), ("n_shifts", ctypes.c_uint32),
         ("shift", ctypes.c_double * 3),
+        ("combine", ctypes.c_uint32), ("near_band", ctypes.c_float),
     ]
 
 
@@ -161,6 +166,8 @@ def lib():
             "mbpt_ctx_set_kernel": [vp, ctypes.c_int, ctypes.c_int],
             "mbpt_ctx_set_launch": [vp, ctypes.c_int, ctypes.c_int],
             "mbpt_ctx_get_launch": [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
+            "mbpt_ctx_set_hist_layout": [vp, ctypes.c_int],
+            "mbpt_ctx_get_hist_layout": [vp, P(ctypes.c_int)],
             "mbpt_ctx_last_timing": [vp, P(ctypes.c_double), P(ctypes.c_double)],
             "mbpt_ctx_stream": [vp, P(vp)],
             "mbpt_create_diagram": [vp, P(mbpt_diagram_desc), P(mbpt_physics), P(mbpt_vegas_cfg), P(vp)],
@@ -182,6 +189,7 @@ def lib():
             "mbpt_philox_device": [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_int64, P(ctypes.c_uint32)],
             "mbpt_vegas_iteration_noalloc": [ctypes.c_int, P(mbpt_diagram_desc), P(mbpt_physics), P(mbpt_vegas_cfg),
                                              ctypes.c_uint32, vp, vp, vp],
+            "mbpt_fp64_rate": [ctypes.c_int, vp, P(ctypes.c_double)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -275,6 +283,16 @@ def mbpt_ctx_get_launch(ctx, order: int):
     t, m, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     check(lib().mbpt_ctx_get_launch(ctx, order, ctypes.byref(t), ctypes.byref(m), ctypes.byref(s)))
     return t.value, m.value, s.value
+
+
+def mbpt_ctx_set_hist_layout(ctx, layout: int):
+    check(lib().mbpt_ctx_set_hist_layout(ctx, layout))
+
+
+def mbpt_ctx_get_hist_layout(ctx) -> int:
+    v = ctypes.c_int()
+    check(lib().mbpt_ctx_get_hist_layout(ctx, ctypes.byref(v)))
+    return v.value
 
 
 def mbpt_ctx_last_timing(ctx):
@@ -382,6 +400,14 @@ def mbpt_philox_device(ctx, ctr: Sequence[int], key: Sequence[int], count: int) 
     return out.reshape(count, 4)
 
 
+def mbpt_fp64_rate(device: int = 0, stream: int = 0) -> float:
+    """FP64 thread operations per second that a dependency-free DFMA loop reaches on the device now
+    (the roofline denominator of the FP64-bound kernels)."""
+    v = ctypes.c_double()
+    check(lib().mbpt_fp64_rate(device, ctypes.c_void_p(stream or None), ctypes.byref(v)))
+    return v.value
+
+
 def mbpt_vegas_iteration_noalloc(device: int, desc: mbpt_diagram_desc, phys: mbpt_physics, cfg: mbpt_vegas_cfg,
                                  iter_: int, grid_ptr: int, out_ptr: int, stream: int = 0):
     """One iteration without device allocation; grid_ptr / out_ptr are device addresses
@@ -394,10 +420,14 @@ def mbpt_vegas_iteration_noalloc(device: int, desc: mbpt_diagram_desc, phys: mbp
 # ---------------------------------------------------------------------------
 # State image layout helpers (header, DiagState, grid, last histogram)
 # ---------------------------------------------------------------------------
+# bytes moved per integral and batch by mbpt_vegas_iterate (work item, work header) and mbpt_estimate_batch
+WORK_ITEM_BYTES = 112
+WORK_HEADER_BYTES = 128
+RESULT_BYTES = 80
 STATE_HEADER_BYTES = 24
 MAX_ITERS = 512
 N_COMP = 4
-DIAGSTATE_BYTES = 7 * 8 + 8 + 4 * 4 + 2 * MAX_ITERS * 8 + 4 * N_COMP * 8
+DIAGSTATE_BYTES = 7 * 8 + 8 + 4 * 4 + 2 * MAX_ITERS * 8 + 4 * N_COMP * 8 + 4 * 8 + 2 * N_COMP * 8   # = 8496
 
 
 def state_grid(image: bytes, d: int, nb: int) -> np.ndarray:
@@ -438,13 +468,15 @@ def physics(kF_n=1.0, kF_p=0.0, hbar2_over_m=41.47, C_S=-50.0, C_Y=-200.0, m_pi=
 
 
 def vegas_cfg(samples=1 << 18, seed=1, stream_id=0, precision=MBPT_FP64, n_bins=50, alpha=1.5, freeze_after=0,
-              target_rel=0.0, target_abs=0.0, train_iters=0, shifts=None) -> mbpt_vegas_cfg:
+              target_rel=0.0, target_abs=0.0, train_iters=0, shifts=None, combine=MBPT_COMBINE_INVVAR,
+              near_band=0.0) -> mbpt_vegas_cfg:
     c = mbpt_vegas_cfg()
     c.n_bins, c.precision, c.alpha = n_bins, precision, alpha
     c.seed, c.stream_id, c.freeze_after = seed, stream_id, freeze_after
     c.samples_per_iter = samples
     c.target_rel, c.target_abs = target_rel, target_abs
     c.train_iters = train_iters
+    c.combine, c.near_band = combine, near_band
     if shifts:
         if len(shifts) != 3:
             raise ValueError("the denominator regulator takes exactly three shifts")

@@ -15,8 +15,14 @@ The loop (one "round" per VEGAS iteration of every resident integral):
   3. read the estimates; after the first round of a request its summed estimate E_sum sets a
      per-integral error budget sigma_G <= target |E_sum| / sqrt(N_int); integrals that reach
      their budget (after at least `min_iters` iterations) retire and stop consuming samples;
-  4. a request completes when all its integrals have retired (or hit `max_iters`); its
-     integrals are destroyed, freeing arena memory for waiting requests.
+  4. a request completes when all its integrals have retired (or hit `max_iters`), or earlier,
+     once the error of its sum, sqrt(sum sigma_G^2), meets target |E_sum|; its integrals are
+     destroyed, freeing arena memory for waiting requests.
+
+With the GPU backend every integral trains its VEGAS grid for a few iterations and then
+estimates on the frozen grid, every evaluation sample carrying the same weight (PVegas'
+training and evaluation phases, Sec. III.C); its error is the standard error of all its
+evaluation samples, which stays honest for the heavy-tailed weights of fourth-order diagrams.
 
 Requests that arrive while others are on the GPU join the next round: their integrals run in
 the same persistent launch as everything else.  Each integral's random stream is keyed by
@@ -65,6 +71,13 @@ class Request:
     budget: Optional[float] = None
     rounds: int = 0
     cancelled: bool = False
+    capped: bool = False      # some integral stopped at the iteration cap before reaching its error budget
+
+    @property
+    def met(self) -> bool:
+        """Finished with a finite energy whose error meets the requested relative target."""
+        return (self.energy is not None and self.sigma is not None and math.isfinite(self.energy)
+                and self.sigma <= self.target * abs(self.energy))
 
     @property
     def latency(self) -> Optional[float]:
@@ -104,9 +117,17 @@ class GroupUnit:
         self.scales = list(scales)
 
 
+# VEGAS grid compression by order (measured: at fourth and fifth order Lepage's alpha = 1.5 concentrates
+# the bins so strongly that rare samples in the wide bins dominate the variance) and training iterations
+ALPHA_BY_ORDER = {2: 1.5, 3: 1.5, 4: 1.0, 5: 0.75, 6: 0.75}
+TRAIN_BY_ORDER = {2: 2, 3: 2, 4: 3, 5: 3, 6: 3}
+
+
 class MbptBackend:
     """The C ABI as the server's backend (all work on the GPU).  With grouped=True each order of a
-    request is a handful of group integrals (Table I's N_grp) instead of one integral per diagram."""
+    request is a handful of group integrals (Table I's N_grp) instead of one integral per diagram.
+    Integrals train their grid for TRAIN_BY_ORDER iterations and are then estimated on the frozen grid
+    (MBPT_COMBINE_POOLED), with grid compression ALPHA_BY_ORDER."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, arena_ptr: int = 0, stream: int = 0,
                  precision: Optional[int] = None, map_kind: int = 1, dedup_mirrors: bool = True,
@@ -156,8 +177,10 @@ class MbptBackend:
     def physics(self, kF_n: float, kF_p: float):
         return self.M.physics(kF_n=kF_n, kF_p=kF_p, K_max=max(kF_n, kF_p) + 6.0, map_kind=self.map_kind)
 
-    def cfg(self, samples: int, stream_id: int, seed: int):
-        return self.M.vegas_cfg(samples=samples, seed=seed, stream_id=stream_id, precision=self.precision)
+    def cfg(self, samples: int, stream_id: int, seed: int, order: int = 2):
+        return self.M.vegas_cfg(samples=samples, seed=seed, stream_id=stream_id, precision=self.precision,
+                                alpha=ALPHA_BY_ORDER[order], train_iters=TRAIN_BY_ORDER[order],
+                                combine=self.M.MBPT_COMBINE_POOLED)
 
     def nbytes(self, desc, cfg) -> int:
         if isinstance(desc, GroupUnit):
@@ -250,8 +273,8 @@ class GridCache:
         return None if best is None else self.entries[k + (best,)]
 
 
-SAMPLES_BY_ORDER = {2: 1 << 16, 3: 1 << 16, 4: 1 << 16, 5: 1 << 16}   # pilot iteration
-MIN_SAMPLES, MAX_SAMPLES = 1 << 14, 1 << 21
+SAMPLES_BY_ORDER = {2: 1 << 16, 3: 1 << 16, 4: 1 << 17, 5: 1 << 17}   # training iterations
+MIN_SAMPLES, MAX_SAMPLES = 1 << 16, 1 << 22
 
 
 class Server:
@@ -300,7 +323,7 @@ class Server:
         for order in range(2, req.cap + 1):
             for d in (self.b.units(order) if hasattr(self.b, "units") else self.b.diagrams(order)):
                 sid = (req.rid * 8 + order) * 1024 + d.diagram_id
-                cfg = self.b.cfg(self.samples[order], sid & 0xFFFFFFFF, self.seed)
+                cfg = self.b.cfg(self.samples[order], sid & 0xFFFFFFFF, self.seed, order=order)
                 plan.append((order, d, phys, cfg, self.b.nbytes(d, cfg)))
         return plan
 
@@ -336,10 +359,19 @@ class Server:
                                 self.b.set_train(h, it.cfg, self.warm_train)
                             it.warm = True
             except MemoryError:
-                # the arena refused (its scratch competes with integral state): roll back, retry later
+                # the arena refused (its scratch competes with integral state): roll back and retry once
+                # running requests have freed memory; with nothing running nothing will be freed, so the
+                # request can never fit and is completed as unfittable instead of blocking the queue
                 for it in created:
                     self.b.destroy(it.handle)
-                return
+                if self.active:
+                    return
+                self.waiting.pop(0)
+                req.completed = now
+                req.energy = float("nan")
+                self.done.append(req)
+                self._log({"event": "unfittable", "rid": req.rid})
+                continue
             self.waiting.pop(0)
             req.admitted = now
             req.integrals = created
@@ -393,8 +425,11 @@ class Server:
                 if it.done:
                     continue
                 it.evals += it.samples
-                if (it.n_iter >= self.min_iters and it.sigma <= req.budget) or it.n_iter >= self.max_iters:
+                if it.n_iter >= self.min_iters and it.sigma <= req.budget:
                     it.done = True
+                elif it.n_iter >= self.max_iters:
+                    it.done = True
+                    req.capped = True
                 elif (self.adaptive and hasattr(self.b, "set_samples") and 0.0 < it.sigma < float("inf")
                       and req.budget > 0.0):
                     # samples still needed if sigma ~ 1/sqrt(evaluations), spread over a few iterations
@@ -405,6 +440,14 @@ class Server:
                     if nxt != it.samples:
                         self.b.set_samples(it.handle, it.cfg, nxt)
                         it.samples = nxt
+            # the request's own error target met: the remaining integrals retire with it (their estimates
+            # already count; every integral has finished its training)
+            if (not all(it.done for it in req.integrals) and req.budget is not None
+                    and all(it.n_iter >= self.min_iters and math.isfinite(it.sigma) for it in req.integrals)
+                    and math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals))
+                    <= req.target * abs(e_sum)):
+                for it in req.integrals:
+                    it.done = True
             if all(it.done for it in req.integrals):
                 req.energy = e_sum
                 req.sigma = math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals))
@@ -483,9 +526,17 @@ def poisson_trace(n_requests: int, rate: float = 20.0, seed: int = 7) -> List[Re
     return out
 
 
-def latency_stats(done: Sequence[Request]):
-    lat = np.array([r.latency for r in done if r.latency is not None and r.energy is not None
-                    and np.isfinite(r.energy)])
+def latency_stats(done: Sequence[Request], which: str = "all"):
+    """Latency percentiles of finished requests with a finite energy: all of them, only those whose
+    error met the target ("met"), or only those stopped by the iteration cap ("capped")."""
+    sel = [r for r in done if r.latency is not None and r.energy is not None and np.isfinite(r.energy)]
+    if which == "met":
+        sel = [r for r in sel if r.met]
+    elif which == "capped":
+        sel = [r for r in sel if r.capped]
+    elif which != "all":
+        raise ValueError(which)
+    lat = np.array([r.latency for r in sel])
     if len(lat) == 0:
         return {"p50_s": None, "p99_s": None, "n": 0}
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),

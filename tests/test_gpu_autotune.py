@@ -57,18 +57,29 @@ def test_all_shapes_agree_and_tuning_restores_state(ctx):
         ref = means[(256, 2, 8)]
         for k, v in means.items():
             assert np.allclose(v, ref, rtol=1e-12, atol=0.0), k
-        res = A.autotune(ctx, gs, spts=(16, 32), trials=1)
+        res = A.autotune(ctx, gs, spts=(16, 32), trials=1, per_order=())
         assert [M.mbpt_get_state(g) for g in gs] == before
         b = res["best"]
         assert M.mbpt_ctx_get_launch(ctx, 3) == (b["threads"], b["min_blocks"], b["spt"])
         assert len(res["table"]) == 2 * len(M.mbpt_kernel_variants())
+        # the histogram layout was searched on the best shape and the chosen one is on the context
+        assert len(res["layout_table"]) == 2
+        want = M.MBPT_HIST_BLOCK_F64 if res["launch"]["hist_layout"] == "block_f64" else M.MBPT_HIST_WARP_F32
+        assert M.mbpt_ctx_get_hist_layout(ctx) == want
+        assert sorted(res["launch"]["spt_by_order"]) == [2, 3, 4, 5]
+        M.mbpt_ctx_set_hist_layout(ctx, M.MBPT_HIST_WARP_F32)
         # per-order refinement of a mixed-order batch: one entry per (order, candidate), the chosen
         # values left on the context, the states untouched
-        res = A.autotune(ctx, gs, spts=(16, 32), trials=1, variants=[(256, 2)], per_order=(3, 5))
+        res = A.autotune(ctx, gs, spts=(16, 32), trials=1, variants=[(256, 2)], per_order=(3, 5),
+                         layouts=(M.MBPT_HIST_WARP_F32,))
         assert [M.mbpt_get_state(g) for g in gs] == before
         assert len(res["per_order_table"]) == 4 and set(res["per_order_spt"]) == {3, 5}
         for o, spt in res["per_order_spt"].items():
             assert M.mbpt_ctx_get_launch(ctx, o) == (256, 2, spt)
+        # by default a batch of several orders is refined order by order
+        res = A.autotune(ctx, gs, spts=(16, 32), trials=1, variants=[(256, 2)], layouts=(M.MBPT_HIST_WARP_F32,))
+        assert set(res["per_order_spt"]) == {2, 3, 4, 5} and len(res["per_order_table"]) == 8
+        assert [M.mbpt_get_state(g) for g in gs] == before
         # deterministic under the tuned shape
         M.mbpt_vegas_iterate(ctx, gs, 2)
         r1 = [r.as_dict() for r in M.mbpt_estimate_batch(gs)]

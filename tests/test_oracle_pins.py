@@ -350,3 +350,53 @@ def test_refine_keeps_uniform_grid_and_endpoints():
 def test_combination_weighted_mean():
     m, s, chi = O.combine([1.0, 3.0], [1.0, 1.0])
     assert m == 2.0 and s == pytest.approx(1 / math.sqrt(2)) and chi == pytest.approx(2.0)
+
+
+# --- evaluation phase of PVegas (Sec. III.C): pooled combination on a frozen grid ---------------------
+
+def test_pooled_combination_is_one_long_run():
+    """combine_pooled of per-iteration sums equals the plain Monte Carlo mean and standard error of all
+    the iterations' samples taken together (numpy on the dumped weights), for iterations of unequal
+    size; the inverse-variance mean of the same iterations differs from it."""
+    rng = np.random.default_rng(11)
+    grid = random_grid(4, 50, rng, strength=0.6)
+    ws, s1, s2, cnt, means, vars_ = [], [], [], [], [], []
+    for t, m in ((0, 3000), (1, 2000), (2, 4096)):
+        sums, _, _, w = O.vegas_samples(2, None, np.array([0.5, 0.1]), 4, grid, 9, 0, t, 0, m, dump=True)
+        ws.append(w)
+        s1.append(sums[0])
+        s2.append(sums[1])
+        cnt.append(m)
+        means.append(sums[0] / m)
+        vars_.append((sums[1] / m - (sums[0] / m) ** 2) / (m - 1))
+    allw = np.concatenate(ws)
+    mean, sigma, chi2 = O.combine_pooled(s1, s2, cnt)
+    assert mean == pytest.approx(float(np.mean(allw)), rel=1e-12)
+    assert sigma == pytest.approx(float(np.std(allw, ddof=1)) / math.sqrt(len(allw)), rel=1e-9)
+    ref_chi2 = sum((mi - mean) ** 2 / vi for mi, vi in zip(means, vars_)) / 2
+    assert chi2 == pytest.approx(ref_chi2, rel=1e-9)
+    assert O.combine(means, vars_)[0] != pytest.approx(mean, rel=1e-12)
+
+
+def test_pooled_vegas_freezes_grid_after_training():
+    """With the pooled combination the grid is refined after the training iterations only (the final grid
+    is the one three refinements give) and the estimate of a known integral lies within 3 sigma."""
+    d = 4
+    ref = math.erf(0.5 / (0.1 * math.sqrt(2))) ** d
+    par = np.array([0.5, 0.1])
+    m, s, chi, grid = O.vegas(None, par, 8, 1 << 14, seed=9, kind=2, d=d, train_iters=3, pooled=True)
+    _, _, _, g3 = O.vegas(None, par, 3, 1 << 14, seed=9, kind=2, d=d)
+    assert np.array_equal(grid, g3)
+    assert within(m, s, ref) and s < 3e-3
+
+
+def test_generator_lists_hole_chords_first():
+    """The canonical chord order (hole chords first, each kind in line order): at orders 2..5 every
+    diagram's chord list starts with its hole chords, and diagrams with equal numbers of hole chords
+    therefore share the radial ranges of the loop-momentum map."""
+    for n in (2, 3, 4, 5):
+        for D in O.enumerate_diagrams(n):
+            holes = [D.hole(l) for l in D.chords]
+            k = O.hole_chords(D)
+            assert holes == [True] * k + [False] * (len(holes) - k)
+            assert D.chords[:k] == sorted(D.chords[:k]) and D.chords[k:] == sorted(D.chords[k:])

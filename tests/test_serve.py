@@ -34,7 +34,7 @@ class FakeBackend:
     def physics(self, kn, kp):
         return (kn, kp)
 
-    def cfg(self, samples, sid, seed):
+    def cfg(self, samples, sid, seed, order=2):
         return (samples, sid, seed)
 
     def nbytes(self, d, cfg):
@@ -146,6 +146,33 @@ def test_arena_refusal_rolls_back():
     while srv.step():
         pass
     assert len(srv.done) == 2
+
+
+def test_arena_refusal_with_nothing_running_completes_unfittable():
+    """An arena that refuses a request while no other request holds memory can never take it: the
+    request completes as unfittable (energy NaN) instead of waiting forever, and the queue moves on."""
+    be = FakeBackend(arena_limit=3)
+    srv = S.Server(be, budget_bytes=10 ** 9, clock=iter(range(10 ** 6)).__next__)
+    big = S.Request(0.1, 0.0, 3, 0.01, rid=0)       # 4 integrals > 3
+    small = S.Request(0.1, 0.0, 2, 0.01, rid=1)     # 1 integral
+    done = srv.run([big, small], realtime=False)
+    assert [r.rid for r in done] == [0, 1]
+    assert math.isnan(big.energy) and not big.met and np.isfinite(small.energy)
+    assert not be.live and srv.used_bytes == 0
+
+
+def test_latency_split_by_outcome():
+    """Requests stopped by the iteration cap are flagged and reported apart from those that met
+    their target."""
+    be = FakeBackend()
+    srv = S.Server(be, min_iters=2, max_iters=3, clock=iter(range(10 ** 6)).__next__)
+    reqs = [S.Request(0.1, 0.0, 2, 0.5, rid=0), S.Request(0.1, 0.0, 2, 1e-6, rid=1)]
+    done = srv.run(reqs, realtime=False)
+    by = {r.rid: r for r in done}
+    assert by[0].met and not by[0].capped
+    assert by[1].capped and not by[1].met
+    assert S.latency_stats(done, "met")["n"] == 1 and S.latency_stats(done, "capped")["n"] == 1
+    assert S.latency_stats(done)["n"] == 2
 
 
 def test_result_same_alone_and_in_mix_fake():
