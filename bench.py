@@ -229,7 +229,7 @@ def run_gpu(args):
     if args.autotune:
         sub, _ = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase, every=4)
         M.mbpt_vegas_iterate(ctx, sub, 2)
-        tuned = autotune(ctx, sub, spts=(8, 16, 32), trials=1)["launch"]
+        tuned = autotune(ctx, sub, trials=1)["launch"]
         destroy(M, sub)
     gs5, meta5 = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase)
     n5 = len(gs5)
@@ -265,33 +265,12 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_value = world * evals_step / e2e_s
 
-    # paired deviation of the mixed mode from FP64 (the FP64 path is parity-pinned to the oracle) on 48
-    # integrals with adapted grids, identical counters: per integral |I_mixed - I_fp64| / max(|I_fp64|,
-    # 1e-3 |E5 of its kF|)
-    res5 = M.mbpt_estimate_batch(gs5)
-    e5 = {kf: sum(r.mean for r, (k, _) in zip(res5, meta5) if k == kf) for kf in KF5}
+    # grids adapted by the timed iterations, for the paired precision check below
+    grids5 = {}
     rng = np.random.default_rng(5)
     pick = sorted(rng.choice(n5, size=48, replace=False))
-    dev5, twins = [], []
     for i in pick:
-        kf, d = meta5[i]
-        ph = M.physics(kF_n=kf, K_max=kf + 6.0)
-        img = M.mbpt_get_state(gs5[i])
-        t64 = M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=1 << 16, seed=seed, stream_id=7,
-                                                            precision=M.MBPT_FP64, alpha=ALPHA5))
-        tmx = M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=1 << 16, seed=seed, stream_id=7,
-                                                            precision=M.MBPT_MIXED, alpha=ALPHA5))
-        for g in (t64, tmx):
-            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), M.state_grid(img, 18, 50)))
-        twins.append((t64, tmx, kf))
-    for k in range(2):
-        M.mbpt_vegas_iterate(ctx, [g for t in twins for g in t[:2]], 1)
-        r64 = M.mbpt_estimate_batch([t[0] for t in twins])
-        rmx = M.mbpt_estimate_batch([t[1] for t in twins])
-        if k == 1:
-            for a, b, (_, _, kf) in zip(r64, rmx, twins):
-                dev5.append(abs(b.last_mean - a.last_mean) / max(abs(a.last_mean), 1e-3 * abs(e5[kf]), 1e-300))
-    destroy(M, [g for t in twins for g in t[:2]])
+        grids5[i] = M.state_grid(M.mbpt_get_state(gs5[i]), 18, 50)
     destroy(M, gs5)
 
     # time for every fifth-order integral to reach 0.5 % relative error: 3 training iterations, then the
@@ -330,6 +309,27 @@ def run_gpu(args):
                         "sigma": float(math.sqrt(sum(rc[i].sigma ** 2 for i in idx))),
                         "floor": floors[kf]}
     destroy(M, gsc)
+
+    # paired deviation of the mixed mode from FP64 (the FP64 path is parity-pinned to the oracle) on 48
+    # integrals, on the grids the timed iterations adapted, identical counters: per integral
+    # |I_mixed - I_fp64| / max(|I_fp64|, 1e-3 |E5 of its kF|), E5 from the evaluation phase above
+    dev5, twins = [], []
+    for i in pick:
+        kf, d = meta5[i]
+        ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+        pair = []
+        for prec in (M.MBPT_FP64, M.MBPT_MIXED):
+            g = M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=1 << 16, seed=seed, stream_id=7,
+                                                              precision=prec, alpha=ALPHA5))
+            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grids5[i]))
+            pair.append(g)
+        twins.append((pair[0], pair[1], kf))
+    M.mbpt_vegas_iterate(ctx, [g for t in twins for g in t[:2]], 1)
+    r64 = M.mbpt_estimate_batch([t[0] for t in twins])
+    rmx = M.mbpt_estimate_batch([t[1] for t in twins])
+    for a, b, (_, _, kf) in zip(r64, rmx, twins):
+        dev5.append(abs(b.last_mean - a.last_mean) / max(abs(a.last_mean), 1e-3 * abs(e5c[str(kf)]["E5"]), 1e-300))
+    destroy(M, [g for t in twins for g in t[:2]])
 
     # the plain per-diagram FP64 loop on every 20th fifth-order integral: one launch per integral and
     # iteration, default launch shape
@@ -621,7 +621,7 @@ def profile_case(args):
     ctx = M.mbpt_ctx_create(0, 8 << 30)
     prec = M.MBPT_MIXED if args.precision == "mixed" else M.MBPT_FP64
     if args.profile_case == "fifth":
-        gs, _ = fifth_order_integrals(M, ctx, prec, samples=args.samples)
+        gs, _ = fifth_order_integrals(M, ctx, prec, samples=args.samples, near_band=args.near_band)
     else:
         descs = M.mbpt_generate(3)
         gs = []
@@ -653,6 +653,7 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 16, help="--profile-case: samples per integral")
     ap.add_argument("--iters", type=int, default=3, help="--profile-case: batched iterations")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="--profile-case precision")
+    ap.add_argument("--near-band", type=float, default=0.0, help="--profile-case: FP64-map band (0 = default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -6,9 +6,11 @@ mixed-precision evaluation from the FP64 oracle on a subset of samples.
     python -m paper_2603_24532_b300.run_fifth_order [--samples 2^20] [--max-iters 40]
         [--target 0.005] [--oracle-integrals 48] [--oracle-samples 4096] [--map-kind 0]
 
-Anomalous diagrams (zero at T = 0) are skipped.  A near-zero diagram cannot reach a relative
-target; its absolute target is 0.5 % of |sum over the order| / sqrt(number of integrals) at that
-density.  Prints one JSON line.
+Anomalous diagrams (zero at T = 0) are skipped.  Every integral trains its grid for `--train`
+iterations (grid compression `--alpha`) and is then estimated on the frozen grid, every evaluation sample
+weighted alike (pooled combination).  A near-zero diagram cannot reach a relative target; its absolute
+target is 0.5 % of |sum over the order| / sqrt(number of integrals) at that density, from the last
+training iteration.  Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -32,6 +34,8 @@ def main():
     ap.add_argument("--oracle-integrals", type=int, default=48)
     ap.add_argument("--oracle-samples", type=int, default=1 << 16)
     ap.add_argument("--map-kind", type=int, default=0)
+    ap.add_argument("--alpha", type=float, default=0.75, help="grid compression exponent")
+    ap.add_argument("--train", type=int, default=3, help="training iterations (grid refined, not combined)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "map64", "fp64"],
                     help="mixed: FP32 sampling map; map64: FP64 map, FP32 potentials and spin sums")
     ap.add_argument("--dedup-mirrors", action="store_true",
@@ -49,23 +53,25 @@ def main():
         ph = M.physics(kF_n=kf, K_max=kf + 6.0, map_kind=a.map_kind)
         for d in descs:
             cfg = M.vegas_cfg(samples=a.samples, seed=1, stream_id=1000 * ki + d.diagram_id, precision=prec,
-                              target_rel=a.target)
+                              target_rel=a.target, alpha=a.alpha, train_iters=a.train,
+                              combine=M.MBPT_COMBINE_POOLED)
             gs.append(M.mbpt_create_diagram(ctx, d, ph, cfg))
             meta.append((kf, d))
     t0 = time.perf_counter()
-    # pilot: two iterations, then absolute floors for near-zero diagrams
-    M.mbpt_vegas_iterate(ctx, gs, 2)
+    # training iterations, then absolute floors for near-zero diagrams from the last one
+    M.mbpt_vegas_iterate(ctx, gs, a.train)
     res = M.mbpt_estimate_batch(gs)
     for ki, kf in enumerate(kfs):
         idx = [i for i, (k, _) in enumerate(meta) if k == kf]
-        order_sum = abs(sum(mult[meta[i][1].diagram_id] * res[i].mean for i in idx))
+        order_sum = abs(sum(mult[meta[i][1].diagram_id] * res[i].last_mean for i in idx))
         floor = a.target * order_sum / math.sqrt(sum(mult[meta[i][1].diagram_id] ** 2 for i in idx))
         for i in idx:
             cfg = M.vegas_cfg(samples=a.samples, seed=1, stream_id=1000 * ki + meta[i][1].diagram_id,
-                              precision=prec, target_rel=a.target, target_abs=floor)
+                              precision=prec, target_rel=a.target, target_abs=floor, alpha=a.alpha,
+                              train_iters=a.train, combine=M.MBPT_COMBINE_POOLED)
             M.mbpt_set_config(gs[i], cfg)
-    evals = 2 * a.samples * len(gs)
-    iters = 2
+    evals = a.train * a.samples * len(gs)
+    iters = a.train
     while iters < a.max_iters:
         live = [g for g, r in zip(gs, M.mbpt_estimate_batch(gs)) if not r.converged]
         if not live:

@@ -1,10 +1,14 @@
 """Fourth-order workload: all 39 fourth-order diagrams x kF {1.0, 1.33, 1.6} fm^-1 x {neutron,
 symmetric} matter = 234 integrals (the 36 anomalous ones are exactly zero and skipped), a fixed number
-of batched VEGAS iterations, then the fourth-order energy per physics point and the deviation of the
-chosen precision from the FP64 oracle on a subset of integrals (same grid and counters).
+of batched VEGAS iterations -- `--train` training iterations, then the evaluation phase on the frozen
+grid (pooled combination), grid compression alpha -- then the fourth-order energy per physics point
+(from the diagrams one by one, and with --groups also from the four aligned particle-hole groups per
+point) and the deviation of the chosen precision from the FP64 oracle on a subset of integrals (same grid
+and counters).
 
-    python -m paper_2603_24532_b300.run_fourth_order [--samples 2^24] [--iters 10] [--precision mixed]
-        [--oracle-integrals 24] [--oracle-samples 65536] [--map-kind 0]
+    python -m paper_2603_24532_b300.run_fourth_order [--samples 2^24] [--iters 10] [--train 4]
+        [--alpha 1.0] [--precision mixed] [--groups] [--oracle-integrals 24] [--oracle-samples 65536]
+        [--map-kind 0]
 
 Prints one JSON line.
 """
@@ -25,7 +29,10 @@ from . import mbpt as M
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=1 << 24)
-    ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--iters", type=int, default=10, help="iterations in all (training + evaluation)")
+    ap.add_argument("--train", type=int, default=4, help="training iterations (grid refined, not combined)")
+    ap.add_argument("--alpha", type=float, default=1.0, help="grid compression exponent")
+    ap.add_argument("--groups", action="store_true", help="also integrate the aligned particle-hole groups")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "map64", "fp64"])
     ap.add_argument("--oracle-integrals", type=int, default=24)
     ap.add_argument("--oracle-samples", type=int, default=1 << 16)
@@ -40,12 +47,26 @@ def main():
         ph = M.physics(kF_n=kf, kF_p=kfp, K_max=kf + 6.0, map_kind=a.map_kind)
         for d in descs:
             sid = 10000 * mi + 100 * ki + d.diagram_id
-            gs.append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=a.samples, seed=1, stream_id=sid,
-                                                                    precision=prec)))
+            gs.append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(
+                samples=a.samples, seed=1, stream_id=sid, precision=prec, alpha=a.alpha, train_iters=a.train,
+                combine=M.MBPT_COMBINE_POOLED)))
             meta.append((kf, kfp, sid, d))
+    gg, gmeta = [], []
+    if a.groups:
+        for kf, kfp, mi, ki in points:
+            ph = M.physics(kF_n=kf, kF_p=kfp, K_max=kf + 6.0, map_kind=a.map_kind)
+            by = {}
+            for d in descs:
+                by.setdefault(M.mbpt_hole_chords(d), []).append(d)
+            for key, mem in sorted(by.items()):
+                gg.append(M.mbpt_create_group(ctx, mem, ph, M.vegas_cfg(
+                    samples=a.samples, seed=1, stream_id=10000 * mi + 100 * ki + 50 + key, precision=prec,
+                    alpha=a.alpha, train_iters=a.train, combine=M.MBPT_COMBINE_POOLED)))
+                gmeta.append((kf, kfp))
     t0 = time.perf_counter()
-    M.mbpt_vegas_iterate(ctx, gs, a.iters)
+    M.mbpt_vegas_iterate(ctx, gs + gg, a.iters)
     res = M.mbpt_estimate_batch(gs)
+    gres = M.mbpt_estimate_batch(gg) if gg else []
     wall = time.perf_counter() - t0
     per_point = {}
     for kf, kfp, mi, ki in points:
@@ -59,6 +80,9 @@ def main():
             "repeated_denominator": {"integrals": len(rep), "sum": float(sum(res[i].mean for i in rep)),
                                      "sigma": float(math.sqrt(sum(res[i].sigma ** 2 for i in rep))),
                                      "max_chi2_dof": float(max(res[i].chi2_dof for i in rep))},
+            "groups": ({"E4": float(sum(r.mean for r, m in zip(gres, gmeta) if m == (kf, kfp))),
+                        "sigma": float(math.sqrt(sum(r.sigma ** 2 for r, m in zip(gres, gmeta) if m == (kf, kfp))))}
+                       if gg else None),
             "others": {"integrals": len(rest), "sum": float(sum(res[i].mean for i in rest)),
                        "sigma": float(math.sqrt(sum(res[i].sigma ** 2 for i in rest))),
                        "max_chi2_dof": float(max(res[i].chi2_dof for i in rest)),
@@ -91,7 +115,8 @@ def main():
                              "same grid and counters; l1 = sum |w - w_oracle| / sum |w_oracle|"}
     evals = a.iters * a.samples * len(gs)
     out = {"workload": "39 fourth-order diagrams (33 non-anomalous) x kF {1.0, 1.33, 1.6} x {PNM, SNM}, %s, "
-                       "%d iterations x %d samples" % (a.precision, a.iters, a.samples),
+                       "%d iterations (%d training) x %d samples, alpha %g" % (a.precision, a.iters, a.train,
+                                                                              a.samples, a.alpha),
            "integrals": len(gs), "wall_s": wall, "evals": evals, "evals_per_s": evals / wall,
            "per_point": per_point, "oracle_deviation": dev}
     print(json.dumps(out))

@@ -12,9 +12,11 @@ The loop (one "round" per VEGAS iteration of every resident integral):
      (memory admission: state bytes from mbpt_diag_bytes, budget in bytes) and the slot
      limit allows;
   2. run one batched iteration of all resident, unfinished integrals (one graph replay);
-  3. read the estimates; after the first round of a request its summed estimate E_sum sets a
-     per-integral error budget sigma_G <= target |E_sum| / sqrt(N_int); integrals that reach
-     their budget (after at least `min_iters` iterations) retire and stop consuming samples;
+  3. read the estimates; the request's summed estimate E_sum sets its error goal target |E_sum|,
+     shared among its integrals in proportion to the square roots of their per-sample variances
+     (the Neyman allocation, the cheapest split of the goal); integrals that reach their share
+     (after at least `min_iters` iterations) retire and stop consuming samples, the others get
+     the samples their share still needs;
   4. a request completes when all its integrals have retired (or hit `max_iters`), or earlier,
      once the error of its sum, sqrt(sum sigma_G^2), meets target |E_sum|; its integrals are
      destroyed, freeing arena memory for waiting requests.
@@ -102,6 +104,8 @@ class Integral:
     sigma: float = float("inf")
     n_iter: int = 0
     done: bool = False
+    n_train: int = 0          # leading training iterations (no estimate of the error yet)
+    eval_samples: int = 0     # samples of the evaluation iterations so far
 
 
 class GroupUnit:
@@ -176,6 +180,9 @@ class MbptBackend:
 
     def physics(self, kF_n: float, kF_p: float):
         return self.M.physics(kF_n=kF_n, kF_p=kF_p, K_max=max(kF_n, kF_p) + 6.0, map_kind=self.map_kind)
+
+    def train_iters(self, order: int) -> int:
+        return TRAIN_BY_ORDER[order]
 
     def cfg(self, samples: int, stream_id: int, seed: int, order: int = 2):
         return self.M.vegas_cfg(samples=samples, seed=seed, stream_id=stream_id, precision=self.precision,
@@ -274,7 +281,7 @@ class GridCache:
 
 
 SAMPLES_BY_ORDER = {2: 1 << 16, 3: 1 << 16, 4: 1 << 17, 5: 1 << 17}   # training iterations
-MIN_SAMPLES, MAX_SAMPLES = 1 << 16, 1 << 22
+MIN_SAMPLES, MAX_SAMPLES = 1 << 16, 1 << 23
 
 
 class Server:
@@ -346,7 +353,8 @@ class Server:
                 for order, d, phys, cfg, nb in plan:
                     h = self.b.create(d, phys, cfg)
                     it = Integral(req, order, d.diagram_id, h, nb, cfg, self.samples[order],
-                                  mult=self.b.multiplicity(d) if hasattr(self.b, "multiplicity") else 1)
+                                  mult=self.b.multiplicity(d) if hasattr(self.b, "multiplicity") else 1,
+                                  n_train=self.b.train_iters(order) if hasattr(self.b, "train_iters") else 0)
                     created.append(it)
                     if self.cache is not None and hasattr(self.b, "set_grid"):
                         g = self.cache.get(order, d.diagram_id, req.delta, req.n_dens)
@@ -416,38 +424,48 @@ class Server:
         for req in self.active:
             req.rounds += 1
             e_sum = sum(it.mult * it.mean for it in req.integrals)
-            if req.budget is None:
-                # per-integral error budget from the first (pilot) estimate of the request's sum
-                # (a representative of a mirror pair counts twice)
-                n_eff = sum(it.mult ** 2 for it in req.integrals)
-                req.budget = req.target * abs(e_sum) / math.sqrt(n_eff)
+            goal = req.target * abs(e_sum)     # the request's error target, from its current estimate
+            req.budget = goal
+            for it in req.integrals:
+                if not it.done:
+                    it.evals += it.samples
+                    if it.n_iter > it.n_train:
+                        it.eval_samples += it.samples
+            trained = all(it.n_iter >= max(self.min_iters, it.n_train + 1) and math.isfinite(it.sigma)
+                          for it in req.integrals)
+            if trained and math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals)) <= goal:
+                # the request's own target is met: every integral retires with it
+                for it in req.integrals:
+                    it.done = True
+            # Neyman allocation of the error budget: with per-sample variances v_i = sigma_i^2 N_i (N_i the
+            # evaluation samples), the evaluation samples that reach a total error `goal` at the least total
+            # cost are N_i = mult_i sqrt(v_i) S / goal^2, S = sum_j mult_j sqrt(v_j); integral i's share of the
+            # error is then sigma_i^2 = sqrt(v_i) goal^2 / (mult_i S).  Integrals still training have no v_i yet.
+            v = {id(it): it.sigma ** 2 * it.eval_samples for it in req.integrals
+                 if math.isfinite(it.sigma) and it.eval_samples > 0}
+            S = sum(it.mult * math.sqrt(v[id(it)]) for it in req.integrals if id(it) in v)
+            n_eff = sum(it.mult ** 2 for it in req.integrals)
             for it in req.integrals:
                 if it.done:
                     continue
-                it.evals += it.samples
-                if it.n_iter >= self.min_iters and it.sigma <= req.budget:
+                if id(it) in v and S > 0.0:
+                    share = goal * math.sqrt(math.sqrt(v[id(it)]) / (it.mult * S))
+                else:
+                    share = goal / math.sqrt(n_eff)
+                if it.n_iter >= self.min_iters and it.sigma <= share:
                     it.done = True
                 elif it.n_iter >= self.max_iters:
                     it.done = True
                     req.capped = True
-                elif (self.adaptive and hasattr(self.b, "set_samples") and 0.0 < it.sigma < float("inf")
-                      and req.budget > 0.0):
-                    # samples still needed if sigma ~ 1/sqrt(evaluations), spread over a few iterations
-                    need = it.evals * ((it.sigma / req.budget) ** 2 - 1.0)
-                    left = max(1, self.min_iters - it.n_iter, 4)
+                elif (self.adaptive and hasattr(self.b, "set_samples") and id(it) in v and share > 0.0):
+                    # evaluation samples still needed for the share, spread over a few iterations
+                    need = v[id(it)] / share ** 2 - it.eval_samples
+                    left = max(1, self.min_iters - it.n_iter, 3)
                     nxt = int(min(MAX_SAMPLES, max(MIN_SAMPLES, need / left)))
                     nxt = 1 << max(0, int(round(math.log2(nxt))))
                     if nxt != it.samples:
                         self.b.set_samples(it.handle, it.cfg, nxt)
                         it.samples = nxt
-            # the request's own error target met: the remaining integrals retire with it (their estimates
-            # already count; every integral has finished its training)
-            if (not all(it.done for it in req.integrals) and req.budget is not None
-                    and all(it.n_iter >= self.min_iters and math.isfinite(it.sigma) for it in req.integrals)
-                    and math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals))
-                    <= req.target * abs(e_sum)):
-                for it in req.integrals:
-                    it.done = True
             if all(it.done for it in req.integrals):
                 req.energy = e_sum
                 req.sigma = math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals))

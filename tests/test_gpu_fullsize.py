@@ -160,3 +160,63 @@ def test_batched_sum_equals_every_sample_dumped(ctx, prec):
     finally:
         for g in gs:
             M.mbpt_destroy_diagram(g)
+
+
+def test_fifth_order_mixed_deviation_48_integrals(ctx):
+    """The headline mode at fifth order (FP32 sampling map, FP64 map near a Fermi surface) against the FP64
+    mode on identical grids and counters: on 48 fifth-order integrals with grids adapted by three training
+    iterations, one iteration of 2^16 samples deviates by at most 1e-4 of max(|I_fp64|, 1e-3 |E5|) per
+    integral (the scale of a near-zero diagram is 1e-3 of the order's sum, E5 here from the evaluation
+    phase of all 668 integrals: an inverse-variance combination of few iterations can underestimate |E5|
+    badly at this order)."""
+    kf = 1.33
+    ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+    descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
+    gs = [M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=1 << 17, seed=3, stream_id=d.diagram_id,
+                                                         precision=M.MBPT_MIXED, alpha=0.75, train_iters=3,
+                                                         combine=M.MBPT_COMBINE_POOLED)) for d in descs]
+    twins = []
+    try:
+        M.mbpt_vegas_iterate(ctx, gs, 6)
+        e5 = abs(sum(r.mean for r in M.mbpt_estimate_batch(gs)))
+        pick = np.random.default_rng(8).choice(len(descs), size=48, replace=False)
+        for i in pick:
+            grid = M.state_grid(M.mbpt_get_state(gs[i]), 18, 50)
+            pair = []
+            for prec in (M.MBPT_FP64, M.MBPT_MIXED):
+                g = M.mbpt_create_diagram(ctx, descs[i], ph, M.vegas_cfg(samples=1 << 16, seed=3, stream_id=9,
+                                                                          precision=prec, alpha=0.75))
+                M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+                pair.append(g)
+            twins.append(pair)
+        M.mbpt_vegas_iterate(ctx, [g for p in twins for g in p], 1)
+        devs = []
+        for (g64, gmx) in twins:
+            a, b = M.mbpt_estimate(g64).last_mean, M.mbpt_estimate(gmx).last_mean
+            devs.append(abs(b - a) / max(abs(a), 1e-3 * e5))
+        assert max(devs) <= 1e-4, (max(devs), np.median(devs))
+    finally:
+        for g in gs + [g for p in twins for g in p]:
+            M.mbpt_destroy_diagram(g)
+
+
+def test_fifth_order_mixed_vs_oracle_on_host_grids(ctx):
+    """The same bound directly against the oracle on strongly non-uniform grids made on the host: eight
+    fifth-order integrals, 4096 samples each, sum of the mixed weights vs the oracle's sum."""
+    from helpers import random_grid
+    rng = np.random.default_rng(12)
+    po, pm = _pair(1.33, 0.0)
+    Ds = [D for D in O.enumerate_diagrams(5) if not O.is_anomalous(D)]
+    for j in rng.choice(len(Ds), size=8, replace=False):
+        D = Ds[j]
+        grid = random_grid(D.d, 50, rng, strength=0.5)
+        g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=4096, seed=6, stream_id=D.diagram_id,
+                                                                      precision=M.MBPT_MIXED))
+        try:
+            M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+            _, wg = M.mbpt_dump_samples(g, 2, 0, 4096, D.d, with_x=False)
+        finally:
+            M.mbpt_destroy_diagram(g)
+        _, wo = oracle_dump(D, po, grid, 6, D.diagram_id, 2, 0, 4096)
+        l1 = float(np.sum(np.abs(wg - wo)) / max(np.sum(np.abs(wo)), 1e-300))
+        assert l1 <= 1e-4, (D.diagram_id, l1)
