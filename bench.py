@@ -462,6 +462,12 @@ def run_gpu(args):
                    "p50_s": S.latency_stats(done)["p50_s"], "p99_s": S.latency_stats(done)["p99_s"],
                    "target_met_fraction": sum(r.met for r in done) / max(1, len(done)),
                    "capped_fraction": sum(r.capped for r in done) / max(1, len(done)),
+                   "capped_by": {"cap": {str(c): sum(r.capped for r in done if r.cap == c) for c in (2, 3, 4)},
+                                 "target": {str(t): sum(r.capped for r in done if r.target == t)
+                                            for t in (0.01, 0.003, 0.001)},
+                                 "delta": {str(d): sum(r.capped for r in done if r.delta == d)
+                                           for d in (0.0, 0.25, 0.5, 0.75, 1.0)}},
+                   "rounds_median": float(np.median([r.rounds for r in done])) if done else None,
                    "integrals_per_s": n_int / wall, "diagrams_per_s": n_diag / wall,
                    "evals_per_s": srv.evals / wall, "budget_bytes": srv.budget,
                    "workload": "Poisson 20/s, n ~ U[0.04, 0.20] fm^-3, delta {0..1}, order cap {2,3,4}, "
