@@ -229,7 +229,12 @@ def run_gpu(args):
     if args.autotune:
         sub, _ = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase, every=4)
         M.mbpt_vegas_iterate(ctx, sub, 2)
-        tuned = autotune(ctx, sub, trials=1)["launch"]
+        at = autotune(ctx, sub, trials=1)
+        tuned = dict(at["launch"])
+        tuned["search_ms"] = {"%dx%d spt%d" % (r["threads"], r["min_blocks"], r["spt"]): round(r["ms"], 2)
+                              for r in at["table"]}
+        tuned["search_ms"].update({"hist %d" % r["layout"]: round(r["ms"], 2) for r in at["layout_table"]})
+        tuned["search_batch"] = "every fourth fifth-order integral (501), one iteration each"
         destroy(M, sub)
     gs5, meta5 = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase)
     n5 = len(gs5)
@@ -290,13 +295,41 @@ def run_gpu(args):
                           precision=M.MBPT_MIXED, alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED,
                           target_rel=0.005, target_abs=floors[kf])
         M.mbpt_set_config(g, cfg)
+    # adaptive samples per iteration (PVegas, Sec. III.C): each live integral's remaining need is its
+    # per-sample variance over its goal squared, less the evaluation samples it has; the integrals closest
+    # to their targets get what they need first (up to 2^22 per iteration), the rest 2^18, within 2^20
+    # samples per unconverged integral per iteration
     iters, conv_evals = 3, 3 * len(gsc) * SAMPLES5
+    cur = {id(g): SAMPLES5 for g in gsc}
     while iters < 40:
-        live = [g for g, r in zip(gsc, M.mbpt_estimate_batch(gsc)) if not r.converged]
+        rc = M.mbpt_estimate_batch(gsc)
+        live = []
+        for g, r, (kf, d) in zip(gsc, rc, metac):
+            if r.converged:
+                continue
+            n_eval = r.n_evals - 3 * SAMPLES5
+            goal = max(0.005 * abs(r.mean), floors[kf])
+            need = (r.sigma ** 2 * n_eval / goal ** 2 - n_eval) if (n_eval > 0 and math.isfinite(r.sigma)
+                                                                  and goal > 0.0) else float(SAMPLES5)
+            live.append((max(need, 1.0), g, kf, d))
         if not live:
             break
-        M.mbpt_vegas_iterate(ctx, live, 1)
-        conv_evals += len(live) * SAMPLES5
+        live.sort(key=lambda x: x[0])
+        left = len(live) * SAMPLES5
+        for need, g, kf, d in live:
+            nxt = 1 << 18
+            if left > 0:
+                nxt = 1 << int(math.ceil(math.log2(min(float(1 << 22), max(float(1 << 18), need)))))
+            left -= nxt
+            if nxt != cur[id(g)]:
+                cfg = M.vegas_cfg(samples=nxt, seed=seed + 100,
+                                  stream_id=sbase + 1000 * KF5.index(kf) + d.diagram_id, precision=M.MBPT_MIXED,
+                                  alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED,
+                                  target_rel=0.005, target_abs=floors[kf])
+                M.mbpt_set_config(g, cfg)
+                cur[id(g)] = nxt
+        M.mbpt_vegas_iterate(ctx, [x[1] for x in live], 1)
+        conv_evals += sum(cur[id(x[1])] for x in live)
         iters += 1
     rc = M.mbpt_estimate_batch(gsc)
     conv_s = time.perf_counter() - t0
@@ -356,6 +389,8 @@ def run_gpu(args):
     timed_steps(g3, 3)
     it3, st3 = timed_steps(g3, args.steps)
     v3 = world * n3 * SAMPLES3 / (float(np.mean(st3)) * 1e-3)
+    ops3 = measured_fp64_ops("third_order_mixed")
+    frac3 = (ops3 * n3 * SAMPLES3 / (float(np.mean(it3)) * 1e-3) / fp64_rate) if ops3 else None
     res3 = M.mbpt_estimate_batch(g3)
     live3 = []
     for g in g3[:: max(1, n3 // 6)]:
@@ -519,10 +554,13 @@ def run_gpu(args):
                                   "evals": conv_evals, "median_rel_err": float(np.median(rel)) if rel else None,
                                   "diagrams_per_s": n_conv / conv_s, "per_kF": e5c,
                                   "k0_diagrams_per_s": n_conv / (conv_evals / vk5),
-                                  "definition": "3 training iterations then the frozen-grid evaluation phase; "
-                                                "converged: sigma <= max(0.5 % |I|, 0.5 % |E5(kF)| / sqrt(668)); "
-                                                "cap 40 iterations; k0: the same evaluations at the plain "
-                                                "per-diagram FP64 loop's rate"},
+                                  "definition": "3 training iterations of 2^20, then the frozen-grid evaluation "
+                                                "phase with adaptive samples per iteration (the integrals closest to "
+                                                "their targets first get what they still need, up to 2^22, the rest "
+                                                "2^18, within 2^20 samples per unconverged integral per iteration); converged: sigma <= "
+                                                "max(0.5 % |I|, 0.5 % |E5(kF)| / sqrt(668)); cap 40 iterations; "
+                                                "k0: the same evaluations at the plain per-diagram FP64 loop's "
+                                                "rate"},
         "k0_plain_fp64_fifth_order": {"value": vk5, "unit": UNIT, "integrals": int(math.ceil(n5 / 20)),
                                       "note": "every 20th integral, one launch per integral and iteration"},
         "speedup_vs_k0": value / vk5,
@@ -533,6 +571,7 @@ def run_gpu(args):
                                                   "1e-3 |E5 of the kF|), one iteration of 2^16 samples"},
         "third_order_scan": {"value": v3, "unit": UNIT, "integrals": n3, "samples_per_iter": SAMPLES3,
                              "kernel_ms": float(np.mean(it3)), "live_fraction": float(np.mean(live3)),
+                             "roofline_frac": frac3, "ops_per_sample": ops3,
                              "launch": tuned3,
                              "fp64_batched": v64, "k0_plain_fp64_per_diagram": vk0, "speedup_vs_k0": v3 / vk0,
                              "rotational_9d": v3r,

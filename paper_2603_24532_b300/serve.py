@@ -74,6 +74,8 @@ class Request:
     rounds: int = 0
     cancelled: bool = False
     capped: bool = False      # some integral stopped at the iteration cap before reaching its error budget
+    remaining: float = 0.0    # estimated samples still to run (scheduling priority)
+    last_run: float = 0.0     # clock of its last round
 
     @property
     def met(self) -> bool:
@@ -106,6 +108,7 @@ class Integral:
     done: bool = False
     n_train: int = 0          # leading training iterations (no estimate of the error yet)
     eval_samples: int = 0     # samples of the evaluation iterations so far
+    need: float = 0.0         # evaluation samples its error share still needs (Neyman allocation)
 
 
 class GroupUnit:
@@ -129,18 +132,21 @@ TRAIN_BY_ORDER = {2: 2, 3: 2, 4: 3, 5: 3, 6: 3}
 
 class MbptBackend:
     """The C ABI as the server's backend (all work on the GPU).  With grouped=True each order of a
-    request is a handful of group integrals (Table I's N_grp) instead of one integral per diagram.
+    request is a handful of group integrals (Table I's N_grp) instead of one integral per diagram;
+    group_orders limits that to some orders (e.g. (4,): fourth order in aligned groups, orders 2-3
+    diagram by diagram).
     Integrals train their grid for TRAIN_BY_ORDER iterations and are then estimated on the frozen grid
     (MBPT_COMBINE_POOLED), with grid compression ALPHA_BY_ORDER."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, arena_ptr: int = 0, stream: int = 0,
                  precision: Optional[int] = None, map_kind: int = 1, dedup_mirrors: bool = True,
-                 grouped: bool = False):
+                 grouped: bool = False, group_orders=None):
         from . import mbpt as M
         self.M = M
         self.map_kind = map_kind
         self.dedup_mirrors = dedup_mirrors
         self.grouped = grouped
+        self.group_orders = None if group_orders is None else set(group_orders)
         self._units = {}
         self.ctx = M.mbpt_ctx_create(device, arena_bytes, arena_ptr=arena_ptr, stream=stream)
         self.precision = M.MBPT_MIXED if precision is None else precision
@@ -160,7 +166,7 @@ class MbptBackend:
 
     def units(self, order: int):
         """What one order of a request expands into: diagrams, or groups of them."""
-        if not self.grouped:
+        if not self.grouped or (self.group_orders is not None and order not in self.group_orders):
             return self.diagrams(order)
         if order not in self._units:
             by_key = {}
@@ -289,9 +295,15 @@ class Server:
                  samples_by_order: Optional[Dict[int, int]] = None, min_iters: int = 3, max_iters: int = 60,
                  seed: int = 1, clock: Callable[[], float] = time.perf_counter, adaptive: bool = True,
                  warm_start: bool = False, warm_window: float = 0.02, warm_blend: float = 0.5,
-                 warm_train: int = 1, log=None):
+                 warm_train: int = 1, log=None, round_samples: Optional[int] = None, max_wait: float = 2.0):
         self.b = backend
         self.log = log                        # optional text stream: one JSON record per finished integral / request
+        # round scheduling: with round_samples set, a round runs the requests with the least estimated work
+        # left first, up to that many samples (at least one request), and any request that has not run for
+        # max_wait seconds before the others; a request that sits out a round keeps its state, so its
+        # result does not depend on the schedule
+        self.round_samples = round_samples
+        self.max_wait = max_wait
         self.adaptive = adaptive
         self.cache = GridCache(warm_window) if warm_start else None
         self.warm_blend = warm_blend          # weight of the donor grid (rest: uniform bins)
@@ -382,6 +394,8 @@ class Server:
                 continue
             self.waiting.pop(0)
             req.admitted = now
+            req.last_run = now
+            req.remaining = float(sum(it.samples * (it.n_train + 2) for it in created))
             req.integrals = created
             self.used_bytes += need
             self.n_integrals += len(plan)
@@ -412,17 +426,19 @@ class Server:
         if self.log is not None:
             self.log.write(json.dumps(rec) + "\n")
 
-    def _retire_and_complete(self, now: float):
-        live = [it for req in self.active for it in req.integrals if not it.done]
+    def _retire_and_complete(self, now: float, batch=None):
+        batch = self.active if batch is None else batch
+        live = [it for req in batch for it in req.integrals if not it.done]
         if hasattr(self.b, "estimate_many"):
             ests = self.b.estimate_many([it.handle for it in live])
         else:
             ests = [self.b.estimate(it.handle) for it in live]
         for it, e in zip(live, ests):
             it.mean, it.sigma, it.n_iter = e
-        still = []
-        for req in self.active:
+        finished = set()
+        for req in batch:
             req.rounds += 1
+            req.last_run = now
             e_sum = sum(it.mult * it.mean for it in req.integrals)
             goal = req.target * abs(e_sum)     # the request's error target, from its current estimate
             req.budget = goal
@@ -460,6 +476,7 @@ class Server:
                 elif (self.adaptive and hasattr(self.b, "set_samples") and id(it) in v and share > 0.0):
                     # evaluation samples still needed for the share, spread over a few iterations
                     need = v[id(it)] / share ** 2 - it.eval_samples
+                    it.need = max(0.0, need)
                     left = max(1, self.min_iters - it.n_iter, 3)
                     nxt = int(min(MAX_SAMPLES, max(MIN_SAMPLES, need / left)))
                     nxt = 1 << max(0, int(round(math.log2(nxt))))
@@ -487,21 +504,40 @@ class Server:
                     self.used_bytes -= it.bytes
                 self.n_integrals -= len(req.integrals)
                 self.done.append(req)
+                finished.add(id(req))
             else:
-                still.append(req)
-        self.active = still
+                # estimated samples still to run: the next iteration's samples of every unfinished integral,
+                # or the samples its share still needs if that is more
+                req.remaining = float(sum(max(it.samples, it.need) for it in req.integrals if not it.done))
+        self.active = [r for r in self.active if id(r) not in finished]
+
+    def _schedule(self, now: float):
+        """The requests of this round (all of them without a round sample limit)."""
+        if self.round_samples is None:
+            return list(self.active)
+        order = sorted(self.active, key=lambda r: (0 if now - r.last_run > self.max_wait else 1, r.remaining,
+                                                   r.arrival, r.rid))
+        batch, total = [], 0
+        for r in order:
+            need = sum(it.samples for it in r.integrals if not it.done)
+            if batch and total + need > self.round_samples:
+                continue
+            batch.append(r)
+            total += need
+        return batch
 
     def step(self) -> bool:
         """One round; returns False when there is nothing to run."""
         now = self.clock()
         self._admit(now)
-        handles = [it.handle for req in self.active for it in req.integrals if not it.done]
+        batch = self._schedule(now)
+        handles = [it.handle for req in batch for it in req.integrals if not it.done]
         if not handles:
             return False
         self.b.iterate(handles)
-        self.evals += sum(it.samples for req in self.active for it in req.integrals if not it.done)
+        self.evals += sum(it.samples for req in batch for it in req.integrals if not it.done)
         self.rounds += 1
-        self._retire_and_complete(self.clock())
+        self._retire_and_complete(self.clock(), batch)
         return True
 
     def run(self, trace: Sequence[Request], realtime: bool = True, time_limit: Optional[float] = None):

@@ -341,3 +341,19 @@ def test_cancel_frees_slots_and_logs():
     kinds = [r["event"] for r in recs]
     assert kinds.count("request") == 3 and kinds.count("cancelled") == 1
     assert kinds.count("integral") == sum(len(r.integrals) for k, r in done.items() if k != victim.rid)
+
+
+def test_round_scheduling_keeps_results_and_bounds_rounds():
+    """With a round sample limit the server runs the requests with the least work left first (and any
+    request that has waited too long); a request that sits out rounds keeps its state, so every result
+    equals the unscheduled run's, and no round exceeds the limit unless a single request does."""
+    be0 = FakeBackend()
+    srv0 = S.Server(be0, clock=iter(range(10 ** 6)).__next__)
+    ref = {r.rid: (r.energy, r.sigma) for r in srv0.run(S.poisson_trace(20), realtime=False)}
+    be = FakeBackend()
+    srv = S.Server(be, clock=iter(range(10 ** 6)).__next__, round_samples=40 * (1 << 16), max_wait=50)
+    done = srv.run(S.poisson_trace(20), realtime=False)
+    assert {r.rid: (r.energy, r.sigma) for r in done} == ref
+    biggest = max(sum(1 for _ in r.integrals) for r in done)
+    assert max(be.iterated) <= max(40, biggest)
+    assert max(be0.iterated) > 40 and srv.rounds > srv0.rounds   # smaller, more rounds than unscheduled

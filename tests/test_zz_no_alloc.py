@@ -61,6 +61,19 @@ def test_noalloc_matches_iterate_on_calls_in_a_row():
             assert mean_b == pytest.approx(mean_a, rel=1e-12, abs=0.0)
             assert sigma_b == pytest.approx(sigma_a, rel=1e-10, abs=0.0)
             assert np.allclose(hist_b, hist_a, rtol=1e-12, atol=0.0)
+        # an invalid descriptor is rejected on the host and leaves the output untouched
+        D = O.enumerate_diagrams(4)[7]
+        po, pm = matter_pair("pnm")
+        bad = make_desc(D)
+        bad.chord_line[0] = 40
+        out = torch.full((2 + D.d * 50,), 12345.0, dtype=torch.float64, device="cuda")
+        g_dev = torch.tensor(O.uniform_grid(D.d, 50), dtype=torch.float64, device="cuda")
+        with pytest.raises(M.MbptError) as e:
+            M.mbpt_vegas_iteration_noalloc(0, bad, pm, M.vegas_cfg(samples=4096), 0, g_dev.data_ptr(),
+                                           out.data_ptr(), 0)
+        assert e.value.status == M.MBPT_EINVAL
+        torch.cuda.synchronize()
+        assert bool(torch.all(out == 12345.0))
         # a request beyond the fixed scratch is rejected with a clear error
         D = O.enumerate_diagrams(5)[3]
         po, pm = matter_pair("pnm")
