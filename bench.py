@@ -364,6 +364,45 @@ def run_gpu(args):
         dev5.append(abs(b.last_mean - a.last_mean) / max(abs(a.last_mean), 1e-3 * abs(e5c[str(kf)]["E5"]), 1e-300))
     destroy(M, [g for t in twins for g in t[:2]])
 
+    # E5 per kF from the 668 diagrams one by one vs from the five aligned particle-hole groups of the same
+    # diagrams (Sec. III.A), at equal member evaluations (2^20 samples per integral and iteration; a group
+    # sample evaluates each member once), 3 training + 6 evaluation iterations, pooled
+    def e5_run(grouped):
+        gs, keys = [], []
+        descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
+        for ki, kf in enumerate(KF5):
+            ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+            if grouped:
+                by = {}
+                for d in descs:
+                    by.setdefault(M.mbpt_hole_chords(d), []).append(d)
+                for key, mem in sorted(by.items()):
+                    gs.append(M.mbpt_create_group(ctx, mem, ph, M.vegas_cfg(
+                        samples=SAMPLES5, seed=seed + 200, stream_id=sbase + 1000 * ki + 900 + key,
+                        precision=M.MBPT_MIXED, alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED)))
+                    keys.append(kf)
+            else:
+                for d in descs:
+                    gs.append(M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(
+                        samples=SAMPLES5, seed=seed + 200, stream_id=sbase + 1000 * ki + d.diagram_id,
+                        precision=M.MBPT_MIXED, alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED)))
+                    keys.append(kf)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.mbpt_vegas_iterate(ctx, gs, 9)
+        rr = M.mbpt_estimate_batch(gs)
+        dt = time.perf_counter() - t0
+        out = {}
+        for kf in KF5:
+            idx = [i for i, k in enumerate(keys) if k == kf]
+            out[str(kf)] = (float(sum(rr[i].mean for i in idx)), float(math.sqrt(sum(rr[i].sigma ** 2 for i in idx))))
+        destroy(M, gs)
+        return out, dt, len(gs)
+
+    e5_sep, t_sep, n_sep = e5_run(False)
+    e5_grp, t_grp, n_grp = e5_run(True)
+    eff = [(e5_sep[k][1] ** 2 * t_sep) / (e5_grp[k][1] ** 2 * t_grp) for k in e5_sep if e5_grp[k][1] > 0]
+
     # the plain per-diagram FP64 loop on every 20th fifth-order integral: one launch per integral and
     # iteration, default launch shape
     launch_now = {o: M.mbpt_ctx_get_launch(ctx, o) for o in (2, 3, 4, 5, 6)}
@@ -483,7 +522,7 @@ def run_gpu(args):
     if args.serve_requests > 0:
         from paper_2603_24532_b300 import serve as S
         be = S.MbptBackend(device=local, arena_bytes=48 << 30)
-        srv = S.Server(be, budget_bytes=40 << 30)
+        srv = S.Server(be, budget_bytes=40 << 30, round_samples=1 << 27, max_wait=2.0)
         trace = S.poisson_trace(args.serve_requests, 20.0, 7 + rank)
         t0 = time.perf_counter()
         done = srv.run(trace, realtime=True, time_limit=args.serve_seconds)
@@ -506,7 +545,8 @@ def run_gpu(args):
                    "integrals_per_s": n_int / wall, "diagrams_per_s": n_diag / wall,
                    "evals_per_s": srv.evals / wall, "budget_bytes": srv.budget,
                    "workload": "Poisson 20/s, n ~ U[0.04, 0.20] fm^-3, delta {0..1}, order cap {2,3,4}, "
-                               "target {1, 0.3, 0.1} %, seed 7 (+rank); 40 GB admission budget; "
+                               "target {1, 0.3, 0.1} %, seed 7 (+rank); 40 GB admission budget; rounds of at "
+                               "most 2^27 samples, least work left first (a request waiting 2 s runs first); "
                                "diagrams/s counts a mirror-pair representative twice"}
         be.close()
     if dist:
@@ -561,6 +601,14 @@ def run_gpu(args):
                                                 "max(0.5 % |I|, 0.5 % |E5(kF)| / sqrt(668)); cap 40 iterations; "
                                                 "k0: the same evaluations at the plain per-diagram FP64 loop's "
                                                 "rate"},
+        "fifth_order_groups": {"per_kF_diagrams": e5_sep, "per_kF_groups": e5_grp, "wall_s_diagrams": t_sep,
+                               "wall_s_groups": t_grp, "integrals": [n_sep, n_grp],
+                               "time_to_equal_error_ratio": eff,
+                               "definition": "E5 (MeV) +- sigma per kF from the 668 diagrams one by one and from the "
+                                             "5 aligned particle-hole groups (hole loop momenta first), 3 training "
+                                             "+ 6 pooled iterations at 2^20 samples per integral each; ratio = "
+                                             "sigma_diagrams^2 t_diagrams / (sigma_groups^2 t_groups), the "
+                                             "speed-up of the groups to a given error on E5"},
         "k0_plain_fp64_fifth_order": {"value": vk5, "unit": UNIT, "integrals": int(math.ceil(n5 / 20)),
                                       "note": "every 20th integral, one launch per integral and iteration"},
         "speedup_vs_k0": value / vk5,
@@ -604,36 +652,33 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------------------------------
-def cpu_baseline(budget_s=12.0):
-    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the headline workload (every
-    one of the 2004 fifth-order integrals, the same number of samples each, uniform grid)."""
+def cpu_baseline(budget_s=12.0, stride=None, n=4096):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the headline workload -- every
+    stride-th of the 2004 fifth-order integrals (in kF, then diagram order), n samples each, uniform grid.
+    Without stride, the stride is calibrated on every 64th integral to take about budget_s seconds."""
     import oracle as O
 
     Ds = [D for D in O.enumerate_diagrams(5) if not O.is_anomalous(D)]
     cores = os.cpu_count() or 1
     grid = O.uniform_grid(18, 50)
-    po = O.Physics(kF_n=1.33, K_max=7.33)
-    # calibrate on a few integrals
-    m, dt = 8, 0.0
-    while dt < 0.5 and m < (1 << 16):
-        m *= 2
+    work = [(ki, kf, D) for ki, kf in enumerate(KF5) for D in Ds]
+
+    def run(sel):
         t0 = time.perf_counter()
-        for D in Ds[:16]:
-            O.vegas_iteration(D, po, grid, 1, D.diagram_id, 0, m, threads=cores)
-        dt = time.perf_counter() - t0
-    per = dt / (m * 16)
-    n = int(max(16, min(1 << 16, budget_s / (per * len(KF5) * len(Ds)))))
-    t0 = time.perf_counter()
-    total = 0
-    for ki, kf in enumerate(KF5):
-        po = O.Physics(kF_n=kf, K_max=kf + 6.0)
-        for D in Ds:
-            O.vegas_iteration(D, po, grid, 1, 1000 * ki + D.diagram_id, 0, n, threads=cores)
-            total += n
-    dt = time.perf_counter() - t0
-    return {"value": total / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d samples of each of the %d fifth-order integrals (uniform grid, iteration 0), %.1f s"
-                      % (n, len(KF5) * len(Ds), dt)}
+        for ki, kf, D in sel:
+            O.vegas_iteration(D, O.Physics(kF_n=kf, K_max=kf + 6.0), grid, 1, 1000 * ki + D.diagram_id, 0, n,
+                              threads=cores)
+        return time.perf_counter() - t0
+
+    if stride is None:
+        sel = work[::64]
+        rate = len(sel) * n / run(sel)
+        stride = max(1, int(math.ceil(len(work) * n / (rate * budget_s))))
+    sel = work[::stride]
+    dt = run(sel)
+    return {"value": len(sel) * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "stride": stride,
+            "sample": "%d samples of every %d-th of the %d fifth-order integrals (%d integrals, uniform grid, "
+                      "iteration 0), %.1f s" % (n, stride, len(work), len(sel), dt)}
 
 
 def run_reference(args):
@@ -642,9 +687,10 @@ def run_reference(args):
         return None
     cb = None
     times = []
+    stride = cpu_baseline(budget_s=args.ref_seconds)["stride"]     # calibration, untimed
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        cb = cpu_baseline(budget_s=args.ref_seconds)
+        cb = cpu_baseline(stride=stride)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world,
@@ -690,7 +736,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
-    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--ref-seconds", type=float, default=6.0, help="reference arm: seconds per step")
     ap.add_argument("--serve-requests", type=int, default=1200, help="serving run (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=150.0)
     ap.add_argument("--profile-case", choices=["fifth", "third"], default=None,

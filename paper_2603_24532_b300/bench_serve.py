@@ -34,7 +34,7 @@ def main():
     ap.add_argument("--warm-blend", type=float, default=0.5, help="weight of the donor grid in a warm start")
     ap.add_argument("--warm-train", type=int, default=1, help="uncombined iterations after a warm start")
     ap.add_argument("--log", default=None, help="JSONL file: one record per finished integral and request")
-    ap.add_argument("--round-samples", type=float, default=0,
+    ap.add_argument("--round-samples", type=float, default=float(1 << 27),
                     help="samples per round (least work left first; 0: every active request every round)")
     ap.add_argument("--max-wait", type=float, default=2.0, help="with --round-samples: seconds before a request runs first")
     a = ap.parse_args()
