@@ -711,6 +711,8 @@ def profile_case(args):
     from paper_2603_24532_b300 import mbpt as M
     ctx = M.mbpt_ctx_create(0, 8 << 30)
     prec = M.MBPT_MIXED if args.precision == "mixed" else M.MBPT_FP64
+    if args.spt:
+        M.mbpt_ctx_set_launch(ctx, 5 if args.profile_case == "fifth" else 3, args.spt)
     if args.profile_case == "fifth":
         gs, _ = fifth_order_integrals(M, ctx, prec, samples=args.samples, near_band=args.near_band)
     else:
@@ -723,8 +725,9 @@ def profile_case(args):
     M.mbpt_vegas_iterate(ctx, gs, args.iters)
     r = M.mbpt_estimate(gs[0])
     it_ms, fin_ms = M.mbpt_ctx_last_timing(ctx)
-    print("%s: integrals %d samples %d iters %d: k_iterate %.3f ms, k_finalize %.3f ms, first mean %.6g +- %.2g"
-          % (args.profile_case, len(gs), args.samples, args.iters, it_ms, fin_ms, r.mean, r.sigma))
+    print("%s: integrals %d samples %d iters %d spt %d: k_iterate %.3f ms, k_finalize %.3f ms, first mean %.6g +- %.2g"
+          % (args.profile_case, len(gs), args.samples, args.iters,
+             M.mbpt_ctx_get_launch(ctx, 5 if args.profile_case == "fifth" else 3)[2], it_ms, fin_ms, r.mean, r.sigma))
     M.mbpt_ctx_destroy(ctx)
 
 
@@ -745,6 +748,7 @@ def main():
     ap.add_argument("--iters", type=int, default=3, help="--profile-case: batched iterations")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="--profile-case precision")
     ap.add_argument("--near-band", type=float, default=0.0, help="--profile-case: FP64-map band (0 = default)")
+    ap.add_argument("--spt", type=int, default=0, help="--profile-case: samples per thread of a chunk (0 = default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

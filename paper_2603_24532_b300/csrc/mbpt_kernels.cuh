@@ -191,12 +191,12 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                         const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
                         const int cls = sc < w_samples
                                             ? sample_class<N, MAPK, PREC>(R, S.grid, (uint32_t)sc, t, w_sid, k0, k1)
-                                            : 0;
+                                            : kClassZero;
                         const uint32_t lt = (1u << lane) - 1u;
-                        const uint32_t b0 = __ballot_sync(0xffffffffu, cls == 1);
-                        const uint32_t b1 = __ballot_sync(0xffffffffu, cls == 2);
-                        if (cls == 1) q[nf + __popc(b0 & lt)] = (uint32_t)sc;
-                        if (cls == 2) q[kQ - 1 - (nn + __popc(b1 & lt))] = (uint32_t)sc;
+                        const uint32_t b0 = __ballot_sync(0xffffffffu, cls == kClassFar);
+                        const uint32_t b1 = __ballot_sync(0xffffffffu, cls == kClassNear);
+                        if (cls == kClassFar) q[nf + __popc(b0 & lt)] = (uint32_t)sc;
+                        if (cls == kClassNear) q[kQ - 1 - (nn + __popc(b1 & lt))] = (uint32_t)sc;
                         nf += __popc(b0);
                         nn += __popc(b1);
                     }
@@ -218,8 +218,9 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                 ++j;
             }
             if (have) {
-                const SampleOut o = eval_sample<N, PREC, MAPK, REG>(R, S.grid, w_grid, (uint32_t)s, t, w_sid,
-                                                                    k0, k1, nullptr, use_near);
+                const SampleOut o = eval_sample<N, PREC, MAPK, REG>(
+                        R, S.grid, w_grid, (uint32_t)s, t, w_sid, k0, k1, nullptr,
+                        !compact ? kClassUnknown : (use_near ? kClassNear : kClassFar));
                 if constexpr (GRP) {
                     // the sample's slot belongs to the lane of this warp that owns it in the chunk layout
                     // (sample first + js * blockDim + own); each slot gets one add per member

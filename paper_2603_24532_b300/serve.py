@@ -461,13 +461,16 @@ class Server:
                  if math.isfinite(it.sigma) and it.eval_samples > 0}
             S = sum(it.mult * math.sqrt(v[id(it)]) for it in req.integrals if id(it) in v)
             n_eff = sum(it.mult ** 2 for it in req.integrals)
+            shares = {}
+            for it in req.integrals:
+                if id(it) in v and S > 0.0:
+                    shares[id(it)] = goal * math.sqrt(math.sqrt(v[id(it)]) / (it.mult * S))
+                else:
+                    shares[id(it)] = goal / math.sqrt(n_eff)
             for it in req.integrals:
                 if it.done:
                     continue
-                if id(it) in v and S > 0.0:
-                    share = goal * math.sqrt(math.sqrt(v[id(it)]) / (it.mult * S))
-                else:
-                    share = goal / math.sqrt(n_eff)
+                share = shares[id(it)]
                 if it.n_iter >= self.min_iters and it.sigma <= share:
                     it.done = True
                 elif it.n_iter >= self.max_iters:
@@ -483,6 +486,13 @@ class Server:
                     if nxt != it.samples:
                         self.b.set_samples(it.handle, it.cfg, nxt)
                         it.samples = nxt
+            if (all(it.done for it in req.integrals) and not req.capped
+                    and math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals)) > goal):
+                # every integral met the share it had when it retired, but the goal and the shares have moved
+                # with the estimate since: reopen those above their current share (at least the largest term)
+                above = [it for it in req.integrals if it.sigma > shares[id(it)]]
+                for it in above or [max(req.integrals, key=lambda x: x.mult * x.sigma)]:
+                    it.done = False
             if all(it.done for it in req.integrals):
                 req.energy = e_sum
                 req.sigma = math.sqrt(sum((it.mult * it.sigma) ** 2 for it in req.integrals))

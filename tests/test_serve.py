@@ -357,3 +357,23 @@ def test_round_scheduling_keeps_results_and_bounds_rounds():
     biggest = max(sum(1 for _ in r.integrals) for r in done)
     assert max(be.iterated) <= max(40, biggest)
     assert max(be0.iterated) > 40 and srv.rounds > srv0.rounds   # smaller, more rounds than unscheduled
+
+
+class DriftBackend(FakeBackend):
+    """As FakeBackend, but each integral's estimate drifts towards zero by up to 40 % over its first
+    iterations, so the request's error goal (target x |energy|) shrinks after some integrals retired."""
+
+    def estimate(self, h):
+        m, sigma, it = super().estimate(h)
+        return m * (0.6 + 0.4 / it), sigma, it
+
+
+def test_every_request_ends_met_or_capped():
+    """A request whose integrals each met their share of the error budget when they retired, but whose
+    total error is above the goal of its final estimate, reopens the integrals above their current share:
+    every completed request either meets its target or was stopped by the iteration cap."""
+    done = S.Server(DriftBackend(), clock=iter(range(10 ** 6)).__next__).run(S.poisson_trace(40), realtime=False)
+    assert len(done) == 40
+    assert all(r.met or r.capped for r in done), [(r.rid, r.sigma, r.target * abs(r.energy)) for r in done
+                                                  if not (r.met or r.capped)]
+    assert sum(r.met for r in done) >= 10
