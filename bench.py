@@ -70,18 +70,26 @@ def job_value(world: int, units_per_rank: float, t_ms: float) -> float:
     return world * units_per_rank / (t_ms * 1e-3)
 
 
-def measured_fp64_ops(workload: str):
-    """FP64 thread operations per sample of a workload, from the committed ncu summary (lines
-    `<workload> <ops per sample> ...`); None if the file has no such line."""
+def measured_counters(workload: str):
+    """ncu counters of one k_iterate launch of a workload, from the committed summary (lines `<workload>
+    <FP64 ops per sample> <samples per launch> <dadd> <dmul> <dfma> <dram read B> <dram write B> <warp
+    instructions> ...`): a dict, or None if the file has no such line."""
     try:
         with open(FP64_OPS_FILE) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) >= 2 and not line.startswith("#") and parts[0] == workload:
-                    return float(parts[1])
-    except OSError:
+                if len(parts) >= 9 and not line.startswith("#") and parts[0] == workload:
+                    return {"ops_per_sample": float(parts[1]), "samples": int(parts[2]),
+                            "dram_bytes": int(parts[6]) + int(parts[7]), "warp_inst": int(parts[8])}
+    except (OSError, ValueError):
         pass
     return None
+
+
+def measured_fp64_ops(workload: str):
+    """FP64 thread operations per sample of a workload (measured_counters), or None."""
+    c = measured_counters(workload)
+    return c["ops_per_sample"] if c else None
 
 
 class Clocks:
@@ -254,9 +262,16 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: measured FP64 thread operations per sample (ncu) x samples per
     # launch / its CUDA-event time, against the FP64 rate measured here with the library's DFMA loop
-    ops5 = measured_fp64_ops("fifth_order_mixed")
+    cnt5 = measured_counters("fifth_order_mixed")
+    ops5 = cnt5["ops_per_sample"] if cnt5 else None
     fp64_rate = M.mbpt_fp64_rate(local, M.mbpt_ctx_stream(ctx))
     achieved = (ops5 * evals_step / (it_ms * 1e-3)) if ops5 else None
+    # DRAM bytes of a launch of this shape (null unless the counters were taken on the same launch shape), and
+    # the share of the SMs' instruction issue slots (4 warp instructions per SM per cycle) the launch uses
+    traffic5 = cnt5["dram_bytes"] if cnt5 and cnt5["samples"] == evals_step else None
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_frac = (cnt5["warp_inst"] / cnt5["samples"] * evals_step / (it_ms * 1e-3)
+                  / (4.0 * n_sm * clk["sm_mhz"] * 1e6)) if cnt5 and clk.get("sm_mhz") else None
 
     # end to end through the public API: per step the work table goes up inside mbpt_vegas_iterate
     # (a WORK_ITEM_BYTES item and an 8-byte histogram pointer per integral, the work header) and every
@@ -583,9 +598,16 @@ def run_gpu(args):
                                      "2032 MHz, scaled to the run's median SM clock",
                      "ops_per_sample": ops5, "ops_source": "ncu DADD + DMUL + DFMA thread instructions per "
                                                           "sample, profiles/fp64_ops_per_sample.txt",
-                     "kernel_ms": it_ms, "traffic": None,
-                     "traffic_note": "HBM idle by design (records, grids, chunk slots); see the k_iterate "
-                                     "profile summary for dram bytes"},
+                     "kernel_ms": it_ms, "traffic": traffic5, "traffic_unit": "bytes per launch",
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch of this shape "
+                                     "(ncu, profiles/fp64_ops_per_sample.txt): the chunk slots written once "
+                                     "(histogram and sums, 3.6 KB per chunk), records and grids; HBM is otherwise "
+                                     "idle by design",
+                     "issue_frac": issue_frac,
+                     "issue_note": "warp instructions per sample (ncu sm__inst_executed.sum of the same launch "
+                                   "shape) x samples / kernel time, over 4 issue slots per SM per cycle at the "
+                                   "run's median SM clock: the kernel is bound by latency and issue, with the "
+                                   "FP64 pipe about half busy"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,   # per step: the k_iterate kernel of the plain order-2..5 part, k_finalize
