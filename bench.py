@@ -559,9 +559,11 @@ def run_gpu(args):
                    "rounds_median": float(np.median([r.rounds for r in done])) if done else None,
                    "integrals_per_s": n_int / wall, "diagrams_per_s": n_diag / wall,
                    "evals_per_s": srv.evals / wall, "budget_bytes": srv.budget,
+                   "max_iters": srv.max_iters, "max_samples_per_iter": srv.max_samples,
                    "workload": "Poisson 20/s, n ~ U[0.04, 0.20] fm^-3, delta {0..1}, order cap {2,3,4}, "
                                "target {1, 0.3, 0.1} %, seed 7 (+rank); 40 GB admission budget; rounds of at "
                                "most 2^27 samples, least work left first (a request waiting 2 s runs first); "
+                               "adaptive samples per integral and iteration up to 2^25, at most 120 iterations; "
                                "diagrams/s counts a mirror-pair representative twice"}
         be.close()
     if dist:

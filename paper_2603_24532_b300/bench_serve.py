@@ -27,7 +27,9 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--arena-gb", type=float, default=48.0)
     ap.add_argument("--time-limit", type=float, default=None)
-    ap.add_argument("--max-iters", type=int, default=60)
+    ap.add_argument("--max-iters", type=int, default=120)
+    ap.add_argument("--max-samples", type=float, default=float(S.MAX_SAMPLES),
+                    help="adaptive samples per iteration of one integral: at most this")
     ap.add_argument("--warm-start", action="store_true")
     ap.add_argument("--grouped", action="store_true", help="one integral per (order, particle-hole group)")
     ap.add_argument("--group-orders", default=None, help="with --grouped: only these orders, e.g. 4 or 3,4")
@@ -43,7 +45,8 @@ def main():
     logf = open(a.log, "w") if a.log else None
     srv = S.Server(be, budget_bytes=int(a.budget_gb * (1 << 30)), max_iters=a.max_iters, warm_start=a.warm_start,
                    warm_blend=a.warm_blend, warm_train=a.warm_train, log=logf,
-                   round_samples=int(a.round_samples) if a.round_samples > 0 else None, max_wait=a.max_wait)
+                   round_samples=int(a.round_samples) if a.round_samples > 0 else None, max_wait=a.max_wait,
+                   max_samples=int(a.max_samples))
     trace = S.poisson_trace(a.requests, a.rate, a.seed)
     t0 = time.perf_counter()
     done = srv.run(trace, realtime=True, time_limit=a.time_limit)
@@ -60,6 +63,7 @@ def main():
            "capped_by_cap": {str(c): sum(r.capped for r in done if r.cap == c) for c in (2, 3, 4)},
            "capped_by_target": {str(t): sum(r.capped for r in done if r.target == t) for t in (0.01, 0.003, 0.001)},
            "group_orders": a.group_orders, "round_samples": a.round_samples, "max_wait": a.max_wait,
+           "max_iters": a.max_iters, "max_samples": a.max_samples,
            "evals_per_request_median": {"cap%d target%g" % (c, t): float(np.median(
                [sum(it.evals for it in r.integrals) for r in done if r.cap == c and r.target == t] or [0]))
                for c in (2, 3, 4) for t in (0.01, 0.003, 0.001)},
