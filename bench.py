@@ -687,11 +687,18 @@ def cpu_baseline(budget_s=12.0, stride=None, n=4096):
     grid = O.uniform_grid(18, 50)
     work = [(ki, kf, D) for ki, kf in enumerate(KF5) for D in Ds]
 
+    need = []     # samples each integral would need for 0.1 % at its own per-sample variance
+
     def run(sel):
+        need.clear()
         t0 = time.perf_counter()
         for ki, kf, D in sel:
-            O.vegas_iteration(D, O.Physics(kF_n=kf, K_max=kf + 6.0), grid, 1, 1000 * ki + D.diagram_id, 0, n,
-                              threads=cores)
+            r = O.vegas_iteration(D, O.Physics(kF_n=kf, K_max=kf + 6.0), grid, 1, 1000 * ki + D.diagram_id, 0, n,
+                                  threads=cores)
+            mean = r.sum_w / n
+            var = max(r.sum_w2 / n - mean * mean, 0.0)
+            if mean != 0.0:
+                need.append(var / (1e-3 * mean) ** 2)
         return time.perf_counter() - t0
 
     if stride is None:
@@ -700,7 +707,13 @@ def cpu_baseline(budget_s=12.0, stride=None, n=4096):
         stride = max(1, int(math.ceil(len(work) * n / (rate * budget_s))))
     sel = work[::stride]
     dt = run(sel)
-    return {"value": len(sel) * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "stride": stride,
+    rate = len(sel) * n / dt
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "stride": stride,
+            "time_to_0p1pct_s": {"median": float(np.median(need)) / rate if need else None,
+                                 "definition": "per sampled integral, its per-sample variance on the uniform grid "
+                                               "over (0.1 % of its mean)^2 samples at the oracle's rate; median "
+                                               "over the sampled integrals (no grid adaptation: an upper "
+                                               "estimate)"},
             "sample": "%d samples of every %d-th of the %d fifth-order integrals (%d integrals, uniform grid, "
                       "iteration 0), %.1f s" % (n, stride, len(work), len(sel), dt)}
 
