@@ -400,9 +400,9 @@ int mbpt_philox_device(mbpt_ctx* ctx, const uint32_t ctr[4], const uint32_t key[
  * order 3) fail with MBPT_EINVAL and a message giving the limit.  The
  * first call on a device looks up the array's device address and sets kernel
  * attributes for that device.  Every call copies its work description from
- * host stack memory with cudaMemcpyAsync, so no call may be captured into a
- * CUDA graph.  Calls that overlap on the GPU (different streams, or different
- * host threads) race on the shared array: serialise them.  Each call resets
+ * host stack memory with cudaMemcpyAsync.  Calls that overlap on the GPU
+ * (different streams, or different host threads) race on the shared array:
+ * serialise them.  Each call resets
  * the parts that must start at zero; the rest of the array keeps the last
  * call's contents.
  *
