@@ -2,7 +2,8 @@
 evaluation).  The evaluation-phase combination against the oracle's pooled combination on one grid,
 the frozen grid, and at fourth order -- where single weights are heavy-tailed -- the scatter of
 independent runs against their own errors: eight seeds of the per-diagram sums and of the aligned group
-sums must scatter as their errors say, the two must agree, and mirror partners must agree."""
+sums must scatter as their errors say, the two must agree, and mirror partners must agree; the same
+scatter test for E5 at fifth order."""
 import math
 
 import numpy as np
@@ -165,6 +166,60 @@ def test_fourth_order_mirror_pairs_agree(fourth_order_runs, name):
         _, mi, si = _chi2dof([R["diag"][k][i][0] for k in range(len(SEEDS))], [R["diag"][k][i][1] for k in range(len(SEEDS))])
         _, mj, sj = _chi2dof([R["diag"][k][j][0] for k in range(len(SEEDS))], [R["diag"][k][j][1] for k in range(len(SEEDS))])
         assert abs(mi - mj) <= 3.0 * math.hypot(si, sj), (descs[i].diagram_id, mi, si, mj, sj)
+
+
+FIFTH_SEEDS = range(11, 19)
+FIFTH_POINTS = (1.0, 1.33)
+
+
+@pytest.fixture(scope="module")
+def fifth_order_runs(ctx):
+    """Per Fermi momentum (PNM) and seed: E5 as the sum of the 668 non-anomalous fifth-order diagrams
+    integrated one by one, and as the sum of the five aligned group integrals; 3 training iterations, then
+    10 frozen-grid iterations of 2^20 samples each, alpha 0.75 (about 1 min on one B300)."""
+    descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
+    groups = {}
+    for d in descs:
+        groups.setdefault(M.mbpt_hole_chords(d), []).append(d)
+
+    def cfg(seed, sid):
+        return M.vegas_cfg(samples=1 << 20, seed=seed, stream_id=sid, precision=M.MBPT_MIXED, alpha=0.75,
+                           train_iters=3, combine=M.MBPT_COMBINE_POOLED)
+
+    out = {}
+    for kf in FIFTH_POINTS:
+        ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+        per, grp = [], []
+        for seed in FIFTH_SEEDS:
+            gs = [M.mbpt_create_diagram(ctx, d, ph, cfg(seed, d.diagram_id)) for d in descs]
+            M.mbpt_vegas_iterate(ctx, gs, 13)
+            r = M.mbpt_estimate_batch(gs)
+            per.append((sum(x.mean for x in r), math.sqrt(sum(x.sigma ** 2 for x in r))))
+            for g in gs:
+                M.mbpt_destroy_diagram(g)
+            gg = [M.mbpt_create_group(ctx, mem, ph, cfg(seed, 5000 + key)) for key, mem in sorted(groups.items())]
+            M.mbpt_vegas_iterate(ctx, gg, 13)
+            r = M.mbpt_estimate_batch(gg)
+            grp.append((sum(x.mean for x in r), math.sqrt(sum(x.sigma ** 2 for x in r))))
+            for g in gg:
+                M.mbpt_destroy_diagram(g)
+        out[kf] = {"per": per, "grp": grp}
+    return out
+
+
+@pytest.mark.parametrize("kf", FIFTH_POINTS)
+def test_fifth_order_seed_scatter(fifth_order_runs, kf):
+    """E5 at fifth order, where single weights are heaviest-tailed: over eight independent seeds the
+    per-diagram sums and the aligned group sums each scatter consistently with their errors (chi^2/dof <= 2
+    over 7 degrees of freedom), their eight-seed means agree within 3 sigma, and the groups are at least as
+    precise at equal member evaluations."""
+    R = fifth_order_runs[kf]
+    c_per, m_per, s_per = _chi2dof(*zip(*R["per"]))
+    c_grp, m_grp, s_grp = _chi2dof(*zip(*R["grp"]))
+    assert c_per <= 2.0, (c_per, R["per"])
+    assert c_grp <= 2.0, (c_grp, R["grp"])
+    assert abs(m_grp - m_per) <= 3.0 * math.hypot(s_grp, s_per), (m_grp, s_grp, m_per, s_per)
+    assert s_grp <= 1.1 * s_per, (s_grp, s_per)
 
 
 def test_histogram_layouts_agree(ctx):
