@@ -274,9 +274,10 @@ def run_gpu(args):
                   / (4.0 * n_sm * clk["sm_mhz"] * 1e6)) if cnt5 and clk.get("sm_mhz") else None
 
     # end to end through the public API: per step the work table goes up inside mbpt_vegas_iterate
-    # (a WORK_ITEM_BYTES item and an 8-byte histogram pointer per integral, the work header) and every
-    # integral's estimate comes back with one synchronisation
-    h2d = n5 * (M.WORK_ITEM_BYTES + 8) + M.WORK_HEADER_BYTES
+    # (a WORK_ITEM_BYTES item and an 8-byte histogram pointer per integral, the work header), and
+    # mbpt_estimate_batch sends the integrals' 8-byte state pointers and reads every integral's 80-byte
+    # state head back in one copy, with one synchronisation
+    h2d = n5 * (M.WORK_ITEM_BYTES + 8 + 8) + M.WORK_HEADER_BYTES
     d2h = n5 * M.RESULT_BYTES + 4
     t0 = time.perf_counter()
     for _ in range(args.steps):

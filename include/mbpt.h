@@ -352,7 +352,10 @@ int mbpt_vegas_iterate(mbpt_ctx* ctx, mbpt_diag* const* diags, int k, int n_iter
 
 /* Synchronise and read an integral's estimate. */
 int mbpt_estimate(const mbpt_diag* diag, mbpt_result* out);
-/* The same for k integrals of one context with a single synchronisation; out[i] for diags[i]. */
+/* The same for k integrals of one context with a single synchronisation; out[i] for diags[i].  A small
+ * kernel gathers the integrals' estimates on the device and one copy brings them back (device and pinned
+ * host staging held by the context, grown to the largest k); without room for the staging it reads
+ * the integrals one copy each instead of failing. */
 int mbpt_estimate_batch(mbpt_diag* const* diags, int k, mbpt_result* out);
 /* Regulator components: mean[k], sigma[k] for shift k = 0..2 and, at index 3, the
  * extrapolation to zero shift.  MBPT_EINVAL if the integral has no shifts. */

@@ -308,6 +308,14 @@ __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members,
 // latency, bounds the loop.  The sink store never happens (the chains stay positive) but keeps the loop.
 __device__ double g_dfma_sink;
 
+// One 16-byte word per thread: word w of the state of integral s, at out[s * words + w].
+__global__ void __launch_bounds__(256) k_gather_heads(const DiagState* const* src, int k, int words, uint4* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k * words) return;
+    const int s = i / words, w = i - s * words;
+    out[i] = reinterpret_cast<const uint4*>(src[s])[w];
+}
+
 __global__ void __launch_bounds__(256) k_dfma_rate(int iters) {
     const double b = 0.9999999, c = 1.0e-7;
     double a0 = 1.0 + 1e-9 * threadIdx.x, a1 = a0 + 0.1, a2 = a0 + 0.2, a3 = a0 + 0.3;

@@ -46,6 +46,8 @@ MBPT_DECLARE_SHAPE(128, 3)
 // per integral: fixed-order reduction of the chunk slots, combination, convergence, refinement
 __global__ void k_finalize(WorkHeader* hdr, const WorkItem* items, const double* csum, const float* chist,
                            double* const* last_hist);
+// batched estimate: the first `words` 16-byte words of each listed integral's state, into one array
+__global__ void k_gather_heads(const DiagState* const* src, int k, int words, uint4* out);
 // test hooks
 __global__ void k_dump(const DiagRec* rec, int n_members, const double* grid, uint64_t seed, uint32_t sid, uint32_t iter,
                        uint64_t first, uint64_t count, double* xo, double* wo);

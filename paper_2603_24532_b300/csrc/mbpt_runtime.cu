@@ -153,6 +153,12 @@ struct mbpt_ctx {
     std::set<mbpt_diag*> diags;
     std::vector<WorkItem> h_items;
     std::vector<double*> h_last_hist;
+    // batched estimate: state pointers and gathered state heads on the device (arena), and their pinned
+    // host staging (gather_cap pointers, then gather_cap heads)
+    const DiagState** d_gather_src = nullptr;
+    uint4* d_gather_out = nullptr;
+    void* h_gather = nullptr;
+    size_t gather_cap = 0;
 };
 
 struct mbpt_diag {
@@ -377,6 +383,7 @@ int mbpt_ctx_destroy(mbpt_ctx* c) {
     for (mbpt_diag* d : c->diags) delete d;
     c->diags.clear();
     if (c->own_arena) cudaFree(c->arena.base);
+    if (c->h_gather) cudaFreeHost(c->h_gather);
     for (int i = 0; i < 3; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -735,13 +742,48 @@ int mbpt_estimate_batch(mbpt_diag* const* diags, int k, mbpt_result* out) {
     DeviceGuard dg(c->device);
     int st = check_device_error(c);
     if (st) return st;
-    std::vector<DiagState> hs((size_t)k);
-    for (int i = 0; i < k; ++i)
-        CUDA_TRY(cudaMemcpyAsync(&hs[i], diags[i]->d_state, offsetof(DiagState, hist_mean), cudaMemcpyDeviceToHost,
-                                 c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    // the states' heads (estimate, error, counters) gathered on the device by one kernel and read back with
+    // one copy; per-integral copies (about 10 us each) only if the gather buffers cannot be had
+    constexpr size_t kHead = offsetof(DiagState, hist_mean);
+    static_assert(kHead % 16 == 0, "the state head is copied as 16-byte words");
+    if ((size_t)k > c->gather_cap) {
+        const size_t cap = std::max((size_t)k, 2 * c->gather_cap);
+        c->arena.release(c->d_gather_src);
+        c->arena.release(c->d_gather_out);
+        if (c->h_gather) cudaFreeHost(c->h_gather);
+        c->h_gather = nullptr;
+        c->gather_cap = 0;
+        c->d_gather_src = (const DiagState**)c->arena.alloc(sizeof(DiagState*) * cap);
+        c->d_gather_out = (uint4*)c->arena.alloc(kHead * cap);
+        if (c->d_gather_src && c->d_gather_out &&
+            cudaMallocHost(&c->h_gather, (sizeof(DiagState*) + kHead) * cap) == cudaSuccess)
+            c->gather_cap = cap;
+        else
+            cudaGetLastError();
+    }
+    std::vector<DiagState> hs;
+    const unsigned char* heads = nullptr;
+    if ((size_t)k <= c->gather_cap) {
+        const DiagState** hp = (const DiagState**)c->h_gather;
+        unsigned char* hh = (unsigned char*)c->h_gather + sizeof(DiagState*) * c->gather_cap;
+        for (int i = 0; i < k; ++i) hp[i] = diags[i]->d_state;
+        CUDA_TRY(cudaMemcpyAsync(c->d_gather_src, hp, sizeof(DiagState*) * k, cudaMemcpyHostToDevice, c->stream));
+        const int words = (int)(kHead / 16);
+        k_gather_heads<<<(k * words + 255) / 256, 256, 0, c->stream>>>(c->d_gather_src, k, words, c->d_gather_out);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(hh, c->d_gather_out, kHead * k, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        heads = hh;
+    } else {
+        hs.resize((size_t)k);
+        for (int i = 0; i < k; ++i)
+            CUDA_TRY(cudaMemcpyAsync(&hs[i], diags[i]->d_state, kHead, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
     for (int i = 0; i < k; ++i) {
-        const DiagState& s = hs[i];
+        DiagState sh;
+        if (heads) memcpy(&sh, heads + kHead * i, kHead);
+        const DiagState& s = heads ? sh : hs[i];
         out[i].mean = s.mean;
         out[i].sigma = s.sigma;
         out[i].chi2_dof = s.chi2;

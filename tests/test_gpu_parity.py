@@ -277,6 +277,30 @@ def test_deterministic_and_alone_equals_mix(ctx):
         assert alone[0] == a[i] and salone[0] == sa[i]
 
 
+def test_batched_estimate_equals_single_estimates(ctx):
+    """mbpt_estimate_batch (the states' heads gathered on the device and read back in one copy) returns
+    exactly what mbpt_estimate returns integral by integral: for a batch, for a larger batch that grows
+    the gather buffers, and for a subset in reverse order."""
+    descs = M.mbpt_generate(3)
+    gs = []
+    for i in range(120):
+        kf = 0.8 + 0.01 * i
+        cfg = M.vegas_cfg(samples=1 << 14, seed=3, stream_id=i, precision=M.MBPT_MIXED)
+        gs.append(M.mbpt_create_diagram(ctx, descs[i % 3], M.physics(kF_n=kf, K_max=kf + 6.0), cfg))
+    try:
+        M.mbpt_vegas_iterate(ctx, gs, 2)
+        for batch in (gs[:37], gs, gs[::-3]):
+            got = [r.as_dict() for r in M.mbpt_estimate_batch(batch)]
+            want = [M.mbpt_estimate(g).as_dict() for g in batch]
+            assert len(got) == len(want)
+            for a, b in zip(got, want):
+                assert all(a[k] == b[k] or (a[k] != a[k] and b[k] != b[k]) for k in a), (a, b)
+            assert all(r["n_iter"] == 2 and r["n_evals"] == 2 << 14 for r in got)
+    finally:
+        for g in gs:
+            M.mbpt_destroy_diagram(g)
+
+
 def test_checkpoint_restore_continues_bitwise(ctx):
     d, p, c = _specs()[2]
     g = M.mbpt_create_diagram(ctx, d, p, c)
