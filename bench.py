@@ -146,13 +146,14 @@ class Clocks:
 # ---------------------------------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------------------------------
-def fifth_order_integrals(M, ctx, precision, samples=SAMPLES5, seed=1, stream_base=0, every=1, **cfg_kw):
-    """The 2004 fifth-order integrals (or every `every`-th of them), with their (kF, descriptor)."""
+def fifth_order_integrals(M, ctx, precision, samples=SAMPLES5, seed=1, stream_base=0, every=1, map_kind=0, **cfg_kw):
+    """The 2004 fifth-order integrals (or every `every`-th of them), with their (kF, descriptor); map_kind 1:
+    the rotational reduction (15 dimensions)."""
     descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
     gs, meta = [], []
     k = 0
     for ki, kf in enumerate(KF5):
-        ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+        ph = M.physics(kF_n=kf, K_max=kf + 6.0, map_kind=map_kind)
         for d in descs:
             k += 1
             if (k - 1) % every:
@@ -383,11 +384,11 @@ def run_gpu(args):
     # E5 per kF from the 668 diagrams one by one vs from the five aligned particle-hole groups of the same
     # diagrams (Sec. III.A), at equal member evaluations (2^20 samples per integral and iteration; a group
     # sample evaluates each member once), 3 training + 6 evaluation iterations, pooled
-    def e5_run(grouped, sd):
+    def e5_run(grouped, sd, map_kind=0):
         gs, keys = [], []
         descs = [d for d in M.mbpt_generate(5) if not d.anomalous]
         for ki, kf in enumerate(KF5):
-            ph = M.physics(kF_n=kf, K_max=kf + 6.0)
+            ph = M.physics(kF_n=kf, K_max=kf + 6.0, map_kind=map_kind)
             if grouped:
                 by = {}
                 for d in descs:
@@ -424,6 +425,18 @@ def run_gpu(args):
     t_grp, n_grp = sum(r[1] for r in runs_grp), runs_grp[0][2]
     eff = [sum(e[k][1] ** 2 for e in e5_sep) * t_sep / (sum(e[k][1] ** 2 for e in e5_grp) * t_grp)
            for k in e5_sep[0] if all(e[k][1] > 0 for e in e5_grp)]
+    # the rotational reduction (one chord on the z axis, one in the xz plane: 15 dimensions), the diagrams
+    # one by one, the same seeds and iterations
+    runs_rot = [e5_run(False, seed + 200 + j, map_kind=1) for j in range(2)]
+    e5_rot = [r[0] for r in runs_rot]
+    t_rot = sum(r[1] for r in runs_rot)
+    eff_rot = [sum(e[k][1] ** 2 for e in e5_sep) * t_sep / (sum(e[k][1] ** 2 for e in e5_rot) * t_rot)
+               for k in e5_sep[0] if all(e[k][1] > 0 for e in e5_rot)]
+    g5r, _ = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase, map_kind=1)
+    timed_steps(g5r, 3)
+    _, st5r = timed_steps(g5r, 5)
+    v5r = world * len(g5r) * SAMPLES5 / (float(np.mean(st5r)) * 1e-3)
+    destroy(M, g5r)
 
     # the plain per-diagram FP64 loop on every 20th fifth-order integral: one launch per integral and
     # iteration, default launch shape
@@ -632,6 +645,13 @@ def run_gpu(args):
                                                 "max(0.5 % |I|, 0.5 % |E5(kF)| / sqrt(668)); cap 40 iterations; "
                                                 "k0: the same evaluations at the plain per-diagram FP64 loop's "
                                                 "rate"},
+        "fifth_order_rotational_15d": {"value": v5r, "unit": UNIT, "integrals": n5, "samples_per_iter": SAMPLES5,
+                                       "per_kF": e5_rot, "wall_s": t_rot, "time_to_equal_error_ratio": eff_rot,
+                                       "definition": "the headline's integrals with the rotational reduction "
+                                                     "(d = 15; 5 timed steps); E5 +- sigma per kF and seed from 3 "
+                                                     "training + 10 pooled iterations at 2^20 (two seeds, as "
+                                                     "fifth_order_groups); ratio per kF = (sum of sigma^2) x "
+                                                     "wall time, 18D over 15D"},
         "fifth_order_groups": {"per_kF_diagrams": e5_sep, "per_kF_groups": e5_grp, "wall_s_diagrams": t_sep,
                                "wall_s_groups": t_grp, "integrals": [n_sep, n_grp],
                                "time_to_equal_error_ratio": eff,
