@@ -12,7 +12,7 @@ per-diagram FP64 loop on a subset, the mixed-vs-FP64 deviation, the third-order 
 FP64 batched path and the plain loop), the fourth-order batch and its aligned groups, the sixth-order
 batch, and the serving stream (p50/p99 latency, diagrams/s).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--profile-case fifth|third]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--profile-case fifth|third|sixth]
 """
 from __future__ import annotations
 
@@ -773,15 +773,23 @@ def run_reference(args):
 
 
 def profile_case(args):
-    """A small case of one workload for ncu captures of k_iterate: `fifth` (the 2004 fifth-order integrals)
-    or `third` (the 30 third-order integrals), args.samples samples each, args.iters batched iterations."""
+    """A small case of one workload for ncu captures of k_iterate: `fifth` (the 2004 fifth-order integrals),
+    `third` (the 30 third-order integrals) or `sixth` (the 11269 sixth-order integrals, one per mirror
+    pair, PNM kF 1.33), args.samples samples each, args.iters batched iterations, in an arena of
+    args.arena_gb GiB."""
     from paper_2603_24532_b300 import mbpt as M
-    ctx = M.mbpt_ctx_create(0, 8 << 30)
+    ctx = M.mbpt_ctx_create(0, int(args.arena_gb * (1 << 30)))
     prec = M.MBPT_MIXED if args.precision == "mixed" else M.MBPT_FP64
+    order = {"fifth": 5, "third": 3, "sixth": 6}[args.profile_case]
     if args.spt:
-        M.mbpt_ctx_set_launch(ctx, 5 if args.profile_case == "fifth" else 3, args.spt)
+        M.mbpt_ctx_set_launch(ctx, order, args.spt)
     if args.profile_case == "fifth":
         gs, _ = fifth_order_integrals(M, ctx, prec, samples=args.samples, near_band=args.near_band)
+    elif args.profile_case == "sixth":
+        ph = M.physics(kF_n=1.33, K_max=7.33)
+        gs = [M.mbpt_create_diagram(ctx, d, ph, M.vegas_cfg(samples=args.samples, stream_id=d.diagram_id,
+                                                            precision=prec, alpha=0.75))
+              for d in M.mbpt_generate(6) if not d.anomalous and d.diagram_id <= d.mirror_id]
     else:
         descs = M.mbpt_generate(3)
         gs = []
@@ -794,7 +802,7 @@ def profile_case(args):
     it_ms, fin_ms = M.mbpt_ctx_last_timing(ctx)
     print("%s: integrals %d samples %d iters %d spt %d: k_iterate %.3f ms, k_finalize %.3f ms, first mean %.6g +- %.2g"
           % (args.profile_case, len(gs), args.samples, args.iters,
-             M.mbpt_ctx_get_launch(ctx, 5 if args.profile_case == "fifth" else 3)[2], it_ms, fin_ms, r.mean, r.sigma))
+             M.mbpt_ctx_get_launch(ctx, order)[2], it_ms, fin_ms, r.mean, r.sigma))
     M.mbpt_ctx_destroy(ctx)
 
 
@@ -809,13 +817,14 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=6.0, help="reference arm: seconds per step")
     ap.add_argument("--serve-requests", type=int, default=1200, help="serving run (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=150.0)
-    ap.add_argument("--profile-case", choices=["fifth", "third"], default=None,
+    ap.add_argument("--profile-case", choices=["fifth", "third", "sixth"], default=None,
                     help="run only a small case of one workload (for ncu captures)")
     ap.add_argument("--samples", type=int, default=1 << 16, help="--profile-case: samples per integral")
     ap.add_argument("--iters", type=int, default=3, help="--profile-case: batched iterations")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="--profile-case precision")
     ap.add_argument("--near-band", type=float, default=0.0, help="--profile-case: FP64-map band (0 = default)")
     ap.add_argument("--spt", type=int, default=0, help="--profile-case: samples per thread of a chunk (0 = default)")
+    ap.add_argument("--arena-gb", type=float, default=8.0, help="--profile-case: device arena (GiB)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
