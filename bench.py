@@ -267,9 +267,11 @@ def run_gpu(args):
     ops5 = cnt5["ops_per_sample"] if cnt5 else None
     fp64_rate = M.mbpt_fp64_rate(local, M.mbpt_ctx_stream(ctx))
     achieved = (ops5 * evals_step / (it_ms * 1e-3)) if ops5 else None
-    # DRAM bytes of a launch of this shape (null unless the counters were taken on the same launch shape), and
+    # DRAM bytes of a launch of this shape: the counters come from a launch of the same kernel, integrals and
+    # samples per thread with fewer samples per integral (2^18), whose traffic -- the chunk slots, written once,
+    # one per 8192 samples -- grows in proportion to the samples, so it is scaled to the headline launch; and
     # the share of the SMs' instruction issue slots (4 warp instructions per SM per cycle) the launch uses
-    traffic5 = cnt5["dram_bytes"] if cnt5 and cnt5["samples"] == evals_step else None
+    traffic5 = (cnt5["dram_bytes"] * evals_step / cnt5["samples"]) if cnt5 else None
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     issue_frac = (cnt5["warp_inst"] / cnt5["samples"] * evals_step / (it_ms * 1e-3)
                   / (4.0 * n_sm * clk["sm_mhz"] * 1e6)) if cnt5 and clk.get("sm_mhz") else None
@@ -621,10 +623,11 @@ def run_gpu(args):
                      "ops_per_sample": ops5, "ops_source": "ncu DADD + DMUL + DFMA thread instructions per "
                                                           "sample, profiles/fp64_ops_per_sample.txt",
                      "kernel_ms": it_ms, "traffic": traffic5, "traffic_unit": "bytes per launch",
-                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch of this shape "
-                                     "(ncu, profiles/fp64_ops_per_sample.txt): the chunk slots written once "
-                                     "(histogram and sums, 3.6 KB per chunk), records and grids; HBM is otherwise "
-                                     "idle by design",
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch of the same kernel "
+                                     "and integrals at 2^18 samples each (ncu, profiles/fp64_ops_per_sample.txt), "
+                                     "scaled by samples to this launch: the chunk slots written once (histogram "
+                                     "and sums, 3.6 KB per 8192 samples), records and grids; HBM is otherwise idle "
+                                     "by design",
                      "issue_frac": issue_frac,
                      "issue_note": "warp instructions per sample (ncu sm__inst_executed.sum of the same launch "
                                    "shape) x samples / kernel time, over 4 issue slots per SM per cycle at the "

@@ -35,6 +35,8 @@ struct alignas(16) ChunkSmemT {
     double gacc[(PART & 2) ? group_slots(PART) : 1][NW * 32];  // group integrals: per-sample sums over the members
     uint32_t queue[NW][queue_len(PART)];     // per-warp stacks of samples past the pre-test
                                              // (away from a Fermi surface from the bottom, near one from the top)
+    uint32_t pool[NW * 64];                  // the chunk's last partial warps of all warps (far, then near)
+    int rem[2][NW];                          // per warp: far and near samples left when the chunk is classified
     double red[2][NW];
     double redc[(PART & 1) ? 2 * kComp : 1][NW];
     uint32_t chunk, item, iter, skip;
@@ -110,7 +112,7 @@ __device__ __forceinline__ void hist_add(float* hist, float* hist_block, uint32_
     }
 }
 
-// Bin indices of sample s alone (the same integer map as eval_sample: i = floor((u + 1/2) 2^-32 nb)).
+// Bin indices of sample s alone (the same integer map as eval_sample: i = floor((u + 1/2) 2^-32 nb), bin_split).
 template <int D>
 __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1,
                                             uint32_t nb, uint32_t* binpack) {
@@ -125,7 +127,8 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
         for (int q = 0; q < 4; ++q) {
             const int a = 4 * j + q;
             if (a < D) {
-                const uint32_t i = (uint32_t)(((2ull * (uint64_t)u[q] + 1ull) * (uint64_t)nb) >> 33);
+                uint32_t i, lo;
+                bin_split(u[q], nb, i, lo);
                 binpack[a >> 2] |= i << (8 * (a & 3));
             }
         }
@@ -139,8 +142,9 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  its own code: class_rounds() rounds of the FP32 front and Fermi-step pre-test, pushing the samples
 //  that may be live onto one of two shared-memory stacks by class (away from / near a Fermi
 //  surface; ballot + prefix count), then full warps of one class popped and evaluated until fewer
-//  than 32 of each remain; the partial warps are evaluated at the end of the chunk.  Which thread
-//  sums which sample depends only on the chunk, so results stay deterministic.
+//  than 32 of each remain; the last partial warps of all the block's warps are pooled and evaluated as
+//  full warps where possible at the end of the chunk.  Which thread sums which sample depends only on the
+//  chunk, so results stay deterministic.
 //  A group integral (n_members > 1; its own kernel, GRP) evaluates every member at each sample, member
 //  by member with the record swapped in shared memory, each member's samples through the phases
 //  above, adding the weights per sample into gacc, zeroed per chunk (spt x (1 + regulator components)
@@ -180,11 +184,16 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
         }
         int j = 0, nf = 0, nn = 0;       // warp-uniform: next round, stack heights (far, near)
         bool drain = false;
+        // Pooled stage: once the chunk (a group: the member) is classified and fewer than 32 samples of
+        // each class are left in every warp's stacks, the block gathers them in warp order (far, then near)
+        // and its warps evaluate the pooled groups of 32, group g by warp g mod NW: fewer partial warps.
+        // In that stage nf and nn hold the pooled counts and j = w_spt + 1 + g (no other loop state, so
+        // that it costs no registers).
         for (;;) {
             uint64_t s;
-                    bool have, use_near = false;
+            bool have, use_near = false, pooled = false;
             int cnt = 0;
-            if (compact) {
+            if (compact && j <= w_spt) {
                 if (!drain && nf < 32 && nn < 32) {
                     const int jend = (j + kRounds < w_spt) ? j + kRounds : w_spt;
                     for (; j < jend; ++j) {
@@ -205,13 +214,47 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                 }
                 if (nf >= 32) cnt = 32;
                 else if (nn >= 32) { cnt = 32; use_near = true; }
-                else if (drain && nf > 0) cnt = nf;
-                else if (drain && nn > 0) { cnt = nn; use_near = true; }
-                else if (drain) break;
-                else continue;
+                else if (!drain) continue;
+                else {
+                    // every warp of the block arrives here exactly once per chunk (and member)
+                    const int warp = (int)(threadIdx.x >> 5);
+                    if (lane == 0) {
+                        S.rem[0][warp] = nf;
+                        S.rem[1][warp] = nn;
+                    }
+                    __syncthreads();
+                    int of = 0, on = 0, tf = 0, tn = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        const int a = S.rem[0][w], b = S.rem[1][w];
+                        of += (w < warp) ? a : 0;
+                        on += (w < warp) ? b : 0;
+                        tf += a;
+                        tn += b;
+                    }
+                    if ((int)lane < nf) S.pool[of + (int)lane] = q[lane];
+                    if ((int)lane < nn) S.pool[tf + on + (int)lane] = q[kQ - 1 - (int)lane];
+                    __syncthreads();
+                    nf = tf;
+                    nn = tn;
+                    j = w_spt + 1 + warp;
+                }
+                if (cnt > 0) {
+                    have = (int)lane < cnt;
+                    s = !have ? 0u : (use_near ? q[kQ - 1 - (nn - cnt + (int)lane)] : q[nf - cnt + (int)lane]);
+                }
+            }
+            if (compact && j > w_spt) {
+                const int g = j - w_spt - 1, n_gf = (nf + 31) >> 5;
+                if (g >= n_gf + ((nn + 31) >> 5)) break;
+                pooled = true;
+                use_near = g >= n_gf;
+                const int base = use_near ? nf + 32 * (g - n_gf) : 32 * g;
+                cnt = min(32, (use_near ? nf + nn : nf) - base);
                 have = (int)lane < cnt;
-                s = !have ? 0u : (use_near ? q[kQ - 1 - (nn - cnt + (int)lane)] : q[nf - cnt + (int)lane]);
-            } else {
+                s = have ? S.pool[base + (int)lane] : 0u;
+                j += NW;
+            } else if (!compact) {
                 if (j >= w_spt) break;
                 s = first + (uint64_t)j * blockDim.x + threadIdx.x;
                 have = s < w_samples;
@@ -222,8 +265,8 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                         R, S.grid, w_grid, (uint32_t)s, t, w_sid, k0, k1, nullptr,
                         !compact ? kClassUnknown : (use_near ? kClassNear : kClassFar));
                 if constexpr (GRP) {
-                    // the sample's slot belongs to the lane of this warp that owns it in the chunk layout
-                    // (sample first + js * blockDim + own); each slot gets one add per member
+                    // the sample's slot belongs to the thread that owns it in the chunk layout (sample
+                    // first + js * blockDim + own), whichever warp evaluates it; each slot gets one add per member
                     const uint32_t off = (uint32_t)(s - first);
                     const int js = (int)(off / blockDim.x), own = (int)(off - (uint32_t)js * blockDim.x);
                     S.gacc[js * PER][own] += o.w;
@@ -246,7 +289,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                     }
                 }
             }
-            if (compact) {
+            if (compact && !pooled) {
                 if (use_near) nn -= cnt;
                 else nf -= cnt;
                 __syncwarp();                  // popped slots may be pushed again by the next phase
@@ -254,7 +297,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
         }
     }
     if constexpr (!GRP) return;
-    __syncwarp();                              // slots were filled by the warp's lanes
+    __syncthreads();                           // slots were filled by the block's warps (pooled stage)
     for (int j = 0; j < w_spt; ++j) {
         const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
         if (s >= w_samples) continue;
