@@ -187,6 +187,7 @@ def run_gpu(args):
     import torch
 
     from paper_2603_24532_b300 import mbpt as M
+    from paper_2603_24532_b300 import run_fifth_order as RF
     from paper_2603_24532_b300.autotune import autotune
 
     rank, world, local = dist_env()
@@ -314,42 +315,18 @@ def run_gpu(args):
                           precision=M.MBPT_MIXED, alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED,
                           target_rel=0.005, target_abs=floors[kf])
         M.mbpt_set_config(g, cfg)
-    # adaptive samples per iteration (PVegas, Sec. III.C): each live integral's remaining need is its
-    # per-sample variance over its goal squared, less the evaluation samples it has; the integrals closest
-    # to their targets get what they need first (up to 2^22 per iteration), the rest 2^18, within 2^20
+    # adaptive samples per iteration (PVegas, Sec. III.C; run_fifth_order.converge): the integrals closest to
+    # their targets get what they still need first (up to 2^22 per iteration), the rest 2^18, within 2^20
     # samples per unconverged integral per iteration
-    iters, conv_evals = 3, 3 * len(gsc) * SAMPLES5
-    cur = {id(g): SAMPLES5 for g in gsc}
-    while iters < 40:
-        rc = M.mbpt_estimate_batch(gsc)
-        live = []
-        for g, r, (kf, d) in zip(gsc, rc, metac):
-            if r.converged:
-                continue
-            n_eval = r.n_evals - 3 * SAMPLES5
-            goal = max(0.005 * abs(r.mean), floors[kf])
-            need = (r.sigma ** 2 * n_eval / goal ** 2 - n_eval) if (n_eval > 0 and math.isfinite(r.sigma)
-                                                                  and goal > 0.0) else float(SAMPLES5)
-            live.append((max(need, 1.0), g, kf, d))
-        if not live:
-            break
-        live.sort(key=lambda x: x[0])
-        left = len(live) * SAMPLES5
-        for need, g, kf, d in live:
-            nxt = 1 << 18
-            if left > 0:
-                nxt = 1 << int(math.ceil(math.log2(min(float(1 << 22), max(float(1 << 18), need)))))
-            left -= nxt
-            if nxt != cur[id(g)]:
-                cfg = M.vegas_cfg(samples=nxt, seed=seed + 100,
-                                  stream_id=sbase + 1000 * KF5.index(kf) + d.diagram_id, precision=M.MBPT_MIXED,
-                                  alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED,
-                                  target_rel=0.005, target_abs=floors[kf])
-                M.mbpt_set_config(g, cfg)
-                cur[id(g)] = nxt
-        M.mbpt_vegas_iterate(ctx, [x[1] for x in live], 1)
-        conv_evals += sum(cur[id(x[1])] for x in live)
-        iters += 1
+    def cfg5(i, n):
+        kf, d = metac[i]
+        return M.vegas_cfg(samples=n, seed=seed + 100, stream_id=sbase + 1000 * KF5.index(kf) + d.diagram_id,
+                           precision=M.MBPT_MIXED, alpha=ALPHA5, train_iters=3, combine=M.MBPT_COMBINE_POOLED,
+                           target_rel=0.005, target_abs=floors[kf])
+    iters, ev, _ = RF.converge(M, ctx, gsc, lambda r, i: max(0.005 * abs(r.mean), floors[metac[i][0]]), cfg5,
+                               lambda r: r.n_evals - 3 * SAMPLES5, base_samples=SAMPLES5, max_iters=40,
+                               iters_done=3)
+    conv_evals = 3 * len(gsc) * SAMPLES5 + ev
     rc = M.mbpt_estimate_batch(gsc)
     conv_s = time.perf_counter() - t0
     n_conv = int(sum(r.converged for r in rc))
