@@ -244,6 +244,8 @@ def run_gpu(args):
         tuned["search_ms"] = {"%dx%d spt%d" % (r["threads"], r["min_blocks"], r["spt"]): round(r["ms"], 2)
                               for r in at["table"]}
         tuned["search_ms"].update({"hist %d" % r["layout"]: round(r["ms"], 2) for r in at["layout_table"]})
+        tuned["search_ms"].update({"spin %s" % ("fold" if r["spin_sum"] == M.MBPT_SPIN_FOLD else "table"):
+                                   round(r["ms"], 2) for r in at["spin_table"]})
         tuned["search_batch"] = "every fourth fifth-order integral (501), one iteration each"
         destroy(M, sub)
     gs5, meta5 = fifth_order_integrals(M, ctx, M.MBPT_MIXED, seed=seed, stream_base=sbase)
@@ -421,6 +423,7 @@ def run_gpu(args):
     # iteration, default launch shape
     launch_now = {o: M.mbpt_ctx_get_launch(ctx, o) for o in (2, 3, 4, 5, 6)}
     layout_now = M.mbpt_ctx_get_hist_layout(ctx)
+    spin_now = M.mbpt_ctx_get_spin_sum(ctx)
     M.mbpt_ctx_set_kernel(ctx, 256, 2)
     M.mbpt_ctx_set_hist_layout(ctx, M.MBPT_HIST_WARP_F32)
     for o in (2, 3, 4, 5, 6):
@@ -432,6 +435,7 @@ def run_gpu(args):
     destroy(M, gk5)
     M.mbpt_ctx_set_kernel(ctx, *launch_now[5][:2])
     M.mbpt_ctx_set_hist_layout(ctx, layout_now)
+    M.mbpt_ctx_set_spin_sum(ctx, spin_now)
     for o, (_, _, spt) in launch_now.items():
         M.mbpt_ctx_set_launch(ctx, o, spt)
 
@@ -486,6 +490,7 @@ def run_gpu(args):
     # ================= fourth order (C3): 198 live integrals x 2^24, and the aligned groups ===============
     M.mbpt_ctx_set_kernel(ctx, *launch_now[5][:2])
     M.mbpt_ctx_set_hist_layout(ctx, layout_now)
+    M.mbpt_ctx_set_spin_sum(ctx, spin_now)
     for o, (_, _, spt) in launch_now.items():
         M.mbpt_ctx_set_launch(ctx, o, spt)
     g4, gg, member_evals = [], [], 0
@@ -763,6 +768,7 @@ def profile_case(args):
     order = {"fifth": 5, "third": 3, "sixth": 6}[args.profile_case]
     if args.spt:
         M.mbpt_ctx_set_launch(ctx, order, args.spt)
+    M.mbpt_ctx_set_spin_sum(ctx, M.MBPT_SPIN_FOLD if args.spin == "fold" else M.MBPT_SPIN_TABLE)
     if args.profile_case == "fifth":
         gs, _ = fifth_order_integrals(M, ctx, prec, samples=args.samples, near_band=args.near_band)
     elif args.profile_case == "sixth":
@@ -780,8 +786,8 @@ def profile_case(args):
     M.mbpt_vegas_iterate(ctx, gs, args.iters)
     r = M.mbpt_estimate(gs[0])
     it_ms, fin_ms = M.mbpt_ctx_last_timing(ctx)
-    print("%s: integrals %d samples %d iters %d spt %d: k_iterate %.3f ms, k_finalize %.3f ms, first mean %.6g +- %.2g"
-          % (args.profile_case, len(gs), args.samples, args.iters,
+    print("%s: integrals %d samples %d iters %d spin %s spt %d: k_iterate %.3f ms, k_finalize %.3f ms, first mean %.6g "
+          "+- %.2g" % (args.profile_case, len(gs), args.samples, args.iters, args.spin,
              M.mbpt_ctx_get_launch(ctx, order)[2], it_ms, fin_ms, r.mean, r.sigma))
     M.mbpt_ctx_destroy(ctx)
 
@@ -804,6 +810,7 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="--profile-case precision")
     ap.add_argument("--near-band", type=float, default=0.0, help="--profile-case: FP64-map band (0 = default)")
     ap.add_argument("--spt", type=int, default=0, help="--profile-case: samples per thread of a chunk (0 = default)")
+    ap.add_argument("--spin", choices=["table", "fold"], default="table", help="--profile-case: Goldstone-sum strategy")
     ap.add_argument("--arena-gb", type=float, default=8.0, help="--profile-case: device arena (GiB)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":

@@ -293,6 +293,21 @@ int mbpt_ctx_get_hist_layout(const mbpt_ctx* ctx, int* layout);
 #define MBPT_HIST_BLOCK_F64 1
 
 /*
+ * Goldstone-sum strategy of the mixed-precision modes in matter with one Fermi momentum (an autotuner
+ * choice; the context starts with MBPT_SPIN_TABLE).  The spin(-isospin) sum of Sec. II / App. B is the
+ * multilinear polynomial sum_A c'(A) prod_{v in A} Delta_v prod_{v not in A} V_v over the subsets A of the
+ * n vertices (V_v the direct matrix element, Delta_v the direct minus the exchange one, c' the
+ * difference-form Goldstone table).  MBPT_SPIN_TABLE forms the 2^n vertex products and sums them with the
+ * table; MBPT_SPIN_FOLD folds the table vertex by vertex (T(A) <- T(A) V_v + T(A + {v}) Delta_v), the
+ * same polynomial with 2^n - 2 fewer FP32 products and fewer live registers.  The two agree to FP32
+ * rounding.  FP64 mode and asymmetric matter always use their product tables.
+ */
+int mbpt_ctx_set_spin_sum(mbpt_ctx* ctx, int strategy);
+int mbpt_ctx_get_spin_sum(const mbpt_ctx* ctx, int* strategy);
+#define MBPT_SPIN_TABLE 0
+#define MBPT_SPIN_FOLD 1
+
+/*
  * Device time of the last mbpt_vegas_iterate iteration: the sample-evaluation
  * launch and the reduce/combine/refine launch, in milliseconds, from CUDA
  * events recorded around them on the context stream.  Synchronises on the
@@ -373,8 +388,9 @@ int mbpt_set_state(mbpt_diag* diag, const void* buf, size_t len);
 /*
  * Test hook: evaluate samples [first, first + count) of iteration `iter` with
  * the integral's current grid and copy to host memory the mapped points
- * x[count][d] (in [0,1]^d) and weights w[count] = J_vegas * f(x).  Does not
- * touch the integral's accumulators.  x may be NULL.
+ * x[count][d] (in [0,1]^d) and weights w[count] = J_vegas * f(x), evaluated as
+ * mbpt_vegas_iterate evaluates them (the context's Goldstone-sum strategy).  Does
+ * not touch the integral's accumulators.  x may be NULL.
  */
 int mbpt_dump_samples(mbpt_diag* diag, int64_t iter, int64_t first, int64_t count, double* x, double* w);
 

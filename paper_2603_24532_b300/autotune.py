@@ -3,8 +3,9 @@
 Times one iteration of the caller's own batch for every compiled kernel shape
 (threads per block x minimum resident blocks, i.e. a register cap) and every
 candidate samples-per-thread; then, on the best shape, the per-chunk histogram
-layout (warp-private FP32 bins or one block-shared FP64 histogram) and, for a
-batch of several orders, samples-per-thread order by order.  Every integral's
+layout (warp-private FP32 bins or one block-shared FP64 histogram), the
+Goldstone-sum strategy of the mixed modes (product table or vertex-by-vertex
+fold) and, for a batch of several orders, samples-per-thread order by order.  Every integral's
 state (grid, sums, iteration counter) is restored after each trial, so tuning
 leaves no trace in the results, and the fastest setting is left on the context.
 """
@@ -38,9 +39,11 @@ def batch_orders(states) -> list:
 
 def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: Optional[Sequence] = None,
              trials: int = 2, orders: Iterable[int] = (2, 3, 4, 5, 6), per_order="auto",
-             layouts: Iterable[int] = (M.MBPT_HIST_WARP_F32, M.MBPT_HIST_BLOCK_F64)) -> Dict:
+             layouts: Iterable[int] = (M.MBPT_HIST_WARP_F32, M.MBPT_HIST_BLOCK_F64),
+             spin_sums: Iterable[int] = (M.MBPT_SPIN_TABLE, M.MBPT_SPIN_FOLD)) -> Dict:
     """Search the kernel shape and one samples-per-thread value for all orders; then the histogram
-    layout on that shape (layout_table; the FP64 block layout is taken only if it is faster); then, for
+    layout on that shape (layout_table; the FP64 block layout is taken only if it is faster); then the
+    Goldstone-sum strategy (spin_table; the fold is taken only if it is faster); then, for
     each order in per_order -- by default ("auto") the orders present when the batch has more than one --
     that order's samples per thread alone with the others held at their best (per_order_table,
     per_order_spt).  The result's "launch" summarises the chosen setting."""
@@ -52,7 +55,7 @@ def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: 
     present = batch_orders(states)
     if per_order == "auto":
         per_order = present if len(present) > 1 else ()
-    table, per_order_table, per_order_spt, layout_table = [], [], {}, []
+    table, per_order_table, per_order_spt, layout_table, spin_table = [], [], {}, [], []
     try:
         for tpb, minb in (variants or M.mbpt_kernel_variants()):
             M.mbpt_ctx_set_kernel(ctx, tpb, minb)
@@ -72,6 +75,13 @@ def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: 
         if layout_table:
             layout = min(layout_table, key=lambda r: r["ms"])["layout"]
         M.mbpt_ctx_set_hist_layout(ctx, layout)
+        spin = M.MBPT_SPIN_TABLE
+        for sp in spin_sums:
+            M.mbpt_ctx_set_spin_sum(ctx, sp)
+            spin_table.append({"spin_sum": sp, "ms": _time_batch(ctx, diags, states, trials)})
+        if spin_table:
+            spin = min(spin_table, key=lambda r: r["ms"])["spin_sum"]
+        M.mbpt_ctx_set_spin_sum(ctx, spin)
         for o in (per_order or ()):
             trial = []
             for spt in spts:
@@ -86,6 +96,7 @@ def autotune(ctx, diags: Sequence, spts: Iterable[int] = DEFAULT_SPT, variants: 
             M.mbpt_set_state(g, st)
     launch = {"threads": best["threads"], "min_blocks": best["min_blocks"],
               "spt_by_order": {o: M.mbpt_ctx_get_launch(ctx, o)[2] for o in present},
-              "hist_layout": "block_f64" if layout == M.MBPT_HIST_BLOCK_F64 else "warp_f32"}
-    return {"best": best, "table": table, "layout_table": layout_table, "per_order_table": per_order_table,
-            "per_order_spt": per_order_spt, "launch": launch}
+              "hist_layout": "block_f64" if layout == M.MBPT_HIST_BLOCK_F64 else "warp_f32",
+              "spin_sum": "fold" if spin == M.MBPT_SPIN_FOLD else "table"}
+    return {"best": best, "table": table, "layout_table": layout_table, "spin_table": spin_table,
+            "per_order_table": per_order_table, "per_order_spt": per_order_spt, "launch": launch}

@@ -493,6 +493,40 @@ __device__ __forceinline__ float spin_sum_diff_f32(const DiagRec& R, const float
     return sum;
 }
 
+// The same sum folded vertex by vertex (the Horner form of the multilinear polynomial, MBPT_SPIN_FOLD): the
+// table index's bit v selects Delta_v over V_v, so folding vertex 0 pairs entries 2b and 2b + 1 into
+// T(b) = c'(2b) V_0 + c'(2b + 1) Delta_0, and every later vertex folds the remaining table the same way;
+// after n folds one entry, the sum, is left.  2 (2^n - 1) FP32 operations against the 2^(n+1) - 4 products
+// and 2^n fused multiply-adds of the table, and at most 2^(n-1) partial sums live.
+template <int N>
+__device__ __forceinline__ float spin_sum_fold_f32(const DiagRec& R, const float (&lf)[3][N + 1]) {
+    constexpr int L = N + 1;
+    float T[1 << (N - 1)];
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+        float P[3], Q[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float p = 0.0f, qq = 0.0f;
+#pragma unroll
+            for (int c = 0; c < L; ++c) {
+                p = fmaf(R.vcoef_out[v][c], lf[q][c], p);
+                qq = fmaf(R.vcoef_in[v][c], lf[q][c], qq);
+            }
+            P[q] = p;
+            Q[q] = qq;
+        }
+        float vd, dl;
+        vertex_pot_delta_f32(R, P[0], P[1], P[2], Q[0], Q[1], Q[2], vd, dl);
+#pragma unroll
+        for (int b = 0; b < (1 << (N - 1 - v)); ++b) {
+            if (v == 0) T[b] = fmaf(R.gdel_f[2 * b + 1], dl, R.gdel_f[2 * b] * vd);
+            else T[b] = fmaf(T[2 * b + 1], dl, T[2 * b] * vd);
+        }
+    }
+    return T[0];
+}
+
 // Spin-isospin sum in asymmetric matter, FP32: products of V_d and V_e over the vertices, each Goldstone
 // term weighted by its loop factors, which depend on the per-line Fermi steps of both species (bit l of
 // okn / okp: line l passes its neutron / proton step).
@@ -550,7 +584,7 @@ template <int N, int PREC, int MAPK, bool REG>
 __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* __restrict__ gs,
                                                  const double* __restrict__ grid64, uint32_t s, uint32_t t,
                                                  uint32_t sid, uint32_t k0, uint32_t k1, double* x_out,
-                                                 int known = kClassUnknown) {
+                                                 int known = kClassUnknown, uint32_t spin = MBPT_SPIN_TABLE) {
     constexpr int L = N + 1;          // chords
     constexpr int D = 3 * L - 3 * MAPK;   // dimensions
     constexpr int NL = 2 * N;         // lines
@@ -685,7 +719,9 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
     // --- spin sum of one Fermi momentum, FP32, before the FP64 work: it needs only the FP32 chord momenta,
     // which are then no longer live through the FP64 section (fewer spills; measured 5 % faster at
     // fifth order).  Asymmetric matter needs the Fermi steps of every line and sums below.
-    const float s_f32 = (PREC != MBPT_FP64 && !R.asym) ? spin_sum_diff_f32<N>(R, lf) : 0.0f;
+    const float s_f32 = (PREC != MBPT_FP64 && !R.asym)
+                            ? (spin == MBPT_SPIN_FOLD ? spin_sum_fold_f32<N>(R, lf) : spin_sum_diff_f32<N>(R, lf))
+                            : 0.0f;
 
     // --- tree lines from momentum conservation: k = k_a + k_b - k_c
 #pragma unroll

@@ -151,7 +151,8 @@ struct alignas(16) WorkItem {
     uint32_t n_members;    // records at rec[0..n_members): > 1 is a group integral (sum of the members)
     uint32_t combine;      // MBPT_COMBINE_INVVAR or MBPT_COMBINE_POOLED
     uint32_t hist_layout;  // kHistWarpF32 or kHistBlockF64
-    uint32_t pad_w[2];
+    uint32_t spin_sum;     // MBPT_SPIN_TABLE or MBPT_SPIN_FOLD
+    uint32_t pad_w;
 };
 
 struct alignas(16) WorkHeader {

@@ -252,17 +252,18 @@ __global__ void __launch_bounds__(256) k_finalize(WorkHeader* hdr, const WorkIte
     }
 }
 
-// Test hook kernel: samples [first, first+count) of iteration `iter`, mapped point and weight.
+// Test hook kernel: samples [first, first+count) of iteration `iter`, mapped point and weight (the spin sum
+// with the context's Goldstone-sum strategy, as k_iterate evaluates it).
 template <int N, int PREC, int MAPK>
 __device__ void dump_one(const DiagRec& R, const Grid2* gs, const double* grid64, uint32_t s, uint32_t t,
-                         uint32_t sid, uint32_t k0, uint32_t k1, double* x, double* w) {
-    const SampleOut o = eval_sample<N, PREC, MAPK, false>(R, gs, grid64, s, t, sid, k0, k1, x);
+                         uint32_t sid, uint32_t k0, uint32_t k1, uint32_t spin, double* x, double* w) {
+    const SampleOut o = eval_sample<N, PREC, MAPK, false>(R, gs, grid64, s, t, sid, k0, k1, x, kClassUnknown, spin);
     *w = o.w;
 }
 
 __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members, const double* grid, uint64_t seed,
                                              uint32_t sid, uint32_t iter, uint64_t first, uint64_t count,
-                                             double* xo, double* wo) {
+                                             uint32_t spin, double* xo, double* wo) {
     __shared__ DiagRec R;
     __shared__ Grid2 gs[kCells];
     load_record(&R, rec);
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(256) k_dump(const DiagRec* rec, int n_members,
         if (active) {
             switch ((R.order * 3 + prec) * 2 + R.map_kind) {
 #define MBPT_CASE(N_, P_, M_) \
-    case (N_ * 3 + P_) * 2 + M_: dump_one<N_, P_, M_>(R, gs, grid, s, iter, sid, k0, k1, m == 0 ? x : nullptr, &w); break;
+    case (N_ * 3 + P_) * 2 + M_: dump_one<N_, P_, M_>(R, gs, grid, s, iter, sid, k0, k1, spin, m == 0 ? x : nullptr, &w); break;
 #define MBPT_CASES(N_) \
     MBPT_CASE(N_, MBPT_FP64, 0) MBPT_CASE(N_, MBPT_MIXED, 0) MBPT_CASE(N_, MBPT_MIXED_MAP64, 0) \
     MBPT_CASE(N_, MBPT_FP64, 1) MBPT_CASE(N_, MBPT_MIXED, 1) MBPT_CASE(N_, MBPT_MIXED_MAP64, 1)

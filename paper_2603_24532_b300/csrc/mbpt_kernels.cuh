@@ -164,6 +164,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
     float* hist = S.hist[threadIdx.x >> 5];
     float* hist_block = &S.hist[0][0];
     const uint32_t layout = W.hist_layout;
+    const uint32_t spin = W.spin_sum;
     uint32_t* q = S.queue[threadIdx.x >> 5];
     const uint32_t lane = threadIdx.x & 31u;
     const int nb = R.nb;
@@ -263,7 +264,7 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
             if (have) {
                 const SampleOut o = eval_sample<N, PREC, MAPK, REG>(
                         R, S.grid, w_grid, (uint32_t)s, t, w_sid, k0, k1, nullptr,
-                        !compact ? kClassUnknown : (use_near ? kClassNear : kClassFar));
+                        !compact ? kClassUnknown : (use_near ? kClassNear : kClassFar), spin);
                 if constexpr (GRP) {
                     // the sample's slot belongs to the thread that owns it in the chunk layout (sample
                     // first + js * blockDim + own), whichever warp evaluates it; each slot gets one add per member

@@ -50,7 +50,7 @@ __global__ void k_finalize(WorkHeader* hdr, const WorkItem* items, const double*
 __global__ void k_gather_heads(const DiagState* const* src, int k, int words, uint4* out);
 // test hooks
 __global__ void k_dump(const DiagRec* rec, int n_members, const double* grid, uint64_t seed, uint32_t sid, uint32_t iter,
-                       uint64_t first, uint64_t count, double* xo, double* wo);
+                       uint64_t first, uint64_t count, uint32_t spin, double* xo, double* wo);
 __global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                          uint64_t count, uint32_t* out);
 

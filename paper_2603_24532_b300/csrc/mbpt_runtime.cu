@@ -140,6 +140,7 @@ struct mbpt_ctx {
     int finalize_blocks = 0;
     int spt[MBPT_MAX_DEVICE_ORDER + 1] = {};  // samples per thread of a chunk by order (kDefaultSpt at creation)
     int hist_layout = kHistWarpF32;          // per-chunk histogram layout of k_iterate
+    int spin_sum = MBPT_SPIN_TABLE;          // Goldstone-sum strategy of the mixed modes
     // batch buffers (arena)
     WorkHeader* d_hdr = nullptr;
     WorkItem* d_items = nullptr;
@@ -481,6 +482,19 @@ int mbpt_ctx_get_hist_layout(const mbpt_ctx* c, int* layout) {
     return MBPT_OK;
 }
 
+int mbpt_ctx_set_spin_sum(mbpt_ctx* c, int strategy) {
+    if (!c || (strategy != MBPT_SPIN_TABLE && strategy != MBPT_SPIN_FOLD))
+        return fail(MBPT_EINVAL, "set_spin_sum: bad argument");
+    c->spin_sum = strategy;
+    return MBPT_OK;
+}
+
+int mbpt_ctx_get_spin_sum(const mbpt_ctx* c, int* strategy) {
+    if (!c || !strategy) return fail(MBPT_EINVAL, "get_spin_sum: NULL argument");
+    *strategy = c->spin_sum;
+    return MBPT_OK;
+}
+
 int mbpt_ctx_get_launch(const mbpt_ctx* c, int order, int* tpb, int* minb, int* spt) {
     if (!c || !tpb || !minb || !spt || order < 2 || order > MBPT_MAX_DEVICE_ORDER)
         return fail(MBPT_EINVAL, "get_launch: bad argument");
@@ -677,6 +691,7 @@ int mbpt_vegas_iterate(mbpt_ctx* c, mbpt_diag* const* diags, int k, int n_iters)
         w.train_iters = g->cfg.train_iters;
         w.combine = g->cfg.combine;
         w.hist_layout = (uint32_t)c->hist_layout;
+        w.spin_sum = (uint32_t)c->spin_sum;
         w.hist_stride = stride;
         chunk += w.n_chunks;
         if (chunk >= (1ull << 31)) return fail(MBPT_EINVAL, "vegas_iterate: batch too large");
@@ -891,7 +906,8 @@ int mbpt_dump_samples(mbpt_diag* g, int64_t iter, int64_t first, int64_t count, 
     }
     const int blocks = (int)((count + 255) / 256);
     k_dump<<<blocks, 256, 0, c->stream>>>(g->d_rec, g->n_members, g->d_grid, g->cfg.seed, g->cfg.stream_id,
-                                          (uint32_t)iter, (uint64_t)first, (uint64_t)count, dx, dw);
+                                          (uint32_t)iter, (uint64_t)first, (uint64_t)count, (uint32_t)c->spin_sum, dx,
+                                          dw);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && x)
         e = cudaMemcpyAsync(x, dx, sizeof(double) * (size_t)count * g->d, cudaMemcpyDeviceToHost, c->stream);

@@ -27,6 +27,8 @@ MBPT_COMBINE_INVVAR = 0
 MBPT_COMBINE_POOLED = 1
 MBPT_HIST_WARP_F32 = 0
 MBPT_HIST_BLOCK_F64 = 1
+MBPT_SPIN_TABLE = 0
+MBPT_SPIN_FOLD = 1
 MAX_ORDER = 6
 MAX_LINES = 12
 MAX_CHORDS = 7
@@ -168,6 +170,8 @@ def lib():
             "mbpt_ctx_get_launch": [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
             "mbpt_ctx_set_hist_layout": [vp, ctypes.c_int],
             "mbpt_ctx_get_hist_layout": [vp, P(ctypes.c_int)],
+            "mbpt_ctx_set_spin_sum": [vp, ctypes.c_int],
+            "mbpt_ctx_get_spin_sum": [vp, P(ctypes.c_int)],
             "mbpt_ctx_last_timing": [vp, P(ctypes.c_double), P(ctypes.c_double)],
             "mbpt_ctx_stream": [vp, P(vp)],
             "mbpt_create_diagram": [vp, P(mbpt_diagram_desc), P(mbpt_physics), P(mbpt_vegas_cfg), P(vp)],
@@ -292,6 +296,16 @@ def mbpt_ctx_set_hist_layout(ctx, layout: int):
 def mbpt_ctx_get_hist_layout(ctx) -> int:
     v = ctypes.c_int()
     check(lib().mbpt_ctx_get_hist_layout(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def mbpt_ctx_set_spin_sum(ctx, strategy: int):
+    check(lib().mbpt_ctx_set_spin_sum(ctx, strategy))
+
+
+def mbpt_ctx_get_spin_sum(ctx) -> int:
+    v = ctypes.c_int()
+    check(lib().mbpt_ctx_get_spin_sum(ctx, ctypes.byref(v)))
     return v.value
 
 

@@ -66,6 +66,11 @@ def test_all_shapes_agree_and_tuning_restores_state(ctx):
         assert len(res["layout_table"]) == 2
         want = M.MBPT_HIST_BLOCK_F64 if res["launch"]["hist_layout"] == "block_f64" else M.MBPT_HIST_WARP_F32
         assert M.mbpt_ctx_get_hist_layout(ctx) == want
+        # so was the Goldstone-sum strategy
+        assert len(res["spin_table"]) == 2
+        want = M.MBPT_SPIN_FOLD if res["launch"]["spin_sum"] == "fold" else M.MBPT_SPIN_TABLE
+        assert M.mbpt_ctx_get_spin_sum(ctx) == want
+        M.mbpt_ctx_set_spin_sum(ctx, M.MBPT_SPIN_TABLE)
         assert sorted(res["launch"]["spt_by_order"]) == [2, 3, 4, 5]
         M.mbpt_ctx_set_hist_layout(ctx, M.MBPT_HIST_WARP_F32)
         # per-order refinement of a mixed-order batch: one entry per (order, candidate), the chosen
@@ -93,3 +98,5 @@ def test_all_shapes_agree_and_tuning_restores_state(ctx):
             M.mbpt_destroy_diagram(g)
     with pytest.raises(M.MbptError):
         M.mbpt_ctx_set_kernel(ctx, 96, 1)
+    with pytest.raises(M.MbptError):
+        M.mbpt_ctx_set_spin_sum(ctx, 2)

@@ -219,6 +219,41 @@ def test_one_iteration_sums_histogram_and_refinement(ctx, prec):
         M.mbpt_destroy_diagram(g)
 
 
+@pytest.mark.parametrize("n,matter", [(2, "pnm"), (3, "snm"), (4, "pnm"), (5, "pnm"), (5, "snm"), (6, "pnm")])
+def test_spin_sum_fold_equals_table(ctx, n, matter):
+    """The vertex-by-vertex fold of the Goldstone table (MBPT_SPIN_FOLD) evaluates the polynomial that the
+    product table does: one mixed-precision iteration on a ragged sample count, same grid and counters,
+    gives a sum of weights within FP32 rounding of the spin sum (1e-5 of sum |w|) of the table's, and
+    both are within the mixed tolerance (1e-4 of sum |w|) of the FP64 oracle's sum over the same samples."""
+    rng = np.random.default_rng(60 + n)
+    po, pm = matter_pair(matter)
+    M_s = (2048 if n == 6 else 8192) + 77
+    for D in _pick(n, 2, rng):
+        if O.is_anomalous(D):
+            continue
+        d = po.dim(D)
+        grid = random_grid(d, 50, rng, strength=0.4)
+        _, _, _, wo = O.vegas_samples(0, D, po.array(), d, grid, 8, 31, 0, 0, M_s, dump=True)
+        s_o, l1_o = float(np.sum(wo)), float(np.sum(np.abs(wo)))
+        sums = {}
+        for strat in (M.MBPT_SPIN_TABLE, M.MBPT_SPIN_FOLD):
+            M.mbpt_ctx_set_spin_sum(ctx, strat)
+            assert M.mbpt_ctx_get_spin_sum(ctx) == strat
+            g = M.mbpt_create_diagram(ctx, make_desc(D), pm, M.vegas_cfg(samples=M_s, seed=8, stream_id=31,
+                                                                          precision=M.MBPT_MIXED))
+            try:
+                M.mbpt_set_state(g, M.state_with_grid(M.mbpt_get_state(g), grid))
+                M.mbpt_vegas_iterate(ctx, [g], 1)
+                sums[strat] = M.mbpt_estimate(g).last_mean * M_s
+            finally:
+                M.mbpt_destroy_diagram(g)
+                M.mbpt_ctx_set_spin_sum(ctx, M.MBPT_SPIN_TABLE)
+        assert l1_o > 0.0
+        assert abs(sums[M.MBPT_SPIN_FOLD] - sums[M.MBPT_SPIN_TABLE]) <= 1e-5 * l1_o, (D.diagram_id, sums, l1_o)
+        for strat, v in sums.items():
+            assert abs(v - s_o) <= 1e-4 * l1_o, (D.diagram_id, strat, v, s_o, l1_o)
+
+
 @pytest.mark.parametrize("mapk", [0, 1])
 def test_second_order_estimate_config1(ctx, mapk):
     """Config 1: one second-order diagram, neutron matter kF = 1, 10 x 2^18 samples,
