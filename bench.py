@@ -73,14 +73,15 @@ def job_value(world: int, units_per_rank: float, t_ms: float) -> float:
 def measured_counters(workload: str):
     """ncu counters of one k_iterate launch of a workload, from the committed summary (lines `<workload>
     <FP64 ops per sample> <samples per launch> <dadd> <dmul> <dfma> <dram read B> <dram write B> <warp
-    instructions> ...`): a dict, or None if the file has no such line."""
+    instructions> <threads per block> <samples per thread> ...`): a dict, or None if the file has no such line."""
     try:
         with open(FP64_OPS_FILE) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) >= 9 and not line.startswith("#") and parts[0] == workload:
+                if len(parts) >= 11 and not line.startswith("#") and parts[0] == workload:
                     return {"ops_per_sample": float(parts[1]), "samples": int(parts[2]),
-                            "dram_bytes": int(parts[6]) + int(parts[7]), "warp_inst": int(parts[8])}
+                            "dram_bytes": int(parts[6]) + int(parts[7]), "warp_inst": int(parts[8]),
+                            "chunk": int(parts[9]) * int(parts[10])}
     except (OSError, ValueError):
         pass
     return None
@@ -270,11 +271,12 @@ def run_gpu(args):
     ops5 = cnt5["ops_per_sample"] if cnt5 else None
     fp64_rate = M.mbpt_fp64_rate(local, M.mbpt_ctx_stream(ctx))
     achieved = (ops5 * evals_step / (it_ms * 1e-3)) if ops5 else None
-    # DRAM bytes of a launch of this shape: the counters come from a launch of the same kernel, integrals and
-    # samples per thread with fewer samples per integral (2^18), whose traffic -- the chunk slots, written once,
-    # one per 8192 samples -- grows in proportion to the samples, so it is scaled to the headline launch; and
+    # DRAM bytes of a launch of this shape: the counters come from a launch of the same kernel and integrals with
+    # fewer samples per integral (2^18), whose traffic -- the chunk slots, written once per chunk -- grows with the
+    # number of chunks, so it is scaled to the headline launch's chunks (its samples over its chunk size); and
     # the share of the SMs' instruction issue slots (4 warp instructions per SM per cycle) the launch uses
-    traffic5 = (cnt5["dram_bytes"] * evals_step / cnt5["samples"]) if cnt5 else None
+    tpb5, _, spt5 = M.mbpt_ctx_get_launch(ctx, 5)
+    traffic5 = (cnt5["dram_bytes"] * (evals_step / (tpb5 * spt5)) / (cnt5["samples"] / cnt5["chunk"])) if cnt5 else None
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     issue_frac = (cnt5["warp_inst"] / cnt5["samples"] * evals_step / (it_ms * 1e-3)
                   / (4.0 * n_sm * clk["sm_mhz"] * 1e6)) if cnt5 and clk.get("sm_mhz") else None
@@ -607,9 +609,9 @@ def run_gpu(args):
                      "kernel_ms": it_ms, "traffic": traffic5, "traffic_unit": "bytes per launch",
                      "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch of the same kernel "
                                      "and integrals at 2^18 samples each (ncu, profiles/fp64_ops_per_sample.txt), "
-                                     "scaled by samples to this launch: the chunk slots written once (histogram "
-                                     "and sums, 3.6 KB per 8192 samples), records and grids; HBM is otherwise idle "
-                                     "by design",
+                                     "scaled by the number of chunks to this launch: the chunk slots written once "
+                                     "(histogram and sums, 3.6 KB per chunk), records and grids; HBM is otherwise "
+                                     "idle by design",
                      "issue_frac": issue_frac,
                      "issue_note": "warp instructions per sample (ncu sm__inst_executed.sum of the same launch "
                                    "shape) x samples / kernel time, over 4 issue slots per SM per cycle at the "

@@ -14,13 +14,13 @@ namespace mbpt {
 // ---------------------------------------------------------------------------
 // pre-test rounds between evaluation phases (longer phases keep the instruction cache warmer; a
 // group chunk has only as many rounds as its samples per thread, so the group parts take short
-// phases and spend the shared memory on per-sample slots), and the per-warp stack length:
-// carried-over entries of both classes plus one phase
+// phases and spend the shared memory on per-sample slots), and the per-warp stack length: one
+// phase of both classes (a phase's stacks are evaluated in full before the next phase)
 __host__ __device__ constexpr int class_rounds(int part) {
     return (part & 3) == 3 ? 4 : ((part & 3) == 2 ? 16 : 32);
 }
 __host__ __device__ constexpr int group_slots(int part) { return (part & 3) == 3 ? kGroupSlotsReg : kGroupSlotsPlain; }
-__host__ __device__ constexpr int queue_len(int part) { return 2 * 31 + 32 * class_rounds(part) + 2; }
+__host__ __device__ constexpr int queue_len(int part) { return 32 * class_rounds(part); }
 
 // Shared memory of one k_iterate block; the regulator and group arrays exist only in their parts
 // (PART bit 0: regulator, bit 1: group; the sixth-order bit does not change the layout), which leaves the
@@ -35,8 +35,7 @@ struct alignas(16) ChunkSmemT {
     double gacc[(PART & 2) ? group_slots(PART) : 1][NW * 32];  // group integrals: per-sample sums over the members
     uint32_t queue[NW][queue_len(PART)];     // per-warp stacks of samples past the pre-test
                                              // (away from a Fermi surface from the bottom, near one from the top)
-    uint32_t pool[NW * 64];                  // the chunk's last partial warps of all warps (far, then near)
-    int rem[2][NW];                          // per warp: far and near samples left when the chunk is classified
+    int rem[2][NW];                          // per warp: far and near samples of the phase on its stacks
     double red[2][NW];
     double redc[(PART & 1) ? 2 * kComp : 1][NW];
     uint32_t chunk, item, iter, skip;
@@ -141,10 +140,10 @@ __device__ __forceinline__ void sample_bins(uint32_t s, uint32_t t, uint32_t sid
 //  take both sampling maps pays for both.  Each warp therefore alternates two phases, each a tight loop over
 //  its own code: class_rounds() rounds of the FP32 front and Fermi-step pre-test, pushing the samples
 //  that may be live onto one of two shared-memory stacks by class (away from / near a Fermi
-//  surface; ballot + prefix count), then full warps of one class popped and evaluated until fewer
-//  than 32 of each remain; the last partial warps of all the block's warps are pooled and evaluated as
-//  full warps where possible at the end of the chunk.  Which thread sums which sample depends only on the
-//  chunk, so results stay deterministic.
+//  surface; ballot + prefix count); then, behind a barrier, the block evaluates all its warps' stacks
+//  together in groups of 32 of one class, spread round-robin over the warps, so a phase leaves at most one
+//  partial group per class in the whole block and every warp gets the same number of groups to within one.
+//  Which thread sums which sample depends only on the chunk, so results stay deterministic.
 //  A group integral (n_members > 1; its own kernel, GRP) evaluates every member at each sample, member
 //  by member with the record swapped in shared memory, each member's samples through the phases
 //  above, adding the weights per sample into gacc, zeroed per chunk (spt x (1 + regulator components)
@@ -183,21 +182,23 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
             load_record(&S.rec, W.rec + m);
             __syncthreads();
         }
-        int j = 0, nf = 0, nn = 0;       // warp-uniform: next round, stack heights (far, near)
-        bool drain = false;
-        // Pooled stage: once the chunk (a group: the member) is classified and fewer than 32 samples of
-        // each class are left in every warp's stacks, the block gathers them in warp order (far, then near)
-        // and its warps evaluate the pooled groups of 32, group g by warp g mod NW: fewer partial warps.
-        // In that stage nf and nn hold the pooled counts and j = w_spt + 1 + g (no other loop state, so
-        // that it costs no registers).
+        // Phases: every warp classifies rounds [j0, j0 + kRounds) of the chunk onto its two stacks; after a
+        // barrier the block evaluates the concatenation of all warps' far stacks (warp order), then of their
+        // near stacks, in groups of 32, group g by warp g mod NW (so at most one partial group per class and
+        // phase, the groups spread evenly over the warps, and the assignment depends only on the chunk);
+        // a second barrier before the stacks are filled again.  pf / pn: lane w < NW holds the inclusive
+        // prefix sum of the far / near counts of warps 0..w.
+        int j0 = 0, g = -1, n_gf = 0, n_g = 0, pf = 0, pn = 0;
         for (;;) {
             uint64_t s;
-            bool have, use_near = false, pooled = false;
-            int cnt = 0;
-            if (compact && j <= w_spt) {
-                if (!drain && nf < 32 && nn < 32) {
-                    const int jend = (j + kRounds < w_spt) ? j + kRounds : w_spt;
-                    for (; j < jend; ++j) {
+            bool have, use_near = false;
+            if (compact) {
+                if (g < 0 || g >= n_g) {
+                    if (g >= 0) __syncthreads();   // end of a phase: the stacks are reused
+                    if (j0 >= w_spt) break;
+                    const int jend = (j0 + kRounds < w_spt) ? j0 + kRounds : w_spt;
+                    int nf = 0, nn = 0;
+                    for (int j = j0; j < jend; ++j) {
                         const uint64_t sc = first + (uint64_t)j * blockDim.x + threadIdx.x;
                         const int cls = sc < w_samples
                                             ? sample_class<N, MAPK, PREC>(R, S.grid, (uint32_t)sc, t, w_sid, k0, k1)
@@ -210,56 +211,48 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                         nf += __popc(b0);
                         nn += __popc(b1);
                     }
-                    if (j >= w_spt) drain = true;
-                    __syncwarp();
-                }
-                if (nf >= 32) cnt = 32;
-                else if (nn >= 32) { cnt = 32; use_near = true; }
-                else if (!drain) continue;
-                else {
-                    // every warp of the block arrives here exactly once per chunk (and member)
+                    j0 = jend;
                     const int warp = (int)(threadIdx.x >> 5);
                     if (lane == 0) {
                         S.rem[0][warp] = nf;
                         S.rem[1][warp] = nn;
                     }
                     __syncthreads();
-                    int of = 0, on = 0, tf = 0, tn = 0;
+                    pf = ((int)lane < NW) ? S.rem[0][lane] : 0;
+                    pn = ((int)lane < NW) ? S.rem[1][lane] : 0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        const int a = S.rem[0][w], b = S.rem[1][w];
-                        of += (w < warp) ? a : 0;
-                        on += (w < warp) ? b : 0;
-                        tf += a;
-                        tn += b;
+                    for (int o = 1; o < NW; o <<= 1) {
+                        const int a = __shfl_up_sync(0xffffffffu, pf, o), b = __shfl_up_sync(0xffffffffu, pn, o);
+                        if ((int)lane >= o) {
+                            pf += a;
+                            pn += b;
+                        }
                     }
-                    if ((int)lane < nf) S.pool[of + (int)lane] = q[lane];
-                    if ((int)lane < nn) S.pool[tf + on + (int)lane] = q[kQ - 1 - (int)lane];
-                    __syncthreads();
-                    nf = tf;
-                    nn = tn;
-                    j = w_spt + 1 + warp;
+                    n_gf = (__shfl_sync(0xffffffffu, pf, NW - 1) + 31) >> 5;
+                    n_g = n_gf + ((__shfl_sync(0xffffffffu, pn, NW - 1) + 31) >> 5);
+                    g = warp;
+                    if (g >= n_g) continue;
                 }
-                if (cnt > 0) {
-                    have = (int)lane < cnt;
-                    s = !have ? 0u : (use_near ? q[kQ - 1 - (nn - cnt + (int)lane)] : q[nf - cnt + (int)lane]);
-                }
-            }
-            if (compact && j > w_spt) {
-                const int g = j - w_spt - 1, n_gf = (nf + 31) >> 5;
-                if (g >= n_gf + ((nn + 31) >> 5)) break;
-                pooled = true;
                 use_near = g >= n_gf;
-                const int base = use_near ? nf + 32 * (g - n_gf) : 32 * g;
-                cnt = min(32, (use_near ? nf + nn : nf) - base);
-                have = (int)lane < cnt;
-                s = have ? S.pool[base + (int)lane] : 0u;
-                j += NW;
-            } else if (!compact) {
-                if (j >= w_spt) break;
-                s = first + (uint64_t)j * blockDim.x + threadIdx.x;
+                const int src = use_near ? pn : pf;
+                const int e = (use_near ? g - n_gf : g) * 32 + (int)lane;
+                have = e < __shfl_sync(0xffffffffu, src, NW - 1);
+                // owner warp of entry e: the first w with prefix(w) > e (binary search over the NW prefixes)
+                int w = 0;
+#pragma unroll
+                for (int step = NW / 2; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, src, w + step - 1);
+                    if (v <= e) w += step;
+                }
+                const int prev = __shfl_sync(0xffffffffu, src, w > 0 ? w - 1 : 0);
+                const int k = e - (w > 0 ? prev : 0);
+                s = !have ? 0u : (use_near ? S.queue[w][kQ - 1 - k] : S.queue[w][k]);
+                g += NW;
+            } else {
+                if (j0 >= w_spt) break;
+                s = first + (uint64_t)j0 * blockDim.x + threadIdx.x;
                 have = s < w_samples;
-                ++j;
+                ++j0;
             }
             if (have) {
                 const SampleOut o = eval_sample<N, PREC, MAPK, REG>(
@@ -290,15 +283,10 @@ __device__ __forceinline__ void run_chunk(ChunkSmemT<NW, (REG ? 1 : 0) | (GRP ? 
                     }
                 }
             }
-            if (compact && !pooled) {
-                if (use_near) nn -= cnt;
-                else nf -= cnt;
-                __syncwarp();                  // popped slots may be pushed again by the next phase
-            }
         }
     }
     if constexpr (!GRP) return;
-    __syncthreads();                           // slots were filled by the block's warps (pooled stage)
+    __syncthreads();                           // slots were filled by the block's warps
     for (int j = 0; j < w_spt; ++j) {
         const uint64_t s = first + (uint64_t)j * blockDim.x + threadIdx.x;
         if (s >= w_samples) continue;
@@ -358,6 +346,7 @@ __device__ __forceinline__ void k_iterate_body(WorkHeader* hdr, const WorkItem* 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr bool REGP = (PART & kPartReg) != 0, GRPP = (PART & kPartGrp) != 0, O6P = (PART & kPartO6) != 0;
     static_assert(NW >= 4, "the FP64 block histogram overlays the FP32 histograms of four warps");
+    static_assert((NW & (NW - 1)) == 0 && NW <= 32, "the search for the warp that holds a pooled entry halves the range of warps");
     uint32_t item0 = 0, chunk0 = 0;
 #pragma unroll
     for (int p = 0; p < PART; ++p) {
