@@ -37,34 +37,22 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[3] = c3;
 }
 
-// select v[idx] for a uniform index with integer selects (no predicated FP64 work)
+// v[lo + k] for a uniform 0 <= k < n (lo and n constants after unrolling) with integer selects, no
+// predicated FP64 work: a tournament on the bits of k -- level b keeps, of each pair of entries b apart, the
+// one that bit b of k picks -- so n - 1 selects of log2(n) depth, and one bit test per level shared by
+// every call with the same k
 template <int NS>
-__device__ __forceinline__ double sel(const double (&v)[16], int idx) {
-    double r = v[0];
+__device__ __forceinline__ double sel_bits(const double (&v)[16], int k, int lo, int n) {
+    double r[NS];
 #pragma unroll
-    for (int j = 1; j < NS; ++j) r = (idx == j) ? v[j] : r;
-    return r;
-}
-
-// the same over the first n_valid entries only (n_valid a constant after unrolling: tree line j reads
-// the chords and the tree lines before it)
-template <int NS>
-__device__ __forceinline__ double sel_upto(const double (&v)[16], int idx, int n_valid) {
-    double r = v[0];
+    for (int j = 0; j < NS; ++j) r[j] = (j < n) ? v[(lo + j) & 15] : 0.0;
 #pragma unroll
-    for (int j = 1; j < NS; ++j)
-        if (j < n_valid) r = (idx == j) ? v[j] : r;
-    return r;
-}
-
-// v[idx] for idx known to lie in lo .. hi (constants after unrolling)
-template <int NS>
-__device__ __forceinline__ double sel_between(const double (&v)[16], int idx, int lo, int hi) {
-    double r = 0.0;
+    for (int b = 1; b < NS; b <<= 1) {
 #pragma unroll
-    for (int j = 0; j < NS; ++j)
-        if (j >= lo && j <= hi) r = (j == lo) ? v[j] : ((idx == j) ? v[j] : r);
-    return r;
+        for (int j = 0; j + b < NS; j += 2 * b)
+            if (j + b < n) r[j] = (k & b) ? r[j + b] : r[j];
+    }
+    return r[0];
 }
 
 __device__ __forceinline__ double neg_if(double x, int neg) {
@@ -729,8 +717,8 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         const int ia = R.tree_a[j], ib = R.tree_b[j], ic = R.tree_c[j];
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            K[q][L + j] = (sel_upto<NL>(K[q], ia, L + j) + sel_upto<NL>(K[q], ib, L + j)) -
-                          sel_upto<NL>(K[q], ic, L + j);
+            K[q][L + j] = (sel_bits<NL>(K[q], ia, 0, L + j) + sel_bits<NL>(K[q], ib, 0, L + j)) -
+                          sel_bits<NL>(K[q], ic, 0, L + j);
         U[L + j] = fma(K[0][L + j], K[0][L + j], fma(K[1][L + j], K[1][L + j], K[2][L + j] * K[2][L + j]));
     }
 
@@ -782,7 +770,7 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
         for (int m = 0; m < N - 1; ++m) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const double uv = neg_if(sel_between<NL>(U, R.cut_slot[m][k], k, NL - 4 + k), R.cut_neg[m][k]);
+                const double uv = neg_if(sel_bits<NL>(U, R.cut_slot[m][k] - k, k, NL - 3), R.cut_neg[m][k]);
                 if (m == 0 && k == 0) Dm = uv;
                 else Dm += uv;
             }
@@ -807,8 +795,8 @@ __device__ __forceinline__ SampleOut eval_sample(const DiagRec& R, const Grid2* 
             const int o1 = R.port_slot[v][0], o2 = R.port_slot[v][1], i1 = R.port_slot[v][2], i2 = R.port_slot[v][3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                P[q] = sel<NL>(K[q], o1) - sel<NL>(K[q], o2);
-                Q[q] = sel<NL>(K[q], i1) - sel<NL>(K[q], i2);
+                P[q] = sel_bits<NL>(K[q], o1, 0, NL) - sel_bits<NL>(K[q], o2, 0, NL);
+                Q[q] = sel_bits<NL>(K[q], i1, 0, NL) - sel_bits<NL>(K[q], i2, 0, NL);
             }
             double vd, ve;
             vertex_pot_f64(R, P[0], P[1], P[2], Q[0], Q[1], Q[2], vd, ve);
