@@ -439,7 +439,8 @@ __device__ __forceinline__ bool pretest_dead(const DiagRec& R, const float (&lf)
             f = f && (hole ? (dp > mp2) : (dp < -mp2));
             nr = nr || (fabsf(dp) <= fmaf(R.near_f, R.kf2_pf, mp2));
         }
-        dead |= f;
+        if (l >= L) dead |= f;    // a chord lies in its own step's range (hole chords in [0, kF_max], particle
+                                  // chords in [kF_min, K_max]) and passes it for some species
         near |= nr;
     }
     return dead;
